@@ -1,0 +1,392 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of batched flexible-ligand docking on GB300.
+
+Metric: ligand-pocket evaluations per second (one evaluation = one ligand
+docked with all its restarts against one pocket and scored).
+
+Workload (one step = one pass of the whole hot path over one batch): one
+synthetic pocket (64^3 FP32 grids at 0.375 A, ellipsoidal cavity 6/8/12 A,
+4,000 shell atoms) and 100,000 synthetic ligands of U{15..60} heavy atoms with
+U{0..12} torsional bonds, 30 restarts, 3 sweep passes, 36 torsion steps.
+Inputs are resident in device memory when the timed region starts; L2 is
+flushed (256 MiB write) before every step.
+
+Under torchrun each rank docks its own 100,000 ligands (disjoint uid ranges,
+weak scaling, no collective on the data path); the time is the maximum over
+ranks.  ``--impl reference`` times the FP64 CPU oracle on the host cores on
+bounded samples of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ligand-pocket evals/s"
+UNIT = "evals/s"
+WORKLOAD = ("1 pocket (64^3 FP32 grids, h=0.375 A, ellipsoid cavity 6/8/12 A, 4,000 shell atoms); "
+            "100,000 ligands of U{15..60} atoms with U{0..12} torsional bonds; 30 restarts, 3 passes, 36 steps")
+CFG = 2
+N_LIGANDS = 100_000
+FP32_LANES_PER_SM = 128          # FP32 FMA lanes per SM (4 SMSPs x 32)
+FLOP_PER_FMA = 2
+# Algorithmic FLOPs: per moving atom and torsion step, 12 for
+# the point on its circle, 3 for the cell fraction, 14 for the trilinear
+# polynomial and 1 for the sum; 30 per moving atom and decision for building
+# its circle and applying the chosen step; per atom and restart 21 for the
+# rigid pose and 44 for the final score; 40 per restart for the pose draw.
+C_LOOKUP, C_BOND, C_POSE_ATOM, C_FINAL_ATOM, C_RESTART = 30, 30, 21, 44, 40
+
+
+def moving_atoms_per_ligand(batch) -> np.ndarray:
+    """Sum over a ligand's torsional bonds of the atoms each bond moves
+    (subtree size of the bond's child minus one)."""
+    aoff = batch.atom_off.astype(np.int64)
+    A = int(aoff[-1])
+    lig = np.repeat(np.arange(batch.L), np.diff(aoff))
+    par = batch.parent.astype(np.int64)
+    gpar = np.where(par >= 0, par + aoff[lig], -1)
+    depth = np.zeros(A, np.int64)
+    nonroot = gpar >= 0
+    for _ in range(int(np.diff(aoff).max(initial=1))):
+        nd = np.where(nonroot, depth[np.maximum(gpar, 0)] + 1, 0)
+        if np.array_equal(nd, depth):
+            break
+        depth = nd
+    size = np.ones(A, np.int64)
+    for d in range(int(depth.max(initial=0)), 0, -1):
+        idx = np.where(depth == d)[0]
+        np.add.at(size, gpar[idx], size[idx])
+    roff = batch.rot_off.astype(np.int64)
+    rl = np.repeat(np.arange(batch.L), np.diff(roff))
+    child = batch.rot_child.astype(np.int64) + aoff[rl]
+    m = size[child] - 1
+    out = np.zeros(batch.L, np.int64)
+    np.add.at(out, rl, m)
+    return out
+
+
+def algorithmic_flops(batch, S, P) -> float:
+    N = np.diff(batch.atom_off).astype(np.float64)
+    msum = moving_atoms_per_ligand(batch).astype(np.float64)
+    per = S * (P * msum * (36 * C_LOOKUP + C_BOND) + N * (C_POSE_ATOM + C_FINAL_ATOM) + C_RESTART)
+    return float(per.sum())
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.th.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def env_rank():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def cpu_cores() -> int:
+    return len(os.sched_getaffinity(0))
+
+
+def oracle_rate(pocket, batch, params, budget_s: float, chunk: int = 256, max_ligands: int = 8192):
+    """Oracle throughput on the first ligands of the workload, in chunks until
+    the time budget is spent.  Returns (evals/s, ligands, seconds)."""
+    import oracle
+    done, t0 = 0, time.perf_counter()
+    while done < max_ligands:
+        sub = batch.subset(range(done, min(done + chunk, batch.L)))
+        oracle.dock(pocket, sub, params, nthreads=cpu_cores())
+        done += sub.L
+        if time.perf_counter() - t0 >= budget_s or done >= batch.L:
+            break
+    dt = time.perf_counter() - t0
+    return done / dt, done, dt
+
+
+def traffic_for_current_kernel():
+    """DRAM bytes per launch of the docking kernel from the committed ncu
+    summary, if it was taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "dock_batched_traffic.json")
+    src = os.path.join(ROOT, "paper_2110_11644_gb300", "csrc", "lg_kernels.cu")
+    try:
+        rec = json.load(open(path))
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        if rec.get("kernel_source_sha") == sha:
+            return rec.get("dram_bytes_per_launch")
+    except (OSError, ValueError):
+        pass
+    return None
+
+
+def run_reference(args):
+    rank, world, _ = env_rank()
+    if rank != 0:
+        return 0
+    from paper_2110_11644_gb300 import synth
+    pocket = synth.config_pocket(CFG)
+    params = synth.config_params(CFG)
+    sample = 192
+    batch = synth.config_ligands(CFG, sample * (args.steps + args.warmup))
+    times = []
+    for s in range(args.warmup + args.steps):
+        sub = batch.subset(range(s * sample, (s + 1) * sample))
+        import oracle
+        t0 = time.perf_counter()
+        oracle.dock(pocket, sub, params, nthreads=cpu_cores())
+        if s >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    T = sum(times)
+    value = sample * args.steps / T
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * T / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "step": f"{sample} ligands of the workload per step (bounded sample)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+                             "sample": f"{sample} ligands per step, {args.steps} steps"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--ligands", type=int, default=N_LIGANDS)
+    ap.add_argument("--plain-sample", type=int, default=16384)
+    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    from paper_2110_11644_gb300 import lg, synth
+
+    rank, world, local = env_rank()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = local
+    torch.cuda.set_device(dev)
+
+    pocket = synth.config_pocket(CFG)
+    params = synth.config_params(CFG)
+    batch = synth.config_ligands(CFG, args.ligands, uid_base=rank * args.ligands) if rank == 0 else \
+        synth.config_ligands(CFG, args.ligands, uid_base=rank * args.ligands)
+    if rank > 0:  # each rank docks its own ligands: disjoint uids (new restart poses) on the same topologies
+        batch.uid = batch.uid.copy()
+    L, S, P = batch.L, params.restarts, params.passes
+    A, R = int(batch.atom_off[-1]), int(batch.rot_off[-1])
+    max_atoms = int(batch.n_atoms().max())
+    max_rot = max(1, int(batch.n_rot().max()))
+
+    ctx = lg.Context(dev)
+    pid = ctx.load_pocket(pocket)
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream
+
+    # device-resident inputs and outputs
+    darr = lg.device_batch_arrays(batch, f"cuda:{dev}")
+    bstruct = lg.make_batch_struct(darr, L)
+    pstruct = lg.make_params(S, P, params.seed, params.d_clash, lg.LG_MODE_BATCHED, 0, max_atoms, max_rot)
+    rstruct, outs = lg.alloc_result(L, A, R, S, P, device=True, pose=True, tors=True)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{dev}")
+
+    def step():
+        flush.fill_(1)
+        lg.lg_dock_batch(ctx.h, pid, bstruct, pstruct, rstruct, sh)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ctx.set_option("timing", 1)
+    clocks = ClockSampler(dev)
+    clocks.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    st = ctx.stats()
+    ctx.set_option("timing", 0)
+    launches_per_step = st.launches
+    if dist:
+        t = torch.tensor([ms], device=f"cuda:{dev}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * L * args.steps / (ms / 1e3)
+
+    # status check of the last step (every ligand must have docked)
+    status = outs["status"][:L].cpu().numpy()
+    assert np.all(status == 0), "some ligands failed to dock"
+
+    # roofline of the docking kernel (FP32 ALU bound)
+    F = algorithmic_flops(batch, S, P)
+    dock_ms = st.dock_ms_total / max(st.dock_calls, 1)
+    props = torch.cuda.get_device_properties(dev)
+    sm_count = props.multi_processor_count
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    sm_max_mhz = float(peaks.get("sm_max_mhz") or (clk or {}).get("sm_max_mhz") or 2070.0)
+    peak_tflops = sm_count * FP32_LANES_PER_SM * FLOP_PER_FMA * sm_max_mhz * 1e6 / 1e12
+    achieved = F / (dock_ms / 1e3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                "frac": achieved / peak_tflops, "traffic": traffic_for_current_kernel(),
+                "kernel": "k_dock_batched", "dock_ms_per_launch": dock_ms, "flop_per_launch": F,
+                "peak_basis": f"{sm_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max_mhz:.0f} MHz"}
+
+    # end to end through the public API with host buffers (pinned)
+    hb = lg.host_batch_arrays(batch)
+    pinned = {k: torch.from_numpy(v.view(np.int64) if v.dtype == np.uint64 else v).pin_memory()
+              for k, v in hb.items()}
+    hstruct = lg.make_batch_struct({k: v.numpy() for k, v in pinned.items()}, L)
+    hout = {"score": torch.zeros(L, dtype=torch.float64).pin_memory(),
+            "best_restart": torch.zeros(L, dtype=torch.int32).pin_memory(),
+            "status": torch.zeros(L, dtype=torch.int32).pin_memory(),
+            "tors_idx": torch.zeros(max(P * R, 1), dtype=torch.uint8).pin_memory(),
+            "pose": torch.zeros(3 * A, dtype=torch.float32).pin_memory()}
+    hres = lg.lg_dock_result()
+    hres.mem = lg.LG_MEM_HOST
+    for k, v in hout.items():
+        setattr(hres, k, v.data_ptr())
+    h2d = sum(v.numel() * v.element_size() for v in pinned.values())
+    d2h = L * (8 + 4 + 4) + P * R + 12 * A
+    e2e_steps = max(2, min(args.steps, 5))
+    lg.lg_dock_batch(ctx.h, pid, hstruct, pstruct, hres, sh)
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        flush.fill_(1)
+        lg.lg_dock_batch(ctx.h, pid, hstruct, pstruct, hres, sh)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], device=f"cuda:{dev}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": world * L * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+           "d2h_bytes_per_step": int(d2h), "steps": e2e_steps}
+    assert np.array_equal(hout["score"].numpy(), outs["score"][:L].cpu().numpy()), "host and device paths disagree"
+
+    line = None
+    if rank == 0:
+        # plain form (one launch per ligand, one warp per restart) on a sample
+        n_plain = min(args.plain_sample, L)
+        sub = batch.subset(range(n_plain))
+        sarr = lg.device_batch_arrays(sub, f"cuda:{dev}")
+        sstruct = lg.make_batch_struct(sarr, n_plain)
+        ppl = lg.make_params(S, P, params.seed, params.d_clash, lg.LG_MODE_PLAIN, 8, max_atoms, max_rot)
+        rpl, opl = lg.alloc_result(n_plain, int(sub.atom_off[-1]), int(sub.rot_off[-1]), S, P, device=True)
+        lg.lg_dock_batch(ctx.h, pid, sstruct, ppl, rpl, sh)   # warm-up
+        torch.cuda.synchronize()
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        lg.lg_dock_batch(ctx.h, pid, sstruct, ppl, rpl, sh)
+        p1.record(stream)
+        torch.cuda.synchronize()
+        plain_value = n_plain / (p0.elapsed_time(p1) / 1e3)
+        assert np.array_equal(opl["score"][:n_plain].cpu().numpy(), outs["score"][:n_plain].cpu().numpy())
+        plain = {"value": plain_value, "unit": UNIT, "sample_ligands": n_plain, "streams": 8,
+                 "batched_over_plain": value / world / plain_value}
+
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            rate, n_done, secs = oracle_rate(pocket, batch, params, args.cpu_budget)
+            cpu = {"value": rate, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+                   "sample": f"first {n_done} ligands of the workload, FP64 oracle, {secs:.1f} s"}
+
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "ligands_per_gpu": L, "restarts": S, "passes": P,
+                           "angle_steps": 36, "mode": "batched persistent, cost-sorted",
+                           "l2": "flushed before every step (256 MiB write)", "inputs": "device-resident",
+                           "warps_per_cta": st.warps_per_cta, "ctas_per_sm": st.ctas_per_sm, "grid": st.grid},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "clocks": clk, "gpu_launches": launches_per_step * args.steps, "plain": plain}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

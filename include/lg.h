@@ -1,0 +1,299 @@
+/*
+ * lg.h -- C-ABI of liblgdock: batched flexible-ligand docking and scoring on
+ * one GB300 (sm_103a).
+ *
+ * The library implements the dock-and-score step of the EXSCALATE platform
+ * (paper Sec. 3.1): every ligand is docked into a rigid binding site by a
+ * greedy optimisation with multiple restarts, driven by a geometric (steric)
+ * score, with the ligand made flexible through its torsional bonds, which are
+ * processed one after the other; the ligand's score is that of its best pose.
+ * The binding site is constant for the life of the application and is loaded
+ * once (Sec. 3.2), and a ligand's own description is all that docking it needs
+ * (Sec. 3.2), so the calls below take a pocket handle plus a batch of ligand
+ * descriptions.  Results depend only on (ligand uid, seed, pocket, parameters),
+ * so a pose can be regenerated on demand from the stored score (Sec. 4.1).
+ *
+ * Concrete readings of the method (restart pose from Philox4x32-10 and
+ * Shoemake rotations, 36 torsion steps of 10 degrees, intra-ligand clash
+ * distance, trilinear grid scoring, tie-breaks) are stated at lg_dock_batch.
+ *
+ * Conventions for every call:
+ *   - Return value: LG_OK or one of the LG_E* codes; lg_last_error() gives a
+ *     message (per calling thread).  No C++ exception crosses this boundary.
+ *   - Pointers are host or device pointers as the struct's `mem` field says.
+ *     Device pointers must be CUDA device (or managed) memory of the device the
+ *     context was created on.  Arrays are dense, with the element types given.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).
+ *   - Nothing the caller passes is retained after a call returns, except where
+ *     stated (asynchronous device-memory docking, stream submission).
+ */
+#ifndef LG_H
+#define LG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- codes */
+#define LG_OK 0
+#define LG_EINVAL 1     /* bad argument or malformed ligand */
+#define LG_ENOMEM 2     /* device or host allocation failed */
+#define LG_EAGAIN 3     /* queue full / not enough free device memory yet */
+#define LG_ETIMEOUT 4   /* a bounded wait ran out */
+#define LG_ECUDA 5      /* a CUDA runtime call failed */
+#define LG_ENOPOCKET 6  /* unknown pocket id */
+
+#define LG_MEM_HOST 0
+#define LG_MEM_DEVICE 1
+
+#define LG_MODE_BATCHED 0 /* persistent, cost-sorted, one launch per batch */
+#define LG_MODE_PLAIN 1   /* one launch per ligand, one warp per restart */
+
+#define LG_MAX_ATOMS 128  /* atoms per ligand */
+#define LG_MAX_ROT 32     /* torsional bonds per ligand */
+#define LG_MAX_PASSES 8
+#define LG_MAX_RESTARTS 1024
+#define LG_ANGLE_STEPS 36 /* torsion steps per bond (10 degrees each) */
+#define LG_NUM_TYPES 5    /* atom types C, N, O, S, Cl */
+
+typedef struct lg_ctx lg_ctx;
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context on CUDA device `device`.  The context owns every device
+ * allocation the library makes (pockets, staging and scratch buffers) and the
+ * serving worker.  Errors: LG_EINVAL (bad device), LG_ECUDA. */
+int lg_create(int device, lg_ctx **out);
+
+/* Destroy a context: stops the serving worker (pending requests fail), frees
+ * every pocket and buffer.  Safe on NULL. */
+void lg_destroy(lg_ctx *ctx);
+
+/* Message of the last error returned to the calling thread (never NULL). */
+const char *lg_last_error(lg_ctx *ctx);
+
+/* ---------------------------------------------------------------- pockets */
+
+/* A rigid binding site (Sec. 3.2: fetched once, stored where each
+ * implementation sees fit -- here packed per grid cell in device memory).
+ * Grids are n^3 FP32 values, x fastest: node (i,j,k) is at origin + h*(i,j,k)
+ * and its value at phi[(k*n + j)*n + i].
+ *   phi_o          pocket-overlap field that drives the torsion sweep
+ *   phi_v, phi_e   vdW-like potential and electrostatic potential per unit
+ *                  charge, used by the final pose score
+ *   pocket_points  n_pp node indices (i,j,k) where restart poses are centred
+ *   type_w         per-type multipliers of phi_v (C, N, O, S, Cl)
+ *   k_out          slope of the penalty for atoms outside the grid box */
+typedef struct {
+    int32_t n;
+    float h;
+    float origin[3];
+    const float *phi_o;
+    const float *phi_v;
+    const float *phi_e;
+    int32_t n_pp;
+    const int32_t *pocket_points;
+    float type_w[LG_NUM_TYPES];
+    float k_out;
+} lg_pocket_desc;
+
+/* Copy a pocket (host pointers) into device memory owned by the context and
+ * return its id.  The caller's buffers may be freed on return.  Requires
+ * 2 <= n <= 512, h > 0, n_pp >= 1 and every pocket point inside the grid.
+ * Errors: LG_EINVAL, LG_ENOMEM, LG_ECUDA. */
+int lg_pocket_load(lg_ctx *ctx, const lg_pocket_desc *d, int32_t *pocket_id);
+
+/* Free a pocket.  The caller must not have docking in flight on it.
+ * Errors: LG_ENOPOCKET. */
+int lg_pocket_unload(lg_ctx *ctx, int32_t pocket_id);
+
+/* ---------------------------------------------------------------- ligands */
+
+/* A batch of L ligands in CSR structure-of-arrays layout (Sec. 4.1: each
+ * ligand is described by atom positions, types and bonds).
+ *   atom_off[L+1]   atoms of ligand l are atom_off[l] .. atom_off[l+1]-1
+ *   x,y,z,q [A]     FP32 coordinates (A) and partial charges
+ *   type [A]        0..4 = C, N, O, S, Cl
+ *   parent [A]      local index of the atom's parent in the ligand's bond tree,
+ *                   -1 for local atom 0; atoms must be in depth-first preorder
+ *                   (parent[i] < i and every subtree a contiguous index range)
+ *   rot_off[L+1]    torsional bonds of ligand l are rot_off[l] .. rot_off[l+1]-1
+ *   rot_child [R]   a torsional bond is named by its child atom b (local index):
+ *                   the bond (parent[b], b); strictly ascending per ligand
+ *   uid [L]         ligand identity; the random restart poses depend on it only
+ * A ligand that breaks these rules gets status LG_EINVAL and the others run.
+ * Limits: 1 <= atoms <= LG_MAX_ATOMS, torsional bonds <= LG_MAX_ROT. */
+typedef struct {
+    int32_t L;
+    int32_t mem; /* LG_MEM_HOST or LG_MEM_DEVICE, for every pointer below */
+    const int32_t *atom_off;
+    const float *x, *y, *z, *q;
+    const uint8_t *type;
+    const int16_t *parent;
+    const int32_t *rot_off;
+    const int16_t *rot_child;
+    const uint64_t *uid;
+} lg_ligand_batch;
+
+/* Docking parameters (Sec. 3.1: restarts of the greedy optimisation; the
+ * paper's run used 256 initial poses per ligand).
+ *   restarts     1..LG_MAX_RESTARTS random initial poses per ligand
+ *   passes       0..LG_MAX_PASSES sweeps over all torsional bonds
+ *   angle_steps  must be LG_ANGLE_STEPS (36 steps of 10 degrees)
+ *   seed         64-bit key of the restart-pose random stream
+ *   d_clash      minimum distance (A) between a moving atom and a fixed atom
+ *                three or more bonds away; > 0
+ *   mode         LG_MODE_BATCHED or LG_MODE_PLAIN
+ *   plain_streams  streams the plain mode spreads its launches over (1..64;
+ *                0 = 8); ignored in batched mode
+ *   max_atoms, max_rot  optional declared maxima over the batch (0 = the
+ *                library limits).  They size the kernels' shared memory: a
+ *                smaller declaration lets more CTAs share an SM.  Ligands
+ *                above a declared maximum get status LG_EINVAL.  For host
+ *                batches the library also measures the maxima itself. */
+typedef struct {
+    int32_t restarts;
+    int32_t passes;
+    int32_t angle_steps;
+    uint64_t seed;
+    float d_clash;
+    int32_t mode;
+    int32_t plain_streams;
+    int32_t max_atoms;
+    int32_t max_rot;
+} lg_dock_params;
+
+/* Caller-owned outputs (all with the location given by `mem`).
+ *   score [L]          FP64 score E of the best pose (lower is better), NaN on error
+ *   best_restart [L]   restart index of the best pose, -1 on error
+ *   tors_idx           optional: torsion step (0..35) chosen at each decision of
+ *                      the best restart, passes*rot_off[l] + pass*R_l + k
+ *   pose               optional: best pose, 3*atom_off[l] + 3*i + {x,y,z} (A)
+ *   status [L]         LG_OK or LG_EINVAL per ligand
+ *   restart_score      optional: E of every restart, l*restarts + r
+ *   restart_tors       optional: steps of every restart,
+ *                      restarts*passes*rot_off[l] + (r*passes + pass)*R_l + k */
+typedef struct {
+    int32_t mem;
+    double *score;
+    int32_t *best_restart;
+    uint8_t *tors_idx;
+    float *pose;
+    int32_t *status;
+    double *restart_score;
+    uint8_t *restart_tors;
+} lg_dock_result;
+
+/* Dock and score a batch of ligands against one pocket (paper Sec. 3.1).
+ *
+ * Per (ligand, restart r):
+ *   1. pose: Philox4x32-10 (key = seed, counter = (uid_lo, uid_hi, r, 0)) gives
+ *      x0..x3; u_i = (x_i >> 8) * 2^-24; Shoemake's uniform quaternion from
+ *      (u0, u1, u2) gives R; the pocket point is number ((x3 >> 8) * n_pp) >> 24;
+ *      atoms are placed at R (x - centroid) + pocket point.
+ *   2. sweep: `passes` times, each torsional bond in ascending child order:
+ *      the atoms hanging below the child turn about the bond axis through the
+ *      child by each of 36 steps of 10 degrees; a step's overlap score is the
+ *      sum of phi_o (trilinear) over those atoms; a step is admissible when it
+ *      is step 0 or no moved atom comes closer than d_clash to an atom outside
+ *      the child's subtree that is three or more bonds away; the admissible
+ *      step with the highest overlap (lowest step on ties) is applied.
+ *   3. score: E = sum over atoms of type_w*phi_v + q*phi_e at the position
+ *      clamped to the grid box, plus k_out times the distance outside the box;
+ *      per-atom terms in FP32, sum in FP64.
+ *   4. best: the lowest E wins, the lowest restart on ties.
+ * Geometry and lookups run in FP32.
+ *
+ * Memory: if the batch and result are device memory the call is asynchronous
+ * on `stream` and the caller keeps every buffer alive until the stream
+ * reaches the end of the call; otherwise the library stages through its own
+ * device buffers and returns after the results are in host memory.
+ * Errors: LG_EINVAL (bad parameters or sizes; per-ligand problems go to
+ * status[] instead), LG_ENOPOCKET, LG_ENOMEM, LG_ECUDA. */
+int lg_dock_batch(lg_ctx *ctx, int32_t pocket_id, const lg_ligand_batch *batch, const lg_dock_params *params,
+                  lg_dock_result *out, void *stream);
+
+/* Given poses to score (step 3 above alone).
+ *   atom_off[L+1], xyz[3*A] (A, interleaved), q[A], type[A]. */
+typedef struct {
+    int32_t L;
+    int32_t mem;
+    const int32_t *atom_off;
+    const float *xyz;
+    const float *q;
+    const uint8_t *type;
+} lg_pose_batch;
+
+/* Score L given poses against a pocket: energies[L] (FP64, same `mem` as the
+ * batch).  Synchronous for host memory, stream-ordered for device memory.
+ * Errors: LG_EINVAL, LG_ENOPOCKET, LG_ENOMEM, LG_ECUDA. */
+int lg_score_poses(lg_ctx *ctx, int32_t pocket_id, const lg_pose_batch *batch, double *energies, void *stream);
+
+/* ---------------------------------------------------------------- serving */
+
+#define LG_REQ_QUEUED 0
+#define LG_REQ_RUNNING 1
+#define LG_REQ_DONE 2
+#define LG_REQ_FAILED 3
+
+/* Submit a docking request to the context's serving loop (the paper streams
+ * a chemical library through a fixed binding site, Sec. 3.2-3.3).  The batch
+ * must be host memory; it is copied before the call returns, so the caller
+ * may free it.  `out` must be host memory and stay alive until the request is
+ * DONE or FAILED.  Requests are admitted to the device when enough free
+ * device memory and in-flight slots exist, and their ligands share the device
+ * with the other requests in flight.  Never blocks on the GPU.
+ * Errors: LG_EINVAL, LG_ENOPOCKET, LG_EAGAIN (host queue full), LG_ENOMEM. */
+int lg_stream_submit(lg_ctx *ctx, int32_t pocket_id, const lg_ligand_batch *batch, const lg_dock_params *params,
+                     lg_dock_result *out, uint64_t *ticket);
+
+/* State of a request (LG_REQ_*) and, once DONE, its submit-to-done latency in
+ * seconds.  Never blocks.  Errors: LG_EINVAL (unknown ticket). */
+int lg_stream_poll(lg_ctx *ctx, uint64_t ticket, int32_t *state, double *latency_s);
+
+/* Block until the request is DONE or FAILED, at most timeout_ms milliseconds.
+ * Errors: LG_ETIMEOUT, LG_EINVAL (unknown ticket), LG_ECUDA (request FAILED). */
+int lg_stream_wait(lg_ctx *ctx, uint64_t ticket, int32_t timeout_ms);
+
+/* ---------------------------------------------------------------- introspection */
+
+/* Figures of the lg_dock_batch calls on this context.  With timing on
+ * (lg_set_option "timing" = 1, which also clears the totals) every call
+ * brackets its docking kernel(s) with CUDA events on the call's stream;
+ * lg_get_stats waits for those events and reports the last call's device time
+ * and the sum over the calls since timing was switched on. */
+typedef struct {
+    float dock_ms;        /* device time of the last call's docking kernel(s) */
+    int32_t dock_calls;   /* timed calls since timing was switched on */
+    double dock_ms_total; /* their summed device time */
+    int32_t launches;     /* kernels launched by the last call */
+    int32_t grid;         /* CTAs of the docking kernel (batched mode) */
+    int32_t warps_per_cta;
+    int32_t ctas_per_sm;
+    int32_t smem_bytes;   /* dynamic shared memory per CTA */
+} lg_stats;
+
+int lg_get_stats(lg_ctx *ctx, lg_stats *out);
+
+/* Context options: "timing" (0/1, default 0), "warps_per_cta" (0 = autotune,
+ * else 1..32), "serve_max_inflight" (requests on the device at once, default 8),
+ * "serve_mem_reserve_mb" (free device memory the server leaves untouched,
+ * default 1024).  Errors: LG_EINVAL. */
+int lg_set_option(lg_ctx *ctx, const char *key, int64_t value);
+
+/* ---------------------------------------------------------------- diagnostics */
+
+/* Philox4x32-10 of n (counter, key) pairs on the device (device pointers:
+ * ctr[4n], key[2n], out[4n] as uint32).  use_curand = 0 runs the library's own
+ * generator, 1 runs cuRAND's curand_Philox4x32_10 for comparison.
+ * Synchronous.  Errors: LG_EINVAL, LG_ECUDA. */
+int lg_diag_philox(lg_ctx *ctx, int32_t n, const uint32_t *ctr, const uint32_t *key, uint32_t *out,
+                   int32_t use_curand);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LG_H */

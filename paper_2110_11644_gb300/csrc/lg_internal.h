@@ -1,0 +1,126 @@
+// Internal declarations shared by the runtime (lg_runtime.cu) and the kernels
+// (lg_kernels.cu).  Not part of the public ABI (include/lg.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lg.h"
+
+namespace lg {
+
+// Device view of a loaded pocket.  Positions inside the kernels live in a
+// frame centred on the grid box ("centred frame", A): x_c = x_world - center.
+// Grid index space: g = x_c * inv_h + c0, with c0 = (n-1)/2, so node (i,j,k)
+// sits at g = (i,j,k).
+//
+// Cells: for every node (i,j,k), i,j,k in [0, n-1], the 8 coefficients of the
+// trilinear polynomial through the values at (i+a, j+b, k+c), a,b,c in {0,1}
+// (indices clamped to n-1, so the last layer repeats the edge):
+//   p(fx,fy,fz) = c0 + c1 fx + c2 fy + c3 fz + c4 fx fy + c5 fx fz + c6 fy fz + c7 fx fy fz
+// stored as two float4 (c0..c3, c4..c7): one 32-byte sector per lookup.
+// cell_ve holds 16 coefficients per node: phi_v's then phi_e's.
+struct PocketDev {
+    int n;
+    float h, inv_h, c0, gmax;  // gmax = n - 1
+    float3 center;             // world position of the box centre
+    const float4 *cell_o;      // 2 float4 per node
+    const float4 *cell_ve;     // 4 float4 per node
+    const float4 *pp;          // pocket points in the centred frame (x, y, z, 0)
+    int n_pp;
+    float type_w[LG_NUM_TYPES];
+    float k_out;
+};
+
+struct BatchDev {
+    int L;
+    const int32_t *atom_off;
+    const float *x, *y, *z, *q;
+    const uint8_t *type;
+    const int16_t *parent;
+    const int32_t *rot_off;
+    const int16_t *rot_child;
+    const uint64_t *uid;
+};
+
+struct OutDev {
+    double *score;
+    int32_t *best_restart;
+    uint8_t *tors_idx;
+    float *pose;
+    int32_t *status;
+    double *restart_score;
+    uint8_t *restart_tors;
+};
+
+// Shared-memory layout of one docking CTA: a part shared by the CTA (the
+// ligand being docked) and one region per warp (one restart at a time).
+struct Layout {
+    int nmax, rmax, P, W, want_pose;
+    // CTA part (byte offsets from the start of dynamic shared memory)
+    int o_dv, o_wE, o_d0, o_wq, o_par, o_rch, o_rend, o_wR, o_scal, cta_bytes;
+    // warp part (byte offsets from the warp's base)
+    int o_bundle, o_axis, o_X, o_best, o_tcur, o_tbest, warp_bytes;
+    int total;
+};
+
+__host__ __device__ inline int lg_align16(int v) { return (v + 15) & ~15; }
+
+__host__ __device__ inline Layout make_layout(int nmax, int rmax, int P, int W, int want_pose) {
+    Layout L;
+    nmax = (nmax + 3) & ~3;
+    if (rmax < 1) rmax = 1;
+    L.nmax = nmax; L.rmax = rmax; L.P = P; L.W = W; L.want_pose = want_pose;
+    int o = 0;
+    L.o_dv = o;   o = lg_align16(o + 16 * rmax);           // float4 bond vectors
+    L.o_wE = o;   o = lg_align16(o + 8 * W);               // double per warp
+    L.o_d0 = o;   o = lg_align16(o + 12 * nmax);           // float x3 SoA
+    L.o_wq = o;   o = lg_align16(o + 8 * nmax);            // float2 (type weight, charge)
+    L.o_par = o;  o = lg_align16(o + 4 * nmax);            // int parent
+    L.o_rch = o;  o = lg_align16(o + 4 * rmax);            // int rotatable child
+    L.o_rend = o; o = lg_align16(o + 4 * rmax);            // int subtree end of child
+    L.o_wR = o;   o = lg_align16(o + 4 * W);               // int per warp
+    L.o_scal = o; o = lg_align16(o + 32);                  // N, R, status, centroid (3 doubles follow)
+    o = lg_align16(o + 32);
+    L.cta_bytes = o;
+    int w = 0;
+    L.o_bundle = w; w = lg_align16(w + 32 * 48);           // 32 atoms x 3 float4 (aliased by T)
+    L.o_axis = w;   w = lg_align16(w + 16 * rmax);         // float4 current bond axes
+    L.o_X = w;      w = lg_align16(w + 12 * nmax);         // float x3 SoA positions
+    L.o_best = w;   w = lg_align16(w + (want_pose ? 12 * nmax : 0));
+    L.o_tcur = w;   w = lg_align16(w + P * rmax);
+    L.o_tbest = w;  w = lg_align16(w + P * rmax);
+    L.warp_bytes = w;
+    L.total = L.cta_bytes + W * L.warp_bytes;
+    return L;
+}
+
+struct DockArgs {
+    PocketDev pocket;
+    BatchDev batch;
+    OutDev out;
+    Layout ly;
+    int S, P;
+    uint32_t seed_lo, seed_hi;
+    float dc2;  // d_clash^2
+    int nmax_decl, rmax_decl;  // declared per-ligand maxima (ligands above them are rejected)
+    const int32_t *order;      // batched mode: ligand visiting order (NULL = identity)
+    int32_t *work_counter;     // batched mode: next item of the persistent loop
+};
+
+// Launchers (lg_kernels.cu)
+void set_angle_tables(const float *cosv, const float *sinv);
+cudaError_t launch_dock_plain(const DockArgs &a, int ligand, cudaStream_t s);
+cudaError_t launch_dock_batched(const DockArgs &a, int grid, cudaStream_t s);
+cudaError_t launch_sort(const DockArgs &a, int32_t *keys, int32_t *hist, int32_t *order, cudaStream_t s,
+                        int *launches);
+cudaError_t launch_score_poses(const PocketDev &p, int L, const int32_t *atom_off, const float *xyz,
+                               const float *q, const uint8_t *type, double *E, cudaStream_t s);
+cudaError_t launch_diag_philox(int n, const uint32_t *ctr, const uint32_t *key, uint32_t *out, int use_curand,
+                               cudaStream_t s);
+cudaError_t dock_kernel_attributes(int W, int smem, int *ctas_per_sm);
+cudaError_t plain_kernel_attributes(int smem);
+
+constexpr int kSortBuckets = 128;
+
+}  // namespace lg

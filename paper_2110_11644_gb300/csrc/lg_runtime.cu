@@ -1,0 +1,637 @@
+// C-ABI runtime of liblgdock (include/lg.h): contexts, pocket registry and
+// cell packing, host<->device staging, launch configuration of the docking
+// kernels, and the serving loop (lg_serve.cu).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "lg_internal.h"
+#include "lg_runtime.h"
+
+using namespace lg;
+
+namespace lg {
+
+thread_local std::string t_err;
+
+int fail(int code, const std::string &msg) {
+    t_err = msg;
+    return code;
+}
+
+int DevBuf::ensure(size_t n) {
+    if (n <= cap) return 0;
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+    if (cudaMalloc(&p, n) != cudaSuccess) {
+        cudaGetLastError();
+        return -1;
+    }
+    cap = n;
+    return 0;
+}
+
+void DevBuf::release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+}
+
+// Carves aligned sub-arrays out of one allocation.
+struct Carve {
+    size_t off = 0;
+    size_t take(size_t bytes) {
+        size_t o = off;
+        off = (off + bytes + 255) & ~(size_t)255;
+        return o;
+    }
+};
+
+int check_params(const lg_dock_params *p) {
+    if (p->restarts < 1 || p->restarts > LG_MAX_RESTARTS) return fail(LG_EINVAL, "restarts out of range");
+    if (p->passes < 0 || p->passes > LG_MAX_PASSES) return fail(LG_EINVAL, "passes out of range");
+    if (p->angle_steps != LG_ANGLE_STEPS) return fail(LG_EINVAL, "angle_steps must be 36");
+    if (!(p->d_clash > 0.0f) || !std::isfinite(p->d_clash)) return fail(LG_EINVAL, "d_clash must be > 0");
+    if (p->mode != LG_MODE_BATCHED && p->mode != LG_MODE_PLAIN) return fail(LG_EINVAL, "unknown mode");
+    if (p->plain_streams < 0 || p->plain_streams > 64) return fail(LG_EINVAL, "plain_streams out of range");
+    if (p->max_atoms < 0 || p->max_atoms > LG_MAX_ATOMS) return fail(LG_EINVAL, "max_atoms out of range");
+    if (p->max_rot < 0 || p->max_rot > LG_MAX_ROT) return fail(LG_EINVAL, "max_rot out of range");
+    return LG_OK;
+}
+
+// Host-side view of a batch's CSR structure (host batches only).
+int host_batch_shape(const lg_ligand_batch *b, int64_t *A, int64_t *R, int *nmax, int *rmax) {
+    const int L = b->L;
+    if (b->atom_off[0] != 0 || b->rot_off[0] != 0) return fail(LG_EINVAL, "atom_off[0] and rot_off[0] must be 0");
+    int nm = 0, rm = 0;
+    for (int l = 0; l < L; l++) {
+        const int64_t n = (int64_t)b->atom_off[l + 1] - b->atom_off[l];
+        const int64_t r = (int64_t)b->rot_off[l + 1] - b->rot_off[l];
+        if (n < 0 || r < 0) return fail(LG_EINVAL, "atom_off / rot_off must be non-decreasing");
+        nm = (int)std::max<int64_t>(nm, n);
+        rm = (int)std::max<int64_t>(rm, r);
+    }
+    *A = b->atom_off[L];
+    *R = b->rot_off[L];
+    *nmax = nm;
+    *rmax = rm;
+    return LG_OK;
+}
+
+// Stage a host batch into device buffer `buf`; fills `d` with device pointers.
+int stage_batch(DevBuf &buf, const lg_ligand_batch *b, int64_t A, int64_t R, BatchDev *d, cudaStream_t s) {
+    const int L = b->L;
+    Carve c;
+    const size_t o_aoff = c.take(4 * (size_t)(L + 1)), o_roff = c.take(4 * (size_t)(L + 1));
+    const size_t o_uid = c.take(8 * (size_t)L);
+    const size_t o_x = c.take(4 * (size_t)A), o_y = c.take(4 * (size_t)A), o_z = c.take(4 * (size_t)A);
+    const size_t o_q = c.take(4 * (size_t)A), o_t = c.take((size_t)A), o_p = c.take(2 * (size_t)A);
+    const size_t o_rc = c.take(2 * (size_t)std::max<int64_t>(R, 1));
+    if (buf.ensure(c.off)) return fail(LG_ENOMEM, "device staging allocation failed");
+    char *base = (char *)buf.p;
+    auto cp = [&](size_t off, const void *src, size_t n) -> cudaError_t {
+        if (n == 0) return cudaSuccess;
+        return cudaMemcpyAsync(base + off, src, n, cudaMemcpyHostToDevice, s);
+    };
+    cudaError_t e = cudaSuccess;
+    e = e ? e : cp(o_aoff, b->atom_off, 4 * (size_t)(L + 1));
+    e = e ? e : cp(o_roff, b->rot_off, 4 * (size_t)(L + 1));
+    e = e ? e : cp(o_uid, b->uid, 8 * (size_t)L);
+    e = e ? e : cp(o_x, b->x, 4 * (size_t)A);
+    e = e ? e : cp(o_y, b->y, 4 * (size_t)A);
+    e = e ? e : cp(o_z, b->z, 4 * (size_t)A);
+    e = e ? e : cp(o_q, b->q, 4 * (size_t)A);
+    e = e ? e : cp(o_t, b->type, (size_t)A);
+    e = e ? e : cp(o_p, b->parent, 2 * (size_t)A);
+    if (R > 0) e = e ? e : cp(o_rc, b->rot_child, 2 * (size_t)R);
+    if (e != cudaSuccess) return fail(LG_ECUDA, std::string("batch upload: ") + cudaGetErrorString(e));
+    d->L = L;
+    d->atom_off = (const int32_t *)(base + o_aoff);
+    d->rot_off = (const int32_t *)(base + o_roff);
+    d->uid = (const uint64_t *)(base + o_uid);
+    d->x = (const float *)(base + o_x);
+    d->y = (const float *)(base + o_y);
+    d->z = (const float *)(base + o_z);
+    d->q = (const float *)(base + o_q);
+    d->type = (const uint8_t *)(base + o_t);
+    d->parent = (const int16_t *)(base + o_p);
+    d->rot_child = (const int16_t *)(base + o_rc);
+    return LG_OK;
+}
+
+// Device output buffers for a host result; fills `d`.
+int stage_out(DevBuf &buf, const lg_dock_result *o, int L, int S, int P, int64_t A, int64_t R, OutDev *d) {
+    Carve c;
+    const size_t o_s = c.take(8 * (size_t)L), o_b = c.take(4 * (size_t)L), o_st = c.take(4 * (size_t)L);
+    const size_t o_t = o->tors_idx ? c.take((size_t)P * R + 1) : 0;
+    const size_t o_p = o->pose ? c.take(12 * (size_t)A) : 0;
+    const size_t o_rs = o->restart_score ? c.take(8 * (size_t)L * S) : 0;
+    const size_t o_rt = o->restart_tors ? c.take((size_t)S * P * R + 1) : 0;
+    if (buf.ensure(c.off)) return fail(LG_ENOMEM, "device output allocation failed");
+    char *base = (char *)buf.p;
+    d->score = (double *)(base + o_s);
+    d->best_restart = (int32_t *)(base + o_b);
+    d->status = (int32_t *)(base + o_st);
+    d->tors_idx = o->tors_idx ? (uint8_t *)(base + o_t) : nullptr;
+    d->pose = o->pose ? (float *)(base + o_p) : nullptr;
+    d->restart_score = o->restart_score ? (double *)(base + o_rs) : nullptr;
+    d->restart_tors = o->restart_tors ? (uint8_t *)(base + o_rt) : nullptr;
+    return LG_OK;
+}
+
+int fetch_out(const OutDev &d, const lg_dock_result *o, int L, int S, int P, int64_t A, int64_t R, cudaStream_t s) {
+    cudaError_t e = cudaSuccess;
+    auto cp = [&](void *dst, const void *src, size_t n) {
+        if (e == cudaSuccess && n) e = cudaMemcpyAsync(dst, src, n, cudaMemcpyDeviceToHost, s);
+    };
+    cp(o->score, d.score, 8 * (size_t)L);
+    cp(o->best_restart, d.best_restart, 4 * (size_t)L);
+    cp(o->status, d.status, 4 * (size_t)L);
+    if (o->tors_idx) cp(o->tors_idx, d.tors_idx, (size_t)P * R);
+    if (o->pose) cp(o->pose, d.pose, 12 * (size_t)A);
+    if (o->restart_score) cp(o->restart_score, d.restart_score, 8 * (size_t)L * S);
+    if (o->restart_tors) cp(o->restart_tors, d.restart_tors, (size_t)S * P * R);
+    if (e != cudaSuccess) return fail(LG_ECUDA, std::string("result download: ") + cudaGetErrorString(e));
+    return LG_OK;
+}
+
+// Warps per CTA for the batched kernel: a divisor of the restart count near
+// 8-10 warps (restarts split evenly), unless the context option fixes it.
+int choose_warps(int S, int opt) {
+    if (opt > 0) return std::min(opt, 32);
+    static const int pref[] = {10, 8, 12, 9, 15, 16, 6, 7, 5, 14, 11, 13};
+    for (int w : pref)
+        if (S % w == 0 && w <= S) return w;
+    if (S <= 16) return std::max(1, S);
+    return 8;
+}
+
+// Launch the docking of a device-resident batch on stream s.
+int dock_device(lg_ctx *ctx, const PocketDev &pk, const BatchDev &bd, const OutDev &od, const lg_dock_params *p,
+                int nmax, int rmax, DevBuf &scratch, cudaStream_t s, lg_stats *st, cudaEvent_t *tev) {
+    const bool timed = tev != nullptr;
+    DockArgs a;
+    memset(&a, 0, sizeof(a));
+    a.pocket = pk;
+    a.batch = bd;
+    a.out = od;
+    a.S = p->restarts;
+    a.P = p->passes;
+    a.seed_lo = (uint32_t)p->seed;
+    a.seed_hi = (uint32_t)(p->seed >> 32);
+    a.dc2 = p->d_clash * p->d_clash;
+    a.nmax_decl = p->max_atoms > 0 ? p->max_atoms : LG_MAX_ATOMS;
+    a.rmax_decl = p->max_rot > 0 ? p->max_rot : LG_MAX_ROT;
+    nmax = std::max(1, std::min(nmax, a.nmax_decl));
+    rmax = std::max(1, std::min(rmax, a.rmax_decl));
+    const int want_pose = od.pose != nullptr;
+    const lg_stats keep = *st;
+    memset(st, 0, sizeof(*st));
+    st->dock_calls = keep.dock_calls;
+    st->dock_ms_total = keep.dock_ms_total;
+    st->dock_ms = keep.dock_ms;
+    cudaError_t e;
+    if (p->mode == LG_MODE_PLAIN) {
+        const int W = std::min(a.S, 32);
+        a.ly = make_layout(nmax, rmax, a.P, W, want_pose);
+        if ((e = plain_kernel_attributes(a.ly.total)) != cudaSuccess)
+            return fail(LG_ECUDA, std::string("plain kernel attributes: ") + cudaGetErrorString(e));
+        const int ns = p->plain_streams > 0 ? p->plain_streams : 8;
+        if (ctx_plain_streams(ctx, ns)) return fail(LG_ECUDA, "plain-mode stream creation failed");
+        std::vector<cudaStream_t> &ps = ctx_streams(ctx);
+        cudaEvent_t fork = ctx_event(ctx, 0);
+        if (timed) cudaEventRecord(tev[0], s);
+        cudaEventRecord(fork, s);
+        for (int i = 0; i < ns; i++) cudaStreamWaitEvent(ps[i], fork, 0);
+        for (int l = 0; l < bd.L; l++) {
+            if ((e = launch_dock_plain(a, l, ps[l % ns])) != cudaSuccess)
+                return fail(LG_ECUDA, std::string("plain launch: ") + cudaGetErrorString(e));
+        }
+        for (int i = 0; i < ns; i++) {
+            cudaEvent_t j = ctx_join_event(ctx, i);
+            cudaEventRecord(j, ps[i]);
+            cudaStreamWaitEvent(s, j, 0);
+        }
+        if (timed) cudaEventRecord(tev[1], s);
+        st->launches = bd.L;
+        st->grid = bd.L;
+        st->warps_per_cta = W;
+        st->ctas_per_sm = 1;
+        st->smem_bytes = a.ly.total;
+        return LG_OK;
+    }
+    // batched: cost-ordered persistent launch
+    int W = choose_warps(a.S, ctx_warps_opt(ctx));
+    int occ = 0;
+    for (;;) {
+        a.ly = make_layout(nmax, rmax, a.P, W, want_pose);
+        if ((e = dock_kernel_attributes(W, a.ly.total, &occ)) != cudaSuccess)
+            return fail(LG_ECUDA, std::string("dock kernel attributes: ") + cudaGetErrorString(e));
+        if (occ > 0 || W == 1) break;
+        W = std::max(1, W / 2);
+    }
+    if (occ <= 0) return fail(LG_EINVAL, "docking kernel does not fit on an SM");
+    const int L = bd.L;
+    Carve c;
+    const size_t o_hist = c.take(4 * (kSortBuckets + 1));
+    const size_t o_keys = c.take(4 * (size_t)L), o_order = c.take(4 * (size_t)L);
+    if (scratch.ensure(c.off)) return fail(LG_ENOMEM, "scratch allocation failed");
+    char *sb = (char *)scratch.p;
+    int32_t *hist = (int32_t *)(sb + o_hist);
+    a.work_counter = hist + kSortBuckets;
+    a.order = (int32_t *)(sb + o_order);
+    if ((e = cudaMemsetAsync(hist, 0, 4 * (kSortBuckets + 1), s)) != cudaSuccess)
+        return fail(LG_ECUDA, std::string("scratch clear: ") + cudaGetErrorString(e));
+    int launches = 0;
+    if ((e = launch_sort(a, (int32_t *)(sb + o_keys), hist, (int32_t *)(sb + o_order), s, &launches)) != cudaSuccess)
+        return fail(LG_ECUDA, std::string("sort launch: ") + cudaGetErrorString(e));
+    const int grid = std::max(1, std::min(ctx_num_sms(ctx) * occ, L));
+    if (timed) cudaEventRecord(tev[0], s);
+    if ((e = launch_dock_batched(a, grid, s)) != cudaSuccess)
+        return fail(LG_ECUDA, std::string("dock launch: ") + cudaGetErrorString(e));
+    if (timed) cudaEventRecord(tev[1], s);
+    st->launches = launches + 1;
+    st->grid = grid;
+    st->warps_per_cta = W;
+    st->ctas_per_sm = occ;
+    st->smem_bytes = a.ly.total;
+    return LG_OK;
+}
+
+// Wait for the timed calls still in the ring and add their device times.
+void harvest_timing(lg_ctx *c) {
+    while (c->tev_pending > 0) {
+        const int i = (c->tev_head - c->tev_pending + lg_ctx::kTimingRing) % lg_ctx::kTimingRing;
+        float ms = 0.0f;
+        if (cudaEventSynchronize(c->tev[i][1]) == cudaSuccess &&
+            cudaEventElapsedTime(&ms, c->tev[i][0], c->tev[i][1]) == cudaSuccess) {
+            c->stats.dock_ms = ms;
+            c->stats.dock_ms_total += ms;
+            c->stats.dock_calls++;
+        } else {
+            cudaGetLastError();
+        }
+        c->tev_pending--;
+    }
+}
+
+// Pocket packing: trilinear coefficients per node (FP64, rounded to FP32).
+static void pack_cells(const float *g, int n, float *out, int stride, int offset) {
+    auto at = [&](int i, int j, int k) -> double {
+        i = std::min(i, n - 1);
+        j = std::min(j, n - 1);
+        k = std::min(k, n - 1);
+        return (double)g[((size_t)k * n + j) * n + i];
+    };
+    for (int k = 0; k < n; k++)
+        for (int j = 0; j < n; j++)
+            for (int i = 0; i < n; i++) {
+                const double v000 = at(i, j, k), v100 = at(i + 1, j, k), v010 = at(i, j + 1, k),
+                             v110 = at(i + 1, j + 1, k), v001 = at(i, j, k + 1), v101 = at(i + 1, j, k + 1),
+                             v011 = at(i, j + 1, k + 1), v111 = at(i + 1, j + 1, k + 1);
+                float *o = out + ((size_t)k * n * n + (size_t)j * n + i) * stride + offset;
+                o[0] = (float)v000;
+                o[1] = (float)(v100 - v000);
+                o[2] = (float)(v010 - v000);
+                o[3] = (float)(v001 - v000);
+                o[4] = (float)(v110 - v100 - v010 + v000);
+                o[5] = (float)(v101 - v100 - v001 + v000);
+                o[6] = (float)(v011 - v010 - v001 + v000);
+                o[7] = (float)(v111 - v110 - v101 - v011 + v100 + v010 + v001 - v000);
+            }
+}
+
+}  // namespace lg
+
+// ======================================================================= C ABI
+extern "C" {
+
+int lg_create(int device, lg_ctx **out) {
+    if (!out) return fail(LG_EINVAL, "out is NULL");
+    *out = nullptr;
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(LG_ECUDA, "no CUDA device");
+    }
+    if (device < 0 || device >= count) return fail(LG_EINVAL, "device out of range");
+    lg_ctx *c = new (std::nothrow) lg_ctx();
+    if (!c) return fail(LG_ENOMEM, "context allocation failed");
+    c->device = device;
+    cudaError_t e;
+    if ((e = cudaSetDevice(device)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device)) != cudaSuccess) {
+        delete c;
+        return fail(LG_ECUDA, std::string("device setup: ") + cudaGetErrorString(e));
+    }
+    for (int i = 0; i < 3; i++) cudaEventCreate(&c->ev[i]);
+    for (int i = 0; i < lg_ctx::kTimingRing; i++)
+        for (int j = 0; j < 2; j++) cudaEventCreate(&c->tev[i][j]);
+    float cs[LG_ANGLE_STEPS], sn[LG_ANGLE_STEPS];
+    for (int t = 0; t < LG_ANGLE_STEPS; t++) {
+        const double th = 2.0 * M_PI * t / LG_ANGLE_STEPS;
+        cs[t] = (float)cos(th);
+        sn[t] = (float)sin(th);
+    }
+    set_angle_tables(cs, sn);
+    if ((e = cudaGetLastError()) != cudaSuccess) {
+        lg_destroy(c);
+        return fail(LG_ECUDA, std::string("angle tables: ") + cudaGetErrorString(e));
+    }
+    *out = c;
+    return LG_OK;
+}
+
+void lg_destroy(lg_ctx *c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    serve_stop(c);
+    cudaDeviceSynchronize();
+    for (auto &p : c->pockets)
+        if (p.mem) cudaFree(p.mem);
+    c->in_buf.release();
+    c->out_buf.release();
+    c->scratch.release();
+    for (auto s : c->plain_streams) cudaStreamDestroy(s);
+    for (auto ev : c->join_events) cudaEventDestroy(ev);
+    for (int i = 0; i < 3; i++)
+        if (c->ev[i]) cudaEventDestroy(c->ev[i]);
+    for (int i = 0; i < lg_ctx::kTimingRing; i++)
+        for (int j = 0; j < 2; j++)
+            if (c->tev[i][j]) cudaEventDestroy(c->tev[i][j]);
+    delete c;
+}
+
+const char *lg_last_error(lg_ctx *) { return t_err.c_str(); }
+
+int lg_pocket_load(lg_ctx *c, const lg_pocket_desc *d, int32_t *pid) {
+    if (!c || !d || !pid) return fail(LG_EINVAL, "null argument");
+    const int n = d->n;
+    if (n < 2 || n > 512) return fail(LG_EINVAL, "grid size n must be in [2, 512]");
+    if (!(d->h > 0.0f) || !std::isfinite(d->h)) return fail(LG_EINVAL, "h must be > 0");
+    if (!d->phi_o || !d->phi_v || !d->phi_e || !d->pocket_points) return fail(LG_EINVAL, "null grid pointer");
+    if (d->n_pp < 1) return fail(LG_EINVAL, "n_pp must be >= 1");
+    for (int c3 = 0; c3 < 3; c3++)
+        if (!std::isfinite(d->origin[c3])) return fail(LG_EINVAL, "origin must be finite");
+    const size_t n3 = (size_t)n * n * n;
+    for (size_t t = 0; t < n3; t++)
+        if (!std::isfinite(d->phi_o[t]) || !std::isfinite(d->phi_v[t]) || !std::isfinite(d->phi_e[t]))
+            return fail(LG_EINVAL, "grid values must be finite");
+    for (int i = 0; i < 3 * d->n_pp; i++)
+        if (d->pocket_points[i] < 0 || d->pocket_points[i] >= n) return fail(LG_EINVAL, "pocket point outside grid");
+    std::lock_guard<std::mutex> g(c->mu);
+    if (cudaSetDevice(c->device) != cudaSuccess) return fail(LG_ECUDA, "cudaSetDevice failed");
+
+    std::vector<float> h_o(n3 * 8), h_ve(n3 * 16), h_pp(4 * (size_t)d->n_pp);
+    pack_cells(d->phi_o, n, h_o.data(), 8, 0);
+    pack_cells(d->phi_v, n, h_ve.data(), 16, 0);
+    pack_cells(d->phi_e, n, h_ve.data(), 16, 8);
+    const double c0 = (n - 1) / 2.0;
+    for (int p = 0; p < d->n_pp; p++) {
+        for (int c3 = 0; c3 < 3; c3++) h_pp[4 * p + c3] = (float)((double)d->h * (d->pocket_points[3 * p + c3] - c0));
+        h_pp[4 * p + 3] = 0.0f;
+    }
+    Carve cv;
+    const size_t o_o = cv.take(h_o.size() * 4), o_ve = cv.take(h_ve.size() * 4), o_pp = cv.take(h_pp.size() * 4);
+    void *mem = nullptr;
+    if (cudaMalloc(&mem, cv.off) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(LG_ENOMEM, "pocket allocation failed");
+    }
+    char *base = (char *)mem;
+    cudaError_t e = cudaMemcpy(base + o_o, h_o.data(), h_o.size() * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(base + o_ve, h_ve.data(), h_ve.size() * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(base + o_pp, h_pp.data(), h_pp.size() * 4, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(mem);
+        return fail(LG_ECUDA, std::string("pocket upload: ") + cudaGetErrorString(e));
+    }
+    PocketRec r;
+    r.live = true;
+    r.mem = mem;
+    r.bytes = cv.off;
+    PocketDev &pd = r.dev;
+    pd.n = n;
+    pd.h = d->h;
+    pd.inv_h = (float)(1.0 / (double)d->h);
+    pd.c0 = (float)c0;
+    pd.gmax = (float)(n - 1);
+    pd.center = make_float3((float)(d->origin[0] + d->h * c0), (float)(d->origin[1] + d->h * c0),
+                            (float)(d->origin[2] + d->h * c0));
+    pd.cell_o = (const float4 *)(base + o_o);
+    pd.cell_ve = (const float4 *)(base + o_ve);
+    pd.pp = (const float4 *)(base + o_pp);
+    pd.n_pp = d->n_pp;
+    for (int t = 0; t < LG_NUM_TYPES; t++) pd.type_w[t] = d->type_w[t];
+    pd.k_out = d->k_out;
+    int id = -1;
+    for (size_t i = 0; i < c->pockets.size(); i++)
+        if (!c->pockets[i].live) {
+            id = (int)i;
+            break;
+        }
+    if (id < 0) {
+        id = (int)c->pockets.size();
+        c->pockets.push_back(r);
+    } else {
+        c->pockets[id] = r;
+    }
+    *pid = id;
+    return LG_OK;
+}
+
+int lg_pocket_unload(lg_ctx *c, int32_t pid) {
+    if (!c) return fail(LG_EINVAL, "null context");
+    std::lock_guard<std::mutex> g(c->mu);
+    if (pid < 0 || pid >= (int)c->pockets.size() || !c->pockets[pid].live) return fail(LG_ENOPOCKET, "unknown pocket");
+    cudaSetDevice(c->device);
+    cudaFree(c->pockets[pid].mem);
+    c->pockets[pid] = PocketRec();
+    return LG_OK;
+}
+
+int lg_dock_batch(lg_ctx *c, int32_t pid, const lg_ligand_batch *b, const lg_dock_params *p, lg_dock_result *o,
+                  void *stream) {
+    if (!c || !b || !p || !o) return fail(LG_EINVAL, "null argument");
+    int rc = check_params(p);
+    if (rc) return rc;
+    if (b->L < 0) return fail(LG_EINVAL, "L must be >= 0");
+    if ((b->mem != LG_MEM_HOST && b->mem != LG_MEM_DEVICE) || (o->mem != LG_MEM_HOST && o->mem != LG_MEM_DEVICE))
+        return fail(LG_EINVAL, "mem must be LG_MEM_HOST or LG_MEM_DEVICE");
+    if (b->L == 0) return LG_OK;
+    if (!b->atom_off || !b->x || !b->y || !b->z || !b->q || !b->type || !b->parent || !b->rot_off || !b->uid)
+        return fail(LG_EINVAL, "null batch array");
+    if (!o->score || !o->best_restart || !o->status) return fail(LG_EINVAL, "score, best_restart and status are required");
+    std::lock_guard<std::mutex> g(c->mu);
+    if (cudaSetDevice(c->device) != cudaSuccess) return fail(LG_ECUDA, "cudaSetDevice failed");
+    PocketRec *pk = (pid >= 0 && pid < (int)c->pockets.size() && c->pockets[pid].live) ? &c->pockets[pid] : nullptr;
+    if (!pk) return fail(LG_ENOPOCKET, "unknown pocket");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int L = b->L, S = p->restarts, P = p->passes;
+
+    int64_t A = -1, R = -1;
+    int nmax = p->max_atoms > 0 ? p->max_atoms : LG_MAX_ATOMS;
+    int rmax = p->max_rot > 0 ? p->max_rot : LG_MAX_ROT;
+    BatchDev bd;
+    if (b->mem == LG_MEM_HOST) {
+        int nm, rm;
+        if ((rc = host_batch_shape(b, &A, &R, &nm, &rm))) return rc;
+        if (R > 0 && !b->rot_child) return fail(LG_EINVAL, "null rot_child");
+        nmax = std::min(nmax, std::max(nm, 1));
+        rmax = std::min(rmax, std::max(rm, 1));
+        if ((rc = stage_batch(c->in_buf, b, A, R, &bd, s))) return rc;
+    } else {
+        if (!b->rot_child) return fail(LG_EINVAL, "null rot_child");
+        bd.L = L;
+        bd.atom_off = b->atom_off;
+        bd.x = b->x;
+        bd.y = b->y;
+        bd.z = b->z;
+        bd.q = b->q;
+        bd.type = b->type;
+        bd.parent = b->parent;
+        bd.rot_off = b->rot_off;
+        bd.rot_child = b->rot_child;
+        bd.uid = b->uid;
+    }
+    OutDev od;
+    if (o->mem == LG_MEM_HOST) {
+        if (A < 0) {  // device batch, host result: read the two totals
+            int32_t tot[2];
+            cudaError_t e = cudaMemcpyAsync(&tot[0], b->atom_off + L, 4, cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(&tot[1], b->rot_off + L, 4, cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) return fail(LG_ECUDA, std::string("batch totals: ") + cudaGetErrorString(e));
+            A = tot[0];
+            R = tot[1];
+        }
+        if ((rc = stage_out(c->out_buf, o, L, S, P, A, R, &od))) return rc;
+    } else {
+        od.score = o->score;
+        od.best_restart = o->best_restart;
+        od.status = o->status;
+        od.tors_idx = o->tors_idx;
+        od.pose = o->pose;
+        od.restart_score = o->restart_score;
+        od.restart_tors = o->restart_tors;
+    }
+    cudaEvent_t *tev = nullptr;
+    if (c->timing) {
+        if (c->tev_pending == lg_ctx::kTimingRing) harvest_timing(c);
+        tev = c->tev[c->tev_head];
+        c->tev_head = (c->tev_head + 1) % lg_ctx::kTimingRing;
+        c->tev_pending++;
+    }
+    if ((rc = dock_device(c, pk->dev, bd, od, p, nmax, rmax, c->scratch, s, &c->stats, tev))) return rc;
+    if (o->mem == LG_MEM_HOST) {
+        if ((rc = fetch_out(od, o, L, S, P, A, R, s))) return rc;
+    }
+    if (b->mem == LG_MEM_HOST || o->mem == LG_MEM_HOST) {
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return fail(LG_ECUDA, std::string("docking: ") + cudaGetErrorString(e));
+    } else {
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return fail(LG_ECUDA, std::string("docking: ") + cudaGetErrorString(e));
+    }
+    return LG_OK;
+}
+
+int lg_score_poses(lg_ctx *c, int32_t pid, const lg_pose_batch *b, double *E, void *stream) {
+    if (!c || !b || !E) return fail(LG_EINVAL, "null argument");
+    if (b->L < 0) return fail(LG_EINVAL, "L must be >= 0");
+    if (b->mem != LG_MEM_HOST && b->mem != LG_MEM_DEVICE) return fail(LG_EINVAL, "bad mem");
+    if (b->L == 0) return LG_OK;
+    if (!b->atom_off || !b->xyz || !b->q || !b->type) return fail(LG_EINVAL, "null pose array");
+    std::lock_guard<std::mutex> g(c->mu);
+    if (cudaSetDevice(c->device) != cudaSuccess) return fail(LG_ECUDA, "cudaSetDevice failed");
+    PocketRec *pk = (pid >= 0 && pid < (int)c->pockets.size() && c->pockets[pid].live) ? &c->pockets[pid] : nullptr;
+    if (!pk) return fail(LG_ENOPOCKET, "unknown pocket");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int L = b->L;
+    const int32_t *aoff = b->atom_off;
+    const float *xyz = b->xyz, *q = b->q;
+    const uint8_t *t = b->type;
+    double *dE = E;
+    cudaError_t e = cudaSuccess;
+    if (b->mem == LG_MEM_HOST) {
+        if (b->atom_off[0] != 0) return fail(LG_EINVAL, "atom_off[0] must be 0");
+        for (int l = 0; l < L; l++)
+            if (b->atom_off[l + 1] < b->atom_off[l]) return fail(LG_EINVAL, "atom_off must be non-decreasing");
+        const int64_t A = b->atom_off[L];
+        Carve cv;
+        const size_t o_a = cv.take(4 * (size_t)(L + 1)), o_x = cv.take(12 * (size_t)A), o_q = cv.take(4 * (size_t)A);
+        const size_t o_t = cv.take((size_t)A), o_e = cv.take(8 * (size_t)L);
+        if (c->in_buf.ensure(cv.off)) return fail(LG_ENOMEM, "staging allocation failed");
+        char *base = (char *)c->in_buf.p;
+        e = cudaMemcpyAsync(base + o_a, aoff, 4 * (size_t)(L + 1), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess && A) e = cudaMemcpyAsync(base + o_x, xyz, 12 * (size_t)A, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess && A) e = cudaMemcpyAsync(base + o_q, q, 4 * (size_t)A, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess && A) e = cudaMemcpyAsync(base + o_t, t, (size_t)A, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return fail(LG_ECUDA, std::string("pose upload: ") + cudaGetErrorString(e));
+        aoff = (const int32_t *)(base + o_a);
+        xyz = (const float *)(base + o_x);
+        q = (const float *)(base + o_q);
+        t = (const uint8_t *)(base + o_t);
+        dE = (double *)(base + o_e);
+    }
+    if ((e = launch_score_poses(pk->dev, L, aoff, xyz, q, t, dE, s)) != cudaSuccess)
+        return fail(LG_ECUDA, std::string("score launch: ") + cudaGetErrorString(e));
+    if (b->mem == LG_MEM_HOST) {
+        e = cudaMemcpyAsync(E, dE, 8 * (size_t)L, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return fail(LG_ECUDA, std::string("scoring: ") + cudaGetErrorString(e));
+    }
+    return LG_OK;
+}
+
+int lg_get_stats(lg_ctx *c, lg_stats *out) {
+    if (!c || !out) return fail(LG_EINVAL, "null argument");
+    std::lock_guard<std::mutex> g(c->mu);
+    cudaSetDevice(c->device);
+    harvest_timing(c);
+    *out = c->stats;
+    return LG_OK;
+}
+
+int lg_set_option(lg_ctx *c, const char *key, int64_t v) {
+    if (!c || !key) return fail(LG_EINVAL, "null argument");
+    std::lock_guard<std::mutex> g(c->mu);
+    if (!strcmp(key, "timing")) {
+        cudaSetDevice(c->device);
+        harvest_timing(c);
+        c->timing = v != 0;
+        c->stats.dock_calls = 0;
+        c->stats.dock_ms_total = 0.0;
+    } else if (!strcmp(key, "warps_per_cta")) {
+        if (v < 0 || v > 32) return fail(LG_EINVAL, "warps_per_cta must be in [0, 32]");
+        c->warps_opt = (int)v;
+    } else if (!strcmp(key, "serve_max_inflight")) {
+        if (v < 1 || v > 64) return fail(LG_EINVAL, "serve_max_inflight must be in [1, 64]");
+        c->serve_max_inflight = (int)v;
+    } else if (!strcmp(key, "serve_mem_reserve_mb")) {
+        if (v < 0) return fail(LG_EINVAL, "serve_mem_reserve_mb must be >= 0");
+        c->serve_reserve_mb = v;
+    } else {
+        return fail(LG_EINVAL, std::string("unknown option ") + key);
+    }
+    return LG_OK;
+}
+
+int lg_diag_philox(lg_ctx *c, int32_t n, const uint32_t *ctr, const uint32_t *key, uint32_t *out, int32_t use_curand) {
+    if (!c || n < 0 || (n > 0 && (!ctr || !key || !out))) return fail(LG_EINVAL, "bad argument");
+    if (n == 0) return LG_OK;
+    std::lock_guard<std::mutex> g(c->mu);
+    if (cudaSetDevice(c->device) != cudaSuccess) return fail(LG_ECUDA, "cudaSetDevice failed");
+    cudaError_t e = launch_diag_philox(n, ctr, key, out, use_curand, 0);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(0);
+    if (e != cudaSuccess) return fail(LG_ECUDA, std::string("philox: ") + cudaGetErrorString(e));
+    return LG_OK;
+}
+
+}  // extern "C"

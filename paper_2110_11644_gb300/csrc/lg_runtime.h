@@ -1,0 +1,88 @@
+// Context state of liblgdock (host side).  Internal; not part of the ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "lg_internal.h"
+
+namespace lg {
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t cap = 0;
+    int ensure(size_t n);  // grow-only; 0 on success
+    void release();
+};
+
+struct PocketRec {
+    bool live = false;
+    PocketDev dev{};
+    void *mem = nullptr;
+    size_t bytes = 0;
+};
+
+struct Server;  // lg_serve.cu
+
+int fail(int code, const std::string &msg);
+int check_params(const lg_dock_params *p);
+int host_batch_shape(const lg_ligand_batch *b, int64_t *A, int64_t *R, int *nmax, int *rmax);
+int stage_batch(DevBuf &buf, const lg_ligand_batch *b, int64_t A, int64_t R, BatchDev *d, cudaStream_t s);
+int stage_out(DevBuf &buf, const lg_dock_result *o, int L, int S, int P, int64_t A, int64_t R, OutDev *d);
+int fetch_out(const OutDev &d, const lg_dock_result *o, int L, int S, int P, int64_t A, int64_t R, cudaStream_t s);
+int dock_device(lg_ctx *ctx, const PocketDev &pk, const BatchDev &bd, const OutDev &od, const lg_dock_params *p,
+                int nmax, int rmax, DevBuf &scratch, cudaStream_t s, lg_stats *st, cudaEvent_t *tev);
+void harvest_timing(lg_ctx *c);
+void serve_stop(lg_ctx *c);
+
+}  // namespace lg
+
+struct lg_ctx {
+    int device = 0;
+    int num_sms = 0;
+    std::mutex mu;  // serialises the calls that use the context's own buffers
+    std::vector<lg::PocketRec> pockets;
+    lg::DevBuf in_buf, out_buf, scratch;
+    std::vector<cudaStream_t> plain_streams;
+    std::vector<cudaEvent_t> join_events;
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};  // plain-mode fork (others unused)
+    bool timing = false;
+    lg_stats stats{};
+    // timing ring: (start, end) event pairs of calls not yet harvested
+    static constexpr int kTimingRing = 64;
+    cudaEvent_t tev[kTimingRing][2] = {};
+    int tev_head = 0, tev_pending = 0;
+    int warps_opt = 0;
+    int serve_max_inflight = 8;
+    int64_t serve_reserve_mb = 1024;
+    std::mutex serve_mu;  // guards `server` creation
+    lg::Server *server = nullptr;
+};
+
+namespace lg {
+
+inline int ctx_num_sms(lg_ctx *c) { return c->num_sms; }
+inline int ctx_warps_opt(lg_ctx *c) { return c->warps_opt; }
+inline bool ctx_timing(lg_ctx *c) { return c->timing; }
+inline cudaEvent_t ctx_event(lg_ctx *c, int i) { return c->ev[i]; }
+inline std::vector<cudaStream_t> &ctx_streams(lg_ctx *c) { return c->plain_streams; }
+inline cudaEvent_t ctx_join_event(lg_ctx *c, int i) { return c->join_events[i]; }
+inline int ctx_plain_streams(lg_ctx *c, int n) {
+    while ((int)c->plain_streams.size() < n) {
+        cudaStream_t s;
+        cudaEvent_t e;
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return -1;
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+            cudaStreamDestroy(s);
+            return -1;
+        }
+        c->plain_streams.push_back(s);
+        c->join_events.push_back(e);
+    }
+    return 0;
+}
+
+}  // namespace lg

@@ -1,0 +1,218 @@
+"""GPU parity: the CUDA path through the C-ABI against the FP64 oracle."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2110_11644_gb300 import lg, synth
+
+from _parity import check
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    c = lg.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def pocket1(ctx, cfg1):
+    return ctx.load_pocket(cfg1[0])
+
+
+def _dock(ctx, pid, batch, params, **kw):
+    return ctx.dock(pid, batch, params, restart_score=True, restart_tors=True, **kw)
+
+
+# ----------------------------------------------------------------------------- primitives
+def test_philox_matches_oracle_and_curand(ctx):
+    import torch
+    n = 1 << 20
+    rng = np.random.default_rng(0)
+    ctr = rng.integers(0, 2 ** 32, size=(n, 4), dtype=np.uint64).astype(np.uint32)
+    key = rng.integers(0, 2 ** 32, size=(n, 2), dtype=np.uint64).astype(np.uint32)
+    dc = torch.from_numpy(ctr.view(np.int32)).cuda()
+    dk = torch.from_numpy(key.view(np.int32)).cuda()
+    out_own = torch.zeros(n * 4, dtype=torch.int32, device="cuda")
+    out_cur = torch.zeros(n * 4, dtype=torch.int32, device="cuda")
+    lg.lg_diag_philox(ctx.h, n, dc.data_ptr(), dk.data_ptr(), out_own.data_ptr(), 0)
+    lg.lg_diag_philox(ctx.h, n, dc.data_ptr(), dk.data_ptr(), out_cur.data_ptr(), 1)
+    a = out_own.cpu().numpy().view(np.uint32).reshape(n, 4)
+    b = out_cur.cpu().numpy().view(np.uint32).reshape(n, 4)
+    assert np.array_equal(a, b)
+    for i in rng.integers(0, n, size=2000):
+        assert np.array_equal(a[i], oracle.philox4x32_10(ctr[i], key[i]))
+
+
+def test_score_poses_matches_oracle(ctx, cfg1, pocket1):
+    pocket, batch, _ = cfg1
+    rng = np.random.default_rng(1)
+    lo, hi = pocket.origin - 3.0, pocket.origin + pocket.h * (pocket.n - 1) + 3.0
+    xyz = rng.uniform(lo, hi, size=(len(batch.x), 3)).astype(np.float32)
+    E_g = ctx.score_poses(pocket1, batch.atom_off, xyz, batch.q, batch.type)
+    E_o, Eabs = oracle.score_poses(pocket, batch.atom_off, xyz.astype(np.float64), batch.q, batch.type)
+    err = np.abs(E_g - E_o) / np.maximum(np.abs(E_o), Eabs)
+    assert err.max() <= 1e-5, err.max()
+
+
+def test_score_poses_at_nodes_equals_direct_sum(ctx, cfg1, pocket1):
+    pocket = cfg1[0]
+    rng = np.random.default_rng(2)
+    ijk = rng.integers(0, pocket.n, size=(500, 3))
+    xyz = pocket.node_xyz(ijk)
+    v, e = synth.direct_potentials(pocket, xyz)
+    q = rng.normal(0, 0.3, size=500).astype(np.float32)
+    t = rng.integers(0, 5, size=500).astype(np.uint8)
+    E_g = ctx.score_poses(pocket1, np.arange(501, dtype=np.int32), xyz.astype(np.float32), q, t)
+    want = pocket.type_w[t].astype(np.float64) * v + q * e
+    assert np.all(np.abs(E_g - want) <= 1e-5 * (np.abs(pocket.type_w[t] * v) + np.abs(q * e) + 1e-3))
+
+
+# ----------------------------------------------------------------------------- docking parity
+def test_dock_config1_matches_oracle(ctx, cfg1, pocket1):
+    pocket, batch, params = cfg1
+    gpu = _dock(ctx, pocket1, batch, params)
+    rep = {}
+    check(pocket, batch, params, gpu, rep)
+    print("config-1 parity:", rep)
+    assert rep["decisions"] > 1000
+    assert rep["deviations"] <= 0.01 * rep["decisions"]
+
+
+def test_plain_and_batched_forms_agree_bitwise(ctx, cfg1, pocket1):
+    _, batch, params = cfg1
+    sub = batch.subset(range(64))
+    a = _dock(ctx, pocket1, sub, params, mode=lg.LG_MODE_BATCHED)
+    b = _dock(ctx, pocket1, sub, params, mode=lg.LG_MODE_PLAIN, plain_streams=4)
+    for k in a:
+        assert np.array_equal(a[k], b[k]), k
+
+
+def test_host_and_device_io_agree_and_runs_repeat(ctx, cfg1, pocket1):
+    _, batch, params = cfg1
+    a = _dock(ctx, pocket1, batch, params)
+    b = _dock(ctx, pocket1, batch, params, device_io=True)
+    c = _dock(ctx, pocket1, batch, params)
+    for k in a:
+        assert np.array_equal(a[k], b[k]), k
+        assert np.array_equal(a[k], c[k]), k
+
+
+def test_result_independent_of_batch_mix(ctx, cfg1, pocket1):
+    _, batch, params = cfg1
+    full = _dock(ctx, pocket1, batch, params)
+    perm = np.random.default_rng(3).permutation(batch.L)[:77]
+    mixed = _dock(ctx, pocket1, batch.subset(perm), params)
+    assert np.array_equal(full["score"][perm], mixed["score"])
+    assert np.array_equal(full["best_restart"][perm], mixed["best_restart"])
+    alone = _dock(ctx, pocket1, batch.subset([int(perm[5])]), params)
+    assert alone["score"][0] == full["score"][perm[5]]
+
+
+def test_dock_config2_sample_matches_oracle(ctx, cfg2_pocket):
+    pid = ctx.load_pocket(cfg2_pocket)
+    params = synth.config_params(2)
+    batch = synth.config_ligands(2, 96)
+    gpu = _dock(ctx, pid, batch, params)
+    rep = {}
+    check(cfg2_pocket, batch, params, gpu, rep)
+    print("config-2 sample parity:", rep)
+    assert rep["deviations"] <= 0.01 * rep["decisions"]
+    ctx.unload_pocket(pid)
+
+
+def test_dock_heavy_tailed_sample_matches_oracle(ctx, cfg2_pocket):
+    pid = ctx.load_pocket(cfg2_pocket)
+    params = synth.config_params(3)
+    full = synth.config_ligands(3, 4000)
+    order = np.argsort(-full.n_atoms(), kind="stable")
+    idx = np.concatenate([order[:24], order[-24:], order[1000:1024]])   # largest, smallest, middle
+    batch = full.subset(idx)
+    gpu = _dock(ctx, pid, batch, params)
+    rep = {}
+    check(cfg2_pocket, batch, params, gpu, rep)
+    print("heavy-tailed sample parity:", rep)
+    ctx.unload_pocket(pid)
+
+
+# ----------------------------------------------------------------------------- edge cases
+def _one(N, parent, rot, uid=5, seed=11):
+    rng = np.random.default_rng(seed)
+    # a chain-like layout with ~1.5 A bonds so distances are realistic
+    pos = np.zeros((N, 3))
+    for i in range(1, N):
+        d = rng.normal(size=3); d /= np.linalg.norm(d)
+        pos[i] = pos[parent[i]] + 1.5 * d
+    return synth.LigandBatch(np.array([0, N], np.int32), pos[:, 0].astype(np.float32), pos[:, 1].astype(np.float32),
+                             pos[:, 2].astype(np.float32), rng.normal(0, 0.2, N).astype(np.float32),
+                             rng.integers(0, 5, N).astype(np.uint8), np.array(parent, np.int16),
+                             np.array([0, len(rot)], np.int32), np.array(rot, np.int16), np.array([uid], np.uint64))
+
+
+def test_edge_cases(ctx, cfg1, pocket1):
+    pocket, batch, params = cfg1
+    # empty batch
+    empty = batch.subset([])
+    out = ctx.dock(pocket1, empty, params)
+    assert len(out["score"]) == 0
+    # single atom, rigid ligand, S = 1, P = 0
+    single = _one(1, [-1], [])
+    p1 = synth.DockParams(restarts=1, passes=0, seed=params.seed)
+    g = _dock(ctx, pocket1, single, p1)
+    check(pocket, single, p1, g)
+    # invalid topology next to valid ligands: only it fails
+    bad = _one(4, [-1, 0, 0, 1], [])
+    mix = synth.LigandBatch.concat([batch.subset([0]), bad, batch.subset([1])])
+    g = ctx.dock(pocket1, mix, params)
+    assert list(g["status"]) == [0, lg.LG_EINVAL, 0]
+    assert np.isnan(g["score"][1]) and g["best_restart"][1] == -1
+    ref = ctx.dock(pocket1, batch.subset([0, 1]), params)
+    assert np.array_equal(g["score"][[0, 2]], ref["score"])
+    # non-ascending torsion list is rejected
+    nonasc = _one(6, [-1, 0, 1, 2, 3, 4], [3, 2])
+    assert ctx.dock(pocket1, nonasc, params)["status"][0] == lg.LG_EINVAL
+
+
+def test_maximum_sizes(ctx, cfg1, pocket1):
+    pocket, _, params = cfg1
+    big = synth.make_ligands(123, np.array([lg.LG_MAX_ATOMS, 100, 2]), np.array([lg.LG_MAX_ROT, 20, 0]))
+    assert big.n_rot()[0] >= 20
+    p = synth.DockParams(restarts=3, passes=2, seed=params.seed)
+    g = _dock(ctx, pocket1, big, p)
+    check(pocket, big, p, g)
+    # the plain form takes at most 32 warps; more restarts tile over them
+    p40 = synth.DockParams(restarts=40, passes=1, seed=params.seed)
+    sub = big.subset([1, 2])
+    a = _dock(ctx, pocket1, sub, p40, mode=lg.LG_MODE_PLAIN)
+    b = _dock(ctx, pocket1, sub, p40)
+    for k in a:
+        assert np.array_equal(a[k], b[k]), k
+    check(pocket, sub, p40, b)
+
+
+def test_declared_maxima_reject_larger_ligands(ctx, cfg1, pocket1):
+    _, batch, params = cfg1
+    n = batch.n_atoms()
+    g = ctx.dock(pocket1, batch.subset(range(40)), params, max_atoms=20)
+    want = np.where(n[:40] <= 20, 0, lg.LG_EINVAL)
+    assert np.array_equal(g["status"], want)
+    ref = ctx.dock(pocket1, batch.subset(range(40)), params)
+    ok = want == 0
+    assert np.array_equal(g["score"][ok], ref["score"][ok])
+
+
+def test_bad_arguments_raise(ctx, cfg1, pocket1):
+    _, batch, params = cfg1
+    with pytest.raises(lg.LgError) as e:
+        ctx.dock(pocket1 + 99, batch.subset([0]), params)
+    assert e.value.code == lg.LG_ENOPOCKET
+    with pytest.raises(lg.LgError) as e:
+        ctx.dock(pocket1, batch.subset([0]), synth.DockParams(restarts=0, passes=1))
+    assert e.value.code == lg.LG_EINVAL
