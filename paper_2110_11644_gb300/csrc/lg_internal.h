@@ -1,5 +1,5 @@
-// Internal declarations shared by the runtime (lg_runtime.cu) and the kernels
-// (lg_kernels.cu).  Not part of the public ABI (include/lg.h).
+// Internal declarations shared by the runtime (lg_runtime.cu, lg_serve.cu) and
+// the kernels (lg_kernels.cu).  Not part of the public ABI (include/lg.h).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -9,12 +9,15 @@
 
 namespace lg {
 
-// Device view of a loaded pocket.  Positions inside the kernels live in a
-// frame centred on the grid box ("centred frame", A): x_c = x_world - center.
-// Grid index space: g = x_c * inv_h + c0, with c0 = (n-1)/2, so node (i,j,k)
-// sits at g = (i,j,k).
+// Device view of a loaded pocket.
 //
-// Cells: for every node (i,j,k), i,j,k in [0, n-1], the 8 coefficients of the
+// Frames.  Kernels keep positions in "centred grid units": x_g = (x_world -
+// center) / h, with center the middle of the grid box, so |x_g| <= (n-1)/2 for
+// atoms inside the box.  The grid index of a position is x_g + c0, c0 = (n-1)/2:
+// node (i,j,k) sits at index (i,j,k).  Rotations commute with the uniform
+// scaling, distances are compared in grid units (d_clash^2 / h^2).
+//
+// Cells.  For every node (i,j,k), i,j,k in [0, n-1], the 8 coefficients of the
 // trilinear polynomial through the values at (i+a, j+b, k+c), a,b,c in {0,1}
 // (indices clamped to n-1, so the last layer repeats the edge):
 //   p(fx,fy,fz) = c0 + c1 fx + c2 fy + c3 fz + c4 fx fy + c5 fx fz + c6 fy fz + c7 fx fy fz
@@ -26,7 +29,7 @@ struct PocketDev {
     float3 center;             // world position of the box centre
     const float4 *cell_o;      // 2 float4 per node
     const float4 *cell_ve;     // 4 float4 per node
-    const float4 *pp;          // pocket points in the centred frame (x, y, z, 0)
+    const float4 *pp;          // pocket points in centred grid units (x, y, z, 0)
     int n_pp;
     float type_w[LG_NUM_TYPES];
     float k_out;
@@ -58,7 +61,7 @@ struct OutDev {
 struct Layout {
     int nmax, rmax, P, W, want_pose;
     // CTA part (byte offsets from the start of dynamic shared memory)
-    int o_dv, o_wE, o_d0, o_wq, o_par, o_rch, o_rend, o_wR, o_scal, cta_bytes;
+    int o_dv, o_wE, o_d0, o_wq, o_par, o_rch, o_rend, o_wR, cta_bytes;
     // warp part (byte offsets from the warp's base)
     int o_bundle, o_axis, o_X, o_best, o_tcur, o_tbest, warp_bytes;
     int total;
@@ -72,19 +75,17 @@ __host__ __device__ inline Layout make_layout(int nmax, int rmax, int P, int W, 
     if (rmax < 1) rmax = 1;
     L.nmax = nmax; L.rmax = rmax; L.P = P; L.W = W; L.want_pose = want_pose;
     int o = 0;
-    L.o_dv = o;   o = lg_align16(o + 16 * rmax);           // float4 bond vectors
+    L.o_dv = o;   o = lg_align16(o + 16 * rmax);           // float4 bond vectors (grid units)
     L.o_wE = o;   o = lg_align16(o + 8 * W);               // double per warp
-    L.o_d0 = o;   o = lg_align16(o + 12 * nmax);           // float x3 SoA
+    L.o_d0 = o;   o = lg_align16(o + 12 * nmax);           // float x3 SoA, centroid-relative (grid units)
     L.o_wq = o;   o = lg_align16(o + 8 * nmax);            // float2 (type weight, charge)
     L.o_par = o;  o = lg_align16(o + 4 * nmax);            // int parent
-    L.o_rch = o;  o = lg_align16(o + 4 * rmax);            // int rotatable child
-    L.o_rend = o; o = lg_align16(o + 4 * rmax);            // int subtree end of child
+    L.o_rch = o;  o = lg_align16(o + 4 * rmax);            // int torsional child
+    L.o_rend = o; o = lg_align16(o + 4 * rmax);            // int end of the child's subtree
     L.o_wR = o;   o = lg_align16(o + 4 * W);               // int per warp
-    L.o_scal = o; o = lg_align16(o + 32);                  // N, R, status, centroid (3 doubles follow)
-    o = lg_align16(o + 32);
     L.cta_bytes = o;
     int w = 0;
-    L.o_bundle = w; w = lg_align16(w + 32 * 48);           // 32 atoms x 3 float4 (aliased by T)
+    L.o_bundle = w; w = lg_align16(w + 32 * 64);           // 32 atoms x 4 float4 circle parameters
     L.o_axis = w;   w = lg_align16(w + 16 * rmax);         // float4 current bond axes
     L.o_X = w;      w = lg_align16(w + 12 * nmax);         // float x3 SoA positions
     L.o_best = w;   w = lg_align16(w + (want_pose ? 12 * nmax : 0));
@@ -95,32 +96,45 @@ __host__ __device__ inline Layout make_layout(int nmax, int rmax, int P, int W, 
     return L;
 }
 
+// Per-launch scratch (device memory beyond the inputs and outputs).
+struct Scratch {
+    int32_t *hist;         // kSortBuckets counters, then the work counter
+    int32_t *keys;         // [L] cost bucket
+    int32_t *order;        // [L] visiting order
+    double *centroid;      // [3L]
+    int16_t *rot_end;      // [L * rmax_lim] end of each torsional child's subtree
+};
+
 struct DockArgs {
     PocketDev pocket;
     BatchDev batch;
     OutDev out;
     Layout ly;
+    Scratch scr;
     int S, P;
     uint32_t seed_lo, seed_hi;
-    float dc2;  // d_clash^2
-    int nmax_decl, rmax_decl;  // declared per-ligand maxima (ligands above them are rejected)
+    float dc2g;                // d_clash^2 in grid units
+    int nmax_lim, rmax_lim;    // per-ligand maxima (declared and within the layout)
     const int32_t *order;      // batched mode: ligand visiting order (NULL = identity)
     int32_t *work_counter;     // batched mode: next item of the persistent loop
 };
 
+constexpr int kSortBuckets = 128;
+
+// Byte size of the scratch of a launch, and its carving.
+size_t scratch_bytes(int L, int rmax);
+Scratch carve_scratch(void *base, int L, int rmax);
+
 // Launchers (lg_kernels.cu)
 void set_angle_tables(const float *cosv, const float *sinv);
+cudaError_t launch_prep(const DockArgs &a, bool sort, cudaStream_t s, int *launches);
 cudaError_t launch_dock_plain(const DockArgs &a, int ligand, cudaStream_t s);
 cudaError_t launch_dock_batched(const DockArgs &a, int grid, cudaStream_t s);
-cudaError_t launch_sort(const DockArgs &a, int32_t *keys, int32_t *hist, int32_t *order, cudaStream_t s,
-                        int *launches);
 cudaError_t launch_score_poses(const PocketDev &p, int L, const int32_t *atom_off, const float *xyz,
                                const float *q, const uint8_t *type, double *E, cudaStream_t s);
 cudaError_t launch_diag_philox(int n, const uint32_t *ctr, const uint32_t *key, uint32_t *out, int use_curand,
                                cudaStream_t s);
 cudaError_t dock_kernel_attributes(int W, int smem, int *ctas_per_sm);
 cudaError_t plain_kernel_attributes(int smem);
-
-constexpr int kSortBuckets = 128;
 
 }  // namespace lg

@@ -1,21 +1,29 @@
 // Docking kernels for sm_103a (GB300).
 //
-// The dock-and-score step of the paper (Sec. 3.1) on the GPU: one CTA docks
-// one ligand, its warps share the ligand's topology in shared memory and each
+// The dock-and-score step of the paper (Sec. 3.1) on the GPU.  One CTA docks
+// one ligand: its warps share the ligand's topology in shared memory and each
 // warp runs one restart at a time (restarts are tiled over the CTA's warps).
-// Inside a warp the 36 torsion steps of a bond map onto lanes: lane t scores
-// step t for every moving atom (steps 32..35 are spread over the warp in a
-// short tail loop), so the per-step overlap sums need no cross-lane reduction
-// and the choice of step is a 5-level shuffle argmax.  Moving atoms are
-// processed in bundles of 32 (the paper's CUDA design also works in bundles
-// of 32 atoms, Sec. 3.1): each lane builds the circle that one atom traces
-// about the bond axis, x(theta) = p + e1 cos(theta) + e2 sin(theta), and every
-// lane then evaluates its own step on that circle with two FMAs per
-// coordinate.  Grids are read as one 32-byte cell of trilinear coefficients
-// per lookup through the read-only path and stay resident in L2.
-// The batched form is a persistent kernel that visits ligands in descending
-// estimated cost (a counting sort on the device), the plain form launches one
-// CTA per ligand with one warp per restart.
+//
+// Inside a warp the 36 torsion steps of a bond map onto lanes: lane t owns
+// step t (steps 32..35 are spread over the warp in a short tail loop), so the
+// per-step overlap sums need no cross-lane reduction and the choice of step is
+// a 5-level shuffle argmax.  Moving atoms are processed in bundles of 32 (the
+// paper's CUDA design also works in bundles of 32 atoms, Sec. 3.1): each lane
+// builds the circle one atom traces about the bond axis,
+//     x(theta) = p + e1 cos(theta) + e2 sin(theta),
+// and every lane evaluates its own step on that circle with two FMAs per
+// coordinate, then reads one 32-byte cell of trilinear coefficients of the
+// overlap grid (L2-resident, read-only path).
+//
+// The clash test uses the same circles: for a moving atom i and a fixed atom j
+//     |x_i(theta) - x_j|^2 = C + 2a cos(theta) + 2b sin(theta),
+//     C = |p - x_j|^2 + |e1|^2,  a = (p - x_j).e1,  b = (p - x_j).e2,
+// whose minimum over the circle is C - 2 sqrt(a^2 + b^2).  Pairs whose minimum
+// stays above d_clash^2 can never clash and are dropped with one test; the few
+// others are evaluated for all 36 steps at once (lanes = steps), so every
+// decision gets its full admissibility mask in one pass.
+//
+// Positions live in centred grid units (see lg_internal.h).
 #include <curand_philox4x32_x.h>
 
 #include "lg_internal.h"
@@ -50,19 +58,20 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
 }
 
 // ------------------------------------------------------------------ grid lookups
-// Cell of an index-space point already clamped to [0, n-1]: floor by adding
-// 1.5*2^23 with round-down (the integer part lands in the low mantissa bits),
-// exact fractions, and the flat node index (k*n + j)*n + i.
-__device__ __forceinline__ uint32_t cell_of(float gx, float gy, float gz, int n, float &fx, float &fy, float &fz) {
-    const float M = 12582912.0f;  // 0x4B400000
-    const float tx = __fadd_rd(gx, M), ty = __fadd_rd(gy, M), tz = __fadd_rd(gz, M);
-    fx = gx - (tx - M);
-    fy = gy - (ty - M);
-    fz = gz - (tz - M);
-    const uint32_t ix = __float_as_uint(tx) - 0x4B400000u;
-    const uint32_t iy = __float_as_uint(ty) - 0x4B400000u;
-    const uint32_t iz = __float_as_uint(tz) - 0x4B400000u;
-    return (iz * (uint32_t)n + iy) * (uint32_t)n + ix;
+// Floor of an index-space coordinate in [0, 2^22) by adding 1.5*2^23 with
+// round-down: the integer part lands in the low mantissa bits of t and
+// t - 1.5*2^23 is exact, as is the fraction g - floor(g).
+constexpr float kMagic = 12582912.0f;  // bit pattern 0x4B400000
+
+__device__ __forceinline__ float floor_frac(float g, float &t) {
+    t = __fadd_rd(g, kMagic);
+    return g - (t - kMagic);
+}
+
+// Flat cell index (k*n + j)*n + i from the three round-down sums (32-bit
+// wrap-around arithmetic; the true result is small and non-negative).
+__device__ __forceinline__ uint32_t cell_index(float tx, float ty, float tz, uint32_t n, uint32_t n2, uint32_t moff) {
+    return __float_as_uint(tz) * n2 + __float_as_uint(ty) * n + __float_as_uint(tx) - moff;
 }
 
 // Trilinear polynomial of one cell: lo = (c0, c1, c2, c3), hi = (c4, c5, c6, c7).
@@ -78,30 +87,48 @@ __device__ __forceinline__ float cell_eval(const float4 lo, const float4 hi, flo
 
 __device__ __forceinline__ float clampg(float g, float gmax) { return fminf(fmaxf(g, 0.0f), gmax); }
 
-// Overlap-field value at index-space point g (clamped to the box).
-__device__ __forceinline__ float lookup_o(const float4 *__restrict__ cells, float gx, float gy, float gz, int n,
-                                          float gmax) {
-    gx = clampg(gx, gmax);
-    gy = clampg(gy, gmax);
-    gz = clampg(gz, gmax);
-    float fx, fy, fz;
-    const uint32_t c = cell_of(gx, gy, gz, n, fx, fy, fz);
-    const float4 *p = cells + 2 * (size_t)c;
+struct GridK {  // lookup constants of a pocket
+    const float4 *cells;
+    uint32_t n, n2, moff;
+    float gmax;
+};
+
+__device__ __forceinline__ GridK grid_k(const PocketDev &P, const float4 *cells) {
+    GridK g;
+    g.cells = cells;
+    g.n = (uint32_t)P.n;
+    g.n2 = g.n * g.n;
+    g.moff = 0x4B400000u * (g.n2 + g.n + 1u);
+    g.gmax = P.gmax;
+    return g;
+}
+
+// Overlap-field value at an index-space point known to lie in [0, n-1]^3.
+__device__ __forceinline__ float lookup_in(const GridK &G, float gx, float gy, float gz) {
+    float tx, ty, tz;
+    const float fx = floor_frac(gx, tx), fy = floor_frac(gy, ty), fz = floor_frac(gz, tz);
+    const float4 *p = G.cells + 2 * (size_t)cell_index(tx, ty, tz, G.n, G.n2, G.moff);
     const float4 lo = __ldg(p), hi = __ldg(p + 1);
     return cell_eval(lo, hi, fx, fy, fz);
 }
 
-// Per-atom energy term at a centred-frame position: type weight * vdW grid +
-// charge * electrostatic grid at the clamped position, plus k_out times the
-// distance outside the box.
-__device__ __forceinline__ float atom_energy(const PocketDev &P, float x, float y, float z, float w, float q) {
-    const float gx = fmaf(x, P.inv_h, P.c0), gy = fmaf(y, P.inv_h, P.c0), gz = fmaf(z, P.inv_h, P.c0);
+// Overlap-field value at any index-space point (clamped to the box).
+__device__ __forceinline__ float lookup_clamped(const GridK &G, float gx, float gy, float gz) {
+    return lookup_in(G, clampg(gx, G.gmax), clampg(gy, G.gmax), clampg(gz, G.gmax));
+}
+
+// Per-atom energy term at a centred-grid-unit position: type weight * vdW grid
+// + charge * electrostatic grid at the clamped position, plus k_out times the
+// distance (A) outside the box.
+__device__ __forceinline__ float atom_energy(const PocketDev &P, const GridK &G, float x, float y, float z, float w,
+                                             float q) {
+    const float gx = x + P.c0, gy = y + P.c0, gz = z + P.c0;
     const float cx = clampg(gx, P.gmax), cy = clampg(gy, P.gmax), cz = clampg(gz, P.gmax);
     const float dx = gx - cx, dy = gy - cy, dz = gz - cz;
     const float out = P.h * sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
-    float fx, fy, fz;
-    const uint32_t c = cell_of(cx, cy, cz, P.n, fx, fy, fz);
-    const float4 *p = P.cell_ve + 4 * (size_t)c;
+    float tx, ty, tz;
+    const float fx = floor_frac(cx, tx), fy = floor_frac(cy, ty), fz = floor_frac(cz, tz);
+    const float4 *p = G.cells + 4 * (size_t)cell_index(tx, ty, tz, G.n, G.n2, G.moff);
     const float v = cell_eval(__ldg(p), __ldg(p + 1), fx, fy, fz);
     const float e = cell_eval(__ldg(p + 2), __ldg(p + 3), fx, fy, fz);
     return fmaf(w, v, fmaf(q, e, P.k_out * out));
@@ -119,12 +146,11 @@ struct CtaView {
     double *wE;
     float *d0x, *d0y, *d0z;
     float2 *wq;
-    int *par, *rch, *rend, *wR, *scal;
-    double *cen;
+    int *par, *rch, *rend, *wR;
 };
 
 struct WarpView {
-    float4 *bundle;  // 32 x 3 float4; also holds T (rotated moving atoms, SoA, 3 x 128 floats)
+    float4 *bundle;  // 32 atoms x 4 float4 (see sweep_bond)
     float4 *axis;
     float *Xx, *Xy, *Xz;
     float *Bx, *By, *Bz;
@@ -143,8 +169,6 @@ __device__ __forceinline__ CtaView cta_view(char *sm, const Layout &L) {
     v.rch = (int *)(sm + L.o_rch);
     v.rend = (int *)(sm + L.o_rend);
     v.wR = (int *)(sm + L.o_wR);
-    v.scal = (int *)(sm + L.o_scal);
-    v.cen = (double *)(sm + L.o_scal + 32);
     return v;
 }
 
@@ -165,11 +189,17 @@ __device__ __forceinline__ WarpView warp_view(char *sm, const Layout &L, int w) 
 }
 
 // ------------------------------------------------------------------ one torsion decision
-// Sweeps bond k of the current pose held by this warp and applies the chosen
-// step.  Returns the chosen step (0..35).
-__device__ int sweep_bond(const DockArgs &A, const CtaView &cv, const WarpView &wv, int N, int R, int k, int lane,
-                          float cl, float sl, float ct, float st) {
-    const PocketDev &P = A.pocket;
+// Sweeps torsional bond k of the pose held by this warp, applies the chosen
+// step and returns it (0..35).  lane owns step `lane` (cos cl, sin sl) and, in
+// the tail, step 32 + (lane & 3) (cos ct, sin st).
+//
+// Bundle entry of a moving atom (index space = centred grid units + c0):
+//   q0 = (P.x, P.y, P.z, e1.x)      P = circle centre in index space
+//   q1 = (e1.y, e1.z, e2.x, e2.y)
+//   q2 = (e2.z, |e1|^2, inside, 0)  inside = 1 when the whole circle is in the box
+//   q3 = (p.x, p.y, p.z, 0)         p = circle centre in centred grid units
+__device__ int sweep_bond(const DockArgs &A, const GridK &G, const CtaView &cv, const WarpView &wv, int N, int R,
+                          int k, int lane, float cl, float sl, float ct, float st) {
     const int b = cv.rch[k], a = cv.par[b], e = cv.rend[k];
     const int m = e - b - 1;
     if (m <= 0) return 0;  // nothing moves: every step scores 0, step 0 wins
@@ -178,9 +208,12 @@ __device__ int sweep_bond(const DockArgs &A, const CtaView &cv, const WarpView &
     const float4 ax = wv.axis[k];
     const float inv = rnorm3df(ax.x, ax.y, ax.z);
     const float ux = ax.x * inv, uy = ax.y * inv, uz = ax.z * inv;
-    const float ih = P.inv_h, c0 = P.c0;
+    const float c0 = A.pocket.c0, lim = G.gmax - 1e-3f;
+    const float dc2 = A.dc2g;
+    const int nF = N - (e - b);  // atoms outside subtree(b): [0, b) and [e, N)
 
     float acc = 0.0f, acc_t = 0.0f;
+    bool clash_lo = false, clash_hi = false;
     for (int base = b + 1; base < e; base += 32) {
         const int cnt = min(32, e - base);
         if (lane < cnt) {
@@ -190,221 +223,155 @@ __device__ int sweep_bond(const DockArgs &A, const CtaView &cv, const WarpView &
             const float px = fmaf(w, ux, xbx), py = fmaf(w, uy, xby), pz = fmaf(w, uz, xbz);
             const float e1x = fmaf(-w, ux, dx), e1y = fmaf(-w, uy, dy), e1z = fmaf(-w, uz, dz);
             const float e2x = fmaf(uy, dz, -uz * dy), e2y = fmaf(uz, dx, -ux * dz), e2z = fmaf(ux, dy, -uy * dx);
-            wv.bundle[3 * lane + 0] = make_float4(fmaf(px, ih, c0), fmaf(py, ih, c0), fmaf(pz, ih, c0), e1x * ih);
-            wv.bundle[3 * lane + 1] = make_float4(e1y * ih, e1z * ih, e2x * ih, e2y * ih);
-            wv.bundle[3 * lane + 2] = make_float4(e2z * ih, 0.0f, 0.0f, 0.0f);
+            const float Px = px + c0, Py = py + c0, Pz = pz + c0;
+            const float rx = fabsf(e1x) + fabsf(e2x), ry = fabsf(e1y) + fabsf(e2y), rz = fabsf(e1z) + fabsf(e2z);
+            const bool inside = Px - rx >= 1e-3f && Px + rx <= lim && Py - ry >= 1e-3f && Py + ry <= lim &&
+                                Pz - rz >= 1e-3f && Pz + rz <= lim;
+            float4 *q = wv.bundle + 4 * lane;
+            q[0] = make_float4(Px, Py, Pz, e1x);
+            q[1] = make_float4(e1y, e1z, e2x, e2y);
+            q[2] = make_float4(e2z, fmaf(e1x, e1x, fmaf(e1y, e1y, e1z * e1z)), inside ? 1.0f : 0.0f, 0.0f);
+            q[3] = make_float4(px, py, pz, 0.0f);
         }
         __syncwarp();
         // steps 0..31: lane t scores step t for every atom of the bundle
-#pragma unroll 2
+#pragma unroll 4
         for (int t = 0; t < cnt; ++t) {
-            const float4 q0 = wv.bundle[3 * t], q1 = wv.bundle[3 * t + 1], q2 = wv.bundle[3 * t + 2];
+            const float4 q0 = wv.bundle[4 * t], q1 = wv.bundle[4 * t + 1], q2 = wv.bundle[4 * t + 2];
             const float gx = fmaf(q1.z, sl, fmaf(q0.w, cl, q0.x));
             const float gy = fmaf(q1.w, sl, fmaf(q1.x, cl, q0.y));
             const float gz = fmaf(q2.x, sl, fmaf(q1.y, cl, q0.z));
-            acc += lookup_o(P.cell_o, gx, gy, gz, P.n, P.gmax);
+            acc += (q2.z != 0.0f) ? lookup_in(G, gx, gy, gz) : lookup_clamped(G, gx, gy, gz);
         }
         // steps 32..35: lane scores step 32 + (lane & 3) for atoms lane>>2, +8, ...
         for (int t = lane >> 2; t < cnt; t += 8) {
-            const float4 q0 = wv.bundle[3 * t], q1 = wv.bundle[3 * t + 1], q2 = wv.bundle[3 * t + 2];
+            const float4 q0 = wv.bundle[4 * t], q1 = wv.bundle[4 * t + 1], q2 = wv.bundle[4 * t + 2];
             const float gx = fmaf(q1.z, st, fmaf(q0.w, ct, q0.x));
             const float gy = fmaf(q1.w, st, fmaf(q1.x, ct, q0.y));
             const float gz = fmaf(q2.x, st, fmaf(q1.y, ct, q0.z));
-            acc_t += lookup_o(P.cell_o, gx, gy, gz, P.n, P.gmax);
+            acc_t += lookup_clamped(G, gx, gy, gz);
+        }
+        // clash pairs (bundle atom ti, fixed atom jj), flattened over the warp
+        const int npairs = cnt * nF;
+        int ti = lane / nF, jj = lane - (lane / nF) * nF;
+        for (int pb = 0; pb < npairs; pb += 32) {
+            bool flag = false;
+            float C = 0.0f, A2 = 0.0f, B2 = 0.0f;
+            if (pb + lane < npairs) {
+                const int j = jj < b ? jj : jj + (e - b);
+                const float4 *q = wv.bundle + 4 * ti;
+                const float4 q0 = q[0], q1 = q[1], q2 = q[2], q3 = q[3];
+                const float wx = q3.x - wv.Xx[j], wy = q3.y - wv.Xy[j], wz = q3.z - wv.Xz[j];
+                const float aa = fmaf(wx, q0.w, fmaf(wy, q1.x, wz * q1.y));
+                const float bb = fmaf(wx, q1.z, fmaf(wy, q1.w, wz * q2.x));
+                C = fmaf(wx, wx, fmaf(wy, wy, fmaf(wz, wz, q2.y)));
+                const float T = C - dc2;
+                const float s2 = fmaf(aa, aa, bb * bb);
+                // the circle comes within d_clash of j iff T < 2 sqrt(a^2 + b^2)
+                flag = (T <= 0.0f || T * T < 4.0004f * s2) && !(j == a && cv.par[base + ti] == b);
+                A2 = 2.0f * aa;
+                B2 = 2.0f * bb;
+            }
+            unsigned msk = __ballot_sync(LG_FULL, flag);
+            while (msk) {
+                const int src = __ffs(msk) - 1;
+                msk &= msk - 1;
+                const float Cs = __shfl_sync(LG_FULL, C, src);
+                const float As = __shfl_sync(LG_FULL, A2, src);
+                const float Bs = __shfl_sync(LG_FULL, B2, src);
+                clash_lo |= fmaf(Bs, sl, fmaf(As, cl, Cs)) < dc2;
+                clash_hi |= fmaf(Bs, st, fmaf(As, ct, Cs)) < dc2;
+            }
+            jj += 32;
+            while (jj >= nF) {
+                jj -= nF;
+                ++ti;
+            }
         }
         __syncwarp();
     }
     acc_t += __shfl_xor_sync(LG_FULL, acc_t, 4);
     acc_t += __shfl_xor_sync(LG_FULL, acc_t, 8);
     acc_t += __shfl_xor_sync(LG_FULL, acc_t, 16);
+    if (lane == 0) clash_lo = false;  // step 0 (the current pose) is always admissible
 
-    // Highest-scoring admissible step, lowest step on ties.  Candidates are
-    // tried in that order; step 0 (the current pose) is always admissible.
-    float *Tx = (float *)wv.bundle;  // rotated moving atoms (SoA, up to 128 each)
-    float *Ty = Tx + LG_MAX_ATOMS, *Tz = Ty + LG_MAX_ATOMS;
-    const int nF = N - (e - b);  // atoms outside subtree(b)
-    int removed = 0;             // bit 0: step lane, bit 1: step 32 + lane (lanes 0..3)
-    int chosen = 0;
-    for (;;) {
-        float bs = (removed & 1) ? -INFINITY : acc;
-        int ba = (removed & 1) ? 1024 : lane;
-        if (lane < 4 && !(removed & 2) && acc_t > bs) {  // equal scores keep the lower step (lane < 32 + lane)
-            bs = acc_t;
-            ba = 32 + lane;
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const float os = __shfl_xor_sync(LG_FULL, bs, o);
-            const int oa = __shfl_xor_sync(LG_FULL, ba, o);
-            if (os > bs || (os == bs && oa < ba)) {
-                bs = os;
-                ba = oa;
-            }
-        }
-        // every lane holds the same winner; take lane 0's so control flow stays
-        // warp-uniform whatever the scores are
-        const int t = __shfl_sync(LG_FULL, ba, 0);
-        if (t <= 0 || t >= LG_ANGLE_STEPS) break;  // step 0 is admissible by definition
-        // rotated positions of the moving atoms for step t
-        const float c = c_cos[t], s = c_sin[t];
-        for (int i = b + 1 + lane; i < e; i += 32) {
-            const float dx = wv.Xx[i] - xbx, dy = wv.Xy[i] - xby, dz = wv.Xz[i] - xbz;
-            const float w = fmaf(ux, dx, fmaf(uy, dy, uz * dz));
-            const float e1x = fmaf(-w, ux, dx), e1y = fmaf(-w, uy, dy), e1z = fmaf(-w, uz, dz);
-            const float e2x = fmaf(uy, dz, -uz * dy), e2y = fmaf(uz, dx, -ux * dz), e2z = fmaf(ux, dy, -uy * dx);
-            const int ii = i - b - 1;
-            Tx[ii] = fmaf(e2x, s, fmaf(e1x, c, fmaf(w, ux, xbx)));
-            Ty[ii] = fmaf(e2y, s, fmaf(e1y, c, fmaf(w, uy, xby)));
-            Tz[ii] = fmaf(e2z, s, fmaf(e1z, c, fmaf(w, uz, xbz)));
-        }
-        __syncwarp();
-        bool clash = false;
-        for (int ii = 0; ii < m; ++ii) {
-            const int i = b + 1 + ii;
-            const float tx = Tx[ii], ty = Ty[ii], tz = Tz[ii];
-            const bool child_of_b = (cv.par[i] == b);
-            bool cl_l = false;
-            for (int jj = lane; jj < nF; jj += 32) {
-                const int j = jj < b ? jj : jj + (e - b);
-                if (child_of_b && j == a) continue;  // two bonds apart through the bond itself
-                const float dx = tx - wv.Xx[j], dy = ty - wv.Xy[j], dz = tz - wv.Xz[j];
-                cl_l |= fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < A.dc2;
-            }
-            if (__any_sync(LG_FULL, cl_l)) {
-                clash = true;
-                break;
-            }
-        }
-        if (!clash) {
-            chosen = t;
-            break;
-        }
-        if (t < 32) {
-            if (lane == t) removed |= 1;
-        } else if (lane == t - 32) {
-            removed |= 2;
-        }
-        __syncwarp();
+    // highest-scoring admissible step, lowest step on ties
+    float bs = clash_lo ? -INFINITY : acc;
+    int ba = clash_lo ? 1024 : lane;
+    if (lane < 4 && !clash_hi && acc_t > bs) {  // equal scores keep the lower step (lane < 32 + lane)
+        bs = acc_t;
+        ba = 32 + lane;
     }
-
-    if (chosen != 0) {
-        for (int i = b + 1 + lane; i < e; i += 32) {
-            const int ii = i - b - 1;
-            wv.Xx[i] = Tx[ii];
-            wv.Xy[i] = Ty[ii];
-            wv.Xz[i] = Tz[ii];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float os = __shfl_xor_sync(LG_FULL, bs, o);
+        const int oa = __shfl_xor_sync(LG_FULL, ba, o);
+        if (os > bs || (os == bs && oa < ba)) {
+            bs = os;
+            ba = oa;
         }
-        // bond axes further down the subtree turn with it
-        const float c = c_cos[chosen], s = c_sin[chosen];
-        for (int kk = k + 1 + lane; kk < R; kk += 32) {
-            if (cv.rch[kk] < e) {
-                const float4 v = wv.axis[kk];
-                const float uv = fmaf(ux, v.x, fmaf(uy, v.y, uz * v.z));
-                const float cx = fmaf(uy, v.z, -uz * v.y), cy = fmaf(uz, v.x, -ux * v.z), cz = fmaf(ux, v.y, -uy * v.x);
-                const float k1 = uv * (1.0f - c);
-                wv.axis[kk] = make_float4(fmaf(cx, s, fmaf(v.x, c, k1 * ux)), fmaf(cy, s, fmaf(v.y, c, k1 * uy)),
-                                          fmaf(cz, s, fmaf(v.z, c, k1 * uz)), 0.0f);
-            }
+    }
+    // every lane holds the same winner; take lane 0's so control flow stays
+    // warp-uniform whatever the scores are
+    const int t = __shfl_sync(LG_FULL, ba, 0);
+    if (t <= 0 || t >= LG_ANGLE_STEPS) return 0;
+
+    const float c = c_cos[t], s = c_sin[t];
+    for (int i = b + 1 + lane; i < e; i += 32) {
+        const float dx = wv.Xx[i] - xbx, dy = wv.Xy[i] - xby, dz = wv.Xz[i] - xbz;
+        const float w = fmaf(ux, dx, fmaf(uy, dy, uz * dz));
+        const float e1x = fmaf(-w, ux, dx), e1y = fmaf(-w, uy, dy), e1z = fmaf(-w, uz, dz);
+        const float e2x = fmaf(uy, dz, -uz * dy), e2y = fmaf(uz, dx, -ux * dz), e2z = fmaf(ux, dy, -uy * dx);
+        wv.Xx[i] = fmaf(e2x, s, fmaf(e1x, c, fmaf(w, ux, xbx)));
+        wv.Xy[i] = fmaf(e2y, s, fmaf(e1y, c, fmaf(w, uy, xby)));
+        wv.Xz[i] = fmaf(e2z, s, fmaf(e1z, c, fmaf(w, uz, xbz)));
+    }
+    // bond axes further down the subtree turn with it
+    for (int kk = k + 1 + lane; kk < R; kk += 32) {
+        if (cv.rch[kk] < e) {
+            const float4 v = wv.axis[kk];
+            const float uv = fmaf(ux, v.x, fmaf(uy, v.y, uz * v.z));
+            const float cx = fmaf(uy, v.z, -uz * v.y), cy = fmaf(uz, v.x, -ux * v.z), cz = fmaf(ux, v.y, -uy * v.x);
+            const float k1 = uv * (1.0f - c);
+            wv.axis[kk] = make_float4(fmaf(cx, s, fmaf(v.x, c, k1 * ux)), fmaf(cy, s, fmaf(v.y, c, k1 * uy)),
+                                      fmaf(cz, s, fmaf(v.z, c, k1 * uz)), 0.0f);
         }
     }
     __syncwarp();
-    return chosen;
+    return t;
 }
 
 // ------------------------------------------------------------------ one ligand, one CTA
 __device__ void dock_ligand_cta(const DockArgs &A, int l, char *sm) {
     const Layout &Ly = A.ly;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, W = blockDim.x >> 5;
+    if (A.out.status[l] != LG_OK) return;  // rejected by the preparation kernel (uniform)
     const CtaView cv = cta_view(sm, Ly);
     const WarpView wv = warp_view(sm, Ly, warp);
     const BatchDev &B = A.batch;
+    const PocketDev &Pk = A.pocket;
     const int a0 = B.atom_off[l], N = B.atom_off[l + 1] - a0;
     const int r0 = B.rot_off[l], R = B.rot_off[l + 1] - r0;
     const int S = A.S, P = A.P;
 
-    const bool size_ok = N >= 1 && N <= A.nmax_decl && N <= Ly.nmax && R >= 0 && R <= A.rmax_decl && R <= Ly.rmax;
-    if (size_ok) {
-        for (int i = tid; i < N; i += blockDim.x) {
-            cv.d0x[i] = B.x[a0 + i];
-            cv.d0y[i] = B.y[a0 + i];
-            cv.d0z[i] = B.z[a0 + i];
-            cv.par[i] = B.parent[a0 + i];
-            const int t = B.type[a0 + i];
-            cv.wq[i] = make_float2(t < LG_NUM_TYPES ? A.pocket.type_w[t] : 0.0f, B.q[a0 + i]);
-        }
-        for (int k = tid; k < R; k += blockDim.x) cv.rch[k] = B.rot_child[r0 + k];
-    }
-    __syncthreads();
-    if (warp == 0) {
-        // validation (lane 0, sequential over the atoms) and centroid (FP64)
-        int ok = size_ok ? 1 : 0;
-        if (ok && lane == 0) {
-            // parent[i] < i, and every subtree contiguous: size(v) == end(v) - v
-            int *endv = (int *)wv.Xx;  // scratch: warp 0's position buffers
-            int *size = (int *)wv.Xy;
-            if (cv.par[0] != -1) ok = 0;
-            for (int i = 1; i < N && ok; i++)
-                if (cv.par[i] < 0 || cv.par[i] >= i) ok = 0;
-            for (int i = 0; i < N && ok; i++) {
-                const int t = B.type[a0 + i];
-                if (t >= LG_NUM_TYPES) ok = 0;
-                if (!isfinite(cv.d0x[i]) || !isfinite(cv.d0y[i]) || !isfinite(cv.d0z[i])) ok = 0;
-            }
-            if (ok) {
-                for (int i = 0; i < N; i++) { endv[i] = i + 1; size[i] = 1; }
-                for (int i = N - 1; i >= 1; i--) {
-                    const int p = cv.par[i];
-                    endv[p] = max(endv[p], endv[i]);
-                    size[p] += size[i];
-                }
-                for (int i = 0; i < N && ok; i++)
-                    if (size[i] != endv[i] - i) ok = 0;
-                for (int k = 0; k < R && ok; k++) {
-                    const int b = cv.rch[k];
-                    if (b < 1 || b >= N || (k > 0 && b <= cv.rch[k - 1])) ok = 0;
-                    else cv.rend[k] = endv[b];
-                }
-            }
-        }
-        ok = __shfl_sync(LG_FULL, ok, 0);
-        if (ok) {
-            double sx = 0.0, sy = 0.0, sz = 0.0;
-            for (int i = lane; i < N; i += 32) {
-                sx += (double)cv.d0x[i];
-                sy += (double)cv.d0y[i];
-                sz += (double)cv.d0z[i];
-            }
-            sx = warp_sum_d(sx); sy = warp_sum_d(sy); sz = warp_sum_d(sz);
-            if (lane == 0) {
-                cv.cen[0] = sx / N;
-                cv.cen[1] = sy / N;
-                cv.cen[2] = sz / N;
-            }
-        }
-        if (lane == 0) cv.scal[0] = ok;
-    }
-    __syncthreads();
-    if (!cv.scal[0]) {
-        if (tid == 0) {
-            A.out.score[l] = __longlong_as_double(0x7ff8000000000000ll);
-            A.out.best_restart[l] = -1;
-            A.out.status[l] = LG_EINVAL;
-        }
-        __syncthreads();
-        return;
-    }
-    // bond vectors from the input coordinates, then centroid-relative atoms
-    for (int k = tid; k < R; k += blockDim.x) {
-        const int b = cv.rch[k], a = cv.par[b];
-        cv.dv[k] = make_float4(cv.d0x[b] - cv.d0x[a], cv.d0y[b] - cv.d0y[a], cv.d0z[b] - cv.d0z[a], 0.0f);
-    }
-    __syncthreads();
+    // stage the ligand: centroid-relative coordinates in grid units (FP64
+    // difference), topology, per-atom weights, bond vectors
     {
-        const double cx = cv.cen[0], cy = cv.cen[1], cz = cv.cen[2];
+        const double cx = A.scr.centroid[3 * l], cy = A.scr.centroid[3 * l + 1], cz = A.scr.centroid[3 * l + 2];
+        const double ih = (double)Pk.inv_h;
         for (int i = tid; i < N; i += blockDim.x) {
-            cv.d0x[i] = (float)((double)cv.d0x[i] - cx);
-            cv.d0y[i] = (float)((double)cv.d0y[i] - cy);
-            cv.d0z[i] = (float)((double)cv.d0z[i] - cz);
+            cv.d0x[i] = (float)(((double)B.x[a0 + i] - cx) * ih);
+            cv.d0y[i] = (float)(((double)B.y[a0 + i] - cy) * ih);
+            cv.d0z[i] = (float)(((double)B.z[a0 + i] - cz) * ih);
+            cv.par[i] = B.parent[a0 + i];
+            cv.wq[i] = make_float2(Pk.type_w[B.type[a0 + i]], B.q[a0 + i]);
+        }
+        for (int k = tid; k < R; k += blockDim.x) {
+            const int b = B.rot_child[r0 + k], p = B.parent[a0 + b];
+            cv.rch[k] = b;
+            cv.rend[k] = A.scr.rot_end[(size_t)l * A.rmax_lim + k];
+            cv.dv[k] = make_float4((B.x[a0 + b] - B.x[a0 + p]) * Pk.inv_h, (B.y[a0 + b] - B.y[a0 + p]) * Pk.inv_h,
+                                   (B.z[a0 + b] - B.z[a0 + p]) * Pk.inv_h, 0.0f);
         }
     }
     __syncthreads();
@@ -414,7 +381,7 @@ __device__ void dock_ligand_cta(const DockArgs &A, int l, char *sm) {
     const float ct = c_cos[32 + (lane & 3)], st = c_sin[32 + (lane & 3)];
     const uint64_t uid = B.uid[l];
     const uint2 key = make_uint2(A.seed_lo, A.seed_hi);
-    const PocketDev &Pk = A.pocket;
+    const GridK Go = grid_k(Pk, Pk.cell_o), Gve = grid_k(Pk, Pk.cell_ve);
     const int PR = P * R;
 
     double bestE = INFINITY;
@@ -450,7 +417,7 @@ __device__ void dock_ligand_cta(const DockArgs &A, int l, char *sm) {
         // 2. greedy torsion sweep
         for (int ps = 0; ps < P; ++ps)
             for (int k = 0; k < R; ++k) {
-                const int t = sweep_bond(A, cv, wv, N, R, k, lane, cl, sl, ct, st);
+                const int t = sweep_bond(A, Go, cv, wv, N, R, k, lane, cl, sl, ct, st);
                 if (lane == 0) wv.tcur[ps * R + k] = (uint8_t)t;
             }
         __syncwarp();
@@ -458,7 +425,7 @@ __device__ void dock_ligand_cta(const DockArgs &A, int l, char *sm) {
         double E = 0.0;
         for (int i = lane; i < N; i += 32) {
             const float2 wq = cv.wq[i];
-            E += (double)atom_energy(Pk, wv.Xx[i], wv.Xy[i], wv.Xz[i], wq.x, wq.y);
+            E += (double)atom_energy(Pk, Gve, wv.Xx[i], wv.Xy[i], wv.Xz[i], wq.x, wq.y);
         }
         E = warp_sum_d(E);
         if (A.out.restart_score && lane == 0) A.out.restart_score[(size_t)l * S + r] = E;
@@ -508,17 +475,17 @@ __device__ void dock_ligand_cta(const DockArgs &A, int l, char *sm) {
         if (tid == 0) {
             A.out.score[l] = be;
             A.out.best_restart[l] = br;
-            A.out.status[l] = LG_OK;
         }
         if (A.out.tors_idx)
             for (int t = tid; t < PR; t += blockDim.x) A.out.tors_idx[(size_t)P * r0 + t] = bv.tbest[t];
         if (A.out.pose && Ly.want_pose) {
             const float3 c = Pk.center;
+            const float h = Pk.h;
             for (int i = tid; i < N; i += blockDim.x) {
                 float *o = A.out.pose + 3 * (size_t)(a0 + i);
-                o[0] = bv.Bx[i] + c.x;
-                o[1] = bv.By[i] + c.y;
-                o[2] = bv.Bz[i] + c.z;
+                o[0] = fmaf(bv.Bx[i], h, c.x);
+                o[1] = fmaf(bv.By[i], h, c.y);
+                o[2] = fmaf(bv.Bz[i], h, c.z);
             }
         }
     }
@@ -546,40 +513,83 @@ __global__ void __launch_bounds__(1024) k_dock_batched(const __grid_constant__ D
     }
 }
 
-// Cost estimate and bucket (log scale, 4 buckets per octave) of every ligand:
-// cost ~ restarts * (passes * 36 * sum of moving atoms + atoms).
-__global__ void k_sort_keys(const __grid_constant__ DockArgs A, int32_t *keys, int32_t *hist) {
+// Preparation, one thread per ligand: validates the ligand (sizes within the
+// limits, parent[0] = -1, parent[i] < i, contiguous subtrees -- subtree size
+// equals end - start --, types, finite coordinates, torsional children strictly
+// ascending in [1, N-1]), writes the end of every torsional child's subtree,
+// the centroid (FP64) and the ligand's status; with `sort` it also files the
+// ligand into a log-scale cost bucket (4 per octave) of
+//   cost ~ restarts * (passes * 36 * sum of moving atoms + 8 * atoms + 64).
+__global__ void k_prep(const __grid_constant__ DockArgs A, int sort) {
     __shared__ int sh[kSortBuckets];
-    for (int t = threadIdx.x; t < kSortBuckets; t += blockDim.x) sh[t] = 0;
+    if (sort)
+        for (int t = threadIdx.x; t < kSortBuckets; t += blockDim.x) sh[t] = 0;
     __syncthreads();
     const int l = blockIdx.x * blockDim.x + threadIdx.x;
     if (l < A.batch.L) {
         const BatchDev &B = A.batch;
         const int a0 = B.atom_off[l], N = B.atom_off[l + 1] - a0;
         const int r0 = B.rot_off[l], R = B.rot_off[l + 1] - r0;
-        double cost = 1.0;
-        if (N >= 1 && N <= LG_MAX_ATOMS && R >= 0 && R <= LG_MAX_ROT) {
-            int endv[LG_MAX_ATOMS];
-            for (int i = 0; i < N; i++) endv[i] = i + 1;
-            for (int i = N - 1; i >= 1; i--) {
-                const int p = B.parent[a0 + i];
-                if (p >= 0 && p < i) endv[p] = max(endv[p], endv[i]);
+        bool ok = N >= 1 && N <= A.nmax_lim && R >= 0 && R <= A.rmax_lim;
+        long msum = 0;
+        if (ok) {
+            int endv[LG_MAX_ATOMS], size[LG_MAX_ATOMS];
+            ok = B.parent[a0] == -1;
+            double sx = 0.0, sy = 0.0, sz = 0.0;
+            for (int i = 0; i < N && ok; i++) {
+                endv[i] = i + 1;
+                size[i] = 1;
+                const float x = B.x[a0 + i], y = B.y[a0 + i], z = B.z[a0 + i];
+                if (i > 0) {
+                    const int p = B.parent[a0 + i];
+                    ok = p >= 0 && p < i;
+                }
+                ok = ok && B.type[a0 + i] < LG_NUM_TYPES && isfinite(x) && isfinite(y) && isfinite(z);
+                sx += x;
+                sy += y;
+                sz += z;
             }
-            long msum = 0;
-            for (int k = 0; k < R; k++) {
-                const int b = B.rot_child[r0 + k];
-                if (b >= 1 && b < N) msum += endv[b] - b - 1;
+            if (ok) {
+                for (int i = N - 1; i >= 1; i--) {
+                    const int p = B.parent[a0 + i];
+                    endv[p] = max(endv[p], endv[i]);
+                    size[p] += size[i];
+                }
+                for (int i = 0; i < N && ok; i++) ok = size[i] == endv[i] - i;
+                int prev = 0;
+                for (int k = 0; k < R && ok; k++) {
+                    const int b = B.rot_child[r0 + k];
+                    ok = b >= 1 && b < N && b > prev;
+                    if (ok) {
+                        A.scr.rot_end[(size_t)l * A.rmax_lim + k] = (int16_t)endv[b];
+                        msum += endv[b] - b - 1;
+                        prev = b;
+                    }
+                }
             }
-            cost = (double)A.S * ((double)A.P * 36.0 * (double)msum + 8.0 * N + 64.0);
+            if (ok) {
+                A.scr.centroid[3 * l] = sx / N;
+                A.scr.centroid[3 * l + 1] = sy / N;
+                A.scr.centroid[3 * l + 2] = sz / N;
+            }
         }
-        int key = (int)(4.0 * log2(cost));
-        key = max(0, min(kSortBuckets - 1, key));
-        keys[l] = key;
-        atomicAdd(&sh[key], 1);
+        A.out.status[l] = ok ? LG_OK : LG_EINVAL;
+        if (!ok) {
+            A.out.score[l] = __longlong_as_double(0x7ff8000000000000ll);
+            A.out.best_restart[l] = -1;
+        }
+        if (sort) {
+            const double cost = ok ? (double)A.S * ((double)A.P * 36.0 * (double)msum + 8.0 * N + 64.0) : 1.0;
+            int key = (int)(4.0 * log2(cost));
+            key = max(0, min(kSortBuckets - 1, key));
+            A.scr.keys[l] = key;
+            atomicAdd(&sh[key], 1);
+        }
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < kSortBuckets; t += blockDim.x)
-        if (sh[t]) atomicAdd(&hist[t], sh[t]);
+    if (sort)
+        for (int t = threadIdx.x; t < kSortBuckets; t += blockDim.x)
+            if (sh[t]) atomicAdd(&A.scr.hist[t], sh[t]);
 }
 
 // Exclusive offsets of the buckets in descending key order (one warp).
@@ -617,13 +627,15 @@ __global__ void k_score_poses(const __grid_constant__ PocketDev P, int L, const 
     const int lane = threadIdx.x & 31;
     const int l = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (l >= L) return;
+    const GridK G = grid_k(P, P.cell_ve);
     const int a0 = atom_off[l], N = atom_off[l + 1] - a0;
     double acc = 0.0;
     for (int i = lane; i < N; i += 32) {
         const int t = type[a0 + i];
         const float w = t < LG_NUM_TYPES ? P.type_w[t] : 0.0f;
         const float *x = xyz + 3 * (size_t)(a0 + i);
-        acc += (double)atom_energy(P, x[0] - P.center.x, x[1] - P.center.y, x[2] - P.center.z, w, q[a0 + i]);
+        acc += (double)atom_energy(P, G, (x[0] - P.center.x) * P.inv_h, (x[1] - P.center.y) * P.inv_h,
+                                   (x[2] - P.center.z) * P.inv_h, w, q[a0 + i]);
     }
     acc = warp_sum_d(acc);
     if (lane == 0) E[l] = acc;
@@ -641,7 +653,30 @@ __global__ void k_diag_philox(int n, const uint32_t *ctr, const uint32_t *key, u
     out[4 * i + 3] = o.w;
 }
 
-// ------------------------------------------------------------------ launchers
+// ------------------------------------------------------------------ host side
+static size_t al256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+size_t scratch_bytes(int L, int rmax) {
+    return al256(4 * (kSortBuckets + 1)) + 2 * al256(4 * (size_t)L) + al256(24 * (size_t)L) +
+           al256(2 * (size_t)L * (rmax > 0 ? rmax : 1));
+}
+
+Scratch carve_scratch(void *base, int L, int rmax) {
+    (void)rmax;
+    char *p = (char *)base;
+    Scratch s;
+    s.hist = (int32_t *)p;
+    p += al256(4 * (kSortBuckets + 1));
+    s.keys = (int32_t *)p;
+    p += al256(4 * (size_t)L);
+    s.order = (int32_t *)p;
+    p += al256(4 * (size_t)L);
+    s.centroid = (double *)p;
+    p += al256(24 * (size_t)L);
+    s.rot_end = (int16_t *)p;
+    return s;
+}
+
 cudaError_t dock_kernel_attributes(int W, int smem, int *ctas_per_sm) {
     cudaError_t e = cudaFuncSetAttribute(k_dock_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
@@ -652,6 +687,19 @@ cudaError_t plain_kernel_attributes(int smem) {
     return cudaFuncSetAttribute(k_dock_plain, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
 }
 
+cudaError_t launch_prep(const DockArgs &a, bool sort, cudaStream_t s, int *launches) {
+    const int L = a.batch.L;
+    const int blocks = (L + 255) / 256;
+    k_prep<<<blocks, 256, 0, s>>>(a, sort ? 1 : 0);
+    *launches += 1;
+    if (sort) {
+        k_sort_scan<<<1, 32, 0, s>>>(a.scr.hist);
+        k_sort_scatter<<<blocks, 256, 0, s>>>(L, a.scr.keys, a.scr.hist, a.scr.order);
+        *launches += 2;
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_dock_plain(const DockArgs &a, int ligand, cudaStream_t s) {
     k_dock_plain<<<1, 32 * a.ly.W, a.ly.total, s>>>(a, ligand);
     return cudaGetLastError();
@@ -659,17 +707,6 @@ cudaError_t launch_dock_plain(const DockArgs &a, int ligand, cudaStream_t s) {
 
 cudaError_t launch_dock_batched(const DockArgs &a, int grid, cudaStream_t s) {
     k_dock_batched<<<grid, 32 * a.ly.W, a.ly.total, s>>>(a);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_sort(const DockArgs &a, int32_t *keys, int32_t *hist, int32_t *order, cudaStream_t s,
-                        int *launches) {
-    const int L = a.batch.L;
-    const int blocks = (L + 255) / 256;
-    k_sort_keys<<<blocks, 256, 0, s>>>(a, keys, hist);
-    k_sort_scan<<<1, 32, 0, s>>>(hist);
-    k_sort_scatter<<<blocks, 256, 0, s>>>(L, keys, hist, order);
-    *launches += 3;
     return cudaGetLastError();
 }
 

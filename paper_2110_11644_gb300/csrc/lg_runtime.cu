@@ -172,7 +172,9 @@ int choose_warps(int S, int opt) {
     return 8;
 }
 
-// Launch the docking of a device-resident batch on stream s.
+// Launch the docking of a device-resident batch on stream s: the preparation
+// kernel (validation, subtree ends, centroids; cost sort in batched mode),
+// then the persistent docking kernel or one plain launch per ligand.
 int dock_device(lg_ctx *ctx, const PocketDev &pk, const BatchDev &bd, const OutDev &od, const lg_dock_params *p,
                 int nmax, int rmax, DevBuf &scratch, cudaStream_t s, lg_stats *st, cudaEvent_t *tev) {
     const bool timed = tev != nullptr;
@@ -185,19 +187,31 @@ int dock_device(lg_ctx *ctx, const PocketDev &pk, const BatchDev &bd, const OutD
     a.P = p->passes;
     a.seed_lo = (uint32_t)p->seed;
     a.seed_hi = (uint32_t)(p->seed >> 32);
-    a.dc2 = p->d_clash * p->d_clash;
-    a.nmax_decl = p->max_atoms > 0 ? p->max_atoms : LG_MAX_ATOMS;
-    a.rmax_decl = p->max_rot > 0 ? p->max_rot : LG_MAX_ROT;
-    nmax = std::max(1, std::min(nmax, a.nmax_decl));
-    rmax = std::max(1, std::min(rmax, a.rmax_decl));
+    const double dc = p->d_clash, h = pk.h;
+    a.dc2g = (float)(dc * dc / (h * h));
+    const int nmax_decl = p->max_atoms > 0 ? p->max_atoms : LG_MAX_ATOMS;
+    const int rmax_decl = p->max_rot > 0 ? p->max_rot : LG_MAX_ROT;
+    nmax = std::max(1, std::min(nmax, nmax_decl));
+    rmax = std::max(1, std::min(rmax, rmax_decl));
+    a.nmax_lim = nmax;
+    a.rmax_lim = rmax;
     const int want_pose = od.pose != nullptr;
     const lg_stats keep = *st;
     memset(st, 0, sizeof(*st));
     st->dock_calls = keep.dock_calls;
     st->dock_ms_total = keep.dock_ms_total;
     st->dock_ms = keep.dock_ms;
+    const int L = bd.L;
+    const bool plain = p->mode == LG_MODE_PLAIN;
+    if (scratch.ensure(scratch_bytes(L, rmax))) return fail(LG_ENOMEM, "scratch allocation failed");
+    a.scr = carve_scratch(scratch.p, L, rmax);
     cudaError_t e;
-    if (p->mode == LG_MODE_PLAIN) {
+    int launches = 0;
+    if (!plain && (e = cudaMemsetAsync(a.scr.hist, 0, 4 * (kSortBuckets + 1), s)) != cudaSuccess)
+        return fail(LG_ECUDA, std::string("scratch clear: ") + cudaGetErrorString(e));
+    if ((e = launch_prep(a, !plain, s, &launches)) != cudaSuccess)
+        return fail(LG_ECUDA, std::string("preparation launch: ") + cudaGetErrorString(e));
+    if (plain) {
         const int W = std::min(a.S, 32);
         a.ly = make_layout(nmax, rmax, a.P, W, want_pose);
         if ((e = plain_kernel_attributes(a.ly.total)) != cudaSuccess)
@@ -209,7 +223,7 @@ int dock_device(lg_ctx *ctx, const PocketDev &pk, const BatchDev &bd, const OutD
         if (timed) cudaEventRecord(tev[0], s);
         cudaEventRecord(fork, s);
         for (int i = 0; i < ns; i++) cudaStreamWaitEvent(ps[i], fork, 0);
-        for (int l = 0; l < bd.L; l++) {
+        for (int l = 0; l < L; l++) {
             if ((e = launch_dock_plain(a, l, ps[l % ns])) != cudaSuccess)
                 return fail(LG_ECUDA, std::string("plain launch: ") + cudaGetErrorString(e));
         }
@@ -219,8 +233,8 @@ int dock_device(lg_ctx *ctx, const PocketDev &pk, const BatchDev &bd, const OutD
             cudaStreamWaitEvent(s, j, 0);
         }
         if (timed) cudaEventRecord(tev[1], s);
-        st->launches = bd.L;
-        st->grid = bd.L;
+        st->launches = launches + L;
+        st->grid = L;
         st->warps_per_cta = W;
         st->ctas_per_sm = 1;
         st->smem_bytes = a.ly.total;
@@ -237,20 +251,8 @@ int dock_device(lg_ctx *ctx, const PocketDev &pk, const BatchDev &bd, const OutD
         W = std::max(1, W / 2);
     }
     if (occ <= 0) return fail(LG_EINVAL, "docking kernel does not fit on an SM");
-    const int L = bd.L;
-    Carve c;
-    const size_t o_hist = c.take(4 * (kSortBuckets + 1));
-    const size_t o_keys = c.take(4 * (size_t)L), o_order = c.take(4 * (size_t)L);
-    if (scratch.ensure(c.off)) return fail(LG_ENOMEM, "scratch allocation failed");
-    char *sb = (char *)scratch.p;
-    int32_t *hist = (int32_t *)(sb + o_hist);
-    a.work_counter = hist + kSortBuckets;
-    a.order = (int32_t *)(sb + o_order);
-    if ((e = cudaMemsetAsync(hist, 0, 4 * (kSortBuckets + 1), s)) != cudaSuccess)
-        return fail(LG_ECUDA, std::string("scratch clear: ") + cudaGetErrorString(e));
-    int launches = 0;
-    if ((e = launch_sort(a, (int32_t *)(sb + o_keys), hist, (int32_t *)(sb + o_order), s, &launches)) != cudaSuccess)
-        return fail(LG_ECUDA, std::string("sort launch: ") + cudaGetErrorString(e));
+    a.work_counter = a.scr.hist + kSortBuckets;
+    a.order = a.scr.order;
     const int grid = std::max(1, std::min(ctx_num_sms(ctx) * occ, L));
     if (timed) cudaEventRecord(tev[0], s);
     if ((e = launch_dock_batched(a, grid, s)) != cudaSuccess)
@@ -394,7 +396,7 @@ int lg_pocket_load(lg_ctx *c, const lg_pocket_desc *d, int32_t *pid) {
     pack_cells(d->phi_e, n, h_ve.data(), 16, 8);
     const double c0 = (n - 1) / 2.0;
     for (int p = 0; p < d->n_pp; p++) {
-        for (int c3 = 0; c3 < 3; c3++) h_pp[4 * p + c3] = (float)((double)d->h * (d->pocket_points[3 * p + c3] - c0));
+        for (int c3 = 0; c3 < 3; c3++) h_pp[4 * p + c3] = (float)(d->pocket_points[3 * p + c3] - c0);
         h_pp[4 * p + 3] = 0.0f;
     }
     Carve cv;
