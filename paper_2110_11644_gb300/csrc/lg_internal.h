@@ -96,6 +96,35 @@ __host__ __device__ inline Layout make_layout(int nmax, int rmax, int P, int W, 
     return L;
 }
 
+// Restart-tiled warps (batched kernel): a warp docks 8 restarts of one ligand
+// at once, 4 lanes per restart, each lane owning 9 of the 36 torsion steps.
+constexpr int kTile = 8;          // restarts per warp tile
+constexpr int kLanesPerRestart = 4;
+constexpr int kStepsPerLane = 9;  // 36 / 4
+constexpr int kPoolCap = 96;      // flagged clash pairs buffered per warp (all 8 restarts)
+
+// Per-warp shared memory of a restart-tiled warp.
+struct LayoutRT {
+    int o_axis, o_X, o_pool, o_mask, o_near, o_best, o_tcur, o_tbest, warp_bytes;
+};
+
+__host__ __device__ inline LayoutRT make_layout_rt(int nmax, int rmax, int P, int want_pose) {
+    LayoutRT L;
+    nmax = (nmax + 3) & ~3;
+    if (rmax < 1) rmax = 1;
+    int w = 0;
+    L.o_axis = w;  w = lg_align16(w + 16 * rmax * kTile);            // float4 [rmax][8]
+    L.o_X = w;     w = lg_align16(w + 12 * nmax * kTile);            // float [3][nmax][8]
+    L.o_pool = w;  w = lg_align16(w + 16 * kPoolCap);                // float4 (C, A2, B2, restart slot)
+    L.o_mask = w;  w = lg_align16(w + 4 * 32);                       // uint32 clash bits per lane
+    L.o_near = w;  w = lg_align16(w + nmax * kTile);                 // uint8 [8][nmax] near fixed atoms
+    L.o_best = w;  w = lg_align16(w + (want_pose ? 12 * nmax : 0));  // float [3][nmax]
+    L.o_tcur = w;  w = lg_align16(w + P * rmax * kTile);             // uint8 [P*rmax][8]
+    L.o_tbest = w; w = lg_align16(w + P * rmax);                     // uint8 [P*rmax]
+    L.warp_bytes = w;
+    return L;
+}
+
 // Per-launch scratch (device memory beyond the inputs and outputs).
 struct Scratch {
     int32_t *hist;         // kSortBuckets counters, then the work counter
@@ -109,7 +138,8 @@ struct DockArgs {
     PocketDev pocket;
     BatchDev batch;
     OutDev out;
-    Layout ly;
+    Layout ly;      // CTA part (both kernels) and the plain kernel's warp part
+    LayoutRT lrt;   // warp part of the restart-tiled kernel
     Scratch scr;
     int S, P;
     uint32_t seed_lo, seed_hi;
@@ -129,7 +159,7 @@ Scratch carve_scratch(void *base, int L, int rmax);
 void set_angle_tables(const float *cosv, const float *sinv);
 cudaError_t launch_prep(const DockArgs &a, bool sort, cudaStream_t s, int *launches);
 cudaError_t launch_dock_plain(const DockArgs &a, int ligand, cudaStream_t s);
-cudaError_t launch_dock_batched(const DockArgs &a, int grid, cudaStream_t s);
+cudaError_t launch_dock_batched(const DockArgs &a, int grid, int smem, cudaStream_t s);
 cudaError_t launch_score_poses(const PocketDev &p, int L, const int32_t *atom_off, const float *xyz,
                                const float *q, const uint8_t *type, double *E, cudaStream_t s);
 cudaError_t launch_diag_philox(int n, const uint32_t *ctr, const uint32_t *key, uint32_t *out, int use_curand,

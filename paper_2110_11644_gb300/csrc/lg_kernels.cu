@@ -1,36 +1,37 @@
-// Docking kernels for sm_103a (GB300).
+// Docking kernels for sm_103a (GB300): the dock-and-score step of the paper
+// (Sec. 3.1) -- restart poses, greedy torsion sweep with clash check, grid
+// scoring, best restart.  All floating-point arithmetic is in lg_device.cuh.
 //
-// The dock-and-score step of the paper (Sec. 3.1) on the GPU.  One CTA docks
-// one ligand: its warps share the ligand's topology in shared memory and each
-// warp runs one restart at a time (restarts are tiled over the CTA's warps).
+// Two forms share it and produce bit-identical results:
 //
-// Inside a warp the 36 torsion steps of a bond map onto lanes: lane t owns
-// step t (steps 32..35 are spread over the warp in a short tail loop), so the
-// per-step overlap sums need no cross-lane reduction and the choice of step is
-// a 5-level shuffle argmax.  Moving atoms are processed in bundles of 32 (the
-// paper's CUDA design also works in bundles of 32 atoms, Sec. 3.1): each lane
-// builds the circle one atom traces about the bond axis,
+//  * k_dock_plain -- one CTA per ligand, one warp per restart, one launch per
+//    ligand.  Lanes own torsion steps: lane t scores step t for every moving
+//    atom (steps 32..35 by lanes 0..3), moving atoms are processed in bundles
+//    of 32 (the paper's CUDA design works in bundles of 32 atoms, Sec. 3.1).
+//
+//  * k_dock_batched -- persistent, ligands in descending estimated cost.  One
+//    CTA docks one ligand; each warp runs a tile of 8 restarts at once with 4
+//    lanes per restart, each lane owning 9 of the 36 steps, so the work that is
+//    paid once per decision (circle set-up, argmax, moves) is shared by 8
+//    restarts, the 9 steps of a lane (every 4th step) are straight-line code,
+//    and the argmax needs 2 shuffles.
+//
+// Every moving atom traces a circle about the bond axis,
 //     x(theta) = p + e1 cos(theta) + e2 sin(theta),
-// and every lane evaluates its own step on that circle with two FMAs per
-// coordinate, then reads one 32-byte cell of trilinear coefficients of the
-// overlap grid (L2-resident, read-only path).
-//
+// so a torsion step costs two FMAs per coordinate plus one 32-byte cell of
+// trilinear coefficients of the overlap grid (L2-resident, read-only path).
 // The clash test uses the same circles: for a moving atom i and a fixed atom j
 //     |x_i(theta) - x_j|^2 = C + 2a cos(theta) + 2b sin(theta),
-//     C = |p - x_j|^2 + |e1|^2,  a = (p - x_j).e1,  b = (p - x_j).e2,
-// whose minimum over the circle is C - 2 sqrt(a^2 + b^2).  Pairs whose minimum
-// stays above d_clash^2 can never clash and are dropped with one test; the few
-// others are evaluated for all 36 steps at once (lanes = steps), so every
-// decision gets its full admissibility mask in one pass.
+// whose minimum over the circle is C - 2 sqrt(a^2 + b^2).  Pairs that stay
+// clear of d_clash at every step are dropped with one test; the others are
+// evaluated step by step.
 //
 // Positions live in centred grid units (see lg_internal.h).
 #include <curand_philox4x32_x.h>
 
-#include "lg_internal.h"
+#include "lg_device.cuh"
 
 namespace lg {
-
-#define LG_FULL 0xffffffffu
 
 __constant__ float c_cos[LG_ANGLE_STEPS];
 __constant__ float c_sin[LG_ANGLE_STEPS];
@@ -40,121 +41,19 @@ void set_angle_tables(const float *cosv, const float *sinv) {
     cudaMemcpyToSymbol(c_sin, sinv, sizeof(float) * LG_ANGLE_STEPS);
 }
 
-// ------------------------------------------------------------------ Philox4x32-10
-// Salmon, Moraes, Dror, Shaw, SC'11: ten rounds; each multiplies words 0 and 2
-// by the round constants, keeps both halves of the products, mixes the high
-// halves with the other two words and the key; the key advances by the two
-// Weyl constants between rounds.
-__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
-#pragma unroll
-    for (int r = 0; r < 10; r++) {
-        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
-        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
-        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
-        k.x += 0x9E3779B9u;
-        k.y += 0xBB67AE85u;
-    }
-    return c;
-}
-
-// ------------------------------------------------------------------ grid lookups
-// Floor of an index-space coordinate in [0, 2^22) by adding 1.5*2^23 with
-// round-down: the integer part lands in the low mantissa bits of t and
-// t - 1.5*2^23 is exact, as is the fraction g - floor(g).
-constexpr float kMagic = 12582912.0f;  // bit pattern 0x4B400000
-
-__device__ __forceinline__ float floor_frac(float g, float &t) {
-    t = __fadd_rd(g, kMagic);
-    return g - (t - kMagic);
-}
-
-// Flat cell index (k*n + j)*n + i from the three round-down sums (32-bit
-// wrap-around arithmetic; the true result is small and non-negative).
-__device__ __forceinline__ uint32_t cell_index(float tx, float ty, float tz, uint32_t n, uint32_t n2, uint32_t moff) {
-    return __float_as_uint(tz) * n2 + __float_as_uint(ty) * n + __float_as_uint(tx) - moff;
-}
-
-// Trilinear polynomial of one cell: lo = (c0, c1, c2, c3), hi = (c4, c5, c6, c7).
-__device__ __forceinline__ float cell_eval(const float4 lo, const float4 hi, float fx, float fy, float fz) {
-    const float t1 = fmaf(fz, hi.w, hi.x);  // c4 + c7 fz
-    const float t2 = fmaf(fz, hi.y, lo.y);  // c1 + c5 fz
-    const float ax = fmaf(fy, t1, t2);      // d p / d fx
-    const float t4 = fmaf(fz, hi.z, lo.z);  // c2 + c6 fz
-    const float t5 = fmaf(fz, lo.w, lo.x);  // c0 + c3 fz
-    const float b = fmaf(fy, t4, t5);
-    return fmaf(fx, ax, b);
-}
-
-__device__ __forceinline__ float clampg(float g, float gmax) { return fminf(fmaxf(g, 0.0f), gmax); }
-
-struct GridK {  // lookup constants of a pocket
-    const float4 *cells;
-    uint32_t n, n2, moff;
-    float gmax;
-};
-
-__device__ __forceinline__ GridK grid_k(const PocketDev &P, const float4 *cells) {
-    GridK g;
-    g.cells = cells;
-    g.n = (uint32_t)P.n;
-    g.n2 = g.n * g.n;
-    g.moff = 0x4B400000u * (g.n2 + g.n + 1u);
-    g.gmax = P.gmax;
-    return g;
-}
-
-// Overlap-field value at an index-space point known to lie in [0, n-1]^3.
-__device__ __forceinline__ float lookup_in(const GridK &G, float gx, float gy, float gz) {
-    float tx, ty, tz;
-    const float fx = floor_frac(gx, tx), fy = floor_frac(gy, ty), fz = floor_frac(gz, tz);
-    const float4 *p = G.cells + 2 * (size_t)cell_index(tx, ty, tz, G.n, G.n2, G.moff);
-    const float4 lo = __ldg(p), hi = __ldg(p + 1);
-    return cell_eval(lo, hi, fx, fy, fz);
-}
-
-// Overlap-field value at any index-space point (clamped to the box).
-__device__ __forceinline__ float lookup_clamped(const GridK &G, float gx, float gy, float gz) {
-    return lookup_in(G, clampg(gx, G.gmax), clampg(gy, G.gmax), clampg(gz, G.gmax));
-}
-
-// Per-atom energy term at a centred-grid-unit position: type weight * vdW grid
-// + charge * electrostatic grid at the clamped position, plus k_out times the
-// distance (A) outside the box.
-__device__ __forceinline__ float atom_energy(const PocketDev &P, const GridK &G, float x, float y, float z, float w,
-                                             float q) {
-    const float gx = x + P.c0, gy = y + P.c0, gz = z + P.c0;
-    const float cx = clampg(gx, P.gmax), cy = clampg(gy, P.gmax), cz = clampg(gz, P.gmax);
-    const float dx = gx - cx, dy = gy - cy, dz = gz - cz;
-    const float out = P.h * sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
-    float tx, ty, tz;
-    const float fx = floor_frac(cx, tx), fy = floor_frac(cy, ty), fz = floor_frac(cz, tz);
-    const float4 *p = G.cells + 4 * (size_t)cell_index(tx, ty, tz, G.n, G.n2, G.moff);
-    const float v = cell_eval(__ldg(p), __ldg(p + 1), fx, fy, fz);
-    const float e = cell_eval(__ldg(p + 2), __ldg(p + 3), fx, fy, fz);
-    return fmaf(w, v, fmaf(q, e, P.k_out * out));
-}
-
 __device__ __forceinline__ double warp_sum_d(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(LG_FULL, v, o);
     return v;
 }
 
-// ------------------------------------------------------------------ shared-memory views
+// ------------------------------------------------------------------ the ligand of a CTA
 struct CtaView {
     float4 *dv;
     double *wE;
     float *d0x, *d0y, *d0z;
     float2 *wq;
     int *par, *rch, *rend, *wR;
-};
-
-struct WarpView {
-    float4 *bundle;  // 32 atoms x 4 float4 (see sweep_bond)
-    float4 *axis;
-    float *Xx, *Xy, *Xz;
-    float *Bx, *By, *Bz;
-    uint8_t *tcur, *tbest;
 };
 
 __device__ __forceinline__ CtaView cta_view(char *sm, const Layout &L) {
@@ -172,288 +71,40 @@ __device__ __forceinline__ CtaView cta_view(char *sm, const Layout &L) {
     return v;
 }
 
-__device__ __forceinline__ WarpView warp_view(char *sm, const Layout &L, int w) {
-    char *b = sm + L.cta_bytes + w * L.warp_bytes;
-    WarpView v;
-    v.bundle = (float4 *)(b + L.o_bundle);
-    v.axis = (float4 *)(b + L.o_axis);
-    v.Xx = (float *)(b + L.o_X);
-    v.Xy = v.Xx + L.nmax;
-    v.Xz = v.Xy + L.nmax;
-    v.Bx = (float *)(b + L.o_best);
-    v.By = v.Bx + L.nmax;
-    v.Bz = v.By + L.nmax;
-    v.tcur = (uint8_t *)(b + L.o_tcur);
-    v.tbest = (uint8_t *)(b + L.o_tbest);
-    return v;
-}
-
-// ------------------------------------------------------------------ one torsion decision
-// Sweeps torsional bond k of the pose held by this warp, applies the chosen
-// step and returns it (0..35).  lane owns step `lane` (cos cl, sin sl) and, in
-// the tail, step 32 + (lane & 3) (cos ct, sin st).
-//
-// Bundle entry of a moving atom (index space = centred grid units + c0):
-//   q0 = (P.x, P.y, P.z, e1.x)      P = circle centre in index space
-//   q1 = (e1.y, e1.z, e2.x, e2.y)
-//   q2 = (e2.z, |e1|^2, inside, 0)  inside = 1 when the whole circle is in the box
-//   q3 = (p.x, p.y, p.z, 0)         p = circle centre in centred grid units
-__device__ int sweep_bond(const DockArgs &A, const GridK &G, const CtaView &cv, const WarpView &wv, int N, int R,
-                          int k, int lane, float cl, float sl, float ct, float st) {
-    const int b = cv.rch[k], a = cv.par[b], e = cv.rend[k];
-    const int m = e - b - 1;
-    if (m <= 0) return 0;  // nothing moves: every step scores 0, step 0 wins
-
-    const float xbx = wv.Xx[b], xby = wv.Xy[b], xbz = wv.Xz[b];
-    const float4 ax = wv.axis[k];
-    const float inv = rnorm3df(ax.x, ax.y, ax.z);
-    const float ux = ax.x * inv, uy = ax.y * inv, uz = ax.z * inv;
-    const float c0 = A.pocket.c0, lim = G.gmax - 1e-3f;
-    const float dc2 = A.dc2g;
-    const int nF = N - (e - b);  // atoms outside subtree(b): [0, b) and [e, N)
-
-    float acc = 0.0f, acc_t = 0.0f;
-    bool clash_lo = false, clash_hi = false;
-    for (int base = b + 1; base < e; base += 32) {
-        const int cnt = min(32, e - base);
-        if (lane < cnt) {
-            const int i = base + lane;
-            const float dx = wv.Xx[i] - xbx, dy = wv.Xy[i] - xby, dz = wv.Xz[i] - xbz;
-            const float w = fmaf(ux, dx, fmaf(uy, dy, uz * dz));
-            const float px = fmaf(w, ux, xbx), py = fmaf(w, uy, xby), pz = fmaf(w, uz, xbz);
-            const float e1x = fmaf(-w, ux, dx), e1y = fmaf(-w, uy, dy), e1z = fmaf(-w, uz, dz);
-            const float e2x = fmaf(uy, dz, -uz * dy), e2y = fmaf(uz, dx, -ux * dz), e2z = fmaf(ux, dy, -uy * dx);
-            const float Px = px + c0, Py = py + c0, Pz = pz + c0;
-            const float rx = fabsf(e1x) + fabsf(e2x), ry = fabsf(e1y) + fabsf(e2y), rz = fabsf(e1z) + fabsf(e2z);
-            const bool inside = Px - rx >= 1e-3f && Px + rx <= lim && Py - ry >= 1e-3f && Py + ry <= lim &&
-                                Pz - rz >= 1e-3f && Pz + rz <= lim;
-            float4 *q = wv.bundle + 4 * lane;
-            q[0] = make_float4(Px, Py, Pz, e1x);
-            q[1] = make_float4(e1y, e1z, e2x, e2y);
-            q[2] = make_float4(e2z, fmaf(e1x, e1x, fmaf(e1y, e1y, e1z * e1z)), inside ? 1.0f : 0.0f, 0.0f);
-            q[3] = make_float4(px, py, pz, 0.0f);
-        }
-        __syncwarp();
-        // steps 0..31: lane t scores step t for every atom of the bundle
-#pragma unroll 4
-        for (int t = 0; t < cnt; ++t) {
-            const float4 q0 = wv.bundle[4 * t], q1 = wv.bundle[4 * t + 1], q2 = wv.bundle[4 * t + 2];
-            const float gx = fmaf(q1.z, sl, fmaf(q0.w, cl, q0.x));
-            const float gy = fmaf(q1.w, sl, fmaf(q1.x, cl, q0.y));
-            const float gz = fmaf(q2.x, sl, fmaf(q1.y, cl, q0.z));
-            acc += (q2.z != 0.0f) ? lookup_in(G, gx, gy, gz) : lookup_clamped(G, gx, gy, gz);
-        }
-        // steps 32..35: lane scores step 32 + (lane & 3) for atoms lane>>2, +8, ...
-        for (int t = lane >> 2; t < cnt; t += 8) {
-            const float4 q0 = wv.bundle[4 * t], q1 = wv.bundle[4 * t + 1], q2 = wv.bundle[4 * t + 2];
-            const float gx = fmaf(q1.z, st, fmaf(q0.w, ct, q0.x));
-            const float gy = fmaf(q1.w, st, fmaf(q1.x, ct, q0.y));
-            const float gz = fmaf(q2.x, st, fmaf(q1.y, ct, q0.z));
-            acc_t += lookup_clamped(G, gx, gy, gz);
-        }
-        // clash pairs (bundle atom ti, fixed atom jj), flattened over the warp
-        const int npairs = cnt * nF;
-        int ti = lane / nF, jj = lane - (lane / nF) * nF;
-        for (int pb = 0; pb < npairs; pb += 32) {
-            bool flag = false;
-            float C = 0.0f, A2 = 0.0f, B2 = 0.0f;
-            if (pb + lane < npairs) {
-                const int j = jj < b ? jj : jj + (e - b);
-                const float4 *q = wv.bundle + 4 * ti;
-                const float4 q0 = q[0], q1 = q[1], q2 = q[2], q3 = q[3];
-                const float wx = q3.x - wv.Xx[j], wy = q3.y - wv.Xy[j], wz = q3.z - wv.Xz[j];
-                const float aa = fmaf(wx, q0.w, fmaf(wy, q1.x, wz * q1.y));
-                const float bb = fmaf(wx, q1.z, fmaf(wy, q1.w, wz * q2.x));
-                C = fmaf(wx, wx, fmaf(wy, wy, fmaf(wz, wz, q2.y)));
-                const float T = C - dc2;
-                const float s2 = fmaf(aa, aa, bb * bb);
-                // the circle comes within d_clash of j iff T < 2 sqrt(a^2 + b^2)
-                flag = (T <= 0.0f || T * T < 4.0004f * s2) && !(j == a && cv.par[base + ti] == b);
-                A2 = 2.0f * aa;
-                B2 = 2.0f * bb;
-            }
-            unsigned msk = __ballot_sync(LG_FULL, flag);
-            while (msk) {
-                const int src = __ffs(msk) - 1;
-                msk &= msk - 1;
-                const float Cs = __shfl_sync(LG_FULL, C, src);
-                const float As = __shfl_sync(LG_FULL, A2, src);
-                const float Bs = __shfl_sync(LG_FULL, B2, src);
-                clash_lo |= fmaf(Bs, sl, fmaf(As, cl, Cs)) < dc2;
-                clash_hi |= fmaf(Bs, st, fmaf(As, ct, Cs)) < dc2;
-            }
-            jj += 32;
-            while (jj >= nF) {
-                jj -= nF;
-                ++ti;
-            }
-        }
-        __syncwarp();
-    }
-    acc_t += __shfl_xor_sync(LG_FULL, acc_t, 4);
-    acc_t += __shfl_xor_sync(LG_FULL, acc_t, 8);
-    acc_t += __shfl_xor_sync(LG_FULL, acc_t, 16);
-    if (lane == 0) clash_lo = false;  // step 0 (the current pose) is always admissible
-
-    // highest-scoring admissible step, lowest step on ties
-    float bs = clash_lo ? -INFINITY : acc;
-    int ba = clash_lo ? 1024 : lane;
-    if (lane < 4 && !clash_hi && acc_t > bs) {  // equal scores keep the lower step (lane < 32 + lane)
-        bs = acc_t;
-        ba = 32 + lane;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const float os = __shfl_xor_sync(LG_FULL, bs, o);
-        const int oa = __shfl_xor_sync(LG_FULL, ba, o);
-        if (os > bs || (os == bs && oa < ba)) {
-            bs = os;
-            ba = oa;
-        }
-    }
-    // every lane holds the same winner; take lane 0's so control flow stays
-    // warp-uniform whatever the scores are
-    const int t = __shfl_sync(LG_FULL, ba, 0);
-    if (t <= 0 || t >= LG_ANGLE_STEPS) return 0;
-
-    const float c = c_cos[t], s = c_sin[t];
-    for (int i = b + 1 + lane; i < e; i += 32) {
-        const float dx = wv.Xx[i] - xbx, dy = wv.Xy[i] - xby, dz = wv.Xz[i] - xbz;
-        const float w = fmaf(ux, dx, fmaf(uy, dy, uz * dz));
-        const float e1x = fmaf(-w, ux, dx), e1y = fmaf(-w, uy, dy), e1z = fmaf(-w, uz, dz);
-        const float e2x = fmaf(uy, dz, -uz * dy), e2y = fmaf(uz, dx, -ux * dz), e2z = fmaf(ux, dy, -uy * dx);
-        wv.Xx[i] = fmaf(e2x, s, fmaf(e1x, c, fmaf(w, ux, xbx)));
-        wv.Xy[i] = fmaf(e2y, s, fmaf(e1y, c, fmaf(w, uy, xby)));
-        wv.Xz[i] = fmaf(e2z, s, fmaf(e1z, c, fmaf(w, uz, xbz)));
-    }
-    // bond axes further down the subtree turn with it
-    for (int kk = k + 1 + lane; kk < R; kk += 32) {
-        if (cv.rch[kk] < e) {
-            const float4 v = wv.axis[kk];
-            const float uv = fmaf(ux, v.x, fmaf(uy, v.y, uz * v.z));
-            const float cx = fmaf(uy, v.z, -uz * v.y), cy = fmaf(uz, v.x, -ux * v.z), cz = fmaf(ux, v.y, -uy * v.x);
-            const float k1 = uv * (1.0f - c);
-            wv.axis[kk] = make_float4(fmaf(cx, s, fmaf(v.x, c, k1 * ux)), fmaf(cy, s, fmaf(v.y, c, k1 * uy)),
-                                      fmaf(cz, s, fmaf(v.z, c, k1 * uz)), 0.0f);
-        }
-    }
-    __syncwarp();
-    return t;
-}
-
-// ------------------------------------------------------------------ one ligand, one CTA
-__device__ void dock_ligand_cta(const DockArgs &A, int l, char *sm) {
-    const Layout &Ly = A.ly;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, W = blockDim.x >> 5;
-    if (A.out.status[l] != LG_OK) return;  // rejected by the preparation kernel (uniform)
-    const CtaView cv = cta_view(sm, Ly);
-    const WarpView wv = warp_view(sm, Ly, warp);
+// Stage ligand l: centroid-relative coordinates in grid units (FP64
+// difference), parents, per-atom (type weight, charge), torsional children,
+// subtree ends and input bond vectors in grid units.
+__device__ __forceinline__ void stage_ligand(const DockArgs &A, const CtaView &cv, int l, int a0, int N, int r0, int R) {
     const BatchDev &B = A.batch;
     const PocketDev &Pk = A.pocket;
-    const int a0 = B.atom_off[l], N = B.atom_off[l + 1] - a0;
-    const int r0 = B.rot_off[l], R = B.rot_off[l + 1] - r0;
-    const int S = A.S, P = A.P;
-
-    // stage the ligand: centroid-relative coordinates in grid units (FP64
-    // difference), topology, per-atom weights, bond vectors
-    {
-        const double cx = A.scr.centroid[3 * l], cy = A.scr.centroid[3 * l + 1], cz = A.scr.centroid[3 * l + 2];
-        const double ih = (double)Pk.inv_h;
-        for (int i = tid; i < N; i += blockDim.x) {
-            cv.d0x[i] = (float)(((double)B.x[a0 + i] - cx) * ih);
-            cv.d0y[i] = (float)(((double)B.y[a0 + i] - cy) * ih);
-            cv.d0z[i] = (float)(((double)B.z[a0 + i] - cz) * ih);
-            cv.par[i] = B.parent[a0 + i];
-            cv.wq[i] = make_float2(Pk.type_w[B.type[a0 + i]], B.q[a0 + i]);
-        }
-        for (int k = tid; k < R; k += blockDim.x) {
-            const int b = B.rot_child[r0 + k], p = B.parent[a0 + b];
-            cv.rch[k] = b;
-            cv.rend[k] = A.scr.rot_end[(size_t)l * A.rmax_lim + k];
-            cv.dv[k] = make_float4((B.x[a0 + b] - B.x[a0 + p]) * Pk.inv_h, (B.y[a0 + b] - B.y[a0 + p]) * Pk.inv_h,
-                                   (B.z[a0 + b] - B.z[a0 + p]) * Pk.inv_h, 0.0f);
-        }
+    const double cx = A.scr.centroid[3 * l], cy = A.scr.centroid[3 * l + 1], cz = A.scr.centroid[3 * l + 2];
+    const double ih = (double)Pk.inv_h;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        cv.d0x[i] = (float)(((double)B.x[a0 + i] - cx) * ih);
+        cv.d0y[i] = (float)(((double)B.y[a0 + i] - cy) * ih);
+        cv.d0z[i] = (float)(((double)B.z[a0 + i] - cz) * ih);
+        cv.par[i] = B.parent[a0 + i];
+        cv.wq[i] = make_float2(Pk.type_w[B.type[a0 + i]], B.q[a0 + i]);
     }
+    for (int k = threadIdx.x; k < R; k += blockDim.x) {
+        const int b = B.rot_child[r0 + k], p = B.parent[a0 + b];
+        cv.rch[k] = b;
+        cv.rend[k] = A.scr.rot_end[(size_t)l * A.rmax_lim + k];
+        cv.dv[k] = make_float4((B.x[a0 + b] - B.x[a0 + p]) * Pk.inv_h, (B.y[a0 + b] - B.y[a0 + p]) * Pk.inv_h,
+                               (B.z[a0 + b] - B.z[a0 + p]) * Pk.inv_h, 0.0f);
+    }
+}
+
+// Best restart over the CTA's warps (lowest E, then lowest restart) and the
+// ligand's outputs.  Bx/By/Bz/tbest of the winning warp hold its best pose and
+// decisions.  Returns after a CTA barrier.
+template <typename BestOf>
+__device__ __forceinline__ void finish_ligand(const DockArgs &A, const CtaView &cv, int l, int a0, int N, int r0,
+                                              int PR, BestOf best_of) {
     __syncthreads();
-
-    // per-lane torsion steps: lane t owns step t, and step 32 + (t & 3) in the tail
-    const float cl = c_cos[lane], sl = c_sin[lane];
-    const float ct = c_cos[32 + (lane & 3)], st = c_sin[32 + (lane & 3)];
-    const uint64_t uid = B.uid[l];
-    const uint2 key = make_uint2(A.seed_lo, A.seed_hi);
-    const GridK Go = grid_k(Pk, Pk.cell_o), Gve = grid_k(Pk, Pk.cell_ve);
-    const int PR = P * R;
-
-    double bestE = INFINITY;
-    int bestR = -1;
-    for (int r = warp; r < S; r += W) {
-        // 1. restart pose
-        const uint4 x4 = philox4x32_10(make_uint4((uint32_t)uid, (uint32_t)(uid >> 32), (uint32_t)r, 0u), key);
-        const float u0 = (float)(x4.x >> 8) * 5.9604644775390625e-08f;  // 2^-24
-        const float u1 = (float)(x4.y >> 8) * 5.9604644775390625e-08f;
-        const float u2 = (float)(x4.z >> 8) * 5.9604644775390625e-08f;
-        const float s1 = sqrtf(1.0f - u0), s2 = sqrtf(u0);
-        float sn1, cs1, sn2, cs2;
-        sincospif(2.0f * u1, &sn1, &cs1);
-        sincospif(2.0f * u2, &sn2, &cs2);
-        const float qx = s1 * sn1, qy = s1 * cs1, qz = s2 * sn2, qw = s2 * cs2;
-        const float R00 = 1.0f - 2.0f * (qy * qy + qz * qz), R01 = 2.0f * (qx * qy - qw * qz), R02 = 2.0f * (qx * qz + qw * qy);
-        const float R10 = 2.0f * (qx * qy + qw * qz), R11 = 1.0f - 2.0f * (qx * qx + qz * qz), R12 = 2.0f * (qy * qz - qw * qx);
-        const float R20 = 2.0f * (qx * qz - qw * qy), R21 = 2.0f * (qy * qz + qw * qx), R22 = 1.0f - 2.0f * (qx * qx + qy * qy);
-        const uint32_t ppi = (uint32_t)(((uint64_t)(x4.w >> 8) * (uint64_t)Pk.n_pp) >> 24);
-        const float4 pp = __ldg(Pk.pp + ppi);
-        for (int i = lane; i < N; i += 32) {
-            const float vx = cv.d0x[i], vy = cv.d0y[i], vz = cv.d0z[i];
-            wv.Xx[i] = fmaf(R00, vx, fmaf(R01, vy, fmaf(R02, vz, pp.x)));
-            wv.Xy[i] = fmaf(R10, vx, fmaf(R11, vy, fmaf(R12, vz, pp.y)));
-            wv.Xz[i] = fmaf(R20, vx, fmaf(R21, vy, fmaf(R22, vz, pp.z)));
-        }
-        for (int k = lane; k < R; k += 32) {
-            const float4 v = cv.dv[k];
-            wv.axis[k] = make_float4(fmaf(R00, v.x, fmaf(R01, v.y, R02 * v.z)), fmaf(R10, v.x, fmaf(R11, v.y, R12 * v.z)),
-                                     fmaf(R20, v.x, fmaf(R21, v.y, R22 * v.z)), 0.0f);
-        }
-        __syncwarp();
-        // 2. greedy torsion sweep
-        for (int ps = 0; ps < P; ++ps)
-            for (int k = 0; k < R; ++k) {
-                const int t = sweep_bond(A, Go, cv, wv, N, R, k, lane, cl, sl, ct, st);
-                if (lane == 0) wv.tcur[ps * R + k] = (uint8_t)t;
-            }
-        __syncwarp();
-        // 3. pose score: FP32 per-atom terms, FP64 sum
-        double E = 0.0;
-        for (int i = lane; i < N; i += 32) {
-            const float2 wq = cv.wq[i];
-            E += (double)atom_energy(Pk, Gve, wv.Xx[i], wv.Xy[i], wv.Xz[i], wq.x, wq.y);
-        }
-        E = warp_sum_d(E);
-        if (A.out.restart_score && lane == 0) A.out.restart_score[(size_t)l * S + r] = E;
-        if (A.out.restart_tors)
-            for (int t = lane; t < PR; t += 32) A.out.restart_tors[(size_t)S * P * r0 + (size_t)r * PR + t] = wv.tcur[t];
-        // 4. best restart of this warp (restarts visited in ascending order)
-        if (E < bestE) {
-            bestE = E;
-            bestR = r;
-            for (int t = lane; t < PR; t += 32) wv.tbest[t] = wv.tcur[t];
-            if (Ly.want_pose)
-                for (int i = lane; i < N; i += 32) {
-                    wv.Bx[i] = wv.Xx[i];
-                    wv.By[i] = wv.Xy[i];
-                    wv.Bz[i] = wv.Xz[i];
-                }
-        }
-        __syncwarp();
-    }
-    if (lane == 0) {
-        cv.wE[warp] = bestE;
-        cv.wR[warp] = bestR;
-    }
-    __syncthreads();
-    // best restart over warps: lowest E, then lowest restart
-    int bw = -1;
+    const int W = blockDim.x >> 5, tid = threadIdx.x;
+    int bw = -1, br = 0x7fffffff;
     double be = INFINITY;
-    int br = 0x7fffffff;
     for (int w = 0; w < W; ++w) {
         const int rr = cv.wR[w];
         if (rr < 0) continue;
@@ -471,35 +122,553 @@ __device__ void dock_ligand_cta(const DockArgs &A, int l, char *sm) {
             A.out.status[l] = LG_EINVAL;
         }
     } else {
-        const WarpView bv = warp_view(sm, Ly, bw);
+        const float *Bx, *By, *Bz;
+        const uint8_t *tb;
+        best_of(bw, Bx, By, Bz, tb);
         if (tid == 0) {
             A.out.score[l] = be;
             A.out.best_restart[l] = br;
         }
         if (A.out.tors_idx)
-            for (int t = tid; t < PR; t += blockDim.x) A.out.tors_idx[(size_t)P * r0 + t] = bv.tbest[t];
-        if (A.out.pose && Ly.want_pose) {
-            const float3 c = Pk.center;
-            const float h = Pk.h;
+            for (int t = tid; t < PR; t += blockDim.x) A.out.tors_idx[(size_t)A.P * r0 + t] = tb[t];
+        if (A.out.pose && A.ly.want_pose) {
+            const float3 c = A.pocket.center;
+            const float h = A.pocket.h;
             for (int i = tid; i < N; i += blockDim.x) {
                 float *o = A.out.pose + 3 * (size_t)(a0 + i);
-                o[0] = fmaf(bv.Bx[i], h, c.x);
-                o[1] = fmaf(bv.By[i], h, c.y);
-                o[2] = fmaf(bv.Bz[i], h, c.z);
+                o[0] = fmaf(Bx[i], h, c.x);
+                o[1] = fmaf(By[i], h, c.y);
+                o[2] = fmaf(Bz[i], h, c.z);
             }
         }
     }
     __syncthreads();
 }
 
-// ------------------------------------------------------------------ kernels
+// ================================================================== plain form
+struct WarpView {
+    float4 *bundle;  // 32 atoms x 4 float4 (see sweep_bond_plain); also per-atom energy terms
+    float4 *axis;
+    float *Xx, *Xy, *Xz;
+    float *Bx, *By, *Bz;
+    uint8_t *tcur, *tbest;
+};
+
+__device__ __forceinline__ WarpView warp_view(char *sm, const Layout &L, int w) {
+    char *b = sm + L.cta_bytes + w * L.warp_bytes;
+    WarpView v;
+    v.bundle = (float4 *)(b + L.o_bundle);
+    v.axis = (float4 *)(b + L.o_axis);
+    v.Xx = (float *)(b + L.o_X);
+    v.Xy = v.Xx + L.nmax;
+    v.Xz = v.Xy + L.nmax;
+    v.Bx = (float *)(b + L.o_best);
+    v.By = v.Bx + L.nmax;
+    v.Bz = v.By + L.nmax;
+    v.tcur = (uint8_t *)(b + L.o_tcur);
+    v.tbest = (uint8_t *)(b + L.o_tbest);
+    return v;
+}
+
+// One torsion decision of the warp's restart.  Bundle entry of a moving atom:
+//   q0 = (P.x, P.y, P.z, e1.x), q1 = (e1.y, e1.z, e2.x, e2.y),
+//   q2 = (e2.z, r2, inside, 0), q3 = (p.x, p.y, p.z, 0).
+__device__ int sweep_bond_plain(const DockArgs &A, const GridK &G, const CtaView &cv, const WarpView &wv, int N,
+                                int R, int k, int lane, float cl, float sl, float ct, float st) {
+    const int b = cv.rch[k], a = cv.par[b], e = cv.rend[k];
+    const int m = e - b - 1;
+    if (m <= 0) return 0;  // nothing moves: every step scores 0, step 0 wins
+
+    const float xbx = wv.Xx[b], xby = wv.Xy[b], xbz = wv.Xz[b];
+    const float3 u = unit_axis(wv.axis[k]);
+    const float dc2 = A.dc2g;
+    const int nF = N - (e - b);  // atoms outside subtree(b): [0, b) and [e, N)
+
+    float acc = 0.0f, acc_t = 0.0f;
+    bool clash_lo = false, clash_hi = false;
+    for (int base = b + 1; base < e; base += 32) {
+        const int cnt = min(32, e - base);
+        if (lane < cnt) {
+            const int i = base + lane;
+            const Circle C = make_circle(wv.Xx[i], wv.Xy[i], wv.Xz[i], xbx, xby, xbz, u, A.pocket.c0, G.gmax);
+            float4 *q = wv.bundle + 4 * lane;
+            q[0] = make_float4(C.Px, C.Py, C.Pz, C.e1x);
+            q[1] = make_float4(C.e1y, C.e1z, C.e2x, C.e2y);
+            q[2] = make_float4(C.e2z, C.r2, C.inside ? 1.0f : 0.0f, 0.0f);
+            q[3] = make_float4(C.px, C.py, C.pz, 0.0f);
+        }
+        __syncwarp();
+        for (int t = 0; t < cnt; ++t) {
+            const float4 q0 = wv.bundle[4 * t], q1 = wv.bundle[4 * t + 1], q2 = wv.bundle[4 * t + 2];
+            const float3 g = circle_index(q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w, q2.x, cl, sl);
+            acc += (q2.z != 0.0f) ? lookup_in(G, g.x, g.y, g.z) : lookup_clamped(G, g.x, g.y, g.z);
+        }
+        if (lane < 4)  // steps 32..35, atoms in order
+            for (int t = 0; t < cnt; ++t) {
+                const float4 q0 = wv.bundle[4 * t], q1 = wv.bundle[4 * t + 1], q2 = wv.bundle[4 * t + 2];
+                const float3 g = circle_index(q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w, q2.x, ct, st);
+                acc_t += lookup_clamped(G, g.x, g.y, g.z);
+            }
+        // clash pairs (bundle atom ti, fixed atom jj), flattened over the warp
+        const int npairs = cnt * nF;
+        int ti = lane / nF, jj = lane - (lane / nF) * nF;
+        for (int pb = 0; pb < npairs; pb += 32) {
+            PairC q;
+            q.near = false;
+            q.C = q.A2 = q.B2 = 0.0f;
+            if (pb + lane < npairs) {
+                const int j = jj < b ? jj : jj + (e - b);
+                if (!(j == a && cv.par[base + ti] == b)) {  // two bonds apart through the bond itself
+                    const float4 *qq = wv.bundle + 4 * ti;
+                    const float4 q0 = qq[0], q1 = qq[1], q2 = qq[2], q3 = qq[3];
+                    q = pair_coeffs(q3.x, q3.y, q3.z, q0.w, q1.x, q1.y, q1.z, q1.w, q2.x, q2.y, wv.Xx[j], wv.Xy[j],
+                                    wv.Xz[j], dc2);
+                }
+            }
+            unsigned msk = __ballot_sync(LG_FULL, q.near);
+            while (msk) {
+                const int src = __ffs(msk) - 1;
+                msk &= msk - 1;
+                const float Cs = __shfl_sync(LG_FULL, q.C, src);
+                const float As = __shfl_sync(LG_FULL, q.A2, src);
+                const float Bs = __shfl_sync(LG_FULL, q.B2, src);
+                clash_lo |= pair_clash(Cs, As, Bs, cl, sl, dc2);
+                clash_hi |= pair_clash(Cs, As, Bs, ct, st, dc2);
+            }
+            jj += 32;
+            while (jj >= nF) {
+                jj -= nF;
+                ++ti;
+            }
+        }
+        __syncwarp();
+    }
+    if (lane == 0) clash_lo = false;  // step 0 (the current pose) is always admissible
+
+    // highest-scoring admissible step, lowest step on ties
+    float bs = clash_lo ? -INFINITY : acc;
+    int ba = clash_lo ? 1024 : lane;
+    if (lane < 4 && !clash_hi && acc_t > bs) {
+        bs = acc_t;
+        ba = 32 + lane;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float os = __shfl_xor_sync(LG_FULL, bs, o);
+        const int oa = __shfl_xor_sync(LG_FULL, ba, o);
+        if (better(os, oa, bs, ba)) {
+            bs = os;
+            ba = oa;
+        }
+    }
+    const int t = __shfl_sync(LG_FULL, ba, 0);  // lane 0's copy keeps control flow warp-uniform
+    if (t <= 0 || t >= LG_ANGLE_STEPS) return 0;
+
+    const float c = c_cos[t], s = c_sin[t];
+    for (int i = b + 1 + lane; i < e; i += 32) {
+        const float3 x = rotate_point(wv.Xx[i], wv.Xy[i], wv.Xz[i], xbx, xby, xbz, u, c, s);
+        wv.Xx[i] = x.x;
+        wv.Xy[i] = x.y;
+        wv.Xz[i] = x.z;
+    }
+    for (int kk = k + 1 + lane; kk < R; kk += 32)  // bond axes further down turn with it
+        if (cv.rch[kk] < e) wv.axis[kk] = rotate_vec(wv.axis[kk], u, c, s);
+    __syncwarp();
+    return t;
+}
+
 __global__ void __launch_bounds__(1024) k_dock_plain(const __grid_constant__ DockArgs A, int l) {
     extern __shared__ __align__(16) char sm[];
-    dock_ligand_cta(A, l, sm);
+    if (A.out.status[l] != LG_OK) return;  // rejected by the preparation kernel
+    const Layout &Ly = A.ly;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
+    const CtaView cv = cta_view(sm, Ly);
+    const WarpView wv = warp_view(sm, Ly, warp);
+    const BatchDev &B = A.batch;
+    const PocketDev &Pk = A.pocket;
+    const int a0 = B.atom_off[l], N = B.atom_off[l + 1] - a0;
+    const int r0 = B.rot_off[l], R = B.rot_off[l + 1] - r0;
+    const int S = A.S, P = A.P, PR = P * R;
+    stage_ligand(A, cv, l, a0, N, r0, R);
+    __syncthreads();
+
+    const float cl = c_cos[lane], sl = c_sin[lane];
+    const float ct = c_cos[32 + (lane & 3)], st = c_sin[32 + (lane & 3)];
+    const uint64_t uid = B.uid[l];
+    const uint2 key = make_uint2(A.seed_lo, A.seed_hi);
+    const GridK Go = grid_k(Pk, Pk.cell_o), Gve = grid_k(Pk, Pk.cell_ve);
+    float *eterm = (float *)wv.bundle;
+
+    double bestE = INFINITY;
+    int bestR = -1;
+    for (int r = warp; r < S; r += W) {
+        const Pose pose = restart_pose(uid, (uint32_t)r, key, Pk.n_pp);
+        const float4 pp = __ldg(Pk.pp + pose.pp);
+        for (int i = lane; i < N; i += 32) {
+            const float3 x = rot_add(pose.R, cv.d0x[i], cv.d0y[i], cv.d0z[i], pp.x, pp.y, pp.z);
+            wv.Xx[i] = x.x;
+            wv.Xy[i] = x.y;
+            wv.Xz[i] = x.z;
+        }
+        for (int k = lane; k < R; k += 32) {
+            const float4 v = cv.dv[k];
+            const float3 w = rot_vec(pose.R, v.x, v.y, v.z);
+            wv.axis[k] = make_float4(w.x, w.y, w.z, 0.0f);
+        }
+        __syncwarp();
+        for (int ps = 0; ps < P; ++ps)
+            for (int k = 0; k < R; ++k) {
+                const int t = sweep_bond_plain(A, Go, cv, wv, N, R, k, lane, cl, sl, ct, st);
+                if (lane == 0) wv.tcur[ps * R + k] = (uint8_t)t;
+            }
+        // pose score: FP32 per-atom terms; FP64 sums s_g over atoms i = g (mod 4)
+        // in order, combined as (s0 + s1) + (s2 + s3)
+        for (int i = lane; i < N; i += 32) {
+            const float2 wq = cv.wq[i];
+            eterm[i] = atom_energy(Pk, Gve, wv.Xx[i], wv.Xy[i], wv.Xz[i], wq.x, wq.y);
+        }
+        __syncwarp();
+        double E = 0.0;
+        if (lane < 4)
+            for (int i = lane; i < N; i += 4) E += (double)eterm[i];
+        E += __shfl_xor_sync(LG_FULL, E, 1);
+        E += __shfl_xor_sync(LG_FULL, E, 2);
+        E = __shfl_sync(LG_FULL, E, 0);
+        if (A.out.restart_score && lane == 0) A.out.restart_score[(size_t)l * S + r] = E;
+        if (A.out.restart_tors)
+            for (int t = lane; t < PR; t += 32) A.out.restart_tors[(size_t)S * P * r0 + (size_t)r * PR + t] = wv.tcur[t];
+        if (E < bestE) {  // restarts visited in ascending order: ties keep the lower one
+            bestE = E;
+            bestR = r;
+            for (int t = lane; t < PR; t += 32) wv.tbest[t] = wv.tcur[t];
+            if (Ly.want_pose)
+                for (int i = lane; i < N; i += 32) {
+                    wv.Bx[i] = wv.Xx[i];
+                    wv.By[i] = wv.Xy[i];
+                    wv.Bz[i] = wv.Xz[i];
+                }
+        }
+        __syncwarp();
+    }
+    if (lane == 0) {
+        cv.wE[warp] = bestE;
+        cv.wR[warp] = bestR;
+    }
+    finish_ligand(A, cv, l, a0, N, r0, PR, [&](int w, const float *&Bx, const float *&By, const float *&Bz,
+                                               const uint8_t *&tb) {
+        const WarpView bv = warp_view(sm, Ly, w);
+        Bx = bv.Bx;
+        By = bv.By;
+        Bz = bv.Bz;
+        tb = bv.tbest;
+    });
+}
+
+// ================================================================== restart-tiled form
+struct RtView {
+    float4 *axis;          // [rmax][8]
+    float *Xx, *Xy, *Xz;   // [nmax][8]
+    float4 *pool;          // [kPoolCap] flagged clash pairs (C, A2, B2, restart slot)
+    unsigned *mask;        // [32] clash bits of each lane's steps
+    uint8_t *near;         // [8][nmax] fixed atoms that can come within d_clash
+    int nstride;
+    float *Bx, *By, *Bz;   // [nmax] best pose of the warp
+    uint8_t *tcur;         // [P*R][8]
+    uint8_t *tbest;        // [P*R]
+};
+
+__device__ __forceinline__ RtView rt_view(char *sm, const Layout &L, const LayoutRT &T, int w) {
+    char *b = sm + L.cta_bytes + w * T.warp_bytes;
+    RtView v;
+    v.axis = (float4 *)(b + T.o_axis);
+    v.Xx = (float *)(b + T.o_X);
+    v.Xy = v.Xx + L.nmax * kTile;
+    v.Xz = v.Xy + L.nmax * kTile;
+    v.pool = (float4 *)(b + T.o_pool);
+    v.mask = (unsigned *)(b + T.o_mask);
+    v.near = (uint8_t *)(b + T.o_near);
+    v.nstride = L.nmax;
+    v.Bx = (float *)(b + T.o_best);
+    v.By = v.Bx + L.nmax;
+    v.Bz = v.By + L.nmax;
+    v.tcur = (uint8_t *)(b + T.o_tcur);
+    v.tbest = (uint8_t *)(b + T.o_tbest);
+    return v;
+}
+
+// Evaluate the pooled flagged pairs: in each round every restart group takes
+// one entry (of any restart) and each of its lanes ORs the clash bits of its
+// own 9 steps into that restart's mask word for the same lane position.
+__device__ __forceinline__ void flush_pool(const RtView &v, int rs, int g, int &pc, const float *cs, const float *sn,
+                                           float dc2) {
+    __syncwarp();
+    for (int base = 0; base < pc; base += kTile) {
+        const int e = base + rs;
+        if (e < pc) {
+            const float4 q = v.pool[e];
+            unsigned bits = 0;
+#pragma unroll
+            for (int j = 0; j < kStepsPerLane; ++j) bits |= (unsigned)pair_clash(q.x, q.y, q.z, cs[j], sn[j], dc2) << j;
+            if (bits) atomicOr(&v.mask[kLanesPerRestart * __float_as_int(q.w) + g], bits);
+        }
+    }
+    __syncwarp();
+    pc = 0;
+}
+
+// One torsion decision for the warp's 8 restarts.  Lane = 4*rs + g: restart
+// slot rs, steps g, g+4, ..., g+32 (cosines cs[], sines sn[]) -- the 4 lanes
+// of a restart score neighbouring steps in the same instruction.  Returns the
+// step chosen for the lane's restart.
+__device__ int sweep_bond_rt(const DockArgs &A, const GridK &G, const CtaView &cv, const RtView &v, int N, int R, int k,
+                             int rs, int g, bool valid, const float *cs, const float *sn) {
+    const int b = cv.rch[k], a = cv.par[b], e = cv.rend[k];
+    const int m = e - b - 1;
+    if (m <= 0) return 0;  // nothing moves: every step scores 0, step 0 wins
+
+    const float xbx = v.Xx[b * kTile + rs], xby = v.Xy[b * kTile + rs], xbz = v.Xz[b * kTile + rs];
+    const float3 u = unit_axis(v.axis[k * kTile + rs]);
+    const float c0 = A.pocket.c0, dc2 = A.dc2g;
+    const int nF = N - (e - b);
+    const int lane = kLanesPerRestart * rs + g;
+    const unsigned gmask = 0xFu << (kLanesPerRestart * rs), below = (1u << lane) - 1u;
+
+    // Every moving atom stays at its distance from xb, so the subtree's circles
+    // lie in the ball of radius max |x_i - xb| about xb: when that ball is in
+    // the grid box for all 8 restarts, no lookup of this decision needs clamping.
+    float rho2 = 0.0f;
+    for (int i = b + 1 + g; i < e; i += kLanesPerRestart) {
+        const float dx = v.Xx[i * kTile + rs] - xbx, dy = v.Xy[i * kTile + rs] - xby, dz = v.Xz[i * kTile + rs] - xbz;
+        rho2 = fmaxf(rho2, fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+    }
+    rho2 = fmaxf(rho2, __shfl_xor_sync(LG_FULL, rho2, 1));
+    rho2 = fmaxf(rho2, __shfl_xor_sync(LG_FULL, rho2, 2));
+    const float rho = sqrtf(rho2) + 1e-2f, lo = 1e-2f, hi = G.gmax - 1e-2f;
+    const bool ball_in = xbx + c0 - rho >= lo && xbx + c0 + rho <= hi && xby + c0 - rho >= lo &&
+                         xby + c0 + rho <= hi && xbz + c0 - rho >= lo && xbz + c0 + rho <= hi;
+    const bool all_in = __all_sync(LG_FULL, ball_in);
+
+    // 1. overlap scores of the lane's 9 steps over all moving atoms (in order)
+    float acc[kStepsPerLane];
+#pragma unroll
+    for (int j = 0; j < kStepsPerLane; ++j) acc[j] = 0.0f;
+    if (all_in) {
+#pragma unroll 2
+        for (int i = b + 1; i < e; ++i) {
+            const Circle C = make_circle(v.Xx[i * kTile + rs], v.Xy[i * kTile + rs], v.Xz[i * kTile + rs], xbx, xby,
+                                         xbz, u, c0, G.gmax);
+#pragma unroll
+            for (int j = 0; j < kStepsPerLane; ++j) {
+                const float3 q = circle_index(C.Px, C.Py, C.Pz, C.e1x, C.e1y, C.e1z, C.e2x, C.e2y, C.e2z, cs[j], sn[j]);
+                acc[j] += lookup_in(G, q.x, q.y, q.z);
+            }
+        }
+    } else {
+#pragma unroll 2
+        for (int i = b + 1; i < e; ++i) {
+            const Circle C = make_circle(v.Xx[i * kTile + rs], v.Xy[i * kTile + rs], v.Xz[i * kTile + rs], xbx, xby,
+                                         xbz, u, c0, G.gmax);
+#pragma unroll
+            for (int j = 0; j < kStepsPerLane; ++j) {
+                const float3 q = circle_index(C.Px, C.Py, C.Pz, C.e1x, C.e1y, C.e1z, C.e2x, C.e2y, C.e2z, cs[j], sn[j]);
+                acc[j] += lookup_clamped(G, q.x, q.y, q.z);
+            }
+        }
+    }
+
+    // 2. clash mask of the lane's 9 steps.  Only fixed atoms within rho +
+    //    d_clash of xb can come within d_clash of a moving atom; for those the
+    //    pairs that can clash somewhere on the circle are pooled over the 8
+    //    restarts and evaluated step by step.
+    const float rlim = sqrtf(rho2) + sqrtf(dc2) + 1e-3f, rlim2 = rlim * rlim;
+    int ncnt = 0;  // near fixed atoms of this restart (same in its 4 lanes)
+    for (int jb = 0; jb < nF; jb += kLanesPerRestart) {
+        const int jj = jb + g;
+        bool nr = false;
+        int j = 0;
+        if (valid && jj < nF) {
+            j = jj < b ? jj : jj + (e - b);
+            const float dx = v.Xx[j * kTile + rs] - xbx, dy = v.Xy[j * kTile + rs] - xby, dz = v.Xz[j * kTile + rs] - xbz;
+            nr = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < rlim2;
+        }
+        const unsigned bal = __ballot_sync(LG_FULL, nr);
+        if (nr) v.near[rs * v.nstride + ncnt + __popc(bal & gmask & below)] = (uint8_t)j;
+        ncnt += __popc(bal & gmask);
+    }
+    v.mask[lane] = 0u;
+    __syncwarp();
+    const int nnear = (int)__reduce_max_sync(LG_FULL, (unsigned)ncnt);
+    int pc = 0;  // pooled pairs (warp-uniform)
+    for (int i = b + 1; i < e && nnear > 0; ++i) {
+        const Circle C = make_circle(v.Xx[i * kTile + rs], v.Xy[i * kTile + rs], v.Xz[i * kTile + rs], xbx, xby, xbz, u,
+                                     c0, G.gmax);
+        const int excl = (cv.par[i] == b) ? a : -1;  // two bonds apart through the bond itself
+        for (int jb = 0; jb < nnear; jb += kLanesPerRestart) {
+            if (pc > kPoolCap - 32) flush_pool(v, rs, g, pc, cs, sn, dc2);
+            const int jj = jb + g;
+            PairC q;
+            q.near = false;
+            if (jj < ncnt) {
+                const int j = v.near[rs * v.nstride + jj];
+                if (j != excl)
+                    q = pair_coeffs(C.px, C.py, C.pz, C.e1x, C.e1y, C.e1z, C.e2x, C.e2y, C.e2z, C.r2, v.Xx[j * kTile + rs],
+                                    v.Xy[j * kTile + rs], v.Xz[j * kTile + rs], dc2);
+            }
+            const unsigned bal = __ballot_sync(LG_FULL, q.near);
+            if (q.near) v.pool[pc + __popc(bal & below)] = make_float4(q.C, q.A2, q.B2, __int_as_float(rs));
+            pc += __popc(bal);
+        }
+    }
+    flush_pool(v, rs, g, pc, cs, sn, dc2);
+    unsigned clash = v.mask[lane];  // bit j: step 4j + g clashes
+    if (g == 0) clash &= ~1u;        // step 0 (the current pose) is always admissible
+
+    // highest-scoring admissible step of the restart, lowest step on ties
+    float bs = -INFINITY;
+    int bt = 1024;
+#pragma unroll
+    for (int j = 0; j < kStepsPerLane; ++j)
+        if (!((clash >> j) & 1u) && acc[j] > bs) {
+            bs = acc[j];
+            bt = kLanesPerRestart * j + g;
+        }
+#pragma unroll
+    for (int o = 1; o < kLanesPerRestart; o <<= 1) {
+        const float os = __shfl_xor_sync(LG_FULL, bs, o);
+        const int ot = __shfl_xor_sync(LG_FULL, bt, o);
+        if (better(os, ot, bs, bt)) {
+            bs = os;
+            bt = ot;
+        }
+    }
+    const int t = (bt > 0 && bt < LG_ANGLE_STEPS) ? bt : 0;
+    if (t != 0) {
+        const float c = c_cos[t], s = c_sin[t];
+        for (int i = b + 1 + g; i < e; i += kLanesPerRestart) {
+            const float3 x = rotate_point(v.Xx[i * kTile + rs], v.Xy[i * kTile + rs], v.Xz[i * kTile + rs], xbx, xby,
+                                          xbz, u, c, s);
+            v.Xx[i * kTile + rs] = x.x;
+            v.Xy[i * kTile + rs] = x.y;
+            v.Xz[i * kTile + rs] = x.z;
+        }
+        for (int kk = k + 1 + g; kk < R; kk += kLanesPerRestart)
+            if (cv.rch[kk] < e) v.axis[kk * kTile + rs] = rotate_vec(v.axis[kk * kTile + rs], u, c, s);
+    }
+    __syncwarp();
+    return t;
+}
+
+__device__ void dock_ligand_rt(const DockArgs &A, int l, char *sm) {
+    if (A.out.status[l] != LG_OK) return;  // rejected by the preparation kernel (uniform)
+    const Layout &Ly = A.ly;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
+    const int rs = lane / kLanesPerRestart, g = lane % kLanesPerRestart;
+    const CtaView cv = cta_view(sm, Ly);
+    const RtView v = rt_view(sm, Ly, A.lrt, warp);
+    const BatchDev &B = A.batch;
+    const PocketDev &Pk = A.pocket;
+    const int a0 = B.atom_off[l], N = B.atom_off[l + 1] - a0;
+    const int r0 = B.rot_off[l], R = B.rot_off[l + 1] - r0;
+    const int S = A.S, P = A.P, PR = P * R;
+    stage_ligand(A, cv, l, a0, N, r0, R);
+    __syncthreads();
+
+    float cs[kStepsPerLane], sn[kStepsPerLane];
+#pragma unroll
+    for (int j = 0; j < kStepsPerLane; ++j) {
+        cs[j] = c_cos[kLanesPerRestart * j + g];
+        sn[j] = c_sin[kLanesPerRestart * j + g];
+    }
+    const uint64_t uid = B.uid[l];
+    const uint2 key = make_uint2(A.seed_lo, A.seed_hi);
+    const GridK Go = grid_k(Pk, Pk.cell_o), Gve = grid_k(Pk, Pk.cell_ve);
+    const int ntiles = (S + kTile - 1) / kTile;
+
+    double bestE = INFINITY;
+    int bestR = -1;
+    for (int tile = warp; tile < ntiles; tile += W) {
+        const int r = tile * kTile + rs;
+        const bool valid = r < S;
+        // 1. restart poses (the 4 lanes of a restart split its atoms and bonds)
+        const Pose pose = restart_pose(uid, (uint32_t)r, key, Pk.n_pp);
+        const float4 pp = __ldg(Pk.pp + pose.pp);
+        for (int i = g; i < N; i += kLanesPerRestart) {
+            const float3 x = rot_add(pose.R, cv.d0x[i], cv.d0y[i], cv.d0z[i], pp.x, pp.y, pp.z);
+            v.Xx[i * kTile + rs] = x.x;
+            v.Xy[i * kTile + rs] = x.y;
+            v.Xz[i * kTile + rs] = x.z;
+        }
+        for (int k = g; k < R; k += kLanesPerRestart) {
+            const float4 d = cv.dv[k];
+            const float3 w = rot_vec(pose.R, d.x, d.y, d.z);
+            v.axis[k * kTile + rs] = make_float4(w.x, w.y, w.z, 0.0f);
+        }
+        __syncwarp();
+        // 2. greedy torsion sweep
+        for (int ps = 0; ps < P; ++ps)
+            for (int k = 0; k < R; ++k) {
+                const int t = sweep_bond_rt(A, Go, cv, v, N, R, k, rs, g, valid, cs, sn);
+                if (g == 0) v.tcur[(ps * R + k) * kTile + rs] = (uint8_t)t;
+            }
+        __syncwarp();
+        // 3. pose score: FP32 per-atom terms; FP64 sums s_g over atoms i = g
+        //    (mod 4) in order, combined as (s0 + s1) + (s2 + s3)
+        double E = 0.0;
+        for (int i = g; i < N; i += kLanesPerRestart) {
+            const float2 wq = cv.wq[i];
+            E += (double)atom_energy(Pk, Gve, v.Xx[i * kTile + rs], v.Xy[i * kTile + rs], v.Xz[i * kTile + rs], wq.x,
+                                     wq.y);
+        }
+        E += __shfl_xor_sync(LG_FULL, E, 1);
+        E += __shfl_xor_sync(LG_FULL, E, 2);
+        if (valid) {
+            if (A.out.restart_score && g == 0) A.out.restart_score[(size_t)l * S + r] = E;
+            if (A.out.restart_tors)
+                for (int t = g; t < PR; t += kLanesPerRestart)
+                    A.out.restart_tors[(size_t)S * P * r0 + (size_t)r * PR + t] = v.tcur[t * kTile + rs];
+        }
+        // 4. best restart of the tile (lowest E, then lowest restart)
+        double te = valid ? E : INFINITY;
+        int tr = valid ? r : 0x7fffffff;
+#pragma unroll
+        for (int o = kLanesPerRestart; o < 32; o <<= 1) {
+            const double oe = __shfl_xor_sync(LG_FULL, te, o);
+            const int orr = __shfl_xor_sync(LG_FULL, tr, o);
+            if (oe < te || (oe == te && orr < tr)) {
+                te = oe;
+                tr = orr;
+            }
+        }
+        if (tr != 0x7fffffff && (bestR < 0 || te < bestE)) {  // later tiles hold higher restarts
+            bestE = te;
+            bestR = tr;
+            const int ws = tr - tile * kTile;
+            for (int t = lane; t < PR; t += 32) v.tbest[t] = v.tcur[t * kTile + ws];
+            if (Ly.want_pose)
+                for (int i = lane; i < N; i += 32) {
+                    v.Bx[i] = v.Xx[i * kTile + ws];
+                    v.By[i] = v.Xy[i * kTile + ws];
+                    v.Bz[i] = v.Xz[i * kTile + ws];
+                }
+        }
+        __syncwarp();
+    }
+    if (lane == 0) {
+        cv.wE[warp] = bestE;
+        cv.wR[warp] = bestR;
+    }
+    finish_ligand(A, cv, l, a0, N, r0, PR, [&](int w, const float *&Bx, const float *&By, const float *&Bz,
+                                               const uint8_t *&tb) {
+        const RtView bv = rt_view(sm, Ly, A.lrt, w);
+        Bx = bv.Bx;
+        By = bv.By;
+        Bz = bv.Bz;
+        tb = bv.tbest;
+    });
 }
 
 // Persistent: CTAs pull ligands from a device counter in cost order.
-__global__ void __launch_bounds__(1024) k_dock_batched(const __grid_constant__ DockArgs A) {
+__global__ void __launch_bounds__(256) k_dock_batched(const __grid_constant__ DockArgs A) {
     extern __shared__ __align__(16) char sm[];
     __shared__ int s_item;
     for (;;) {
@@ -508,14 +677,14 @@ __global__ void __launch_bounds__(1024) k_dock_batched(const __grid_constant__ D
         const int item = s_item;
         __syncthreads();
         if (item >= A.batch.L) break;
-        const int l = A.order ? A.order[item] : item;
-        dock_ligand_cta(A, l, sm);
+        dock_ligand_rt(A, A.order ? A.order[item] : item, sm);
     }
 }
 
-// Preparation, one thread per ligand: validates the ligand (sizes within the
-// limits, parent[0] = -1, parent[i] < i, contiguous subtrees -- subtree size
-// equals end - start --, types, finite coordinates, torsional children strictly
+// ================================================================== preparation and sorting
+// One thread per ligand: validates the ligand (sizes within the limits,
+// parent[0] = -1, parent[i] < i, contiguous subtrees -- subtree size equals
+// end - start --, types, finite coordinates, torsional children strictly
 // ascending in [1, N-1]), writes the end of every torsional child's subtree,
 // the centroid (FP64) and the ligand's status; with `sort` it also files the
 // ligand into a log-scale cost bucket (4 per octave) of
@@ -622,6 +791,7 @@ __global__ void k_sort_scatter(int L, const int32_t *keys, int32_t *hist, int32_
     if (l < L) order[atomicAdd(&hist[keys[l]], 1)] = l;
 }
 
+// ================================================================== pose scoring and diagnostics
 __global__ void k_score_poses(const __grid_constant__ PocketDev P, int L, const int32_t *atom_off, const float *xyz,
                               const float *q, const uint8_t *type, double *E) {
     const int lane = threadIdx.x & 31;
@@ -653,7 +823,7 @@ __global__ void k_diag_philox(int n, const uint32_t *ctr, const uint32_t *key, u
     out[4 * i + 3] = o.w;
 }
 
-// ------------------------------------------------------------------ host side
+// ================================================================== host side
 static size_t al256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 size_t scratch_bytes(int L, int rmax) {
@@ -705,8 +875,8 @@ cudaError_t launch_dock_plain(const DockArgs &a, int ligand, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_dock_batched(const DockArgs &a, int grid, cudaStream_t s) {
-    k_dock_batched<<<grid, 32 * a.ly.W, a.ly.total, s>>>(a);
+cudaError_t launch_dock_batched(const DockArgs &a, int grid, int smem, cudaStream_t s) {
+    k_dock_batched<<<grid, 32 * a.ly.W, smem, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -161,15 +161,15 @@ int fetch_out(const OutDev &d, const lg_dock_result *o, int L, int S, int P, int
     return LG_OK;
 }
 
-// Warps per CTA for the batched kernel: a divisor of the restart count near
-// 8-10 warps (restarts split evenly), unless the context option fixes it.
+// Warps per CTA for the batched kernel: restart tiles of 8 are spread over
+// the CTA's warps; up to 4 warps, dividing the tile count when possible,
+// unless the context option fixes the count.
 int choose_warps(int S, int opt) {
-    if (opt > 0) return std::min(opt, 32);
-    static const int pref[] = {10, 8, 12, 9, 15, 16, 6, 7, 5, 14, 11, 13};
-    for (int w : pref)
-        if (S % w == 0 && w <= S) return w;
-    if (S <= 16) return std::max(1, S);
-    return 8;
+    const int tiles = (S + kTile - 1) / kTile;
+    if (opt > 0) return std::min(opt, 8);
+    for (int w = std::min(tiles, 4); w >= 1; --w)
+        if (tiles % w == 0) return w;
+    return 1;
 }
 
 // Launch the docking of a device-resident batch on stream s: the preparation
@@ -240,12 +240,14 @@ int dock_device(lg_ctx *ctx, const PocketDev &pk, const BatchDev &bd, const OutD
         st->smem_bytes = a.ly.total;
         return LG_OK;
     }
-    // batched: cost-ordered persistent launch
+    // batched: cost-ordered persistent launch of restart-tiled warps
     int W = choose_warps(a.S, ctx_warps_opt(ctx));
-    int occ = 0;
+    int occ = 0, smem = 0;
     for (;;) {
         a.ly = make_layout(nmax, rmax, a.P, W, want_pose);
-        if ((e = dock_kernel_attributes(W, a.ly.total, &occ)) != cudaSuccess)
+        a.lrt = make_layout_rt(nmax, rmax, a.P, want_pose);
+        smem = a.ly.cta_bytes + W * a.lrt.warp_bytes;
+        if ((e = dock_kernel_attributes(W, smem, &occ)) != cudaSuccess)
             return fail(LG_ECUDA, std::string("dock kernel attributes: ") + cudaGetErrorString(e));
         if (occ > 0 || W == 1) break;
         W = std::max(1, W / 2);
@@ -255,14 +257,14 @@ int dock_device(lg_ctx *ctx, const PocketDev &pk, const BatchDev &bd, const OutD
     a.order = a.scr.order;
     const int grid = std::max(1, std::min(ctx_num_sms(ctx) * occ, L));
     if (timed) cudaEventRecord(tev[0], s);
-    if ((e = launch_dock_batched(a, grid, s)) != cudaSuccess)
+    if ((e = launch_dock_batched(a, grid, smem, s)) != cudaSuccess)
         return fail(LG_ECUDA, std::string("dock launch: ") + cudaGetErrorString(e));
     if (timed) cudaEventRecord(tev[1], s);
     st->launches = launches + 1;
     st->grid = grid;
     st->warps_per_cta = W;
     st->ctas_per_sm = occ;
-    st->smem_bytes = a.ly.total;
+    st->smem_bytes = smem;
     return LG_OK;
 }
 
