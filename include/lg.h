@@ -216,6 +216,31 @@ typedef struct {
 int lg_dock_batch(lg_ctx *ctx, int32_t pocket_id, const lg_ligand_batch *batch, const lg_dock_params *params,
                   lg_dock_result *out, void *stream);
 
+/* Allocation-free docking (the paper has no counterpart to this call).
+ * Some callers cannot let a library allocate device memory: applications that
+ * give all device memory to their own pool allocator at start-up (a cudaMalloc
+ * from outside the pool fails or fragments it), and latency-critical callers
+ * that cannot accept the device-wide synchronisation cudaMalloc / cudaFree may
+ * cause.  This call docks exactly like lg_dock_batch in LG_MODE_BATCHED but
+ * allocates nothing: the scratch of the batched kernels lives in a fixed
+ * device array of LG_NOALLOC_SCRATCH_BYTES that every device loading the
+ * library holds until the process exits.
+ *   - batch and out must be device memory (host staging would allocate); the
+ *     call is asynchronous on `stream` like lg_dock_batch.
+ *   - The scratch needs about 32 + 2 * max_rot bytes per ligand (max_rot = 32
+ *     when 0) plus 1 KiB; larger batches are rejected with LG_EINVAL.
+ *   - The first call on a device looks up the array's device address (once per
+ *     device, with that device current): make that first call before any
+ *     stream capture.
+ *   - Every call shares the array and finds the previous call's contents in
+ *     it; the call clears the counters that must start at zero.  Calls whose
+ *     work overlaps on the GPU race on the array: order them on one stream.
+ *   - The pocket must already be loaded (lg_pocket_load allocates).
+ * Errors: LG_EINVAL, LG_ENOPOCKET, LG_ECUDA. */
+#define LG_NOALLOC_SCRATCH_BYTES (4u << 20)
+int lg_dock_batch_noalloc(lg_ctx *ctx, int32_t pocket_id, const lg_ligand_batch *batch, const lg_dock_params *params,
+                          lg_dock_result *out, void *stream);
+
 /* Given poses to score (step 3 above alone).
  *   atom_off[L+1], xyz[3*A] (A, interleaved), q[A], type[A]. */
 typedef struct {

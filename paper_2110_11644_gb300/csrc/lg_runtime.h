@@ -37,6 +37,7 @@ int dock_device(lg_ctx *ctx, const PocketDev &pk, const BatchDev &bd, const OutD
                 int nmax, int rmax, DevBuf &scratch, cudaStream_t s, lg_stats *st, cudaEvent_t *tev);
 void harvest_timing(lg_ctx *c);
 void serve_stop(lg_ctx *c);
+int choose_warps(int S, int opt);
 
 }  // namespace lg
 

@@ -63,7 +63,7 @@ class lg_stats(ctypes.Structure):
 # Every symbol include/lg.h declares (checked by the ABI test).
 EXPORTS = ("lg_create", "lg_destroy", "lg_last_error", "lg_pocket_load", "lg_pocket_unload", "lg_dock_batch",
            "lg_score_poses", "lg_stream_submit", "lg_stream_poll", "lg_stream_wait", "lg_get_stats", "lg_set_option",
-           "lg_diag_philox")
+           "lg_diag_philox", "lg_dock_batch_noalloc")
 
 _lib = None
 _lock = threading.Lock()
@@ -99,6 +99,8 @@ def load():
             lib.lg_get_stats.argtypes = [V, c.POINTER(lg_stats)]
             lib.lg_set_option.argtypes = [V, c.c_char_p, c.c_int64]
             lib.lg_diag_philox.argtypes = [V, c.c_int32, V, V, V, c.c_int32]
+            lib.lg_dock_batch_noalloc.argtypes = [V, c.c_int32, c.POINTER(lg_ligand_batch), c.POINTER(lg_dock_params),
+                                                  c.POINTER(lg_dock_result), V]
             for name in EXPORTS:
                 if name not in ("lg_destroy", "lg_last_error"):
                     getattr(lib, name).restype = c.c_int
@@ -146,6 +148,12 @@ def lg_pocket_unload(h, pid: int):
 
 def lg_dock_batch(h, pid, batch: lg_ligand_batch, params: lg_dock_params, out: lg_dock_result, stream=None):
     _check(h, load().lg_dock_batch(h, pid, ctypes.byref(batch), ctypes.byref(params), ctypes.byref(out), stream))
+
+
+def lg_dock_batch_noalloc(h, pid, batch: lg_ligand_batch, params: lg_dock_params, out: lg_dock_result, stream=None):
+    """Batched docking of a device-memory batch that allocates no memory (see lg.h)."""
+    _check(h, load().lg_dock_batch_noalloc(h, pid, ctypes.byref(batch), ctypes.byref(params), ctypes.byref(out),
+                                           stream))
 
 
 def lg_score_poses(h, pid, poses: lg_pose_batch, energies_ptr, stream=None):
