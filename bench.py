@@ -213,7 +213,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--ligands", type=int, default=N_LIGANDS)
-    ap.add_argument("--plain-sample", type=int, default=16384)
+    ap.add_argument("--plain-sample", type=int, default=4096)
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -29,8 +29,10 @@ def nvcc() -> str:
 
 
 def flags(extra=()):
+    # LG_NVCC_EXTRA: extra nvcc flags for tuning builds (e.g. -DLG_RT_UNROLL=1)
+    env = os.environ.get("LG_NVCC_EXTRA", "").split()
     return ["-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC,
-            "--expt-relaxed-constexpr", *extra]
+            "--expt-relaxed-constexpr", *env, *extra]
 
 
 def _sources():

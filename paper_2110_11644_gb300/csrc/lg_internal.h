@@ -101,7 +101,10 @@ __host__ __device__ inline Layout make_layout(int nmax, int rmax, int P, int W, 
 constexpr int kTile = 8;          // restarts per warp tile
 constexpr int kLanesPerRestart = 4;
 constexpr int kStepsPerLane = 9;  // 36 / 4
-constexpr int kPoolCap = 96;      // flagged clash pairs buffered per warp (all 8 restarts)
+#ifndef LG_RT_POOL
+#define LG_RT_POOL 96
+#endif
+constexpr int kPoolCap = LG_RT_POOL;  // flagged clash pairs buffered per warp (all 8 restarts)
 
 // Per-warp shared memory of a restart-tiled warp.
 struct LayoutRT {

@@ -416,6 +416,11 @@ __device__ __forceinline__ void flush_pool(const RtView &v, int rs, int g, int &
     pc = 0;
 }
 
+#ifndef LG_RT_UNROLL
+#define LG_RT_UNROLL 1
+#endif
+constexpr int kRtUnroll = LG_RT_UNROLL;  // moving atoms unrolled in the lookup phase
+
 // One torsion decision for the warp's 8 restarts.  Lane = 4*rs + g: restart
 // slot rs, steps g, g+4, ..., g+32 (cosines cs[], sines sn[]) -- the 4 lanes
 // of a restart score neighbouring steps in the same instruction.  Returns the
@@ -446,14 +451,17 @@ __device__ int sweep_bond_rt(const DockArgs &A, const GridK &G, const CtaView &c
     const float rho = sqrtf(rho2) + 1e-2f, lo = 1e-2f, hi = G.gmax - 1e-2f;
     const bool ball_in = xbx + c0 - rho >= lo && xbx + c0 + rho <= hi && xby + c0 - rho >= lo &&
                          xby + c0 + rho <= hi && xbz + c0 - rho >= lo && xbz + c0 + rho <= hi;
-    const bool all_in = __all_sync(LG_FULL, ball_in);
+#ifndef LG_RT_INSIDE_PATH
+#define LG_RT_INSIDE_PATH 1
+#endif
+    const bool all_in = LG_RT_INSIDE_PATH && __all_sync(LG_FULL, ball_in);
 
     // 1. overlap scores of the lane's 9 steps over all moving atoms (in order)
     float acc[kStepsPerLane];
 #pragma unroll
     for (int j = 0; j < kStepsPerLane; ++j) acc[j] = 0.0f;
     if (all_in) {
-#pragma unroll 2
+#pragma unroll kRtUnroll
         for (int i = b + 1; i < e; ++i) {
             const Circle C = make_circle(v.Xx[i * kTile + rs], v.Xy[i * kTile + rs], v.Xz[i * kTile + rs], xbx, xby,
                                          xbz, u, c0, G.gmax);
@@ -464,7 +472,7 @@ __device__ int sweep_bond_rt(const DockArgs &A, const GridK &G, const CtaView &c
             }
         }
     } else {
-#pragma unroll 2
+#pragma unroll kRtUnroll
         for (int i = b + 1; i < e; ++i) {
             const Circle C = make_circle(v.Xx[i * kTile + rs], v.Xy[i * kTile + rs], v.Xz[i * kTile + rs], xbx, xby,
                                          xbz, u, c0, G.gmax);
@@ -668,7 +676,10 @@ __device__ void dock_ligand_rt(const DockArgs &A, int l, char *sm) {
 }
 
 // Persistent: CTAs pull ligands from a device counter in cost order.
-__global__ void __launch_bounds__(256) k_dock_batched(const __grid_constant__ DockArgs A) {
+#ifndef LG_RT_MIN_BLOCKS
+#define LG_RT_MIN_BLOCKS 4
+#endif
+__global__ void __launch_bounds__(128, LG_RT_MIN_BLOCKS) k_dock_batched(const __grid_constant__ DockArgs A) {
     extern __shared__ __align__(16) char sm[];
     __shared__ int s_item;
     for (;;) {

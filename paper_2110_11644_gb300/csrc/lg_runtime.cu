@@ -166,7 +166,7 @@ int fetch_out(const OutDev &d, const lg_dock_result *o, int L, int S, int P, int
 // unless the context option fixes the count.
 int choose_warps(int S, int opt) {
     const int tiles = (S + kTile - 1) / kTile;
-    if (opt > 0) return std::min(opt, 8);
+    if (opt > 0) return std::min(opt, 4);
     for (int w = std::min(tiles, 4); w >= 1; --w)
         if (tiles % w == 0) return w;
     return 1;
