@@ -161,15 +161,24 @@ def oracle_rate(pocket, batch, params, budget_s: float, chunk: int = 256, max_li
     return done / dt, done, dt
 
 
+KERNEL_SOURCES = ("lg_kernels.cu", "lg_device.cuh", "lg_internal.h")
+
+
+def kernel_source_sha() -> str:
+    """Hash of the sources that define the docking kernels."""
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_2110_11644_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def traffic_for_current_kernel():
     """DRAM bytes per launch of the docking kernel from the committed ncu
-    summary, if it was taken on the current kernel source (else None)."""
+    summary, if it was taken on the current kernel sources (else None)."""
     path = os.path.join(ROOT, "profiles", "dock_batched_traffic.json")
-    src = os.path.join(ROOT, "paper_2110_11644_gb300", "csrc", "lg_kernels.cu")
     try:
         rec = json.load(open(path))
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-        if rec.get("kernel_source_sha") == sha:
+        if rec.get("kernel_source_sha") == kernel_source_sha():
             return rec.get("dram_bytes_per_launch")
     except (OSError, ValueError):
         pass
