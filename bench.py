@@ -41,47 +41,16 @@ CFG = 2
 N_LIGANDS = 100_000
 FP32_LANES_PER_SM = 128          # FP32 FMA lanes per SM (4 SMSPs x 32)
 FLOP_PER_FMA = 2
-# Algorithmic FLOPs: per moving atom and torsion step, 12 for
-# the point on its circle, 3 for the cell fraction, 14 for the trilinear
-# polynomial and 1 for the sum; 30 per moving atom and decision for building
-# its circle and applying the chosen step; per atom and restart 21 for the
-# rigid pose and 44 for the final score; 40 per restart for the pose draw.
-C_LOOKUP, C_BOND, C_POSE_ATOM, C_FINAL_ATOM, C_RESTART = 30, 30, 21, 44, 40
-
-
-def moving_atoms_per_ligand(batch) -> np.ndarray:
-    """Sum over a ligand's torsional bonds of the atoms each bond moves
-    (subtree size of the bond's child minus one)."""
-    aoff = batch.atom_off.astype(np.int64)
-    A = int(aoff[-1])
-    lig = np.repeat(np.arange(batch.L), np.diff(aoff))
-    par = batch.parent.astype(np.int64)
-    gpar = np.where(par >= 0, par + aoff[lig], -1)
-    depth = np.zeros(A, np.int64)
-    nonroot = gpar >= 0
-    for _ in range(int(np.diff(aoff).max(initial=1))):
-        nd = np.where(nonroot, depth[np.maximum(gpar, 0)] + 1, 0)
-        if np.array_equal(nd, depth):
-            break
-        depth = nd
-    size = np.ones(A, np.int64)
-    for d in range(int(depth.max(initial=0)), 0, -1):
-        idx = np.where(depth == d)[0]
-        np.add.at(size, gpar[idx], size[idx])
-    roff = batch.rot_off.astype(np.int64)
-    rl = np.repeat(np.arange(batch.L), np.diff(roff))
-    child = batch.rot_child.astype(np.int64) + aoff[rl]
-    m = size[child] - 1
-    out = np.zeros(batch.L, np.int64)
-    np.add.at(out, rl, m)
-    return out
 
 
 def algorithmic_flops(batch, S, P) -> float:
-    N = np.diff(batch.atom_off).astype(np.float64)
-    msum = moving_atoms_per_ligand(batch).astype(np.float64)
-    per = S * (P * msum * (36 * C_LOOKUP + C_BOND) + N * (C_POSE_ATOM + C_FINAL_ATOM) + C_RESTART)
-    return float(per.sum())
+    """Algorithmic FLOPs of docking a batch (cost model in shard.py): per moving
+    atom and torsion step 12 for the point on its circle, 3 for the cell
+    fraction, 14 for the trilinear polynomial and 1 for the sum; 30 per moving
+    atom and decision for its circle and the move; per atom and restart 21 for
+    the rigid pose and 44 for the final score; 40 per restart for the pose draw."""
+    from paper_2110_11644_gb300 import shard
+    return float(shard.ligand_flops(batch, S, P).sum())
 
 
 class ClockSampler:
@@ -185,6 +154,72 @@ def traffic_for_current_kernel():
     return None
 
 
+def contiguous_request(pool, start, size):
+    """Ligands start .. start+size-1 of a CSR batch as host arrays (views of
+    the pool; only the offsets are rebased)."""
+    from paper_2110_11644_gb300 import lg
+    a0, a1 = int(pool.atom_off[start]), int(pool.atom_off[start + size])
+    r0, r1 = int(pool.rot_off[start]), int(pool.rot_off[start + size])
+    arrs = dict(atom_off=np.ascontiguousarray(pool.atom_off[start:start + size + 1] - a0, np.int32),
+                rot_off=np.ascontiguousarray(pool.rot_off[start:start + size + 1] - r0, np.int32),
+                x=pool.x[a0:a1], y=pool.y[a0:a1], z=pool.z[a0:a1], q=pool.q[a0:a1], type=pool.type[a0:a1],
+                parent=pool.parent[a0:a1], rot_child=pool.rot_child[r0:r1] if r1 > r0 else pool.rot_child[:1],
+                uid=pool.uid[start:start + size])
+    return arrs, size, a1 - a0, r1 - r0
+
+
+def serving_leg(ctx, pid, pool, params, rate_evals, load, duration_s, seed=5, max_size=4096):
+    """Poisson arrivals of requests of floor(exp(U(0, ln max_size))) ligands at
+    `load` times `rate_evals` ligands/s for `duration_s` seconds, submitted to
+    the library's serving loop; latency is submit-to-done as the library
+    measures it."""
+    from paper_2110_11644_gb300 import lg
+    rng = np.random.default_rng(seed)
+    mean_size = (max_size - 1) / np.log(max_size)
+    lam = load * rate_evals / mean_size
+    n = int(lam * duration_s) + 1
+    sizes = np.maximum(1, np.minimum(max_size, np.floor(np.exp(rng.uniform(0, np.log(max_size), n))))).astype(int)
+    gaps = rng.exponential(1.0 / lam, n)
+    arrive = np.cumsum(gaps)
+    p = lg.make_params(params.restarts, params.passes, params.seed, params.d_clash)
+    cursor, pending, done_lat, live = 0, [], [], {}
+    t0 = time.perf_counter()
+    i = 0
+    while i < n:
+        now = time.perf_counter() - t0
+        if now >= arrive[i]:
+            size = int(sizes[i])
+            if cursor + size > pool.L:
+                cursor = 0
+            arrs, L, A, R = contiguous_request(pool, cursor, size)
+            cursor += size
+            b = lg.make_batch_struct(arrs, L)
+            r, outs = lg.alloc_result(L, A, R, params.restarts, params.passes, device=False, pose=False, tors=False)
+            t = lg.lg_stream_submit(ctx.h, pid, b, p, r)
+            live[t] = (arrs, outs, L)
+            pending.append(t)
+            i += 1
+        else:
+            while pending:
+                st, lat = lg.lg_stream_poll(ctx.h, pending[0])
+                if st < lg.LG_REQ_DONE:
+                    break
+                done_lat.append((lat, live.pop(pending[0])[2]))
+                pending.pop(0)
+            time.sleep(2e-4)
+    for t in pending:
+        lg.lg_stream_wait(ctx.h, t, 600000)
+        st, lat = lg.lg_stream_poll(ctx.h, t)
+        done_lat.append((lat, live.pop(t)[2]))
+    wall = time.perf_counter() - t0
+    lat = np.array([x for x, _ in done_lat])
+    ligs = int(sum(s for _, s in done_lat))
+    return {"offered_load": load, "offered_evals_per_s": load * rate_evals, "duration_s": round(wall, 2),
+            "requests": len(lat), "ligands": ligs, "sustained_evals_per_s": ligs / wall,
+            "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+            "request_sizes": f"floor(exp(U(0, ln {max_size}))) ligands, Poisson arrivals"}
+
+
 def run_reference(args):
     rank, world, _ = env_rank()
     if rank != 0:
@@ -225,6 +260,8 @@ def main():
     ap.add_argument("--plain-sample", type=int, default=4096)
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=4.0, help="serving leg at 50%% of the measured peak (0 = off)")
+    ap.add_argument("--serve-loads", default="0.5", help="comma-separated offered loads for the serving leg")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -317,7 +354,9 @@ def main():
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": achieved / peak_tflops, "traffic": traffic_for_current_kernel(),
                 "kernel": "k_dock_batched", "dock_ms_per_launch": dock_ms, "flop_per_launch": F,
-                "peak_basis": f"{sm_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max_mhz:.0f} MHz"}
+                "peak_basis": f"{sm_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max_mhz:.0f} MHz",
+                "limiter": "scattered L2->L1 gathers of 32-byte trilinear cells (L1TEX ~74% of peak in ncu) "
+                           "and instruction issue; see profiles/dock_batched_ncu_small.md"}
 
     # end to end through the public API with host buffers (pinned)
     hb = lg.host_batch_arrays(batch)
@@ -380,6 +419,11 @@ def main():
             cpu = {"value": rate, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
                    "sample": f"first {n_done} ligands of the workload, FP64 oracle, {secs:.1f} s"}
 
+        serving = None
+        if args.serve_seconds > 0:
+            serving = [serving_leg(ctx, pid, batch, params, value / world, float(ld), args.serve_seconds)
+                       for ld in args.serve_loads.split(",")]
+
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -388,7 +432,8 @@ def main():
                            "l2": "flushed before every step (256 MiB write)", "inputs": "device-resident",
                            "warps_per_cta": st.warps_per_cta, "ctas_per_sm": st.ctas_per_sm, "grid": st.grid},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "clocks": clk, "gpu_launches": launches_per_step * args.steps, "plain": plain}
+                "clocks": clk, "gpu_launches": launches_per_step * args.steps, "plain": plain,
+                "serving": serving}
         print(json.dumps(line), flush=True)
     ctx.close()
     if dist:

@@ -1,0 +1,101 @@
+"""Sharding a ligand library over GPUs (host logic).
+
+Every (ligand, pocket) evaluation is independent (paper Sec. 3.2: a ligand's
+description is all a dock needs), so a screening run splits the library over
+ranks and needs no exchange while docking; only the final ranking is gathered.
+The paper splits its input file into equal-size slabs per MPI rank and notes
+that this static split cannot balance ligands of very different cost
+(Sec. 3.2-3.3); here shards are balanced by the estimated docking cost instead.
+
+Cost model (also the bench's algorithmic FLOP count per ligand):
+  restarts * (passes * sum_k m_k * (36*30 + 30) + atoms * 65 + 40)
+with m_k the atoms torsional bond k moves.
+"""
+from __future__ import annotations
+
+import heapq
+
+import numpy as np
+
+C_LOOKUP, C_BOND, C_POSE_ATOM, C_FINAL_ATOM, C_RESTART = 30, 30, 21, 44, 40
+
+
+def moving_atoms_per_ligand(batch) -> np.ndarray:
+    """Sum over each ligand's torsional bonds of the atoms the bond moves
+    (subtree size of the bond's child minus one)."""
+    aoff = batch.atom_off.astype(np.int64)
+    A = int(aoff[-1])
+    L = len(aoff) - 1
+    lig = np.repeat(np.arange(L), np.diff(aoff))
+    par = batch.parent.astype(np.int64)
+    gpar = np.where(par >= 0, par + aoff[lig], -1)
+    depth = np.zeros(A, np.int64)
+    nonroot = gpar >= 0
+    for _ in range(int(np.diff(aoff).max(initial=1))):
+        nd = np.where(nonroot, depth[np.maximum(gpar, 0)] + 1, 0)
+        if np.array_equal(nd, depth):
+            break
+        depth = nd
+    size = np.ones(A, np.int64)
+    for d in range(int(depth.max(initial=0)), 0, -1):
+        idx = np.where(depth == d)[0]
+        np.add.at(size, gpar[idx], size[idx])
+    roff = batch.rot_off.astype(np.int64)
+    rl = np.repeat(np.arange(L), np.diff(roff))
+    child = batch.rot_child.astype(np.int64) + aoff[rl]
+    out = np.zeros(L, np.int64)
+    np.add.at(out, rl, size[child] - 1)
+    return out
+
+
+def ligand_flops(batch, restarts: int, passes: int) -> np.ndarray:
+    """Algorithmic FLOPs of docking each ligand (see the module docstring)."""
+    N = np.diff(batch.atom_off).astype(np.float64)
+    msum = moving_atoms_per_ligand(batch).astype(np.float64)
+    return restarts * (passes * msum * (36 * C_LOOKUP + C_BOND) + N * (C_POSE_ATOM + C_FINAL_ATOM) + C_RESTART)
+
+
+def partition(costs, world: int):
+    """Split ligands over `world` ranks with balanced total cost (longest
+    processing time first: each ligand, in descending cost, goes to the least
+    loaded rank).  Returns one sorted index array per rank."""
+    costs = np.asarray(costs, np.float64)
+    heap = [(0.0, r) for r in range(world)]
+    parts = [[] for _ in range(world)]
+    for l in np.argsort(-costs, kind="stable"):
+        load, r = heapq.heappop(heap)
+        parts[r].append(int(l))
+        heapq.heappush(heap, (load + float(costs[l]), r))
+    return [np.array(sorted(p), np.int64) for p in parts]
+
+
+def gather_ranking(uid, score, k: int, group=None):
+    """Global k best (lowest score, then lowest uid) over all ranks of the
+    default process group: each rank sends its own k best, rank 0 merges.
+    Returns (uid, score) arrays on rank 0 and None elsewhere."""
+    import torch
+    import torch.distributed as dist
+
+    uid = np.asarray(uid, np.int64)
+    score = np.asarray(score, np.float64)
+    ok = np.isfinite(score)
+    uid, score = uid[ok], score[ok]
+    order = np.lexsort((uid, score))[:k]
+    mine = torch.from_numpy(np.stack([uid[order].astype(np.float64), score[order]], 1) if len(order)
+                            else np.zeros((0, 2)))
+    world = dist.get_world_size(group)
+    n = torch.tensor([mine.shape[0]], dtype=torch.int64)
+    counts = [torch.zeros(1, dtype=torch.int64) for _ in range(world)]
+    dist.all_gather(counts, n, group=group)
+    kmax = int(max(c.item() for c in counts))
+    pad = torch.full((kmax, 2), float("nan"), dtype=torch.float64)
+    pad[: mine.shape[0]] = mine
+    bufs = [torch.empty((kmax, 2), dtype=torch.float64) for _ in range(world)]
+    dist.all_gather(bufs, pad, group=group)
+    if dist.get_rank(group) != 0:
+        return None
+    allv = torch.cat([b[: int(c.item())] for b, c in zip(bufs, counts)]).numpy()
+    u = allv[:, 0].astype(np.int64)
+    s = allv[:, 1]
+    order = np.lexsort((u, s))[:k]
+    return u[order], s[order]

@@ -1,0 +1,131 @@
+"""Serving loop (lg_stream_submit / poll / wait) on the GPU: continuous batching
+of requests of uneven size, results identical to docking each request alone,
+bounded waits, admission under a tight free-memory reserve."""
+import time
+
+import numpy as np
+import pytest
+
+from paper_2110_11644_gb300 import lg, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def served():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    ctx = lg.Context(0)
+    pocket = synth.config_pocket(1)
+    pid = ctx.load_pocket(pocket)
+    yield ctx, pid
+    ctx.close()
+
+
+def _request(batch, params):
+    """Host arrays + structs of one request (kept alive by the caller)."""
+    arrs = lg.host_batch_arrays(batch)
+    b = lg.make_batch_struct(arrs, batch.L)
+    p = lg.make_params(params.restarts, params.passes, params.seed, params.d_clash)
+    r, outs = lg.alloc_result(batch.L, int(batch.atom_off[-1]), int(batch.rot_off[-1]), params.restarts,
+                              params.passes, device=False, pose=True, tors=True)
+    return dict(arrs=arrs, b=b, p=p, r=r, outs=outs, L=batch.L, A=int(batch.atom_off[-1]),
+                R=int(batch.rot_off[-1]))
+
+
+def _trim(req, P):
+    n = dict(score=req["L"], best_restart=req["L"], status=req["L"], tors_idx=P * req["R"], pose=3 * req["A"])
+    return {k: v[:n[k]] for k, v in req["outs"].items() if k in n}
+
+
+def test_results_same_alone_and_in_the_mix(served):
+    ctx, pid = served
+    params = synth.config_params(1)
+    full = synth.config_ligands(1)
+    rng = np.random.default_rng(0)
+    sizes = [1, 7, 40, 3, 64, 17, 100, 24]
+    starts = np.cumsum([0] + sizes)
+    reqs, tickets = [], []
+    for k, s in enumerate(sizes):  # submitted back to back: they are merged and overlap on the device
+        sub = full.subset(range(starts[k], starts[k] + s))
+        req = _request(sub, params)
+        reqs.append((sub, req))
+        tickets.append(lg.lg_stream_submit(ctx.h, pid, req["b"], req["p"], req["r"]))
+    for t in tickets:
+        assert lg.lg_stream_wait(ctx.h, t, 60000) == lg.LG_OK
+        st, lat = lg.lg_stream_poll(ctx.h, t)
+        assert st == lg.LG_REQ_DONE and lat >= 0.0
+    for sub, req in reqs:
+        alone = ctx.dock(pid, sub, params)
+        got = _trim(req, params.passes)
+        for k in got:
+            assert np.array_equal(got[k], alone[k][:len(got[k])]), k
+    # and equal to the same ligands docked inside the whole batch
+    whole = ctx.dock(pid, full.subset(range(int(starts[-1]))), params)
+    mixed = np.concatenate([_trim(req, params.passes)["score"] for _, req in reqs])
+    assert np.array_equal(mixed, whole["score"])
+
+
+def test_bounded_wait_and_unknown_ticket(served):
+    ctx, pid = served
+    params = synth.DockParams(restarts=16, passes=2)
+    batch = synth.config_ligands(1, 200)
+    req = _request(batch, params)
+    t = lg.lg_stream_submit(ctx.h, pid, req["b"], req["p"], req["r"])
+    try:
+        lg.lg_stream_wait(ctx.h, t, 0)
+    except lg.LgError as e:
+        assert e.code == lg.LG_ETIMEOUT
+    assert lg.lg_stream_wait(ctx.h, t, 60000) == lg.LG_OK
+    with pytest.raises(lg.LgError) as e:
+        lg.lg_stream_poll(ctx.h, 10 ** 12)
+    assert e.value.code == lg.LG_EINVAL
+    with pytest.raises(lg.LgError) as e:
+        lg.lg_stream_wait(ctx.h, 10 ** 12, 10)
+    assert e.value.code == lg.LG_EINVAL
+
+
+def test_admission_under_tight_memory_still_completes():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    ctx = lg.Context(0)
+    try:
+        # a reserve larger than the device: every request beyond the first in
+        # flight waits for memory, but an idle device always admits one
+        ctx.set_option("serve_mem_reserve_mb", 1 << 30)
+        ctx.set_option("serve_max_inflight", 4)
+        pid = ctx.load_pocket(synth.config_pocket(1))
+        params = synth.config_params(1)
+        full = synth.config_ligands(1)
+        reqs, tickets = [], []
+        for k in range(6):
+            sub = full.subset(range(40 * k, 40 * k + 40))
+            req = _request(sub, params)
+            reqs.append((sub, req))
+            tickets.append(lg.lg_stream_submit(ctx.h, pid, req["b"], req["p"], req["r"]))
+        for t in tickets:
+            assert lg.lg_stream_wait(ctx.h, t, 60000) == lg.LG_OK
+        ref = ctx.dock(pid, full.subset(range(240)), params)
+        got = np.concatenate([_trim(req, params.passes)["score"] for _, req in reqs])
+        assert np.array_equal(got, ref["score"])
+    finally:
+        ctx.close()
+
+
+def test_many_small_requests_latency_recorded(served):
+    ctx, pid = served
+    params = synth.config_params(1)
+    full = synth.config_ligands(1)
+    reqs, tickets = [], []
+    t0 = time.perf_counter()
+    for k in range(64):
+        sub = full.subset([k % full.L])
+        req = _request(sub, params)
+        reqs.append(req)
+        tickets.append(lg.lg_stream_submit(ctx.h, pid, req["b"], req["p"], req["r"]))
+    for t in tickets:
+        lg.lg_stream_wait(ctx.h, t, 60000)
+    lats = [lg.lg_stream_poll(ctx.h, t)[1] for t in tickets]
+    assert all(0.0 <= x <= time.perf_counter() - t0 + 1e-3 for x in lats)
