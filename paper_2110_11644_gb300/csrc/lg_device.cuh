@@ -124,8 +124,13 @@ __device__ __forceinline__ GridK grid_k(const PocketDev &P, const float4 *cells)
 
 // One 32-byte cell (8 coefficients) with a single 256-bit read-only load
 // (sm_100+); cells are 32-byte aligned.
+// Cells are rarely reused from L1 (scattered lookups), so they bypass L1
+// allocation; this measured faster than caching them.
+#ifndef LG_CELL_LOAD
+#define LG_CELL_LOAD "ld.global.nc.L1::no_allocate.v8.f32"
+#endif
 __device__ __forceinline__ void load_cell(const float4 *p, float4 &lo, float4 &hi) {
-    asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+    asm(LG_CELL_LOAD " {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
                  : "=f"(lo.x), "=f"(lo.y), "=f"(lo.z), "=f"(lo.w), "=f"(hi.x), "=f"(hi.y), "=f"(hi.z), "=f"(hi.w)
                  : "l"(p));
 }
