@@ -416,11 +416,6 @@ __device__ __forceinline__ void flush_pool(const RtView &v, int rs, int g, int &
     pc = 0;
 }
 
-#ifndef LG_RT_UNROLL
-#define LG_RT_UNROLL 1
-#endif
-constexpr int kRtUnroll = LG_RT_UNROLL;  // moving atoms unrolled in the lookup phase
-
 // One torsion decision for the warp's 8 restarts.  Lane = 4*rs + g: restart
 // slot rs, steps g, g+4, ..., g+32 (cosines cs[], sines sn[]) -- the 4 lanes
 // of a restart score neighbouring steps in the same instruction.  Returns the
@@ -456,38 +451,8 @@ __device__ int sweep_bond_rt(const DockArgs &A, const GridK &G, const CtaView &c
 #endif
     const bool all_in = LG_RT_INSIDE_PATH && __all_sync(LG_FULL, ball_in);
 
-    // 1. overlap scores of the lane's 9 steps over all moving atoms (in order)
-    float acc[kStepsPerLane];
-#pragma unroll
-    for (int j = 0; j < kStepsPerLane; ++j) acc[j] = 0.0f;
-    if (all_in) {
-#pragma unroll kRtUnroll
-        for (int i = b + 1; i < e; ++i) {
-            const Circle C = make_circle(v.Xx[i * kTile + rs], v.Xy[i * kTile + rs], v.Xz[i * kTile + rs], xbx, xby,
-                                         xbz, u, c0, G.gmax);
-#pragma unroll
-            for (int j = 0; j < kStepsPerLane; ++j) {
-                const float3 q = circle_index(C.Px, C.Py, C.Pz, C.e1x, C.e1y, C.e1z, C.e2x, C.e2y, C.e2z, cs[j], sn[j]);
-                acc[j] += lookup_in(G, q.x, q.y, q.z);
-            }
-        }
-    } else {
-#pragma unroll kRtUnroll
-        for (int i = b + 1; i < e; ++i) {
-            const Circle C = make_circle(v.Xx[i * kTile + rs], v.Xy[i * kTile + rs], v.Xz[i * kTile + rs], xbx, xby,
-                                         xbz, u, c0, G.gmax);
-#pragma unroll
-            for (int j = 0; j < kStepsPerLane; ++j) {
-                const float3 q = circle_index(C.Px, C.Py, C.Pz, C.e1x, C.e1y, C.e1z, C.e2x, C.e2y, C.e2z, cs[j], sn[j]);
-                acc[j] += lookup_clamped(G, q.x, q.y, q.z);
-            }
-        }
-    }
-
-    // 2. clash mask of the lane's 9 steps.  Only fixed atoms within rho +
-    //    d_clash of xb can come within d_clash of a moving atom; for those the
-    //    pairs that can clash somewhere on the circle are pooled over the 8
-    //    restarts and evaluated step by step.
+    // Fixed atoms farther than rho + d_clash from xb can never come within
+    // d_clash of a moving atom: each restart keeps a list of the others.
     const float rlim = sqrtf(rho2) + sqrtf(dc2) + 1e-3f, rlim2 = rlim * rlim;
     int ncnt = 0;  // near fixed atoms of this restart (same in its 4 lanes)
     for (int jb = 0; jb < nF; jb += kLanesPerRestart) {
@@ -506,10 +471,12 @@ __device__ int sweep_bond_rt(const DockArgs &A, const GridK &G, const CtaView &c
     v.mask[lane] = 0u;
     __syncwarp();
     const int nnear = (int)__reduce_max_sync(LG_FULL, (unsigned)ncnt);
+
+    // Clash pairs of moving atom i (circle C): pairs that can come within
+    // d_clash somewhere on the circle are pooled over the 8 restarts and
+    // evaluated step by step.
     int pc = 0;  // pooled pairs (warp-uniform)
-    for (int i = b + 1; i < e && nnear > 0; ++i) {
-        const Circle C = make_circle(v.Xx[i * kTile + rs], v.Xy[i * kTile + rs], v.Xz[i * kTile + rs], xbx, xby, xbz, u,
-                                     c0, G.gmax);
+    auto pool_pairs = [&](int i, const Circle &C) {
         const int excl = (cv.par[i] == b) ? a : -1;  // two bonds apart through the bond itself
         for (int jb = 0; jb < nnear; jb += kLanesPerRestart) {
             if (pc > kPoolCap - 32) flush_pool(v, rs, g, pc, cs, sn, dc2);
@@ -526,6 +493,30 @@ __device__ int sweep_bond_rt(const DockArgs &A, const GridK &G, const CtaView &c
             if (q.near) v.pool[pc + __popc(bal & below)] = make_float4(q.C, q.A2, q.B2, __int_as_float(rs));
             pc += __popc(bal);
         }
+    };
+
+    // Overlap scores of the lane's 9 steps over the moving atoms (in order),
+    // and each atom's clash pairs while its cell loads are in flight.
+    float acc[kStepsPerLane];
+#pragma unroll
+    for (int j = 0; j < kStepsPerLane; ++j) acc[j] = 0.0f;
+    for (int i = b + 1; i < e; ++i) {
+        const Circle C = make_circle(v.Xx[i * kTile + rs], v.Xy[i * kTile + rs], v.Xz[i * kTile + rs], xbx, xby, xbz, u,
+                                     c0, G.gmax);
+        if (all_in) {
+#pragma unroll
+            for (int j = 0; j < kStepsPerLane; ++j) {
+                const float3 q = circle_index(C.Px, C.Py, C.Pz, C.e1x, C.e1y, C.e1z, C.e2x, C.e2y, C.e2z, cs[j], sn[j]);
+                acc[j] += lookup_in(G, q.x, q.y, q.z);
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < kStepsPerLane; ++j) {
+                const float3 q = circle_index(C.Px, C.Py, C.Pz, C.e1x, C.e1y, C.e1z, C.e2x, C.e2y, C.e2z, cs[j], sn[j]);
+                acc[j] += lookup_clamped(G, q.x, q.y, q.z);
+            }
+        }
+        if (nnear > 0) pool_pairs(i, C);
     }
     flush_pool(v, rs, g, pc, cs, sn, dc2);
     unsigned clash = v.mask[lane];  // bit j: step 4j + g clashes
