@@ -52,7 +52,8 @@ class _Pocket(ctypes.Structure):
 
 class _Params(ctypes.Structure):
     _fields_ = [("restarts", ctypes.c_int32), ("passes", ctypes.c_int32), ("angle_steps", ctypes.c_int32),
-                ("seed", ctypes.c_uint64), ("d_clash", ctypes.c_double)]
+                ("seed", ctypes.c_uint64), ("d_clash", ctypes.c_double), ("cluster_rmsd", ctypes.c_double),
+                ("rescore_top", ctypes.c_int32)]
 
 
 def _load():
@@ -72,7 +73,8 @@ def _load():
             lib.or_topology.argtypes = [i32, P, P]
             lib.or_topology.restype = ctypes.c_int
             lib.or_dock_ligand.restype = ctypes.c_int
-            lib.or_dock_batch.argtypes = [P, P, i32] + [P] * 10 + [P] * 11 + [P, i32]
+            lib.or_dock_batch.argtypes = [P, P, i32] + [P] * 10 + [P] * 11 + [P, P, P, i32]
+            lib.or_rank_poses.argtypes = [P, i32, i32, P, P, d, i32, P, P, P, P, P]
             lib.or_dock_batch.restype = ctypes.c_int
             lib.or_score_poses.argtypes = [P, i32, P, P, P, P, P, P]
             _lib = lib
@@ -119,6 +121,8 @@ def _params(params):
     s.restarts, s.passes, s.angle_steps = int(params.restarts), int(params.passes), int(params.angle_steps)
     s.seed = int(params.seed)
     s.d_clash = float(np.float32(params.d_clash))
+    s.cluster_rmsd = float(np.float32(getattr(params, "cluster_rmsd", 0.0)))
+    s.rescore_top = int(getattr(params, "rescore_top", 0))
     return s
 
 
@@ -224,6 +228,10 @@ def dock(pocket, batch, params, *, replay=None, trace=False, poses=False, nthrea
         out["trace_s"] = np.zeros(max(ndec * A, 1)); out["trace_d2"] = np.zeros(max(ndec * A, 1))
     if poses:
         out["poses"] = np.zeros(max(3 * S * natoms, 1))
+    ranking = pr.cluster_rmsd > 0 or 0 < pr.rescore_top < S
+    if ranking:
+        out["rank"] = np.zeros(max(2 * S * L, 1), np.int32)
+        out["geo"] = np.zeros(max(S * L, 1))
     rep = None
     if replay is not None:
         rep = np.ascontiguousarray(replay, np.uint8)
@@ -235,7 +243,26 @@ def dock(pocket, batch, params, *, replay=None, trace=False, poses=False, nthrea
                       _ptr(out["restart_E"]), _ptr(out["restart_Eabs"]), _ptr(out["choice"]), _ptr(out["own"]),
                       _ptr(out.get("trace_s")), _ptr(out.get("trace_d2")), _ptr(out.get("poses")),
                       _ptr(out["best_pose"]), _ptr(out["best_r"]), _ptr(out["best_E"]), _ptr(out["status"]),
-                      int(nthreads))
+                      _ptr(out.get("rank")), _ptr(out.get("geo")), int(nthreads))
     out["restart_E"] = out["restart_E"].reshape(L, S)
     out["restart_Eabs"] = out["restart_Eabs"].reshape(L, S)
+    if ranking:
+        rk = out.pop("rank")[: 2 * S * L].reshape(L, 2, S)
+        out["order"], out["leader"] = rk[:, 0, :].copy(), rk[:, 1, :].copy()
+        out["geo"] = out["geo"][: S * L].reshape(L, S)
     return out
+
+
+def rank_poses(pocket, poses, E, thr, K):
+    """Ranking of one ligand's S final poses (poses[S][N][3], E[S]): returns
+    (G, order, leader, best_r, best_E)."""
+    lib = _load()
+    op = _as_oracle_pocket(pocket)
+    poses = np.ascontiguousarray(poses, np.float64)
+    S, N = poses.shape[0], poses.shape[1]
+    E = np.ascontiguousarray(E, np.float64)
+    G = np.empty(S); order = np.empty(S, np.int32); leader = np.empty(S, np.int32)
+    br = ctypes.c_int32(); be = ctypes.c_double()
+    lib.or_rank_poses(op.ref, S, N, _ptr(poses), _ptr(E), float(thr), int(K), _ptr(G), _ptr(order), _ptr(leader),
+                      ctypes.byref(br), ctypes.byref(be))
+    return G, order, leader, br.value, be.value

@@ -34,6 +34,14 @@
  *   score   E = sum_i [ w_type(i) Vgrid(xhat_i) + q_i Egrid(xhat_i) + k_out |x_i - xhat_i| ]
  *           with xhat the position clamped to the grid box.
  *   best    The restart with the lowest E wins, the lowest restart on ties.
+ *   rank    (optional, Sec. 3.1 steps 3-4) The poses are ordered by geometric
+ *           score G = sum over all atoms of the overlap grid (higher first,
+ *           lower restart on ties) and clustered greedily: a pose whose RMSD
+ *           (no superposition) to an earlier cluster leader is at most the
+ *           threshold joins the first such leader, otherwise it leads a new
+ *           cluster.  The ranking lists the leaders in order, then the other
+ *           poses in order; the first K ranked poses are rescored and the one
+ *           with the lowest E (lowest restart on ties) is the ligand's result.
  *
  * Trilinear interpolation (textbook definition): node (i,j,k) at origin +
  * h (i,j,k), flat index (k n + j) n + i; g = (xhat - origin)/h; i0 =
@@ -65,6 +73,8 @@ typedef struct {
     int32_t restarts, passes, angle_steps;
     uint64_t seed;
     double d_clash;
+    double cluster_rmsd; /* 0: no clustering */
+    int32_t rescore_top; /* K; 0 or >= restarts: all poses */
 } or_params;
 
 /* ------------------------------------------------------------------ Philox4x32-10
@@ -236,6 +246,62 @@ int or_validate(int32_t N, const int16_t *parent, const uint8_t *type, int32_t R
     return 0;
 }
 
+/* ------------------------------------------------------------------ ranking */
+/* Rank the S final poses (poses[S][N][3]) of a ligand and rescore the first K.
+ * Outputs: G[S] geometric scores, order[S] ranked restarts, leader[S] cluster
+ * leader of each restart (the restart itself when it leads), best_r/best_E. */
+void or_rank_poses(const or_pocket *P, int32_t S, int32_t N, const double *poses, const double *E, double thr,
+                   int32_t K, double *G, int32_t *order, int32_t *leader, int32_t *best_r, double *best_E) {
+    for (int r = 0; r < S; r++) {
+        double g = 0.0;
+        for (int i = 0; i < N; i++) g += or_trilinear(P, P->phi_o, poses + ((size_t)r * N + i) * 3);
+        G[r] = g;
+    }
+    /* geometric order: higher G first, lower restart on ties (insertion sort) */
+    int32_t *geo = (int32_t *)malloc(sizeof(int32_t) * S);
+    for (int r = 0; r < S; r++) {
+        int p = r;
+        while (p > 0 && G[geo[p - 1]] < G[r]) { geo[p] = geo[p - 1]; p--; }
+        geo[p] = r;
+    }
+    /* greedy leader clustering in geometric order */
+    int32_t *leads = (int32_t *)malloc(sizeof(int32_t) * S);
+    int nl = 0;
+    for (int p = 0; p < S; p++) {
+        const int r = geo[p];
+        leader[r] = r;
+        if (thr > 0.0) {
+            for (int k = 0; k < nl; k++) {
+                const int q = leads[k];
+                double ss = 0.0;
+                for (int i = 0; i < N; i++)
+                    for (int c = 0; c < 3; c++) {
+                        const double d = poses[((size_t)r * N + i) * 3 + c] - poses[((size_t)q * N + i) * 3 + c];
+                        ss += d * d;
+                    }
+                if (ss / N <= thr * thr) { leader[r] = q; break; }
+            }
+        }
+        if (leader[r] == r) leads[nl++] = r;
+    }
+    /* ranking: leaders in geometric order, then the others */
+    int n = 0;
+    for (int p = 0; p < S; p++) if (leader[geo[p]] == geo[p]) order[n++] = geo[p];
+    for (int p = 0; p < S; p++) if (leader[geo[p]] != geo[p]) order[n++] = geo[p];
+    /* rescore the first K */
+    const int k = (K <= 0 || K > S) ? S : K;
+    int br = -1;
+    double be = INFINITY;
+    for (int p = 0; p < k; p++) {
+        const int r = order[p];
+        if (E[r] < be || (E[r] == be && r < br)) { be = E[r]; br = r; }
+    }
+    *best_r = br;
+    *best_E = be;
+    free(geo);
+    free(leads);
+}
+
 /* ------------------------------------------------------------------ docking */
 /* Outputs (any may be NULL except restart_E):
  *   restart_E[S], restart_Eabs[S]      score and sum of |per-atom terms| per restart
@@ -245,13 +311,16 @@ int or_validate(int32_t N, const int16_t *parent, const uint8_t *type, int32_t R
  *                                      (+inf when the bond has no checked pair)
  *   poses[S][N][3]                     final pose of every restart
  *   best_pose[N][3]                    final pose of the best restart
+ *   rank_out[2S] (with ranking)        ranked restarts, then each restart's leader
+ *   geo_out[S] (with ranking)          geometric score of every restart
  * replay[S][P][R] (optional): apply these steps instead of the oracle's own,
  * still recording what the oracle would have chosen. */
 int or_dock_ligand(const or_pocket *P, const or_params *prm, int32_t N, const float *x, const float *y,
                    const float *z, const float *q, const uint8_t *type, const int16_t *parent, int32_t R,
                    const int16_t *rot_child, uint64_t uid, const uint8_t *replay, double *restart_E,
                    double *restart_Eabs, uint8_t *choice, uint8_t *own, double *trace_s, double *trace_d2,
-                   double *poses, double *best_pose, int32_t *best_r, double *best_E) {
+                   double *poses, double *best_pose, int32_t *best_r, double *best_E, int32_t *rank_out,
+                   double *geo_out) {
     int32_t end[OR_MAXN];
     if (or_validate(N, parent, type, R, rot_child, end) != 0) return -1;
     const int S = prm->restarts, PS = prm->passes, A = prm->angle_steps;
@@ -265,6 +334,8 @@ int or_dock_ligand(const or_pocket *P, const or_params *prm, int32_t N, const fl
     double bestE = INFINITY;
     int bestR = -1;
     const double dc2 = prm->d_clash * prm->d_clash;
+    const int ranking = prm->cluster_rmsd > 0.0 || (prm->rescore_top > 0 && prm->rescore_top < S);
+    double *allposes = ranking ? (double *)malloc(sizeof(double) * 3 * (size_t)S * N) : NULL;
 
     for (int r = 0; r < S; r++) {
         double Rm[9], p[3];
@@ -321,11 +392,28 @@ int or_dock_ligand(const or_pocket *P, const or_params *prm, int32_t N, const fl
         restart_E[r] = E;
         if (restart_Eabs) restart_Eabs[r] = eabs;
         if (poses) memcpy(poses + (size_t)r * N * 3, &X[0][0], sizeof(double) * 3 * N);
+        if (allposes) memcpy(allposes + (size_t)r * N * 3, &X[0][0], sizeof(double) * 3 * N);
         if (E < bestE) {
             bestE = E;
             bestR = r;
             if (best_pose) memcpy(best_pose, &X[0][0], sizeof(double) * 3 * N);
         }
+    }
+    if (ranking) {
+        double *G = (double *)malloc(sizeof(double) * S);
+        int32_t *ord = (int32_t *)malloc(sizeof(int32_t) * S), *lead = (int32_t *)malloc(sizeof(int32_t) * S);
+        or_rank_poses(P, S, N, allposes, restart_E, prm->cluster_rmsd, prm->rescore_top, G, ord, lead, &bestR,
+                      &bestE);
+        if (rank_out) {
+            memcpy(rank_out, ord, sizeof(int32_t) * S);
+            memcpy(rank_out + S, lead, sizeof(int32_t) * S);
+        }
+        if (geo_out) memcpy(geo_out, G, sizeof(double) * S);
+        if (best_pose && bestR >= 0) memcpy(best_pose, allposes + (size_t)bestR * N * 3, sizeof(double) * 3 * N);
+        free(G);
+        free(ord);
+        free(lead);
+        free(allposes);
     }
     if (best_r) *best_r = bestR;
     if (best_E) *best_E = bestE;
@@ -334,13 +422,14 @@ int or_dock_ligand(const or_pocket *P, const or_params *prm, int32_t N, const fl
 
 /* Batch in CSR layout (see the generator for the layout).  Per-ligand output
  * offsets: restart arrays l*S; decisions S*P*rot_off[l]; traces A*S*P*rot_off[l];
- * poses 3*S*atom_off[l]; best poses 3*atom_off[l].  status[l] = 0 or -1. */
+ * poses 3*S*atom_off[l]; best poses 3*atom_off[l]; rankings 2*S*l; geometric
+ * scores S*l.  status[l] = 0 or -1. */
 int or_dock_batch(const or_pocket *P, const or_params *prm, int32_t L, const int32_t *atom_off, const float *x,
                   const float *y, const float *z, const float *q, const uint8_t *type, const int16_t *parent,
                   const int32_t *rot_off, const int16_t *rot_child, const uint64_t *uid, const uint8_t *replay,
                   double *restart_E, double *restart_Eabs, uint8_t *choice, uint8_t *own, double *trace_s,
                   double *trace_d2, double *poses, double *best_pose, int32_t *best_r, double *best_E,
-                  int32_t *status, int32_t nthreads) {
+                  int32_t *status, int32_t *rank_out, double *geo_out, int32_t nthreads) {
     const int S = prm->restarts, PS = prm->passes, A = prm->angle_steps;
     int bad = 0;
 #pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads > 0 ? nthreads : 1) reduction(+ : bad)
@@ -353,7 +442,8 @@ int or_dock_batch(const or_pocket *P, const or_params *prm, int32_t L, const int
             replay ? replay + d0 : NULL, restart_E + (size_t)l * S, restart_Eabs ? restart_Eabs + (size_t)l * S : NULL,
             choice ? choice + d0 : NULL, own ? own + d0 : NULL, trace_s ? trace_s + d0 * A : NULL,
             trace_d2 ? trace_d2 + d0 * A : NULL, poses ? poses + (size_t)3 * S * a0 : NULL,
-            best_pose ? best_pose + (size_t)3 * a0 : NULL, best_r + l, best_E + l);
+            best_pose ? best_pose + (size_t)3 * a0 : NULL, best_r + l, best_E + l,
+            rank_out ? rank_out + (size_t)2 * S * l : NULL, geo_out ? geo_out + (size_t)S * l : NULL);
         status[l] = rc;
         if (rc != 0) bad++;
     }

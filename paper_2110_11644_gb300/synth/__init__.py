@@ -263,6 +263,8 @@ class DockParams:
     angle_steps: int = 36
     seed: int = 0x2110116440000000
     d_clash: float = 2.0
+    cluster_rmsd: float = 0.0   # 0: no clustering
+    rescore_top: int = 0        # 0: rescore every pose
 
 
 CONFIG_SEEDS = {1: 0, 2: 2, 3: 3, 4: 4, 5: 5}

@@ -539,3 +539,70 @@ def test_degenerate_ligands(cfg1):
                             np.array([-1, 0, 3], np.int16), np.array([0, 0], np.int32), np.zeros(0, np.int16),
                             np.array([1], np.uint64))
     assert oracle.dock(pocket, bad, prm)["status"][0] != 0
+
+
+# ----------------------------------------------------------------------------- ranking (clustering + rescoring)
+def _check_ranking(pocket, poses, E, G, order, leader, thr, K, best_r, best_E):
+    S, N = poses.shape[0], poses.shape[1]
+    # G is the total overlap of the final pose (scipy interpolation)
+    for r in range(S):
+        assert abs(G[r] - _scipy_trilinear(pocket, pocket.phi_o, poses[r]).sum()) < 1e-9 * max(1.0, abs(G[r]))
+    geo = sorted(range(S), key=lambda r: (-G[r], r))
+    rmsd = lambda a, b: np.sqrt(((poses[a] - poses[b]) ** 2).sum(1).mean())
+    leaders = [r for r in geo if leader[r] == r]
+    for i, a in enumerate(leaders):                       # leaders are mutually farther than thr
+        for b in leaders[i + 1:]:
+            assert rmsd(a, b) > thr
+    pos = {r: i for i, r in enumerate(geo)}
+    for r in range(S):
+        if leader[r] != r:
+            q = leader[r]
+            assert leader[q] == q and pos[q] < pos[r] and rmsd(q, r) <= thr
+            earlier = [l for l in leaders if pos[l] < pos[q]]
+            assert all(rmsd(l, r) > thr for l in earlier)   # it joined the first leader within thr
+        else:
+            assert all(rmsd(l, r) > thr for l in leaders if pos[l] < pos[r])
+    assert list(order) == leaders + [r for r in geo if leader[r] != r]
+    k = S if K <= 0 or K > S else K
+    top = list(order[:k])
+    want = min(top, key=lambda r: (E[r], r))
+    assert best_r == want and best_E == E[want]
+
+
+def test_ranking_clusters_and_rescores(cfg1):
+    pocket, batch, prm = cfg1
+    sub = batch.subset(range(24))
+    grouped = {}
+    for thr, K in ((3.0, 5), (1.5, 3), (9.0, 16), (9.0, 4), (3.0, 0)):
+        p = synth.DockParams(restarts=16, passes=2, seed=prm.seed, cluster_rmsd=thr, rescore_top=K)
+        out = oracle.dock(pocket, sub, p, poses=True)
+        n_clusters = []
+        for l in range(sub.L):
+            N = int(sub.n_atoms()[l])
+            a0 = int(sub.atom_off[l])
+            poses = out["poses"][3 * 16 * a0: 3 * 16 * (a0 + N)].reshape(16, N, 3)
+            _check_ranking(pocket, poses, out["restart_E"][l], out["geo"][l], out["order"][l], out["leader"][l],
+                           thr, K, int(out["best_r"][l]), out["best_E"][l])
+            n_clusters.append(int((out["leader"][l] == np.arange(16)).sum()))
+        grouped[thr] = np.mean(n_clusters)
+    assert grouped[9.0] < 12 < grouped[3.0]          # the larger threshold actually groups poses
+
+
+def test_ranking_limits():
+    # threshold 0: every pose leads its own cluster -> pure geometric order;
+    # a huge threshold: one cluster -> geometric order as well; K = all -> min E
+    rng = np.random.default_rng(12)
+    from paper_2110_11644_gb300 import synth as sy
+    pocket = sy.config_pocket(1)
+    poses = pocket.center + rng.normal(0, 4, size=(10, 7, 3))
+    E = rng.normal(size=10)
+    for thr in (0.0, 1e6):
+        G, order, leader, br, be = oracle.rank_poses(pocket, poses, E, thr, 0)
+        geo = sorted(range(10), key=lambda r: (-G[r], r))
+        assert list(order) == geo
+        assert br == int(np.argmin(E)) and be == E.min()
+    G, order, leader, br, be = oracle.rank_poses(pocket, poses, E, 1e6, 0)
+    assert (leader == geo[0]).all()
+    # rescoring only the first K ranked poses
+    G, order, leader, br, be = oracle.rank_poses(pocket, poses, E, 0.0, 3)
+    assert br == min(order[:3], key=lambda r: (E[r], r))
