@@ -153,7 +153,22 @@ typedef struct {
  *                library limits).  They size the kernels' shared memory: a
  *                smaller declaration lets more CTAs share an SM.  Ligands
  *                above a declared maximum get status LG_EINVAL.  For host
- *                batches the library also measures the maxima itself. */
+ *                batches the library also measures the maxima itself.
+ *   cluster_rmsd, rescore_top  pose ranking (paper Sec. 3.1, steps 3-4), off
+ *                when cluster_rmsd = 0 and rescore_top is 0 or >= restarts:
+ *                the restart poses are ordered by geometric score (the total
+ *                overlap of the pose, higher first, lower restart on ties) and
+ *                clustered greedily -- a pose within cluster_rmsd A RMSD (no
+ *                superposition) of an earlier cluster leader joins the first
+ *                such leader, else it leads a new cluster; the ranking lists
+ *                the leaders, then the other poses, in that order; the first
+ *                rescore_top ranked poses (all when 0) are rescored and the
+ *                lowest score among them is the ligand's result.  The paper's
+ *                setting is 256 restarts, 3 A and the top 30.  Ranking keeps
+ *                every restart's final pose in device scratch (12 bytes per
+ *                atom and restart for each ligand docked at once) and needs
+ *                shared memory growing as restarts^2 / 16 bytes (68 KB at
+ *                1,024 restarts), which can lower the kernels' occupancy. */
 typedef struct {
     int32_t restarts;
     int32_t passes;
@@ -164,6 +179,8 @@ typedef struct {
     int32_t plain_streams;
     int32_t max_atoms;
     int32_t max_rot;
+    float cluster_rmsd;
+    int32_t rescore_top;
 } lg_dock_params;
 
 /* Caller-owned outputs (all with the location given by `mem`).
@@ -175,7 +192,10 @@ typedef struct {
  *   status [L]         LG_OK or LG_EINVAL per ligand
  *   restart_score      optional: E of every restart, l*restarts + r
  *   restart_tors       optional: steps of every restart,
- *                      restarts*passes*rot_off[l] + (r*passes + pass)*R_l + k */
+ *                      restarts*passes*rot_off[l] + (r*passes + pass)*R_l + k
+ *   rank, leader, restart_geo  optional, with pose ranking on: the ranked
+ *                      restarts (l*restarts + position), each restart's cluster
+ *                      leader and geometric score (l*restarts + r) */
 typedef struct {
     int32_t mem;
     double *score;
@@ -185,6 +205,9 @@ typedef struct {
     int32_t *status;
     double *restart_score;
     uint8_t *restart_tors;
+    int32_t *rank;
+    int32_t *leader;
+    double *restart_geo;
 } lg_dock_result;
 
 /* Dock and score a batch of ligands against one pocket (paper Sec. 3.1).
@@ -204,7 +227,10 @@ typedef struct {
  *   3. score: E = sum over atoms of type_w*phi_v + q*phi_e at the position
  *      clamped to the grid box, plus k_out times the distance outside the box;
  *      per-atom terms in FP32, sum in FP64.
- *   4. best: the lowest E wins, the lowest restart on ties.
+ *   4. best: the lowest E wins, the lowest restart on ties.  With pose
+ *      ranking on (cluster_rmsd > 0, or 0 < rescore_top < restarts) the best
+ *      is instead the lowest E among the first rescore_top ranked poses; see
+ *      lg_dock_params and lg_dock_result for the ranking's definition.
  * Geometry and lookups run in FP32.
  *
  * Memory: if the batch and result are device memory the call is asynchronous
@@ -236,6 +262,8 @@ int lg_dock_batch(lg_ctx *ctx, int32_t pocket_id, const lg_ligand_batch *batch, 
  *     it; the call clears the counters that must start at zero.  Calls whose
  *     work overlaps on the GPU race on the array: order them on one stream.
  *   - The pocket must already be loaded (lg_pocket_load allocates).
+ *   - Pose ranking (cluster_rmsd > 0, or 0 < rescore_top < restarts) needs
+ *     per-CTA pose slots that the fixed array does not hold: LG_EINVAL.
  * Errors: LG_EINVAL, LG_ENOPOCKET, LG_ECUDA. */
 #define LG_NOALLOC_SCRATCH_BYTES (4u << 20)
 int lg_dock_batch_noalloc(lg_ctx *ctx, int32_t pocket_id, const lg_ligand_batch *batch, const lg_dock_params *params,

@@ -54,6 +54,9 @@ struct OutDev {
     int32_t *status;
     double *restart_score;
     uint8_t *restart_tors;
+    int32_t *rank;
+    int32_t *leader;
+    double *restart_geo;
 };
 
 // Shared-memory layout of one docking CTA: a part shared by the CTA (the
@@ -135,7 +138,28 @@ struct Scratch {
     int32_t *order;        // [L] visiting order
     double *centroid;      // [3L]
     int16_t *rot_end;      // [L * rmax_lim] end of each torsional child's subtree
+    // pose ranking: per CTA slot, every restart's final pose (centred grid
+    // units, [S][nmax][3]), score and decisions ([S][P*rmax])
+    float *rk_pose;
+    double *rk_E;
+    uint8_t *rk_tors;
 };
+
+// Ranking step: row p of the "within the RMSD threshold" bit matrix holds
+// one bit per earlier position q < p, packed in ceil(p/32) words; rank_row_off
+// is the word offset of row p (the sum of ceil(i/32) over i < p).
+__host__ __device__ inline int rank_row_off(int p) {
+    const int n = p - 1;
+    if (n <= 0) return 0;
+    const int k = (n + 31) / 32;
+    return 16 * k * (k - 1) + k * (n - 32 * (k - 1));
+}
+
+// Shared memory the ranking step needs (it reuses the warps' regions):
+// geometric scores and centroids (FP64), order, leaders, ranking, bit matrix.
+__host__ __device__ inline int rank_smem_bytes(int S) {
+    return lg_align16(8 * S) + lg_align16(24 * S) + 3 * lg_align16(4 * S) + lg_align16(4 * (rank_row_off(S) + 1)) + 64;
+}
 
 struct DockArgs {
     PocketDev pocket;
@@ -148,6 +172,9 @@ struct DockArgs {
     uint32_t seed_lo, seed_hi;
     float dc2g;                // d_clash^2 in grid units
     int nmax_lim, rmax_lim;    // per-ligand maxima (declared and within the layout)
+    int ranking;               // pose ranking on
+    float thr2g;               // cluster RMSD^2 in grid units
+    int rescore_top;           // K (0 = all)
     const int32_t *order;      // batched mode: ligand visiting order (NULL = identity)
     int32_t *work_counter;     // batched mode: next item of the persistent loop
 };
@@ -155,13 +182,13 @@ struct DockArgs {
 constexpr int kSortBuckets = 128;
 
 // Byte size of the scratch of a launch, and its carving.
-size_t scratch_bytes(int L, int rmax);
-Scratch carve_scratch(void *base, int L, int rmax);
+size_t scratch_bytes(int L, int rmax, int rank_slots = 0, int S = 0, int P = 0, int nmax = 0);
+Scratch carve_scratch(void *base, int L, int rmax, int rank_slots = 0, int S = 0, int P = 0, int nmax = 0);
 
 // Launchers (lg_kernels.cu)
 void set_angle_tables(const float *cosv, const float *sinv);
 cudaError_t launch_prep(const DockArgs &a, bool sort, cudaStream_t s, int *launches);
-cudaError_t launch_dock_plain(const DockArgs &a, int ligand, cudaStream_t s);
+cudaError_t launch_dock_plain(const DockArgs &a, int ligand, int slot, cudaStream_t s);
 cudaError_t launch_dock_batched(const DockArgs &a, int grid, int smem, cudaStream_t s);
 cudaError_t launch_score_poses(const PocketDev &p, int L, const int32_t *atom_off, const float *xyz,
                                const float *q, const uint8_t *type, double *E, cudaStream_t s);

@@ -145,6 +145,198 @@ __device__ __forceinline__ void finish_ligand(const DockArgs &A, const CtaView &
     __syncthreads();
 }
 
+// Keep restart r's final pose (centred grid units), score and decisions in
+// the CTA's ranking slot.  X is the pose with a stride between atoms.
+__device__ __forceinline__ size_t rk_pose_off(const DockArgs &A, int slot, int r) {
+    return ((size_t)slot * A.S + r) * (size_t)A.ly.nmax * 3;
+}
+
+// Pose ranking (paper Sec. 3.1, steps 3-4) of ligand l from the restarts kept
+// in the CTA's slot, and the ligand's outputs.  All threads of the CTA call it
+// after a barrier; it reuses the warps' shared memory.
+//   1. geometric score G_r = sum over atoms of the overlap grid (FP32 terms,
+//      FP64 warp sum in a fixed order);
+//   2. geometric order: higher G first, lower restart on ties;
+//   3. greedy leader clustering in that order: a pose joins the first earlier
+//      leader whose RMSD (no superposition) is at most the threshold;
+//   4. ranking = leaders in order, then the other poses in order;
+//   5. the lowest score among the first K ranked poses (lowest restart on ties).
+// Step 3 first marks every pair within the threshold (a bit matrix), then walks
+// the positions in order on one warp.  A pair is within the threshold when the
+// FP32 sum of squared coordinate differences is at most thr^2 * N; pairs whose
+// centroids are farther apart than the threshold (with a 1e-4 relative margin
+// over the FP32 sum's rounding) cannot be, since the mean squared distance is
+// at least the squared distance of the means, and skip the sum.
+__device__ void rank_finish(const DockArgs &A, int l, int slot, int a0, int N, int r0, int PR, char *rbase) {
+    const int S = A.S, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, W = blockDim.x >> 5;
+    const PocketDev &Pk = A.pocket;
+    char *q = rbase;
+    double *sG = (double *)q;
+    q += lg_align16(8 * S);
+    double *cen = (double *)q;  // [S][3], by restart
+    q += lg_align16(24 * S);
+    int *ord = (int *)q;        // restart at each geometric position
+    q += lg_align16(4 * S);
+    int *lpos = (int *)q;       // leader position of each geometric position
+    q += lg_align16(4 * S);
+    int *rk = (int *)q;         // ranked restarts
+    q += lg_align16(4 * S);
+    unsigned *bits = (unsigned *)q;
+    q += lg_align16(4 * (rank_row_off(S) + 1));
+    int *bestv = (int *)q;
+    const GridK Go = grid_k(Pk, Pk.cell_o);
+    const float *pose0 = A.scr.rk_pose + rk_pose_off(A, slot, 0);
+    const size_t pstride = (size_t)A.ly.nmax * 3;
+    const bool cluster = A.thr2g > 0.0f;
+
+    // 1. geometric scores (and centroids for the clustering bound)
+    for (int r = warp; r < S; r += W) {
+        const float *x = pose0 + pstride * r;
+        double g = 0.0, cx = 0.0, cy = 0.0, cz = 0.0;
+        for (int i = lane; i < N; i += 32) {
+            const float px = x[3 * i], py = x[3 * i + 1], pz = x[3 * i + 2];
+            g += (double)lookup_clamped(Go, px + Pk.c0, py + Pk.c0, pz + Pk.c0);
+            cx += px;
+            cy += py;
+            cz += pz;
+        }
+        g = warp_sum_d(g);
+        if (cluster) {
+            cx = warp_sum_d(cx);
+            cy = warp_sum_d(cy);
+            cz = warp_sum_d(cz);
+        }
+        if (lane == 0) {
+            sG[r] = g;
+            cen[3 * r] = cx / N;
+            cen[3 * r + 1] = cy / N;
+            cen[3 * r + 2] = cz / N;
+        }
+    }
+    __syncthreads();
+    // 2. geometric order
+    for (int r = tid; r < S; r += blockDim.x) {
+        const double gr = sG[r];
+        int c = 0;
+        for (int o = 0; o < S; ++o) {
+            const double go = sG[o];
+            c += (go > gr) || (go == gr && o < r);
+        }
+        ord[c] = r;
+    }
+    __syncthreads();
+    // 3a. pairs within the threshold: bit q of row p for positions q < p
+    const float lim = A.thr2g * (float)N;
+    if (cluster) {
+        const double cut = (double)A.thr2g * (1.0 + 1e-4);
+        for (int p = warp; p < S; p += W) {
+            const int rp = ord[p];
+            const float *x = pose0 + pstride * rp;
+            const double px = cen[3 * rp], py = cen[3 * rp + 1], pz = cen[3 * rp + 2];
+            for (int w = 0; 32 * w < p; ++w) {
+                const int qq = 32 * w + lane;
+                bool within = false;
+                if (qq < p) {
+                    const int rq = ord[qq];
+                    const double dx = cen[3 * rq] - px, dy = cen[3 * rq + 1] - py, dz = cen[3 * rq + 2] - pz;
+                    if (dx * dx + dy * dy + dz * dz <= cut) {
+                        const float *y = pose0 + pstride * rq;
+                        float ss = 0.0f;
+                        for (int i = 0; i < 3 * N; ++i) {
+                            const float d = x[i] - y[i];
+                            ss = fmaf(d, d, ss);
+                        }
+                        within = ss <= lim;
+                    }
+                }
+                const unsigned word = __ballot_sync(LG_FULL, within);
+                if (lane == 0) bits[rank_row_off(p) + w] = word;
+            }
+        }
+    }
+    __syncthreads();
+    if (warp == 0) {
+        // 3b. leaders in geometric order; lane w keeps word w of the leader set
+        unsigned lead = 0;
+        for (int p = 0; p < S; ++p) {
+            const int nw = (p + 31) >> 5;
+            const unsigned cand = (cluster && lane < nw) ? (bits[rank_row_off(p) + lane] & lead) : 0u;
+            const unsigned any = __ballot_sync(LG_FULL, cand != 0u);
+            if (any) {
+                const int fw = __ffs(any) - 1;
+                const unsigned c = __shfl_sync(LG_FULL, cand, fw);
+                if (lane == 0) lpos[p] = 32 * fw + __ffs(c) - 1;
+            } else {
+                if (lane == (p >> 5)) lead |= 1u << (p & 31);
+                if (lane == 0) lpos[p] = p;
+            }
+        }
+        __syncwarp();
+        // 4. ranking: leaders, then the others, each in geometric order
+        int n = 0;
+        for (int pass = 0; pass < 2; ++pass)
+            for (int b0 = 0; b0 < S; b0 += 32) {
+                const int p = b0 + lane;
+                const bool take = p < S && ((lpos[p] == p) == (pass == 0));
+                const unsigned bal = __ballot_sync(LG_FULL, take);
+                if (take) rk[n + __popc(bal & ((1u << lane) - 1u))] = ord[p];
+                n += __popc(bal);
+            }
+        __syncwarp();
+        // 5. rescore the first K
+        const int K = (A.rescore_top <= 0 || A.rescore_top > S) ? S : A.rescore_top;
+        double be = INFINITY;
+        int br = 0x7fffffff;
+        for (int p = lane; p < K; p += 32) {
+            const int r = rk[p];
+            const double e = A.scr.rk_E[(size_t)slot * S + r];
+            if (e < be || (e == be && r < br)) {
+                be = e;
+                br = r;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double oe = __shfl_xor_sync(LG_FULL, be, o);
+            const int orr = __shfl_xor_sync(LG_FULL, br, o);
+            if (oe < be || (oe == be && orr < br)) {
+                be = oe;
+                br = orr;
+            }
+        }
+        if (lane == 0) {
+            const bool ok = br != 0x7fffffff && isfinite(be);
+            bestv[0] = ok ? br : -1;
+            A.out.score[l] = ok ? be : __longlong_as_double(0x7ff8000000000000ll);
+            A.out.best_restart[l] = ok ? br : -1;
+            if (!ok) A.out.status[l] = LG_EINVAL;
+        }
+    }
+    __syncthreads();
+    const int br = bestv[0];
+    if (br >= 0) {
+        if (A.out.tors_idx)
+            for (int t = tid; t < PR; t += blockDim.x)
+                A.out.tors_idx[(size_t)A.P * r0 + t] = A.scr.rk_tors[((size_t)slot * S + br) * A.P * A.ly.rmax + t];
+        if (A.out.pose) {
+            const float *x = pose0 + pstride * br;
+            const float3 c = Pk.center;
+            for (int i = tid; i < N; i += blockDim.x) {
+                float *o = A.out.pose + 3 * (size_t)(a0 + i);
+                o[0] = fmaf(x[3 * i], Pk.h, c.x);
+                o[1] = fmaf(x[3 * i + 1], Pk.h, c.y);
+                o[2] = fmaf(x[3 * i + 2], Pk.h, c.z);
+            }
+        }
+    }
+    for (int p = tid; p < S; p += blockDim.x) {
+        if (A.out.rank) A.out.rank[(size_t)l * S + p] = rk[p];
+        if (A.out.leader) A.out.leader[(size_t)l * S + ord[p]] = ord[lpos[p]];
+        if (A.out.restart_geo) A.out.restart_geo[(size_t)l * S + ord[p]] = sG[ord[p]];
+    }
+    __syncthreads();
+}
+
 // ================================================================== plain form
 struct WarpView {
     float4 *bundle;  // 32 atoms x 4 float4 (see sweep_bond_plain); also per-atom energy terms
@@ -277,7 +469,7 @@ __device__ int sweep_bond_plain(const DockArgs &A, const GridK &G, const CtaView
     return t;
 }
 
-__global__ void __launch_bounds__(1024) k_dock_plain(const __grid_constant__ DockArgs A, int l) {
+__global__ void __launch_bounds__(1024) k_dock_plain(const __grid_constant__ DockArgs A, int l, int slot) {
     extern __shared__ __align__(16) char sm[];
     if (A.out.status[l] != LG_OK) return;  // rejected by the preparation kernel
     const Layout &Ly = A.ly;
@@ -337,6 +529,16 @@ __global__ void __launch_bounds__(1024) k_dock_plain(const __grid_constant__ Doc
         if (A.out.restart_score && lane == 0) A.out.restart_score[(size_t)l * S + r] = E;
         if (A.out.restart_tors)
             for (int t = lane; t < PR; t += 32) A.out.restart_tors[(size_t)S * P * r0 + (size_t)r * PR + t] = wv.tcur[t];
+        if (A.ranking) {  // keep the restart for the ranking step
+            float *x = A.scr.rk_pose + rk_pose_off(A, slot, r);
+            for (int i = lane; i < N; i += 32) {
+                x[3 * i] = wv.Xx[i];
+                x[3 * i + 1] = wv.Xy[i];
+                x[3 * i + 2] = wv.Xz[i];
+            }
+            for (int t = lane; t < PR; t += 32) A.scr.rk_tors[((size_t)slot * S + r) * P * Ly.rmax + t] = wv.tcur[t];
+            if (lane == 0) A.scr.rk_E[(size_t)slot * S + r] = E;
+        }
         if (E < bestE) {  // restarts visited in ascending order: ties keep the lower one
             bestE = E;
             bestR = r;
@@ -349,6 +551,11 @@ __global__ void __launch_bounds__(1024) k_dock_plain(const __grid_constant__ Doc
                 }
         }
         __syncwarp();
+    }
+    if (A.ranking) {
+        __syncthreads();
+        rank_finish(A, l, slot, a0, N, r0, PR, sm + Ly.cta_bytes);
+        return;
     }
     if (lane == 0) {
         cv.wE[warp] = bestE;
@@ -625,6 +832,17 @@ __device__ void dock_ligand_rt(const DockArgs &A, int l, char *sm) {
             if (A.out.restart_tors)
                 for (int t = g; t < PR; t += kLanesPerRestart)
                     A.out.restart_tors[(size_t)S * P * r0 + (size_t)r * PR + t] = v.tcur[t * kTile + rs];
+            if (A.ranking) {  // keep the restart for the ranking step
+                float *x = A.scr.rk_pose + rk_pose_off(A, blockIdx.x, r);
+                for (int i = g; i < N; i += kLanesPerRestart) {
+                    x[3 * i] = v.Xx[i * kTile + rs];
+                    x[3 * i + 1] = v.Xy[i * kTile + rs];
+                    x[3 * i + 2] = v.Xz[i * kTile + rs];
+                }
+                for (int t = g; t < PR; t += kLanesPerRestart)
+                    A.scr.rk_tors[((size_t)blockIdx.x * S + r) * P * Ly.rmax + t] = v.tcur[t * kTile + rs];
+                if (g == 0) A.scr.rk_E[(size_t)blockIdx.x * S + r] = E;
+            }
         }
         // 4. best restart of the tile (lowest E, then lowest restart)
         double te = valid ? E : INFINITY;
@@ -651,6 +869,11 @@ __device__ void dock_ligand_rt(const DockArgs &A, int l, char *sm) {
                 }
         }
         __syncwarp();
+    }
+    if (A.ranking) {
+        __syncthreads();
+        rank_finish(A, l, blockIdx.x, a0, N, r0, PR, sm + Ly.cta_bytes);
+        return;
     }
     if (lane == 0) {
         cv.wE[warp] = bestE;
@@ -828,13 +1051,20 @@ __global__ void k_diag_philox(int n, const uint32_t *ctr, const uint32_t *key, u
 // ================================================================== host side
 static size_t al256(size_t v) { return (v + 255) & ~(size_t)255; }
 
-size_t scratch_bytes(int L, int rmax) {
-    return al256(4 * (kSortBuckets + 1)) + 2 * al256(4 * (size_t)L) + al256(24 * (size_t)L) +
-           al256(2 * (size_t)L * (rmax > 0 ? rmax : 1));
+size_t scratch_bytes(int L, int rmax, int rank_slots, int S, int P, int nmax) {
+    rmax = rmax > 0 ? rmax : 1;
+    size_t b = al256(4 * (kSortBuckets + 1)) + 2 * al256(4 * (size_t)L) + al256(24 * (size_t)L) +
+               al256(2 * (size_t)L * rmax);
+    if (rank_slots > 0) {
+        const size_t nm = (size_t)((nmax + 3) & ~3);
+        b += al256(12 * (size_t)rank_slots * S * nm) + al256(8 * (size_t)rank_slots * S) +
+             al256((size_t)rank_slots * S * P * rmax + 1);
+    }
+    return b;
 }
 
-Scratch carve_scratch(void *base, int L, int rmax) {
-    (void)rmax;
+Scratch carve_scratch(void *base, int L, int rmax, int rank_slots, int S, int P, int nmax) {
+    rmax = rmax > 0 ? rmax : 1;
     char *p = (char *)base;
     Scratch s;
     s.hist = (int32_t *)p;
@@ -846,6 +1076,18 @@ Scratch carve_scratch(void *base, int L, int rmax) {
     s.centroid = (double *)p;
     p += al256(24 * (size_t)L);
     s.rot_end = (int16_t *)p;
+    p += al256(2 * (size_t)L * rmax);
+    s.rk_pose = nullptr;
+    s.rk_E = nullptr;
+    s.rk_tors = nullptr;
+    if (rank_slots > 0) {
+        const size_t nm = (size_t)((nmax + 3) & ~3);
+        s.rk_pose = (float *)p;
+        p += al256(12 * (size_t)rank_slots * S * nm);
+        s.rk_E = (double *)p;
+        p += al256(8 * (size_t)rank_slots * S);
+        s.rk_tors = (uint8_t *)p;
+    }
     return s;
 }
 
@@ -872,8 +1114,11 @@ cudaError_t launch_prep(const DockArgs &a, bool sort, cudaStream_t s, int *launc
     return cudaGetLastError();
 }
 
-cudaError_t launch_dock_plain(const DockArgs &a, int ligand, cudaStream_t s) {
-    k_dock_plain<<<1, 32 * a.ly.W, a.ly.total, s>>>(a, ligand);
+cudaError_t launch_dock_plain(const DockArgs &a, int ligand, int slot, cudaStream_t s) {
+    const int smem = a.ranking ? (a.ly.total > a.ly.cta_bytes + rank_smem_bytes(a.S) ? a.ly.total
+                                                                                    : a.ly.cta_bytes + rank_smem_bytes(a.S))
+                               : a.ly.total;
+    k_dock_plain<<<1, 32 * a.ly.W, smem, s>>>(a, ligand, slot);
     return cudaGetLastError();
 }
 

@@ -59,6 +59,7 @@ extern "C" int lg_dock_batch_noalloc(lg_ctx *c, int32_t pid, const lg_ligand_bat
     int rc = check_params(p);
     if (rc) return rc;
     if (p->mode != LG_MODE_BATCHED) return fail(LG_EINVAL, "lg_dock_batch_noalloc runs the batched mode only");
+    if (ranking_on(p)) return fail(LG_EINVAL, "lg_dock_batch_noalloc does not run pose ranking (cluster_rmsd, rescore_top)");
     if (b->mem != LG_MEM_DEVICE || o->mem != LG_MEM_DEVICE)
         return fail(LG_EINVAL, "lg_dock_batch_noalloc takes device memory only (host staging would allocate)");
     if (b->L < 0) return fail(LG_EINVAL, "L must be >= 0");

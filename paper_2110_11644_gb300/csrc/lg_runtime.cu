@@ -53,6 +53,12 @@ struct Carve {
     }
 };
 
+// Pose ranking replaces the plain lowest-score choice when poses are
+// clustered or only the first K ranked poses are rescored.
+bool ranking_on(const lg_dock_params *p) {
+    return p->cluster_rmsd > 0.0f || (p->rescore_top > 0 && p->rescore_top < p->restarts);
+}
+
 int check_params(const lg_dock_params *p) {
     if (p->restarts < 1 || p->restarts > LG_MAX_RESTARTS) return fail(LG_EINVAL, "restarts out of range");
     if (p->passes < 0 || p->passes > LG_MAX_PASSES) return fail(LG_EINVAL, "passes out of range");
@@ -62,6 +68,9 @@ int check_params(const lg_dock_params *p) {
     if (p->plain_streams < 0 || p->plain_streams > 64) return fail(LG_EINVAL, "plain_streams out of range");
     if (p->max_atoms < 0 || p->max_atoms > LG_MAX_ATOMS) return fail(LG_EINVAL, "max_atoms out of range");
     if (p->max_rot < 0 || p->max_rot > LG_MAX_ROT) return fail(LG_EINVAL, "max_rot out of range");
+    if (!(p->cluster_rmsd >= 0.0f) || !std::isfinite(p->cluster_rmsd))
+        return fail(LG_EINVAL, "cluster_rmsd must be finite and >= 0");
+    if (p->rescore_top < 0) return fail(LG_EINVAL, "rescore_top must be >= 0");
     return LG_OK;
 }
 
@@ -133,6 +142,9 @@ int stage_out(DevBuf &buf, const lg_dock_result *o, int L, int S, int P, int64_t
     const size_t o_p = o->pose ? c.take(12 * (size_t)A) : 0;
     const size_t o_rs = o->restart_score ? c.take(8 * (size_t)L * S) : 0;
     const size_t o_rt = o->restart_tors ? c.take((size_t)S * P * R + 1) : 0;
+    const size_t o_rk = o->rank ? c.take(4 * (size_t)L * S) : 0;
+    const size_t o_ld = o->leader ? c.take(4 * (size_t)L * S) : 0;
+    const size_t o_g = o->restart_geo ? c.take(8 * (size_t)L * S) : 0;
     if (buf.ensure(c.off)) return fail(LG_ENOMEM, "device output allocation failed");
     char *base = (char *)buf.p;
     d->score = (double *)(base + o_s);
@@ -142,6 +154,9 @@ int stage_out(DevBuf &buf, const lg_dock_result *o, int L, int S, int P, int64_t
     d->pose = o->pose ? (float *)(base + o_p) : nullptr;
     d->restart_score = o->restart_score ? (double *)(base + o_rs) : nullptr;
     d->restart_tors = o->restart_tors ? (uint8_t *)(base + o_rt) : nullptr;
+    d->rank = o->rank ? (int32_t *)(base + o_rk) : nullptr;
+    d->leader = o->leader ? (int32_t *)(base + o_ld) : nullptr;
+    d->restart_geo = o->restart_geo ? (double *)(base + o_g) : nullptr;
     return LG_OK;
 }
 
@@ -157,6 +172,9 @@ int fetch_out(const OutDev &d, const lg_dock_result *o, int L, int S, int P, int
     if (o->pose) cp(o->pose, d.pose, 12 * (size_t)A);
     if (o->restart_score) cp(o->restart_score, d.restart_score, 8 * (size_t)L * S);
     if (o->restart_tors) cp(o->restart_tors, d.restart_tors, (size_t)S * P * R);
+    if (o->rank) cp(o->rank, d.rank, 4 * (size_t)L * S);
+    if (o->leader) cp(o->leader, d.leader, 4 * (size_t)L * S);
+    if (o->restart_geo) cp(o->restart_geo, d.restart_geo, 8 * (size_t)L * S);
     if (e != cudaSuccess) return fail(LG_ECUDA, std::string("result download: ") + cudaGetErrorString(e));
     return LG_OK;
 }
@@ -203,20 +221,32 @@ int dock_device(lg_ctx *ctx, const PocketDev &pk, const BatchDev &bd, const OutD
     st->dock_ms = keep.dock_ms;
     const int L = bd.L;
     const bool plain = p->mode == LG_MODE_PLAIN;
-    if (scratch.ensure(scratch_bytes(L, rmax))) return fail(LG_ENOMEM, "scratch allocation failed");
-    a.scr = carve_scratch(scratch.p, L, rmax);
+    a.ranking = ranking_on(p) ? 1 : 0;
+    a.thr2g = (float)((double)p->cluster_rmsd * p->cluster_rmsd / (h * h));
+    a.rescore_top = p->rescore_top;
     cudaError_t e;
     int launches = 0;
-    if (!plain && (e = cudaMemsetAsync(a.scr.hist, 0, 4 * (kSortBuckets + 1), s)) != cudaSuccess)
-        return fail(LG_ECUDA, std::string("scratch clear: ") + cudaGetErrorString(e));
-    if ((e = launch_prep(a, !plain, s, &launches)) != cudaSuccess)
-        return fail(LG_ECUDA, std::string("preparation launch: ") + cudaGetErrorString(e));
+    // scratch holds one ranking slot per concurrently docked ligand: one per
+    // plain-mode stream, one per CTA of the persistent kernel
+    auto setup_scratch = [&](int slots) -> int {
+        if (scratch.ensure(scratch_bytes(L, rmax, a.ranking ? slots : 0, a.S, a.P, a.ly.nmax)))
+            return fail(LG_ENOMEM, "scratch allocation failed");
+        a.scr = carve_scratch(scratch.p, L, rmax, a.ranking ? slots : 0, a.S, a.P, a.ly.nmax);
+        if (!plain && (e = cudaMemsetAsync(a.scr.hist, 0, 4 * (kSortBuckets + 1), s)) != cudaSuccess)
+            return fail(LG_ECUDA, std::string("scratch clear: ") + cudaGetErrorString(e));
+        if ((e = launch_prep(a, !plain, s, &launches)) != cudaSuccess)
+            return fail(LG_ECUDA, std::string("preparation launch: ") + cudaGetErrorString(e));
+        return LG_OK;
+    };
+    const int rank_smem = a.ranking ? rank_smem_bytes(a.S) : 0;
     if (plain) {
         const int W = std::min(a.S, 32);
         a.ly = make_layout(nmax, rmax, a.P, W, want_pose);
-        if ((e = plain_kernel_attributes(a.ly.total)) != cudaSuccess)
+        const int psmem = std::max(a.ly.total, a.ly.cta_bytes + rank_smem);
+        if ((e = plain_kernel_attributes(psmem)) != cudaSuccess)
             return fail(LG_ECUDA, std::string("plain kernel attributes: ") + cudaGetErrorString(e));
         const int ns = p->plain_streams > 0 ? p->plain_streams : 8;
+        if (int rc = setup_scratch(ns)) return rc;
         if (ctx_plain_streams(ctx, ns)) return fail(LG_ECUDA, "plain-mode stream creation failed");
         std::vector<cudaStream_t> &ps = ctx_streams(ctx);
         cudaEvent_t fork = ctx_event(ctx, 0);
@@ -224,7 +254,7 @@ int dock_device(lg_ctx *ctx, const PocketDev &pk, const BatchDev &bd, const OutD
         cudaEventRecord(fork, s);
         for (int i = 0; i < ns; i++) cudaStreamWaitEvent(ps[i], fork, 0);
         for (int l = 0; l < L; l++) {
-            if ((e = launch_dock_plain(a, l, ps[l % ns])) != cudaSuccess)
+            if ((e = launch_dock_plain(a, l, l % ns, ps[l % ns])) != cudaSuccess)
                 return fail(LG_ECUDA, std::string("plain launch: ") + cudaGetErrorString(e));
         }
         for (int i = 0; i < ns; i++) {
@@ -237,7 +267,7 @@ int dock_device(lg_ctx *ctx, const PocketDev &pk, const BatchDev &bd, const OutD
         st->grid = L;
         st->warps_per_cta = W;
         st->ctas_per_sm = 1;
-        st->smem_bytes = a.ly.total;
+        st->smem_bytes = psmem;
         return LG_OK;
     }
     // batched: cost-ordered persistent launch of restart-tiled warps
@@ -246,16 +276,17 @@ int dock_device(lg_ctx *ctx, const PocketDev &pk, const BatchDev &bd, const OutD
     for (;;) {
         a.ly = make_layout(nmax, rmax, a.P, W, want_pose);
         a.lrt = make_layout_rt(nmax, rmax, a.P, want_pose);
-        smem = a.ly.cta_bytes + W * a.lrt.warp_bytes;
+        smem = std::max(a.ly.cta_bytes + W * a.lrt.warp_bytes, a.ly.cta_bytes + rank_smem);
         if ((e = dock_kernel_attributes(W, smem, &occ)) != cudaSuccess)
             return fail(LG_ECUDA, std::string("dock kernel attributes: ") + cudaGetErrorString(e));
         if (occ > 0 || W == 1) break;
         W = std::max(1, W / 2);
     }
     if (occ <= 0) return fail(LG_EINVAL, "docking kernel does not fit on an SM");
+    const int grid = std::max(1, std::min(ctx_num_sms(ctx) * occ, L));
+    if (int rc = setup_scratch(grid)) return rc;
     a.work_counter = a.scr.hist + kSortBuckets;
     a.order = a.scr.order;
-    const int grid = std::max(1, std::min(ctx_num_sms(ctx) * occ, L));
     if (timed) cudaEventRecord(tev[0], s);
     if ((e = launch_dock_batched(a, grid, smem, s)) != cudaSuccess)
         return fail(LG_ECUDA, std::string("dock launch: ") + cudaGetErrorString(e));
@@ -524,6 +555,9 @@ int lg_dock_batch(lg_ctx *c, int32_t pid, const lg_ligand_batch *b, const lg_doc
         od.pose = o->pose;
         od.restart_score = o->restart_score;
         od.restart_tors = o->restart_tors;
+        od.rank = o->rank;
+        od.leader = o->leader;
+        od.restart_geo = o->restart_geo;
     }
     cudaEvent_t *tev = nullptr;
     if (c->timing) {

@@ -28,6 +28,7 @@ struct PocketRec {
 struct Server;  // lg_serve.cu
 
 int fail(int code, const std::string &msg);
+bool ranking_on(const lg_dock_params *p);
 int check_params(const lg_dock_params *p);
 int host_batch_shape(const lg_ligand_batch *b, int64_t *A, int64_t *R, int *nmax, int *rmax);
 int stage_batch(DevBuf &buf, const lg_ligand_batch *b, int64_t A, int64_t R, BatchDev *d, cudaStream_t s);

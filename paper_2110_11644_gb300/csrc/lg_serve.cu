@@ -100,7 +100,11 @@ static bool same_kind(const Request &a, const Request &b) {
            a.params.d_clash == b.params.d_clash && (a.out.pose != nullptr) == (b.out.pose != nullptr) &&
            (a.out.tors_idx != nullptr) == (b.out.tors_idx != nullptr) &&
            (a.out.restart_score != nullptr) == (b.out.restart_score != nullptr) &&
-           (a.out.restart_tors != nullptr) == (b.out.restart_tors != nullptr);
+           (a.out.restart_tors != nullptr) == (b.out.restart_tors != nullptr) &&
+           a.params.cluster_rmsd == b.params.cluster_rmsd && a.params.rescore_top == b.params.rescore_top &&
+           (a.out.rank != nullptr) == (b.out.rank != nullptr) &&
+           (a.out.leader != nullptr) == (b.out.leader != nullptr) &&
+           (a.out.restart_geo != nullptr) == (b.out.restart_geo != nullptr);
 }
 
 // Concatenate the requests into the slot's pinned buffer and launch them.
@@ -168,7 +172,11 @@ static int launch_slot(Server *sv, Slot &sl) {
     hr.mem = LG_MEM_HOST;
     size_t ob = 8 * (size_t)L + 4 * (size_t)L + 4 * (size_t)L;
     const bool want_t = r0.out.tors_idx, want_p = r0.out.pose, want_rs = r0.out.restart_score,
-               want_rt = r0.out.restart_tors;
+               want_rt = r0.out.restart_tors, want_rk = r0.out.rank, want_ld = r0.out.leader,
+               want_g = r0.out.restart_geo;
+    ob += want_rk ? 4 * (size_t)L * S : 0;
+    ob += want_ld ? 4 * (size_t)L * S : 0;
+    ob += want_g ? 8 * (size_t)L * S : 0;
     ob += want_t ? (size_t)P * R : 0;
     ob += want_p ? 12 * (size_t)A : 0;
     ob += want_rs ? 8 * (size_t)L * S : 0;
@@ -177,8 +185,11 @@ static int launch_slot(Server *sv, Slot &sl) {
     char *o = (char *)sl.hout.p;
     hr.score = (double *)o; o += 8 * (size_t)L;
     if (want_rs) { hr.restart_score = (double *)o; o += 8 * (size_t)L * S; }
+    if (want_g) { hr.restart_geo = (double *)o; o += 8 * (size_t)L * S; }
     hr.best_restart = (int32_t *)o; o += 4 * (size_t)L;
     hr.status = (int32_t *)o; o += 4 * (size_t)L;
+    if (want_rk) { hr.rank = (int32_t *)o; o += 4 * (size_t)L * S; }
+    if (want_ld) { hr.leader = (int32_t *)o; o += 4 * (size_t)L * S; }
     if (want_p) { hr.pose = (float *)o; o += 12 * (size_t)A; }
     if (want_t) { hr.tors_idx = (uint8_t *)o; o += (size_t)P * R; }
     if (want_rt) { hr.restart_tors = (uint8_t *)o; }
@@ -216,6 +227,10 @@ static void finish_slot(Slot &sl, bool ok) {
                 memcpy(r->out.restart_score, hr.restart_score + (size_t)S * l0, 8 * (size_t)S * r->L);
             if (r->out.restart_tors && r->R)
                 memcpy(r->out.restart_tors, hr.restart_tors + (size_t)S * P * k0, (size_t)S * P * r->R);
+            if (r->out.rank) memcpy(r->out.rank, hr.rank + (size_t)S * l0, 4 * (size_t)S * r->L);
+            if (r->out.leader) memcpy(r->out.leader, hr.leader + (size_t)S * l0, 4 * (size_t)S * r->L);
+            if (r->out.restart_geo)
+                memcpy(r->out.restart_geo, hr.restart_geo + (size_t)S * l0, 8 * (size_t)S * r->L);
         }
         l0 += r->L;
         a0 += r->A;
@@ -239,7 +254,8 @@ static size_t request_device_bytes(const Request &r) {
     const size_t S = r.params.restarts, P = r.params.passes;
     return 40 * (size_t)r.L + 19 * (size_t)r.A + 2 * (size_t)r.R + (r.out.pose ? 12 * (size_t)r.A : 0) +
            (r.out.tors_idx ? P * r.R : 0) + (r.out.restart_score ? 8 * S * r.L : 0) +
-           (r.out.restart_tors ? S * P * r.R : 0) + 8 * (size_t)r.L + 4096;
+           (r.out.restart_tors ? S * P * r.R : 0) + (r.out.rank ? 4 * S * r.L : 0) +
+           (r.out.leader ? 4 * S * r.L : 0) + (r.out.restart_geo ? 8 * S * r.L : 0) + 8 * (size_t)r.L + 4096;
 }
 
 static void worker(Server *sv) {

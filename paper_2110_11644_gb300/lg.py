@@ -41,12 +41,14 @@ class lg_ligand_batch(ctypes.Structure):
 class lg_dock_params(ctypes.Structure):
     _fields_ = [("restarts", ctypes.c_int32), ("passes", ctypes.c_int32), ("angle_steps", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("d_clash", ctypes.c_float), ("mode", ctypes.c_int32),
-                ("plain_streams", ctypes.c_int32), ("max_atoms", ctypes.c_int32), ("max_rot", ctypes.c_int32)]
+                ("plain_streams", ctypes.c_int32), ("max_atoms", ctypes.c_int32), ("max_rot", ctypes.c_int32),
+                ("cluster_rmsd", ctypes.c_float), ("rescore_top", ctypes.c_int32)]
 
 
 class lg_dock_result(ctypes.Structure):
     _fields_ = [("mem", ctypes.c_int32), ("score", _P), ("best_restart", _P), ("tors_idx", _P), ("pose", _P),
-                ("status", _P), ("restart_score", _P), ("restart_tors", _P)]
+                ("status", _P), ("restart_score", _P), ("restart_tors", _P), ("rank", _P), ("leader", _P),
+                ("restart_geo", _P)]
 
 
 class lg_pose_batch(ctypes.Structure):
@@ -245,7 +247,8 @@ def make_batch_struct(arrs: dict, L: int) -> lg_ligand_batch:
     return b
 
 
-def make_params(restarts, passes, seed, d_clash=2.0, mode=LG_MODE_BATCHED, plain_streams=0, max_atoms=0, max_rot=0):
+def make_params(restarts, passes, seed, d_clash=2.0, mode=LG_MODE_BATCHED, plain_streams=0, max_atoms=0, max_rot=0,
+                cluster_rmsd=0.0, rescore_top=0):
     p = lg_dock_params()
     p.restarts, p.passes, p.angle_steps = int(restarts), int(passes), LG_ANGLE_STEPS
     p.seed = int(seed)
@@ -253,10 +256,12 @@ def make_params(restarts, passes, seed, d_clash=2.0, mode=LG_MODE_BATCHED, plain
     p.mode = int(mode)
     p.plain_streams = int(plain_streams)
     p.max_atoms, p.max_rot = int(max_atoms), int(max_rot)
+    p.cluster_rmsd, p.rescore_top = float(cluster_rmsd), int(rescore_top)
     return p
 
 
-def alloc_result(L, A, R, S, P, device=False, pose=True, tors=True, restart_score=False, restart_tors=False):
+def alloc_result(L, A, R, S, P, device=False, pose=True, tors=True, restart_score=False, restart_tors=False,
+                 ranking=False):
     """Output arrays for a batch: numpy (host) or CUDA torch tensors (device)."""
     if device:
         import torch
@@ -264,13 +269,17 @@ def alloc_result(L, A, R, S, P, device=False, pose=True, tors=True, restart_scor
         arrs = dict(score=z(L, torch.float64), best_restart=z(L, torch.int32), status=z(L, torch.int32),
                     tors_idx=z(P * R, torch.uint8) if tors else None, pose=z(3 * A, torch.float32) if pose else None,
                     restart_score=z(L * S, torch.float64) if restart_score else None,
-                    restart_tors=z(S * P * R, torch.uint8) if restart_tors else None)
+                    restart_tors=z(S * P * R, torch.uint8) if restart_tors else None,
+                    rank=z(L * S, torch.int32) if ranking else None, leader=z(L * S, torch.int32) if ranking else None,
+                    restart_geo=z(L * S, torch.float64) if ranking else None)
     else:
         z = lambda n, dt: np.zeros(max(n, 1), dt)
         arrs = dict(score=z(L, np.float64), best_restart=z(L, np.int32), status=z(L, np.int32),
                     tors_idx=z(P * R, np.uint8) if tors else None, pose=z(3 * A, np.float32) if pose else None,
                     restart_score=z(L * S, np.float64) if restart_score else None,
-                    restart_tors=z(S * P * R, np.uint8) if restart_tors else None)
+                    restart_tors=z(S * P * R, np.uint8) if restart_tors else None,
+                    rank=z(L * S, np.int32) if ranking else None, leader=z(L * S, np.int32) if ranking else None,
+                    restart_geo=z(L * S, np.float64) if ranking else None)
     r = lg_dock_result()
     r.mem = LG_MEM_DEVICE if device else LG_MEM_HOST
     for k, v in arrs.items():
@@ -334,15 +343,20 @@ class Context:
              restart_score=False, restart_tors=False, stream=None, plain_streams=0, max_atoms=0, max_rot=0):
         """Dock a CSR batch (numpy attributes).  With device_io=True the batch is
         copied to the GPU first and the results come back from device buffers;
-        otherwise the library stages host memory itself.  Returns numpy arrays."""
+        otherwise the library stages host memory itself.  Returns numpy arrays.
+        Pose ranking follows params.cluster_rmsd / params.rescore_top when the
+        params object has them; its outputs are then rank, leader, restart_geo."""
         L = len(batch.atom_off) - 1
         A, R = int(batch.atom_off[-1]), int(batch.rot_off[-1])
         S, P = int(params.restarts), int(params.passes)
         arrs = device_batch_arrays(batch) if device_io else host_batch_arrays(batch)
         b = make_batch_struct(arrs, L)
-        p = make_params(S, P, params.seed, params.d_clash, mode, plain_streams, max_atoms, max_rot)
+        thr = float(getattr(params, "cluster_rmsd", 0.0))
+        K = int(getattr(params, "rescore_top", 0))
+        ranking = thr > 0.0 or 0 < K < S
+        p = make_params(S, P, params.seed, params.d_clash, mode, plain_streams, max_atoms, max_rot, thr, K)
         r, outs = alloc_result(L, A, R, S, P, device=device_io, pose=pose, tors=tors, restart_score=restart_score,
-                               restart_tors=restart_tors)
+                               restart_tors=restart_tors, ranking=ranking)
         if device_io:
             import torch
             s = torch.cuda.current_stream()
@@ -352,7 +366,7 @@ class Context:
         else:
             lg_dock_batch(self.h, pid, b, p, r, stream)
         n = dict(score=L, best_restart=L, status=L, tors_idx=P * R, pose=3 * A, restart_score=L * S,
-                 restart_tors=S * P * R)
+                 restart_tors=S * P * R, rank=L * S, leader=L * S, restart_geo=L * S)
         return {k: (v[:n[k]] if v is not None else None) for k, v in outs.items()}
 
     def score_poses(self, pid, atom_off, xyz, q, type_):
