@@ -45,12 +45,17 @@ FLOP_PER_FMA = 2
 
 def algorithmic_flops(batch, S, P) -> float:
     """Algorithmic FLOPs of docking a batch (cost model in shard.py): per moving
-    atom and torsion step 12 for the point on its circle, 3 for the cell
-    fraction, 14 for the trilinear polynomial and 1 for the sum; 30 per moving
-    atom and decision for its circle and the move; per atom and restart 21 for
-    the rigid pose and 44 for the final score; 40 per restart for the pose draw."""
+    atom and torsion step 21 to rotate it and 30 for the trilinear lookup; 8 per
+    clash pair once per decision; per restart 21 per atom for the rigid pose,
+    40 for the pose draw and 64 per atom for the final score."""
     from paper_2110_11644_gb300 import shard
     return float(shard.ligand_flops(batch, S, P).sum())
+
+
+def circle_form_flops(batch, S, P) -> float:
+    """The lower FLOP count of the circle form the kernels evaluate."""
+    from paper_2110_11644_gb300 import shard
+    return float(shard.ligand_flops_circle(batch, S, P).sum())
 
 
 class ClockSampler:
@@ -354,6 +359,7 @@ def main():
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": achieved / peak_tflops, "traffic": traffic_for_current_kernel(),
                 "kernel": "k_dock_batched", "dock_ms_per_launch": dock_ms, "flop_per_launch": F,
+                "flop_per_launch_circle_form": circle_form_flops(batch, S, P),
                 "peak_basis": f"{sm_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max_mhz:.0f} MHz",
                 "limiter": "scattered L2->L1 gathers of 32-byte trilinear cells (L1TEX ~74% of peak in ncu) "
                            "and instruction issue; see profiles/dock_batched_ncu_small.md"}

@@ -7,9 +7,17 @@ The paper splits its input file into equal-size slabs per MPI rank and notes
 that this static split cannot balance ligands of very different cost
 (Sec. 3.2-3.3); here shards are balanced by the estimated docking cost instead.
 
-Cost model (also the bench's algorithmic FLOP count per ligand):
-  restarts * (passes * sum_k m_k * (36*30 + 30) + atoms * 65 + 40)
-with m_k the atoms torsional bond k moves.
+Cost model (also the bench's algorithmic FLOP count per ligand), the
+rotate-then-interpolate accounting of the method with an FMA counted as 2:
+  restarts * (21 N + 40 + passes * sum_k (36 m_k (21 + 30) + 8 Pi_k) + 64 N)
+with N the atoms, m_k the atoms torsional bond k moves and Pi_k the clash
+pairs of bond k (moving atom, atom outside the child's subtree, three or more
+bonds apart).  Per step and moving atom: 21 to rotate it about the bond,
+30 for a trilinear lookup; per restart 21 N + 40 for the rigid pose and 64 per
+atom for the final score.  A clash pair costs 8 and is credited once per
+decision (the chosen step's check, the least any method needs); clash checks
+of the other steps are not credited.  ligand_flops_circle counts the lower
+figure of the circle form the kernels evaluate.
 """
 from __future__ import annotations
 
@@ -17,12 +25,16 @@ import heapq
 
 import numpy as np
 
-C_LOOKUP, C_BOND, C_POSE_ATOM, C_FINAL_ATOM, C_RESTART = 30, 30, 21, 44, 40
+C_ROT, C_TRI, C_PAIR, C_FIN, C_POSE_ATOM, C_RESTART = 21, 30, 8, 64, 21, 40
+# circle form: 12 (point on the circle) + 3 (cell fractions) + 14 (polynomial)
+# + 1 (sum) per moving atom and step; 30 per moving atom and decision for its
+# circle and the move; 21 + 44 per atom and restart
+C_LOOKUP_CIRCLE, C_BOND_CIRCLE, C_FINAL_CIRCLE = 30, 30, 44
 
 
-def moving_atoms_per_ligand(batch) -> np.ndarray:
-    """Sum over each ligand's torsional bonds of the atoms the bond moves
-    (subtree size of the bond's child minus one)."""
+def _bond_counts(batch):
+    """Per torsional bond (CSR order): atoms moved m_k, clash pairs Pi_k, and
+    the ligand index of the bond."""
     aoff = batch.atom_off.astype(np.int64)
     A = int(aoff[-1])
     L = len(aoff) - 1
@@ -40,19 +52,52 @@ def moving_atoms_per_ligand(batch) -> np.ndarray:
     for d in range(int(depth.max(initial=0)), 0, -1):
         idx = np.where(depth == d)[0]
         np.add.at(size, gpar[idx], size[idx])
+    nchild = np.zeros(A, np.int64)
+    np.add.at(nchild, gpar[nonroot], 1)
     roff = batch.rot_off.astype(np.int64)
     rl = np.repeat(np.arange(L), np.diff(roff))
     child = batch.rot_child.astype(np.int64) + aoff[rl]
+    m = size[child] - 1
+    N = np.diff(aoff)[rl]
+    # moving atom i, fixed atom j: the path runs i .. child - parent .. j, so
+    # only (child of the bond's child, the bond's parent) is closer than 3 bonds
+    pairs = m * (N - m - 1) - nchild[child]
+    return m, pairs, rl, L
+
+
+def moving_atoms_per_ligand(batch) -> np.ndarray:
+    """Sum over each ligand's torsional bonds of the atoms the bond moves
+    (subtree size of the bond's child minus one)."""
+    m, _, rl, L = _bond_counts(batch)
     out = np.zeros(L, np.int64)
-    np.add.at(out, rl, size[child] - 1)
+    np.add.at(out, rl, m)
+    return out
+
+
+def clash_pairs_per_ligand(batch) -> np.ndarray:
+    """Sum over each ligand's torsional bonds of the clash pairs Pi_k."""
+    _, pairs, rl, L = _bond_counts(batch)
+    out = np.zeros(L, np.int64)
+    np.add.at(out, rl, pairs)
     return out
 
 
 def ligand_flops(batch, restarts: int, passes: int) -> np.ndarray:
     """Algorithmic FLOPs of docking each ligand (see the module docstring)."""
     N = np.diff(batch.atom_off).astype(np.float64)
+    m, pairs, rl, L = _bond_counts(batch)
+    per_bond = 36.0 * m * (C_ROT + C_TRI) + C_PAIR * pairs.astype(np.float64)
+    sweep = np.zeros(L)
+    np.add.at(sweep, rl, per_bond)
+    return restarts * (C_POSE_ATOM * N + C_RESTART + passes * sweep + C_FIN * N)
+
+
+def ligand_flops_circle(batch, restarts: int, passes: int) -> np.ndarray:
+    """FLOPs of the circle form the kernels evaluate (no clash pairs)."""
+    N = np.diff(batch.atom_off).astype(np.float64)
     msum = moving_atoms_per_ligand(batch).astype(np.float64)
-    return restarts * (passes * msum * (36 * C_LOOKUP + C_BOND) + N * (C_POSE_ATOM + C_FINAL_ATOM) + C_RESTART)
+    return restarts * (passes * msum * (36 * C_LOOKUP_CIRCLE + C_BOND_CIRCLE) +
+                       N * (C_POSE_ATOM + C_FINAL_CIRCLE) + C_RESTART)
 
 
 def partition(costs, world: int):

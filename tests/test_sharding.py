@@ -87,3 +87,50 @@ def test_two_rank_gather_equals_single_process():
     order = np.lexsort((batch.uid.astype(np.int64), out["best_E"]))[:20]
     assert got[0] == batch.uid[order].astype(np.int64).tolist()
     assert np.allclose(got[1], out["best_E"][order], rtol=0, atol=0)
+
+
+def test_cost_model_counts_match_brute_force():
+    # moving atoms and clash pairs per ligand against breadth-first topological
+    # distances on the bond tree
+    from collections import deque
+    batch = synth.config_ligands(2, 60)
+    m_got = shard.moving_atoms_per_ligand(batch)
+    p_got = shard.clash_pairs_per_ligand(batch)
+    for l in range(batch.L):
+        a0, a1 = int(batch.atom_off[l]), int(batch.atom_off[l + 1])
+        N = a1 - a0
+        par = batch.parent[a0:a1].astype(int)
+        adj = [[] for _ in range(N)]
+        for i in range(1, N):
+            adj[i].append(par[i])
+            adj[par[i]].append(i)
+        dist = np.zeros((N, N), int)
+        for s in range(N):
+            d = [-1] * N
+            d[s] = 0
+            dq = deque([s])
+            while dq:
+                u = dq.popleft()
+                for v in adj[u]:
+                    if d[v] < 0:
+                        d[v] = d[u] + 1
+                        dq.append(v)
+            dist[s] = d
+        m_want = p_want = 0
+        for k in range(int(batch.rot_off[l]), int(batch.rot_off[l + 1])):
+            b = int(batch.rot_child[k])
+            sub = {b}
+            for i in range(b + 1, N):       # preorder: a subtree is contiguous
+                if par[i] in sub:
+                    sub.add(i)
+                else:
+                    break
+            moving = sorted(sub - {b})
+            fixed = [j for j in range(N) if j not in sub]
+            m_want += len(moving)
+            p_want += sum(1 for i in moving for j in fixed if dist[i, j] >= 3)
+        assert m_got[l] == m_want and p_got[l] == p_want, l
+    F = shard.ligand_flops(batch, 30, 3)
+    N = np.diff(batch.atom_off)
+    want = 30 * (21 * N + 40 + 3 * (36 * 51 * m_got + 8 * p_got) + 64 * N)
+    assert np.allclose(F, want, rtol=0, atol=1e-6)
