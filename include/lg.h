@@ -242,6 +242,21 @@ typedef struct {
 int lg_dock_batch(lg_ctx *ctx, int32_t pocket_id, const lg_ligand_batch *batch, const lg_dock_params *params,
                   lg_dock_result *out, void *stream);
 
+/* Dock one batch against several loaded pockets in one launch: the
+ * screening campaign's pattern, a ligand library against every binding site
+ * (paper Sec. 1 and 4: 15 binding sites).  Results are those of n_pockets
+ * lg_dock_batch calls, bit for bit: outs[k] receives the results for
+ * pocket_ids[k].  The per-ligand preparation (validation, subtree ends,
+ * centroid, cost order) runs once for all pockets; the docking kernel visits
+ * (pocket, ligand) pairs pocket-major (context option "multi_order"), so the
+ * grids of one pocket at a time need to be in L2.
+ *   - Batched mode only (params->mode = LG_MODE_BATCHED).
+ *   - Every outs[k] has the same mem and the same set of optional outputs.
+ *   - Memory and errors as lg_dock_batch.  1 <= n_pockets <= 64. */
+#define LG_MAX_MULTI_POCKETS 64
+int lg_dock_multi(lg_ctx *ctx, const int32_t *pocket_ids, int32_t n_pockets, const lg_ligand_batch *batch,
+                  const lg_dock_params *params, lg_dock_result *outs, void *stream);
+
 /* Allocation-free docking (the paper has no counterpart to this call).
  * Some callers cannot let a library allocate device memory: applications that
  * give all device memory to their own pool allocator at start-up (a cudaMalloc
@@ -334,7 +349,9 @@ int lg_get_stats(lg_ctx *ctx, lg_stats *out);
 /* Context options: "timing" (0/1, default 0), "warps_per_cta" (0 = autotune,
  * else 1..32), "serve_max_inflight" (requests on the device at once, default 8),
  * "serve_mem_reserve_mb" (free device memory the server leaves untouched,
- * default 1024).  Errors: LG_EINVAL. */
+ * default 1024), "multi_order" (lg_dock_multi's visiting order: 0 =
+ * pocket-major, the default; 1 = ligand-major, a CTA docks one ligand against
+ * every pocket in turn).  Errors: LG_EINVAL. */
 int lg_set_option(lg_ctx *ctx, const char *key, int64_t value);
 
 /* ---------------------------------------------------------------- diagnostics */

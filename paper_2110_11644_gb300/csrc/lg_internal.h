@@ -181,6 +181,17 @@ struct DockArgs {
 
 constexpr int kSortBuckets = 128;
 
+// Several pockets in one persistent launch: work items are (pocket, ligand)
+// pairs.  pocket_major = 1 visits every ligand against pocket 0, then pocket 1,
+// ... (one pocket's grids in L2 at a time); 0 gives a CTA one ligand and docks
+// it against every pocket in turn.
+struct MultiDev {
+    int np;
+    int pocket_major;
+    const PocketDev *pk;  // [np] device array
+    const OutDev *out;    // [np] device array; out[0] receives the preparation's status
+};
+
 // Byte size of the scratch of a launch, and its carving.
 size_t scratch_bytes(int L, int rmax, int rank_slots = 0, int S = 0, int P = 0, int nmax = 0);
 Scratch carve_scratch(void *base, int L, int rmax, int rank_slots = 0, int S = 0, int P = 0, int nmax = 0);
@@ -194,7 +205,9 @@ cudaError_t launch_score_poses(const PocketDev &p, int L, const int32_t *atom_of
                                const float *q, const uint8_t *type, double *E, cudaStream_t s);
 cudaError_t launch_diag_philox(int n, const uint32_t *ctr, const uint32_t *key, uint32_t *out, int use_curand,
                                cudaStream_t s);
-cudaError_t dock_kernel_attributes(int W, int smem, int *ctas_per_sm);
+cudaError_t launch_dock_multi(const DockArgs &a, const MultiDev &m, int grid, int smem, cudaStream_t s);
+cudaError_t dock_kernel_attributes(int W, int smem, int *ctas_per_sm, bool ranking);
+cudaError_t multi_kernel_attributes(int W, int smem, int *ctas_per_sm, bool ranking);
 cudaError_t plain_kernel_attributes(int smem);
 
 }  // namespace lg

@@ -627,7 +627,7 @@ __device__ __forceinline__ void flush_pool(const RtView &v, int rs, int g, int &
 // slot rs, steps g, g+4, ..., g+32 (cosines cs[], sines sn[]) -- the 4 lanes
 // of a restart score neighbouring steps in the same instruction.  Returns the
 // step chosen for the lane's restart.
-__device__ int sweep_bond_rt(const DockArgs &A, const GridK &G, const CtaView &cv, const RtView &v, int N, int R, int k,
+__device__ __forceinline__ int sweep_bond_rt(const DockArgs &A, const GridK &G, const CtaView &cv, const RtView &v, int N, int R, int k,
                              int rs, int g, bool valid, const float *cs, const float *sn) {
     const int b = cv.rch[k], a = cv.par[b], e = cv.rend[k];
     const int m = e - b - 1;
@@ -764,7 +764,10 @@ __device__ int sweep_bond_rt(const DockArgs &A, const GridK &G, const CtaView &c
     return t;
 }
 
-__device__ void dock_ligand_rt(const DockArgs &A, int l, char *sm) {
+// kRank: pose ranking on (a separate instantiation, so the plain best-restart
+// form carries none of its code)
+template <bool kRank>
+__device__ __forceinline__ void dock_ligand_rt(const DockArgs &A, int l, char *sm) {
     if (A.out.status[l] != LG_OK) return;  // rejected by the preparation kernel (uniform)
     const Layout &Ly = A.ly;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
@@ -832,7 +835,7 @@ __device__ void dock_ligand_rt(const DockArgs &A, int l, char *sm) {
             if (A.out.restart_tors)
                 for (int t = g; t < PR; t += kLanesPerRestart)
                     A.out.restart_tors[(size_t)S * P * r0 + (size_t)r * PR + t] = v.tcur[t * kTile + rs];
-            if (A.ranking) {  // keep the restart for the ranking step
+            if (kRank) {  // keep the restart for the ranking step
                 float *x = A.scr.rk_pose + rk_pose_off(A, blockIdx.x, r);
                 for (int i = g; i < N; i += kLanesPerRestart) {
                     x[3 * i] = v.Xx[i * kTile + rs];
@@ -870,7 +873,7 @@ __device__ void dock_ligand_rt(const DockArgs &A, int l, char *sm) {
         }
         __syncwarp();
     }
-    if (A.ranking) {
+    if (kRank) {
         __syncthreads();
         rank_finish(A, l, blockIdx.x, a0, N, r0, PR, sm + Ly.cta_bytes);
         return;
@@ -893,6 +896,7 @@ __device__ void dock_ligand_rt(const DockArgs &A, int l, char *sm) {
 #ifndef LG_RT_MIN_BLOCKS
 #define LG_RT_MIN_BLOCKS 4
 #endif
+template <bool kRank>
 __global__ void __launch_bounds__(128, LG_RT_MIN_BLOCKS) k_dock_batched(const __grid_constant__ DockArgs A) {
     extern __shared__ __align__(16) char sm[];
     __shared__ int s_item;
@@ -902,7 +906,58 @@ __global__ void __launch_bounds__(128, LG_RT_MIN_BLOCKS) k_dock_batched(const __
         const int item = s_item;
         __syncthreads();
         if (item >= A.batch.L) break;
-        dock_ligand_rt(A, A.order ? A.order[item] : item, sm);
+        dock_ligand_rt<kRank>(A, A.order ? A.order[item] : item, sm);
+    }
+}
+
+// Several pockets (MultiDev): the CTA keeps a copy of the launch arguments in
+// shared memory and swaps in the pocket and outputs of each work item, so the
+// docking code is the single-pocket code.  The preparation kernel validated
+// every ligand once and wrote its status to the first pocket's outputs; the
+// other pockets' outputs get the same status here.
+template <bool kRank>
+__global__ void __launch_bounds__(128, LG_RT_MIN_BLOCKS) k_dock_multi(const __grid_constant__ DockArgs A,
+                                                                       const MultiDev M) {
+    extern __shared__ __align__(16) char sm[];
+    __shared__ __align__(16) DockArgs sA;
+    __shared__ int s_item;
+    {
+        const int *src = (const int *)&A;
+        int *dst = (int *)&sA;
+        for (int t = threadIdx.x; t < (int)(sizeof(DockArgs) / sizeof(int)); t += blockDim.x) dst[t] = src[t];
+    }
+    const int L = A.batch.L;
+    const int items = M.pocket_major ? M.np * L : L;
+    auto dock_one = [&](int p, int l) {
+        if (threadIdx.x == 0) {
+            sA.pocket = M.pk[p];
+            sA.out = M.out[p];
+            if (p > 0) {
+                const int st = M.out[0].status[l];
+                sA.out.status[l] = st;
+                if (st != LG_OK) {
+                    sA.out.score[l] = __longlong_as_double(0x7ff8000000000000ll);
+                    sA.out.best_restart[l] = -1;
+                }
+            }
+        }
+        __syncthreads();
+        dock_ligand_rt<kRank>(sA, l, sm);
+        __syncthreads();
+    };
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(A.work_counter, 1);
+        __syncthreads();
+        const int item = s_item;
+        __syncthreads();
+        if (item >= items) break;
+        if (M.pocket_major) {
+            const int p = item / L, i = item - p * L;
+            dock_one(p, A.order ? A.order[i] : i);
+        } else {
+            const int l = A.order ? A.order[item] : item;
+            for (int p = 0; p < M.np; ++p) dock_one(p, l);
+        }
     }
 }
 
@@ -1091,10 +1146,21 @@ Scratch carve_scratch(void *base, int L, int rmax, int rank_slots, int S, int P,
     return s;
 }
 
-cudaError_t dock_kernel_attributes(int W, int smem, int *ctas_per_sm) {
-    cudaError_t e = cudaFuncSetAttribute(k_dock_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+template <typename K>
+static cudaError_t kernel_attributes(K kernel, int W, int smem, int *ctas_per_sm) {
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k_dock_batched, 32 * W, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, kernel, 32 * W, smem);
+}
+
+cudaError_t dock_kernel_attributes(int W, int smem, int *ctas_per_sm, bool ranking) {
+    return ranking ? kernel_attributes(k_dock_batched<true>, W, smem, ctas_per_sm)
+                   : kernel_attributes(k_dock_batched<false>, W, smem, ctas_per_sm);
+}
+
+cudaError_t multi_kernel_attributes(int W, int smem, int *ctas_per_sm, bool ranking) {
+    return ranking ? kernel_attributes(k_dock_multi<true>, W, smem, ctas_per_sm)
+                   : kernel_attributes(k_dock_multi<false>, W, smem, ctas_per_sm);
 }
 
 cudaError_t plain_kernel_attributes(int smem) {
@@ -1123,7 +1189,18 @@ cudaError_t launch_dock_plain(const DockArgs &a, int ligand, int slot, cudaStrea
 }
 
 cudaError_t launch_dock_batched(const DockArgs &a, int grid, int smem, cudaStream_t s) {
-    k_dock_batched<<<grid, 32 * a.ly.W, smem, s>>>(a);
+    if (a.ranking)
+        k_dock_batched<true><<<grid, 32 * a.ly.W, smem, s>>>(a);
+    else
+        k_dock_batched<false><<<grid, 32 * a.ly.W, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dock_multi(const DockArgs &a, const MultiDev &m, int grid, int smem, cudaStream_t s) {
+    if (a.ranking)
+        k_dock_multi<true><<<grid, 32 * a.ly.W, smem, s>>>(a, m);
+    else
+        k_dock_multi<false><<<grid, 32 * a.ly.W, smem, s>>>(a, m);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,83 @@
+// lg_dock_multi: one ligand batch against several loaded pockets in one
+// persistent launch (the screening campaign's access pattern: a library
+// against every binding site).  The preparation (validation, subtree ends,
+// centroids, cost order) runs once for all pockets; work items are (pocket,
+// ligand) pairs, visited pocket-major by default so one pocket's grids are in
+// L2 at a time.
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "lg_runtime.h"
+
+using namespace lg;
+
+extern "C" int lg_dock_multi(lg_ctx *c, const int32_t *pocket_ids, int32_t n_pockets, const lg_ligand_batch *b,
+                             const lg_dock_params *p, lg_dock_result *outs, void *stream) {
+    if (!c || !pocket_ids || !b || !p || !outs) return fail(LG_EINVAL, "null argument");
+    if (n_pockets < 1 || n_pockets > LG_MAX_MULTI_POCKETS) return fail(LG_EINVAL, "n_pockets out of range");
+    int rc = check_params(p);
+    if (rc) return rc;
+    if (p->mode != LG_MODE_BATCHED) return fail(LG_EINVAL, "lg_dock_multi runs the batched mode only");
+    if (b->L < 0) return fail(LG_EINVAL, "L must be >= 0");
+    if (b->mem != LG_MEM_HOST && b->mem != LG_MEM_DEVICE) return fail(LG_EINVAL, "bad batch mem");
+    const int32_t omem = outs[0].mem;
+    for (int k = 0; k < n_pockets; k++) {
+        const lg_dock_result &o = outs[k];
+        if (o.mem != omem || (o.mem != LG_MEM_HOST && o.mem != LG_MEM_DEVICE))
+            return fail(LG_EINVAL, "every result must have the same mem, LG_MEM_HOST or LG_MEM_DEVICE");
+        if (!o.score || !o.best_restart || !o.status) return fail(LG_EINVAL, "score, best_restart and status are required");
+        // optional outputs are all present or all absent, so every pocket runs the same kernel configuration
+        if ((o.pose != nullptr) != (outs[0].pose != nullptr) || (o.tors_idx != nullptr) != (outs[0].tors_idx != nullptr))
+            return fail(LG_EINVAL, "pose and tors_idx must be given for every pocket or for none");
+    }
+    if (b->L == 0) return LG_OK;
+    if (!b->atom_off || !b->x || !b->y || !b->z || !b->q || !b->type || !b->parent || !b->rot_off || !b->uid)
+        return fail(LG_EINVAL, "null batch array");
+    std::lock_guard<std::mutex> g(c->mu);
+    if (cudaSetDevice(c->device) != cudaSuccess) return fail(LG_ECUDA, "cudaSetDevice failed");
+    std::vector<PocketDev> pk(n_pockets);
+    for (int k = 0; k < n_pockets; k++) {
+        const int pid = pocket_ids[k];
+        if (pid < 0 || pid >= (int)c->pockets.size() || !c->pockets[pid].live) return fail(LG_ENOPOCKET, "unknown pocket");
+        pk[k] = c->pockets[pid].dev;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const int L = b->L, S = p->restarts, P = p->passes;
+    int64_t A = -1, R = -1;
+    int nmax, rmax;
+    BatchDev bd;
+    if ((rc = resolve_batch(c, b, p, s, &bd, &A, &R, &nmax, &rmax))) return rc;
+    if ((int)c->multi_out.size() < n_pockets) c->multi_out.resize(n_pockets);
+    std::vector<OutDev> od(n_pockets);
+    for (int k = 0; k < n_pockets; k++)
+        if ((rc = resolve_out(c, c->multi_out[k], b, &outs[k], S, P, s, &A, &R, &od[k]))) return rc;
+    // pocket and output descriptors for the kernel
+    const size_t o_out = (sizeof(PocketDev) * n_pockets + 255) & ~(size_t)255;
+    const size_t bytes = o_out + sizeof(OutDev) * n_pockets;
+    if (c->multi_desc.ensure(bytes)) return fail(LG_ENOMEM, "descriptor allocation failed");
+    std::vector<char> img(bytes);
+    memcpy(img.data(), pk.data(), sizeof(PocketDev) * n_pockets);
+    memcpy(img.data() + o_out, od.data(), sizeof(OutDev) * n_pockets);
+    // pageable source: the call returns once the bytes have left `img`
+    cudaError_t e = cudaMemcpyAsync(c->multi_desc.p, img.data(), bytes, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return fail(LG_ECUDA, std::string("descriptor upload: ") + cudaGetErrorString(e));
+    MultiDev m;
+    m.np = n_pockets;
+    m.pocket_major = c->multi_pocket_major;
+    m.pk = (const PocketDev *)c->multi_desc.p;
+    m.out = (const OutDev *)((char *)c->multi_desc.p + o_out);
+    cudaEvent_t *tev = next_timing_events(c);
+    if ((rc = dock_device(c, pk[0], bd, od[0], p, nmax, rmax, c->scratch, s, &c->stats, tev, &m))) return rc;
+    if (omem == LG_MEM_HOST)
+        for (int k = 0; k < n_pockets; k++)
+            if ((rc = fetch_out(od[k], &outs[k], L, S, P, A, R, s))) return rc;
+    if (b->mem == LG_MEM_HOST || omem == LG_MEM_HOST) {
+        e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return fail(LG_ECUDA, std::string("docking: ") + cudaGetErrorString(e));
+    } else {
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return fail(LG_ECUDA, std::string("docking: ") + cudaGetErrorString(e));
+    }
+    return LG_OK;
+}

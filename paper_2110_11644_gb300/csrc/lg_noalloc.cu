@@ -125,7 +125,7 @@ extern "C" int lg_dock_batch_noalloc(lg_ctx *c, int32_t pid, const lg_ligand_bat
         a.ly = make_layout(nmax, rmax, a.P, W, want_pose);
         a.lrt = make_layout_rt(nmax, rmax, a.P, want_pose);
         smem = a.ly.cta_bytes + W * a.lrt.warp_bytes;
-        if ((e = dock_kernel_attributes(W, smem, &occ)) != cudaSuccess)
+        if ((e = dock_kernel_attributes(W, smem, &occ, false)) != cudaSuccess)
             return fail(LG_ECUDA, std::string("dock kernel attributes: ") + cudaGetErrorString(e));
         if (occ > 0 || W == 1) break;
         W = std::max(1, W / 2);

@@ -194,7 +194,8 @@ int choose_warps(int S, int opt) {
 // kernel (validation, subtree ends, centroids; cost sort in batched mode),
 // then the persistent docking kernel or one plain launch per ligand.
 int dock_device(lg_ctx *ctx, const PocketDev &pk, const BatchDev &bd, const OutDev &od, const lg_dock_params *p,
-                int nmax, int rmax, DevBuf &scratch, cudaStream_t s, lg_stats *st, cudaEvent_t *tev) {
+                int nmax, int rmax, DevBuf &scratch, cudaStream_t s, lg_stats *st, cudaEvent_t *tev,
+                const MultiDev *multi) {
     const bool timed = tev != nullptr;
     DockArgs a;
     memset(&a, 0, sizeof(a));
@@ -221,6 +222,7 @@ int dock_device(lg_ctx *ctx, const PocketDev &pk, const BatchDev &bd, const OutD
     st->dock_ms = keep.dock_ms;
     const int L = bd.L;
     const bool plain = p->mode == LG_MODE_PLAIN;
+    if (plain && multi) return fail(LG_EINVAL, "several pockets run in the batched mode only");
     a.ranking = ranking_on(p) ? 1 : 0;
     a.thr2g = (float)((double)p->cluster_rmsd * p->cluster_rmsd / (h * h));
     a.rescore_top = p->rescore_top;
@@ -277,18 +279,20 @@ int dock_device(lg_ctx *ctx, const PocketDev &pk, const BatchDev &bd, const OutD
         a.ly = make_layout(nmax, rmax, a.P, W, want_pose);
         a.lrt = make_layout_rt(nmax, rmax, a.P, want_pose);
         smem = std::max(a.ly.cta_bytes + W * a.lrt.warp_bytes, a.ly.cta_bytes + rank_smem);
-        if ((e = dock_kernel_attributes(W, smem, &occ)) != cudaSuccess)
+        e = multi ? multi_kernel_attributes(W, smem, &occ, a.ranking) : dock_kernel_attributes(W, smem, &occ, a.ranking);
+        if (e != cudaSuccess)
             return fail(LG_ECUDA, std::string("dock kernel attributes: ") + cudaGetErrorString(e));
         if (occ > 0 || W == 1) break;
         W = std::max(1, W / 2);
     }
     if (occ <= 0) return fail(LG_EINVAL, "docking kernel does not fit on an SM");
-    const int grid = std::max(1, std::min(ctx_num_sms(ctx) * occ, L));
+    const long items = multi && multi->pocket_major ? (long)L * multi->np : (long)L;
+    const int grid = (int)std::max(1L, std::min((long)ctx_num_sms(ctx) * occ, items));
     if (int rc = setup_scratch(grid)) return rc;
     a.work_counter = a.scr.hist + kSortBuckets;
     a.order = a.scr.order;
     if (timed) cudaEventRecord(tev[0], s);
-    if ((e = launch_dock_batched(a, grid, smem, s)) != cudaSuccess)
+    if ((e = multi ? launch_dock_multi(a, *multi, grid, smem, s) : launch_dock_batched(a, grid, smem, s)) != cudaSuccess)
         return fail(LG_ECUDA, std::string("dock launch: ") + cudaGetErrorString(e));
     if (timed) cudaEventRecord(tev[1], s);
     st->launches = launches + 1;
@@ -297,6 +301,81 @@ int dock_device(lg_ctx *ctx, const PocketDev &pk, const BatchDev &bd, const OutD
     st->ctas_per_sm = occ;
     st->smem_bytes = smem;
     return LG_OK;
+}
+
+// Device view of a batch: staged into the context's input buffer for host
+// batches (which also yields the totals and the measured maxima), as given
+// for device batches.
+int resolve_batch(lg_ctx *c, const lg_ligand_batch *b, const lg_dock_params *p, cudaStream_t s, BatchDev *bd,
+                  int64_t *A, int64_t *R, int *nmax, int *rmax) {
+    const int L = b->L;
+    int rc;
+    *A = -1;
+    *R = -1;
+    *nmax = p->max_atoms > 0 ? p->max_atoms : LG_MAX_ATOMS;
+    *rmax = p->max_rot > 0 ? p->max_rot : LG_MAX_ROT;
+    if (b->mem == LG_MEM_HOST) {
+        int nm, rm;
+        if ((rc = host_batch_shape(b, A, R, &nm, &rm))) return rc;
+        if (*R > 0 && !b->rot_child) return fail(LG_EINVAL, "null rot_child");
+        *nmax = std::min(*nmax, std::max(nm, 1));
+        *rmax = std::min(*rmax, std::max(rm, 1));
+        return stage_batch(c->in_buf, b, *A, *R, bd, s);
+    }
+    if (!b->rot_child) return fail(LG_EINVAL, "null rot_child");
+    bd->L = L;
+    bd->atom_off = b->atom_off;
+    bd->x = b->x;
+    bd->y = b->y;
+    bd->z = b->z;
+    bd->q = b->q;
+    bd->type = b->type;
+    bd->parent = b->parent;
+    bd->rot_off = b->rot_off;
+    bd->rot_child = b->rot_child;
+    bd->uid = b->uid;
+    return LG_OK;
+}
+
+// Device view of a result: device buffers from `buf` for host results (the
+// totals of a device batch are read back first), as given for device results.
+int resolve_out(lg_ctx *c, DevBuf &buf, const lg_ligand_batch *b, const lg_dock_result *o, int S, int P, cudaStream_t s,
+                int64_t *A, int64_t *R, OutDev *od) {
+    (void)c;
+    const int L = b->L;
+    if (o->mem == LG_MEM_HOST) {
+        if (*A < 0) {  // device batch, host result: read the two totals
+            int32_t tot[2];
+            cudaError_t e = cudaMemcpyAsync(&tot[0], b->atom_off + L, 4, cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(&tot[1], b->rot_off + L, 4, cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) return fail(LG_ECUDA, std::string("batch totals: ") + cudaGetErrorString(e));
+            *A = tot[0];
+            *R = tot[1];
+        }
+        return stage_out(buf, o, L, S, P, *A, *R, od);
+    }
+    od->score = o->score;
+    od->best_restart = o->best_restart;
+    od->status = o->status;
+    od->tors_idx = o->tors_idx;
+    od->pose = o->pose;
+    od->restart_score = o->restart_score;
+    od->restart_tors = o->restart_tors;
+    od->rank = o->rank;
+    od->leader = o->leader;
+    od->restart_geo = o->restart_geo;
+    return LG_OK;
+}
+
+// Event pair of the next timed call (NULL when timing is off).
+cudaEvent_t *next_timing_events(lg_ctx *c) {
+    if (!c->timing) return nullptr;
+    if (c->tev_pending == lg_ctx::kTimingRing) harvest_timing(c);
+    cudaEvent_t *tev = c->tev[c->tev_head];
+    c->tev_head = (c->tev_head + 1) % lg_ctx::kTimingRing;
+    c->tev_pending++;
+    return tev;
 }
 
 // Wait for the timed calls still in the ring and add their device times.
@@ -393,6 +472,8 @@ void lg_destroy(lg_ctx *c) {
     c->in_buf.release();
     c->out_buf.release();
     c->scratch.release();
+    for (auto &m : c->multi_out) m.release();
+    c->multi_desc.release();
     for (auto s : c->plain_streams) cudaStreamDestroy(s);
     for (auto ev : c->join_events) cudaEventDestroy(ev);
     for (int i = 0; i < 3; i++)
@@ -511,61 +592,12 @@ int lg_dock_batch(lg_ctx *c, int32_t pid, const lg_ligand_batch *b, const lg_doc
     const int L = b->L, S = p->restarts, P = p->passes;
 
     int64_t A = -1, R = -1;
-    int nmax = p->max_atoms > 0 ? p->max_atoms : LG_MAX_ATOMS;
-    int rmax = p->max_rot > 0 ? p->max_rot : LG_MAX_ROT;
+    int nmax, rmax;
     BatchDev bd;
-    if (b->mem == LG_MEM_HOST) {
-        int nm, rm;
-        if ((rc = host_batch_shape(b, &A, &R, &nm, &rm))) return rc;
-        if (R > 0 && !b->rot_child) return fail(LG_EINVAL, "null rot_child");
-        nmax = std::min(nmax, std::max(nm, 1));
-        rmax = std::min(rmax, std::max(rm, 1));
-        if ((rc = stage_batch(c->in_buf, b, A, R, &bd, s))) return rc;
-    } else {
-        if (!b->rot_child) return fail(LG_EINVAL, "null rot_child");
-        bd.L = L;
-        bd.atom_off = b->atom_off;
-        bd.x = b->x;
-        bd.y = b->y;
-        bd.z = b->z;
-        bd.q = b->q;
-        bd.type = b->type;
-        bd.parent = b->parent;
-        bd.rot_off = b->rot_off;
-        bd.rot_child = b->rot_child;
-        bd.uid = b->uid;
-    }
+    if ((rc = resolve_batch(c, b, p, s, &bd, &A, &R, &nmax, &rmax))) return rc;
     OutDev od;
-    if (o->mem == LG_MEM_HOST) {
-        if (A < 0) {  // device batch, host result: read the two totals
-            int32_t tot[2];
-            cudaError_t e = cudaMemcpyAsync(&tot[0], b->atom_off + L, 4, cudaMemcpyDeviceToHost, s);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(&tot[1], b->rot_off + L, 4, cudaMemcpyDeviceToHost, s);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-            if (e != cudaSuccess) return fail(LG_ECUDA, std::string("batch totals: ") + cudaGetErrorString(e));
-            A = tot[0];
-            R = tot[1];
-        }
-        if ((rc = stage_out(c->out_buf, o, L, S, P, A, R, &od))) return rc;
-    } else {
-        od.score = o->score;
-        od.best_restart = o->best_restart;
-        od.status = o->status;
-        od.tors_idx = o->tors_idx;
-        od.pose = o->pose;
-        od.restart_score = o->restart_score;
-        od.restart_tors = o->restart_tors;
-        od.rank = o->rank;
-        od.leader = o->leader;
-        od.restart_geo = o->restart_geo;
-    }
-    cudaEvent_t *tev = nullptr;
-    if (c->timing) {
-        if (c->tev_pending == lg_ctx::kTimingRing) harvest_timing(c);
-        tev = c->tev[c->tev_head];
-        c->tev_head = (c->tev_head + 1) % lg_ctx::kTimingRing;
-        c->tev_pending++;
-    }
+    if ((rc = resolve_out(c, c->out_buf, b, o, S, P, s, &A, &R, &od))) return rc;
+    cudaEvent_t *tev = next_timing_events(c);
     if ((rc = dock_device(c, pk->dev, bd, od, p, nmax, rmax, c->scratch, s, &c->stats, tev))) return rc;
     if (o->mem == LG_MEM_HOST) {
         if ((rc = fetch_out(od, o, L, S, P, A, R, s))) return rc;
@@ -652,6 +684,9 @@ int lg_set_option(lg_ctx *c, const char *key, int64_t v) {
     } else if (!strcmp(key, "serve_max_inflight")) {
         if (v < 1 || v > 64) return fail(LG_EINVAL, "serve_max_inflight must be in [1, 64]");
         c->serve_max_inflight = (int)v;
+    } else if (!strcmp(key, "multi_order")) {
+        if (v != 0 && v != 1) return fail(LG_EINVAL, "multi_order must be 0 or 1");
+        c->multi_pocket_major = v == 0 ? 1 : 0;
     } else if (!strcmp(key, "serve_mem_reserve_mb")) {
         if (v < 0) return fail(LG_EINVAL, "serve_mem_reserve_mb must be >= 0");
         c->serve_reserve_mb = v;

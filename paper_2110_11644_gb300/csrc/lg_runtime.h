@@ -35,7 +35,13 @@ int stage_batch(DevBuf &buf, const lg_ligand_batch *b, int64_t A, int64_t R, Bat
 int stage_out(DevBuf &buf, const lg_dock_result *o, int L, int S, int P, int64_t A, int64_t R, OutDev *d);
 int fetch_out(const OutDev &d, const lg_dock_result *o, int L, int S, int P, int64_t A, int64_t R, cudaStream_t s);
 int dock_device(lg_ctx *ctx, const PocketDev &pk, const BatchDev &bd, const OutDev &od, const lg_dock_params *p,
-                int nmax, int rmax, DevBuf &scratch, cudaStream_t s, lg_stats *st, cudaEvent_t *tev);
+                int nmax, int rmax, DevBuf &scratch, cudaStream_t s, lg_stats *st, cudaEvent_t *tev,
+                const MultiDev *multi = nullptr);
+int resolve_batch(lg_ctx *c, const lg_ligand_batch *b, const lg_dock_params *p, cudaStream_t s, BatchDev *bd,
+                  int64_t *A, int64_t *R, int *nmax, int *rmax);
+int resolve_out(lg_ctx *c, DevBuf &buf, const lg_ligand_batch *b, const lg_dock_result *o, int S, int P, cudaStream_t s,
+                int64_t *A, int64_t *R, OutDev *od);
+cudaEvent_t *next_timing_events(lg_ctx *c);
 void harvest_timing(lg_ctx *c);
 void serve_stop(lg_ctx *c);
 int choose_warps(int S, int opt);
@@ -62,6 +68,10 @@ struct lg_ctx {
     int64_t serve_reserve_mb = 1024;
     std::mutex serve_mu;  // guards `server` creation
     lg::Server *server = nullptr;
+    // several pockets in one launch (lg_dock_multi)
+    std::vector<lg::DevBuf> multi_out;
+    lg::DevBuf multi_desc;
+    int multi_pocket_major = 1;
 };
 
 namespace lg {

@@ -65,7 +65,7 @@ class lg_stats(ctypes.Structure):
 # Every symbol include/lg.h declares (checked by the ABI test).
 EXPORTS = ("lg_create", "lg_destroy", "lg_last_error", "lg_pocket_load", "lg_pocket_unload", "lg_dock_batch",
            "lg_score_poses", "lg_stream_submit", "lg_stream_poll", "lg_stream_wait", "lg_get_stats", "lg_set_option",
-           "lg_diag_philox", "lg_dock_batch_noalloc")
+           "lg_diag_philox", "lg_dock_batch_noalloc", "lg_dock_multi")
 
 _lib = None
 _lock = threading.Lock()
@@ -103,6 +103,8 @@ def load():
             lib.lg_diag_philox.argtypes = [V, c.c_int32, V, V, V, c.c_int32]
             lib.lg_dock_batch_noalloc.argtypes = [V, c.c_int32, c.POINTER(lg_ligand_batch), c.POINTER(lg_dock_params),
                                                   c.POINTER(lg_dock_result), V]
+            lib.lg_dock_multi.argtypes = [V, c.POINTER(c.c_int32), c.c_int32, c.POINTER(lg_ligand_batch),
+                                          c.POINTER(lg_dock_params), c.POINTER(lg_dock_result), V]
             for name in EXPORTS:
                 if name not in ("lg_destroy", "lg_last_error"):
                     getattr(lib, name).restype = c.c_int
@@ -156,6 +158,15 @@ def lg_dock_batch_noalloc(h, pid, batch: lg_ligand_batch, params: lg_dock_params
     """Batched docking of a device-memory batch that allocates no memory (see lg.h)."""
     _check(h, load().lg_dock_batch_noalloc(h, pid, ctypes.byref(batch), ctypes.byref(params), ctypes.byref(out),
                                            stream))
+
+
+def lg_dock_multi(h, pids, batch: lg_ligand_batch, params: lg_dock_params, outs, stream=None):
+    """Dock one batch against several pockets in one launch; outs is a sequence
+    of lg_dock_result, one per pocket id."""
+    n = len(pids)
+    ids = (ctypes.c_int32 * n)(*[int(p) for p in pids])
+    res = (lg_dock_result * n)(*outs)
+    _check(h, load().lg_dock_multi(h, ids, n, ctypes.byref(batch), ctypes.byref(params), res, stream))
 
 
 def lg_score_poses(h, pid, poses: lg_pose_batch, energies_ptr, stream=None):
@@ -368,6 +379,37 @@ class Context:
         n = dict(score=L, best_restart=L, status=L, tors_idx=P * R, pose=3 * A, restart_score=L * S,
                  restart_tors=S * P * R, rank=L * S, leader=L * S, restart_geo=L * S)
         return {k: (v[:n[k]] if v is not None else None) for k, v in outs.items()}
+
+    def dock_multi(self, pids, batch, params, *, device_io=False, pose=True, tors=True, restart_score=False,
+                   restart_tors=False, stream=None, max_atoms=0, max_rot=0):
+        """Dock a CSR batch against several pockets in one launch; returns one
+        dict of numpy arrays per pocket (as dock())."""
+        L = len(batch.atom_off) - 1
+        A, R = int(batch.atom_off[-1]), int(batch.rot_off[-1])
+        S, P = int(params.restarts), int(params.passes)
+        thr = float(getattr(params, "cluster_rmsd", 0.0))
+        K = int(getattr(params, "rescore_top", 0))
+        ranking = thr > 0.0 or 0 < K < S
+        arrs = device_batch_arrays(batch) if device_io else host_batch_arrays(batch)
+        b = make_batch_struct(arrs, L)
+        p = make_params(S, P, params.seed, params.d_clash, LG_MODE_BATCHED, 0, max_atoms, max_rot, thr, K)
+        res = [alloc_result(L, A, R, S, P, device=device_io, pose=pose, tors=tors, restart_score=restart_score,
+                            restart_tors=restart_tors, ranking=ranking) for _ in pids]
+        if device_io:
+            import torch
+            s = torch.cuda.current_stream()
+            lg_dock_multi(self.h, pids, b, p, [r for r, _ in res], s.cuda_stream if stream is None else stream)
+            s.synchronize()
+        else:
+            lg_dock_multi(self.h, pids, b, p, [r for r, _ in res], stream)
+        n = dict(score=L, best_restart=L, status=L, tors_idx=P * R, pose=3 * A, restart_score=L * S,
+                 restart_tors=S * P * R, rank=L * S, leader=L * S, restart_geo=L * S)
+        out = []
+        for _, outs in res:
+            if device_io:
+                outs = {k: (v.cpu().numpy() if v is not None else None) for k, v in outs.items()}
+            out.append({k: (v[:n[k]] if v is not None else None) for k, v in outs.items()})
+        return out
 
     def score_poses(self, pid, atom_off, xyz, q, type_):
         atom_off = np.ascontiguousarray(atom_off, np.int32)
