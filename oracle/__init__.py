@@ -77,6 +77,8 @@ def _load():
             lib.or_rank_poses.argtypes = [P, i32, i32, P, P, d, i32, P, P, P, P, P]
             lib.or_dock_batch.restype = ctypes.c_int
             lib.or_score_poses.argtypes = [P, i32, P, P, P, P, P, P]
+            lib.or_flatten_batch.argtypes = [i32, P, P, P, P, P, P, P, P, i32, i32, d] + [P] * 8 + [i32]
+            lib.or_flatten_batch.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -266,3 +268,41 @@ def rank_poses(pocket, poses, E, thr, K):
     lib.or_rank_poses(op.ref, S, N, _ptr(poses), _ptr(E), float(thr), int(K), _ptr(G), _ptr(order), _ptr(leader),
                       ctypes.byref(br), ctypes.byref(be))
     return G, order, leader, br.value, be.value
+
+
+# ------------------------------------------------------------------ flattening
+def flatten(batch, passes: int, d_clash: float = 2.0, *, angle_steps: int = 36, replay=None, trace=False,
+            nthreads=None) -> dict:
+    """Flatten every ligand of a CSR batch (Sec. 3.1, step 1): returns xyz
+    (flat, 3*atom_off), D[L] (sum of all pairwise distances of the result),
+    choice / own (flat, passes*rot_off[l] per ligand), status[L], and with
+    trace=True trace_D / trace_d2 (flat, A*passes*rot_off[l])."""
+    lib = _load()
+    aoff = np.ascontiguousarray(batch.atom_off, np.int32)
+    roff = np.ascontiguousarray(batch.rot_off, np.int32)
+    L = len(aoff) - 1
+    natoms, nrot = int(aoff[-1]), int(roff[-1])
+    arr = {k: np.ascontiguousarray(getattr(batch, k), np.float32) for k in ("x", "y", "z")}
+    t = np.ascontiguousarray(batch.type, np.uint8)
+    par = np.ascontiguousarray(batch.parent, np.int16)
+    rc = np.ascontiguousarray(batch.rot_child, np.int16)
+    ndec = passes * nrot
+    out = dict(xyz=np.zeros(max(3 * natoms, 1)), D=np.full(L, np.nan), choice=np.zeros(max(ndec, 1), np.uint8),
+               own=np.zeros(max(ndec, 1), np.uint8), status=np.zeros(L, np.int32))
+    if trace:
+        out["trace_D"] = np.zeros(max(ndec * angle_steps, 1))
+        out["trace_d2"] = np.zeros(max(ndec * angle_steps, 1))
+    rep = None
+    if replay is not None:
+        rep = np.ascontiguousarray(replay, np.uint8)
+        assert rep.size >= ndec
+    if nthreads is None:
+        nthreads = len(os.sched_getaffinity(0))
+    lib.or_flatten_batch(L, _ptr(aoff), _ptr(arr["x"]), _ptr(arr["y"]), _ptr(arr["z"]), _ptr(t), _ptr(par),
+                         _ptr(roff), _ptr(rc), int(passes), int(angle_steps), float(d_clash), _ptr(rep),
+                         _ptr(out["xyz"]), _ptr(out["choice"]), _ptr(out["own"]), _ptr(out.get("trace_D")),
+                         _ptr(out.get("trace_d2")), _ptr(out["D"]), _ptr(out["status"]), int(nthreads))
+    out["xyz"] = out["xyz"][:3 * natoms]
+    out["choice"] = out["choice"][:ndec]
+    out["own"] = out["own"][:ndec]
+    return out

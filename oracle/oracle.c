@@ -34,6 +34,8 @@
  *   score   E = sum_i [ w_type(i) Vgrid(xhat_i) + q_i Egrid(xhat_i) + k_out |x_i - xhat_i| ]
  *           with xhat the position clamped to the grid box.
  *   best    The restart with the lowest E wins, the lowest restart on ties.
+ *   flatten (separate entry, Sec. 3.1 step 1) The same greedy sweep, without
+ *           a pocket, maximising the sum of all pairwise atom distances.
  *   rank    (optional, Sec. 3.1 steps 3-4) The poses are ordered by geometric
  *           score G = sum over all atoms of the overlap grid (higher first,
  *           lower restart on ties) and clustered greedily: a pose whose RMSD
@@ -457,4 +459,107 @@ void or_score_poses(const or_pocket *P, int32_t L, const int32_t *atom_off, cons
         int a0 = atom_off[l], N = atom_off[l + 1] - a0;
         E[l] = or_pose_energy(P, N, xyz + 3 * (size_t)a0, q + a0, type + a0, Eabs ? Eabs + l : NULL);
     }
+}
+
+/* ------------------------------------------------------------------ flattening
+ * Ligand pre-processing (Sec. 3.1, step 1; protein independent): the torsional
+ * bonds are turned to maximise the sum of the distances between all atom
+ * pairs.  Reading: the greedy sweep of the docking step with this objective in
+ * place of the overlap score -- for pass = 0..P-1 and torsional bond k in
+ * ascending child order, step t = 0..A-1 turns the moving set about the bond
+ * axis as in the sweep; D(t) = sum over all pairs i < j of |x_i - x_j|; the
+ * admissible step (the sweep's clash rule) with the largest D is applied, the
+ * lowest step on ties.  The ligand stays in its input frame.
+ * Outputs: xyz_out[N][3]; choice/own[P][R]; trace_D/trace_d2[P][R][A] (D and
+ * the minimum clash distance^2 of every step, +inf without checked pairs);
+ * D_out = D of the final conformation.  replay[P][R] (optional) applies the
+ * given steps instead, still recording the oracle's own choices. */
+static double or_pair_distance_sum(int32_t N, double (*T)[3]) {
+    double D = 0.0;
+    for (int i = 0; i < N; i++)
+        for (int j = i + 1; j < N; j++) {
+            double dx = T[i][0] - T[j][0], dy = T[i][1] - T[j][1], dz = T[i][2] - T[j][2];
+            D += sqrt(dx * dx + dy * dy + dz * dz);
+        }
+    return D;
+}
+
+int or_flatten_ligand(int32_t N, const float *x, const float *y, const float *z, const uint8_t *type,
+                      const int16_t *parent, int32_t R, const int16_t *rot_child, int32_t passes, int32_t A,
+                      double d_clash, const uint8_t *replay, double *xyz_out, uint8_t *choice, uint8_t *own,
+                      double *trace_D, double *trace_d2, double *D_out) {
+    int32_t end[OR_MAXN];
+    if (or_validate(N, parent, type, R, rot_child, end) != 0) return -1;
+    if (passes < 0 || A < 1 || A > 255) return -1;
+    double X[OR_MAXN][3], T[OR_MAXN][3];
+    for (int i = 0; i < N; i++) { X[i][0] = x[i]; X[i][1] = y[i]; X[i][2] = z[i]; }
+    const double dc2 = d_clash * d_clash;
+    for (int ps = 0; ps < passes; ps++) {
+        for (int k = 0; k < R; k++) {
+            const int b = rot_child[k], a = parent[b], e = end[b];
+            const size_t dec = (size_t)ps * R + k;
+            int own_t = 0;
+            double own_D = -INFINITY;
+            for (int t = 0; t < A; t++) {
+                double th = 2.0 * M_PI * t / A, c = cos(th), s = sin(th);
+                memcpy(T, X, sizeof(double) * 3 * N);
+                if (t != 0)
+                    for (int i = b + 1; i < e; i++) or_rotate_about(X[a], X[b], c, s, X[i], T[i]);
+                double D = or_pair_distance_sum(N, T);
+                double d2min = INFINITY;
+                for (int i = b + 1; i < e; i++)
+                    for (int j = 0; j < N; j++) {
+                        if (j >= b && j < e) continue;
+                        if (j == a && parent[i] == b) continue;
+                        double dx = T[i][0] - T[j][0], dy = T[i][1] - T[j][1], dz = T[i][2] - T[j][2];
+                        double d2 = dx * dx + dy * dy + dz * dz;
+                        if (d2 < d2min) d2min = d2;
+                    }
+                if (trace_D) trace_D[dec * A + t] = D;
+                if (trace_d2) trace_d2[dec * A + t] = d2min;
+                int admissible = (t == 0) || (d2min >= dc2);
+                if (admissible && D > own_D) { own_D = D; own_t = t; }
+            }
+            int ch = replay ? replay[dec] : own_t;
+            if (ch < 0 || ch >= A) return -2;
+            if (own) own[dec] = (uint8_t)own_t;
+            if (choice) choice[dec] = (uint8_t)ch;
+            if (ch != 0) {
+                double th = 2.0 * M_PI * ch / A, c = cos(th), s = sin(th);
+                double xa[3] = {X[a][0], X[a][1], X[a][2]}, xb[3] = {X[b][0], X[b][1], X[b][2]};
+                for (int i = b + 1; i < e; i++) {
+                    double o[3];
+                    or_rotate_about(xa, xb, c, s, X[i], o);
+                    memcpy(X[i], o, sizeof(o));
+                }
+            }
+        }
+    }
+    if (xyz_out) memcpy(xyz_out, X, sizeof(double) * 3 * N);
+    if (D_out) *D_out = or_pair_distance_sum(N, X);
+    return 0;
+}
+
+/* Batch in CSR layout.  Per-ligand offsets: xyz 3*atom_off[l]; decisions
+ * P*rot_off[l]; traces A*P*rot_off[l]; D l.  status[l] = 0 or -1. */
+int or_flatten_batch(int32_t L, const int32_t *atom_off, const float *x, const float *y, const float *z,
+                     const uint8_t *type, const int16_t *parent, const int32_t *rot_off, const int16_t *rot_child,
+                     int32_t passes, int32_t A, double d_clash, const uint8_t *replay, double *xyz_out,
+                     uint8_t *choice, uint8_t *own, double *trace_D, double *trace_d2, double *D_out,
+                     int32_t *status, int32_t nthreads) {
+    int bad = 0;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads > 0 ? nthreads : 1) reduction(+ : bad)
+    for (int l = 0; l < L; l++) {
+        const int a0 = atom_off[l], N = atom_off[l + 1] - a0;
+        const int r0 = rot_off[l], Rl = rot_off[l + 1] - r0;
+        const size_t d0 = (size_t)passes * r0;
+        int rc = or_flatten_ligand(N, x + a0, y + a0, z + a0, type + a0, parent + a0, Rl, rot_child + r0, passes, A,
+                                   d_clash, replay ? replay + d0 : NULL, xyz_out ? xyz_out + (size_t)3 * a0 : NULL,
+                                   choice ? choice + d0 : NULL, own ? own + d0 : NULL,
+                                   trace_D ? trace_D + d0 * A : NULL, trace_d2 ? trace_d2 + d0 * A : NULL,
+                                   D_out ? D_out + l : NULL);
+        status[l] = rc;
+        if (rc != 0) bad++;
+    }
+    return bad;
 }
