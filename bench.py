@@ -488,6 +488,29 @@ def main():
         plain = {"value": plain_value, "unit": UNIT, "sample_ligands": n_plain, "streams": 8,
                  "batched_over_plain": value / world / plain_value}
 
+        # ligand flattening (protein independent pre-processing) on the whole batch, device-resident
+        fpar = lg.make_flatten_params(P, params.d_clash, max_atoms, max_rot)
+        fres = lg.lg_flatten_result()
+        fres.mem = lg.LG_MEM_DEVICE
+        fout = dict(xyz=torch.empty(3 * A, dtype=torch.float32, device=f"cuda:{dev}"),
+                    dsum=torch.empty(L, dtype=torch.float64, device=f"cuda:{dev}"),
+                    status=torch.empty(L, dtype=torch.int32, device=f"cuda:{dev}"))
+        fres.xyz, fres.dsum, fres.status = (fout[k].data_ptr() for k in ("xyz", "dsum", "status"))
+        lg.lg_flatten_batch(ctx.h, bstruct, fpar, fres, sh)   # warm-up
+        torch.cuda.synchronize()
+        f_ms = 0.0
+        for _ in range(3):
+            flush.fill_(1)
+            p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            p0.record(stream)
+            lg.lg_flatten_batch(ctx.h, bstruct, fpar, fres, sh)
+            p1.record(stream)
+            torch.cuda.synchronize()
+            f_ms += p0.elapsed_time(p1) / 3
+        assert int((fout["status"] != 0).sum()) == 0
+        flatten = {"value": L / (f_ms / 1e3), "unit": "ligands/s", "ms_per_call": f_ms, "passes": P,
+                   "ligands": L, "launches_per_call": 2}
+
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
             rate, n_done, secs = oracle_rate(pocket, batch, params, args.cpu_budget)
@@ -512,7 +535,7 @@ def main():
                            "warps_per_cta": st.warps_per_cta, "ctas_per_sm": st.ctas_per_sm, "grid": st.grid},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "clocks": clk, "gpu_launches": launches_per_step * args.steps, "plain": plain,
-                "serving": serving, "multi_pocket": multi}
+                "serving": serving, "multi_pocket": multi, "flatten": flatten}
         print(json.dumps(line), flush=True)
     ctx.close()
     if dist:

@@ -257,6 +257,50 @@ int lg_dock_batch(lg_ctx *ctx, int32_t pocket_id, const lg_ligand_batch *batch, 
 int lg_dock_multi(lg_ctx *ctx, const int32_t *pocket_ids, int32_t n_pockets, const lg_ligand_batch *batch,
                   const lg_dock_params *params, lg_dock_result *outs, void *stream);
 
+/* Ligand flattening (paper Sec. 3.1, step 1: before docking, the torsional
+ * bonds are turned to maximise the sum of the distances between all atom
+ * pairs; protein independent, so done once per ligand for every pocket).
+ * Reading: the docking's greedy sweep without a pocket -- for pass =
+ * 0..passes-1 and each torsional bond in ascending child order, the 36 steps
+ * of 10 degrees turn the bond's moving atoms; the admissible step (the clash
+ * rule of lg_dock_batch with d_clash) with the largest sum of pairwise
+ * distances is applied, the lowest step on ties.  The ligand stays in its
+ * input frame.  Distances are FP32, summed in FP32 within 32 pairs and in FP64
+ * across them.
+ *   passes       0..LG_MAX_PASSES sweeps over the torsional bonds
+ *   angle_steps  must be LG_ANGLE_STEPS
+ *   d_clash      clash distance (A), > 0
+ *   max_atoms, max_rot  optional declared maxima (0 = the library limits) */
+typedef struct {
+    int32_t passes;
+    int32_t angle_steps;
+    float d_clash;
+    int32_t max_atoms;
+    int32_t max_rot;
+} lg_flatten_params;
+
+/* Caller-owned outputs (location given by `mem`):
+ *   xyz [3*A]      flattened coordinates, 3*atom_off[l] + 3*i + {x,y,z}; a
+ *                  rejected ligand's input coordinates
+ *   tors           optional: step applied at each decision,
+ *                  passes*rot_off[l] + pass*R_l + k
+ *   dsum [L]       optional: FP64 sum of all pairwise distances of the result
+ *                  (NaN for a rejected ligand)
+ *   status [L]     LG_OK or LG_EINVAL per ligand (the checks of lg_dock_batch) */
+typedef struct {
+    int32_t mem;
+    float *xyz;
+    uint8_t *tors;
+    double *dsum;
+    int32_t *status;
+} lg_flatten_result;
+
+/* Flatten a batch.  Memory rules as lg_dock_batch (asynchronous on `stream`
+ * when batch and result are device memory).  Errors: LG_EINVAL, LG_ENOMEM,
+ * LG_ECUDA. */
+int lg_flatten_batch(lg_ctx *ctx, const lg_ligand_batch *batch, const lg_flatten_params *params,
+                     lg_flatten_result *out, void *stream);
+
 /* Allocation-free docking (the paper has no counterpart to this call).
  * Some callers cannot let a library allocate device memory: applications that
  * give all device memory to their own pool allocator at start-up (a cudaMalloc

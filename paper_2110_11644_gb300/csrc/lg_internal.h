@@ -181,15 +181,37 @@ struct DockArgs {
 
 constexpr int kSortBuckets = 128;
 
+// Ligand flattening (one warp per ligand; see k_flatten).
+struct FlatArgs {
+    BatchDev batch;
+    const int16_t *rot_end;   // from the preparation kernel, [L * rmax_lim]
+    const double *centroid;   // [3L]
+    int rmax_lim;
+    int P;                    // passes
+    float dc2;                // d_clash^2 (A^2)
+    int nmax;                 // atoms per warp region (multiple of 4)
+    float *xyz;               // [3A] output
+    uint8_t *tors;            // [P * rot_off] output (optional)
+    double *dsum;             // [L] output (optional)
+    const int32_t *status;    // [L] from the preparation kernel
+};
+
+constexpr int kFlatWarps = 4;
+__host__ __device__ inline int flat_warp_bytes(int nmax) {
+    return lg_align16(12 * nmax) + lg_align16(4 * nmax) + lg_align16(48 * nmax) + 32 * 16;
+}
+
 // Several pockets in one persistent launch: work items are (pocket, ligand)
 // pairs.  pocket_major = 1 visits every ligand against pocket 0, then pocket 1,
 // ... (one pocket's grids in L2 at a time); 0 gives a CTA one ligand and docks
 // it against every pocket in turn.
+// Passed by value (kernel parameter space): the hot loops read the pocket
+// through the same constant path as the single-pocket kernel.
 struct MultiDev {
     int np;
     int pocket_major;
-    const PocketDev *pk;  // [np] device array
-    const OutDev *out;    // [np] device array; out[0] receives the preparation's status
+    PocketDev pk[LG_MAX_MULTI_POCKETS];
+    OutDev out[LG_MAX_MULTI_POCKETS];  // out[0] receives the preparation's status
 };
 
 // Byte size of the scratch of a launch, and its carving.
@@ -206,6 +228,7 @@ cudaError_t launch_score_poses(const PocketDev &p, int L, const int32_t *atom_of
 cudaError_t launch_diag_philox(int n, const uint32_t *ctr, const uint32_t *key, uint32_t *out, int use_curand,
                                cudaStream_t s);
 cudaError_t launch_dock_multi(const DockArgs &a, const MultiDev &m, int grid, int smem, cudaStream_t s);
+cudaError_t launch_flatten(const FlatArgs &f, int L, cudaStream_t s);
 cudaError_t dock_kernel_attributes(int W, int smem, int *ctas_per_sm, bool ranking);
 cudaError_t multi_kernel_attributes(int W, int smem, int *ctas_per_sm, bool ranking);
 cudaError_t plain_kernel_attributes(int smem);

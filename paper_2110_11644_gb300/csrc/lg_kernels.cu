@@ -74,9 +74,9 @@ __device__ __forceinline__ CtaView cta_view(char *sm, const Layout &L) {
 // Stage ligand l: centroid-relative coordinates in grid units (FP64
 // difference), parents, per-atom (type weight, charge), torsional children,
 // subtree ends and input bond vectors in grid units.
-__device__ __forceinline__ void stage_ligand(const DockArgs &A, const CtaView &cv, int l, int a0, int N, int r0, int R) {
+__device__ __forceinline__ void stage_ligand(const DockArgs &A, const PocketDev &Pk, const CtaView &cv, int l, int a0,
+                                             int N, int r0, int R) {
     const BatchDev &B = A.batch;
-    const PocketDev &Pk = A.pocket;
     const double cx = A.scr.centroid[3 * l], cy = A.scr.centroid[3 * l + 1], cz = A.scr.centroid[3 * l + 2];
     const double ih = (double)Pk.inv_h;
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
@@ -99,7 +99,8 @@ __device__ __forceinline__ void stage_ligand(const DockArgs &A, const CtaView &c
 // ligand's outputs.  Bx/By/Bz/tbest of the winning warp hold its best pose and
 // decisions.  Returns after a CTA barrier.
 template <typename BestOf>
-__device__ __forceinline__ void finish_ligand(const DockArgs &A, const CtaView &cv, int l, int a0, int N, int r0,
+__device__ __forceinline__ void finish_ligand(const DockArgs &A, const PocketDev &Pk, const OutDev &O, const CtaView &cv,
+                                              int l, int a0, int N, int r0,
                                               int PR, BestOf best_of) {
     __syncthreads();
     const int W = blockDim.x >> 5, tid = threadIdx.x;
@@ -117,25 +118,25 @@ __device__ __forceinline__ void finish_ligand(const DockArgs &A, const CtaView &
     }
     if (bw < 0) {  // every restart produced a non-finite score
         if (tid == 0) {
-            A.out.score[l] = __longlong_as_double(0x7ff8000000000000ll);
-            A.out.best_restart[l] = -1;
-            A.out.status[l] = LG_EINVAL;
+            O.score[l] = __longlong_as_double(0x7ff8000000000000ll);
+            O.best_restart[l] = -1;
+            O.status[l] = LG_EINVAL;
         }
     } else {
         const float *Bx, *By, *Bz;
         const uint8_t *tb;
         best_of(bw, Bx, By, Bz, tb);
         if (tid == 0) {
-            A.out.score[l] = be;
-            A.out.best_restart[l] = br;
+            O.score[l] = be;
+            O.best_restart[l] = br;
         }
-        if (A.out.tors_idx)
-            for (int t = tid; t < PR; t += blockDim.x) A.out.tors_idx[(size_t)A.P * r0 + t] = tb[t];
-        if (A.out.pose && A.ly.want_pose) {
-            const float3 c = A.pocket.center;
-            const float h = A.pocket.h;
+        if (O.tors_idx)
+            for (int t = tid; t < PR; t += blockDim.x) O.tors_idx[(size_t)A.P * r0 + t] = tb[t];
+        if (O.pose && A.ly.want_pose) {
+            const float3 c = Pk.center;
+            const float h = Pk.h;
             for (int i = tid; i < N; i += blockDim.x) {
-                float *o = A.out.pose + 3 * (size_t)(a0 + i);
+                float *o = O.pose + 3 * (size_t)(a0 + i);
                 o[0] = fmaf(Bx[i], h, c.x);
                 o[1] = fmaf(By[i], h, c.y);
                 o[2] = fmaf(Bz[i], h, c.z);
@@ -167,9 +168,9 @@ __device__ __forceinline__ size_t rk_pose_off(const DockArgs &A, int slot, int r
 // centroids are farther apart than the threshold (with a 1e-4 relative margin
 // over the FP32 sum's rounding) cannot be, since the mean squared distance is
 // at least the squared distance of the means, and skip the sum.
-__device__ void rank_finish(const DockArgs &A, int l, int slot, int a0, int N, int r0, int PR, char *rbase) {
+__device__ void rank_finish(const DockArgs &A, const PocketDev &Pk, const OutDev &O, int l, int slot, int a0, int N, int r0,
+                            int PR, char *rbase) {
     const int S = A.S, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, W = blockDim.x >> 5;
-    const PocketDev &Pk = A.pocket;
     char *q = rbase;
     double *sG = (double *)q;
     q += lg_align16(8 * S);
@@ -307,22 +308,22 @@ __device__ void rank_finish(const DockArgs &A, int l, int slot, int a0, int N, i
         if (lane == 0) {
             const bool ok = br != 0x7fffffff && isfinite(be);
             bestv[0] = ok ? br : -1;
-            A.out.score[l] = ok ? be : __longlong_as_double(0x7ff8000000000000ll);
-            A.out.best_restart[l] = ok ? br : -1;
-            if (!ok) A.out.status[l] = LG_EINVAL;
+            O.score[l] = ok ? be : __longlong_as_double(0x7ff8000000000000ll);
+            O.best_restart[l] = ok ? br : -1;
+            if (!ok) O.status[l] = LG_EINVAL;
         }
     }
     __syncthreads();
     const int br = bestv[0];
     if (br >= 0) {
-        if (A.out.tors_idx)
+        if (O.tors_idx)
             for (int t = tid; t < PR; t += blockDim.x)
-                A.out.tors_idx[(size_t)A.P * r0 + t] = A.scr.rk_tors[((size_t)slot * S + br) * A.P * A.ly.rmax + t];
-        if (A.out.pose) {
+                O.tors_idx[(size_t)A.P * r0 + t] = A.scr.rk_tors[((size_t)slot * S + br) * A.P * A.ly.rmax + t];
+        if (O.pose) {
             const float *x = pose0 + pstride * br;
             const float3 c = Pk.center;
             for (int i = tid; i < N; i += blockDim.x) {
-                float *o = A.out.pose + 3 * (size_t)(a0 + i);
+                float *o = O.pose + 3 * (size_t)(a0 + i);
                 o[0] = fmaf(x[3 * i], Pk.h, c.x);
                 o[1] = fmaf(x[3 * i + 1], Pk.h, c.y);
                 o[2] = fmaf(x[3 * i + 2], Pk.h, c.z);
@@ -330,9 +331,9 @@ __device__ void rank_finish(const DockArgs &A, int l, int slot, int a0, int N, i
         }
     }
     for (int p = tid; p < S; p += blockDim.x) {
-        if (A.out.rank) A.out.rank[(size_t)l * S + p] = rk[p];
-        if (A.out.leader) A.out.leader[(size_t)l * S + ord[p]] = ord[lpos[p]];
-        if (A.out.restart_geo) A.out.restart_geo[(size_t)l * S + ord[p]] = sG[ord[p]];
+        if (O.rank) O.rank[(size_t)l * S + p] = rk[p];
+        if (O.leader) O.leader[(size_t)l * S + ord[p]] = ord[lpos[p]];
+        if (O.restart_geo) O.restart_geo[(size_t)l * S + ord[p]] = sG[ord[p]];
     }
     __syncthreads();
 }
@@ -382,7 +383,7 @@ __device__ int sweep_bond_plain(const DockArgs &A, const GridK &G, const CtaView
         const int cnt = min(32, e - base);
         if (lane < cnt) {
             const int i = base + lane;
-            const Circle C = make_circle(wv.Xx[i], wv.Xy[i], wv.Xz[i], xbx, xby, xbz, u, A.pocket.c0, G.gmax);
+            const Circle C = make_circle(wv.Xx[i], wv.Xy[i], wv.Xz[i], xbx, xby, xbz, u, 0.5f * G.gmax, G.gmax);
             float4 *q = wv.bundle + 4 * lane;
             q[0] = make_float4(C.Px, C.Py, C.Pz, C.e1x);
             q[1] = make_float4(C.e1y, C.e1z, C.e2x, C.e2y);
@@ -481,7 +482,7 @@ __global__ void __launch_bounds__(1024) k_dock_plain(const __grid_constant__ Doc
     const int a0 = B.atom_off[l], N = B.atom_off[l + 1] - a0;
     const int r0 = B.rot_off[l], R = B.rot_off[l + 1] - r0;
     const int S = A.S, P = A.P, PR = P * R;
-    stage_ligand(A, cv, l, a0, N, r0, R);
+    stage_ligand(A, Pk, cv, l, a0, N, r0, R);
     __syncthreads();
 
     const float cl = c_cos[lane], sl = c_sin[lane];
@@ -554,15 +555,15 @@ __global__ void __launch_bounds__(1024) k_dock_plain(const __grid_constant__ Doc
     }
     if (A.ranking) {
         __syncthreads();
-        rank_finish(A, l, slot, a0, N, r0, PR, sm + Ly.cta_bytes);
+        rank_finish(A, Pk, A.out, l, slot, a0, N, r0, PR, sm + Ly.cta_bytes);
         return;
     }
     if (lane == 0) {
         cv.wE[warp] = bestE;
         cv.wR[warp] = bestR;
     }
-    finish_ligand(A, cv, l, a0, N, r0, PR, [&](int w, const float *&Bx, const float *&By, const float *&Bz,
-                                               const uint8_t *&tb) {
+    finish_ligand(A, Pk, A.out, cv, l, a0, N, r0, PR, [&](int w, const float *&Bx, const float *&By, const float *&Bz,
+                                                         const uint8_t *&tb) {
         const WarpView bv = warp_view(sm, Ly, w);
         Bx = bv.Bx;
         By = bv.By;
@@ -635,7 +636,7 @@ __device__ __forceinline__ int sweep_bond_rt(const DockArgs &A, const GridK &G, 
 
     const float xbx = v.Xx[b * kTile + rs], xby = v.Xy[b * kTile + rs], xbz = v.Xz[b * kTile + rs];
     const float3 u = unit_axis(v.axis[k * kTile + rs]);
-    const float c0 = A.pocket.c0, dc2 = A.dc2g;
+    const float c0 = 0.5f * G.gmax, dc2 = A.dc2g;  // (n - 1) / 2, exact
     const int nF = N - (e - b);
     const int lane = kLanesPerRestart * rs + g;
     const unsigned gmask = 0xFu << (kLanesPerRestart * rs), below = (1u << lane) - 1u;
@@ -767,19 +768,18 @@ __device__ __forceinline__ int sweep_bond_rt(const DockArgs &A, const GridK &G, 
 // kRank: pose ranking on (a separate instantiation, so the plain best-restart
 // form carries none of its code)
 template <bool kRank>
-__device__ __forceinline__ void dock_ligand_rt(const DockArgs &A, int l, char *sm) {
-    if (A.out.status[l] != LG_OK) return;  // rejected by the preparation kernel (uniform)
+__device__ __forceinline__ void dock_ligand_rt(const DockArgs &A, const PocketDev &Pk, const OutDev &O, int l, char *sm) {
+    if (O.status[l] != LG_OK) return;  // rejected by the preparation kernel (uniform)
     const Layout &Ly = A.ly;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
     const int rs = lane / kLanesPerRestart, g = lane % kLanesPerRestart;
     const CtaView cv = cta_view(sm, Ly);
     const RtView v = rt_view(sm, Ly, A.lrt, warp);
     const BatchDev &B = A.batch;
-    const PocketDev &Pk = A.pocket;
     const int a0 = B.atom_off[l], N = B.atom_off[l + 1] - a0;
     const int r0 = B.rot_off[l], R = B.rot_off[l + 1] - r0;
     const int S = A.S, P = A.P, PR = P * R;
-    stage_ligand(A, cv, l, a0, N, r0, R);
+    stage_ligand(A, Pk, cv, l, a0, N, r0, R);
     __syncthreads();
 
     float cs[kStepsPerLane], sn[kStepsPerLane];
@@ -831,10 +831,10 @@ __device__ __forceinline__ void dock_ligand_rt(const DockArgs &A, int l, char *s
         E += __shfl_xor_sync(LG_FULL, E, 1);
         E += __shfl_xor_sync(LG_FULL, E, 2);
         if (valid) {
-            if (A.out.restart_score && g == 0) A.out.restart_score[(size_t)l * S + r] = E;
-            if (A.out.restart_tors)
+            if (O.restart_score && g == 0) O.restart_score[(size_t)l * S + r] = E;
+            if (O.restart_tors)
                 for (int t = g; t < PR; t += kLanesPerRestart)
-                    A.out.restart_tors[(size_t)S * P * r0 + (size_t)r * PR + t] = v.tcur[t * kTile + rs];
+                    O.restart_tors[(size_t)S * P * r0 + (size_t)r * PR + t] = v.tcur[t * kTile + rs];
             if (kRank) {  // keep the restart for the ranking step
                 float *x = A.scr.rk_pose + rk_pose_off(A, blockIdx.x, r);
                 for (int i = g; i < N; i += kLanesPerRestart) {
@@ -875,15 +875,15 @@ __device__ __forceinline__ void dock_ligand_rt(const DockArgs &A, int l, char *s
     }
     if (kRank) {
         __syncthreads();
-        rank_finish(A, l, blockIdx.x, a0, N, r0, PR, sm + Ly.cta_bytes);
+        rank_finish(A, Pk, O, l, blockIdx.x, a0, N, r0, PR, sm + Ly.cta_bytes);
         return;
     }
     if (lane == 0) {
         cv.wE[warp] = bestE;
         cv.wR[warp] = bestR;
     }
-    finish_ligand(A, cv, l, a0, N, r0, PR, [&](int w, const float *&Bx, const float *&By, const float *&Bz,
-                                               const uint8_t *&tb) {
+    finish_ligand(A, Pk, O, cv, l, a0, N, r0, PR, [&](int w, const float *&Bx, const float *&By, const float *&Bz,
+                                                     const uint8_t *&tb) {
         const RtView bv = rt_view(sm, Ly, A.lrt, w);
         Bx = bv.Bx;
         By = bv.By;
@@ -906,43 +906,36 @@ __global__ void __launch_bounds__(128, LG_RT_MIN_BLOCKS) k_dock_batched(const __
         const int item = s_item;
         __syncthreads();
         if (item >= A.batch.L) break;
-        dock_ligand_rt<kRank>(A, A.order ? A.order[item] : item, sm);
+        dock_ligand_rt<kRank>(A, A.pocket, A.out, A.order ? A.order[item] : item, sm);
     }
 }
 
-// Several pockets (MultiDev): the CTA keeps a copy of the launch arguments in
-// shared memory and swaps in the pocket and outputs of each work item, so the
-// docking code is the single-pocket code.  The preparation kernel validated
-// every ligand once and wrote its status to the first pocket's outputs; the
-// other pockets' outputs get the same status here.
+// Several pockets (MultiDev): work items are (pocket, ligand) pairs; the
+// docking code is the single-pocket code with the item's pocket and outputs.
+// The preparation kernel validated every ligand once and wrote its status to
+// the first pocket's outputs; the other pockets' outputs get the same status
+// here.
 template <bool kRank>
 __global__ void __launch_bounds__(128, LG_RT_MIN_BLOCKS) k_dock_multi(const __grid_constant__ DockArgs A,
-                                                                       const MultiDev M) {
+                                                                       const __grid_constant__ MultiDev M) {
     extern __shared__ __align__(16) char sm[];
-    __shared__ __align__(16) DockArgs sA;
     __shared__ int s_item;
-    {
-        const int *src = (const int *)&A;
-        int *dst = (int *)&sA;
-        for (int t = threadIdx.x; t < (int)(sizeof(DockArgs) / sizeof(int)); t += blockDim.x) dst[t] = src[t];
-    }
     const int L = A.batch.L;
     const int items = M.pocket_major ? M.np * L : L;
     auto dock_one = [&](int p, int l) {
-        if (threadIdx.x == 0) {
-            sA.pocket = M.pk[p];
-            sA.out = M.out[p];
-            if (p > 0) {
+        const OutDev &O = M.out[p];
+        if (p > 0) {
+            if (threadIdx.x == 0) {
                 const int st = M.out[0].status[l];
-                sA.out.status[l] = st;
+                O.status[l] = st;
                 if (st != LG_OK) {
-                    sA.out.score[l] = __longlong_as_double(0x7ff8000000000000ll);
-                    sA.out.best_restart[l] = -1;
+                    O.score[l] = __longlong_as_double(0x7ff8000000000000ll);
+                    O.best_restart[l] = -1;
                 }
             }
+            __syncthreads();
         }
-        __syncthreads();
-        dock_ligand_rt<kRank>(sA, l, sm);
+        dock_ligand_rt<kRank>(A, M.pk[p], O, l, sm);
         __syncthreads();
     };
     for (;;) {
@@ -958,6 +951,143 @@ __global__ void __launch_bounds__(128, LG_RT_MIN_BLOCKS) k_dock_multi(const __gr
             const int l = A.order ? A.order[item] : item;
             for (int p = 0; p < M.np; ++p) dock_one(p, l);
         }
+    }
+}
+
+// ================================================================== flattening
+// Ligand pre-processing (paper Sec. 3.1, step 1; no pocket): the greedy sweep
+// with the sum of all pairwise atom distances as its objective.  One warp per
+// ligand, positions centroid-relative in A (FP32).  Lanes own torsion steps
+// (lane t: step t, lanes 0..3 also steps 32..35).  Only the (moving, fixed)
+// pairs change with the step: their distance on the step's circle point is
+//     |x_i(theta) - x_j| = sqrt(C + A2 cos(theta) + B2 sin(theta)),
+// with the pair coefficients built once per decision, 32 pairs at a time by the
+// lanes and read back by broadcast.  Per step, distances are summed in FP32
+// within a 32-pair chunk and the chunks in FP64; the clash rule of the sweep
+// (pairs at least three bonds apart, at least d_clash) decides admissibility;
+// the admissible step with the largest sum wins, the lowest step on ties.
+__global__ void __launch_bounds__(32 * kFlatWarps) k_flatten(const __grid_constant__ FlatArgs F) {
+    extern __shared__ __align__(16) char sm[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int l = blockIdx.x * kFlatWarps + warp;
+    if (l >= F.batch.L) return;  // warp-uniform; no CTA barriers below
+    const BatchDev &B = F.batch;
+    const int a0 = B.atom_off[l], N = B.atom_off[l + 1] - a0;
+    if (F.status[l] != LG_OK) {  // rejected by the preparation kernel: coordinates pass through
+        for (int i = lane; i < N && i < LG_MAX_ATOMS; i += 32) {
+            F.xyz[3 * (size_t)(a0 + i)] = B.x[a0 + i];
+            F.xyz[3 * (size_t)(a0 + i) + 1] = B.y[a0 + i];
+            F.xyz[3 * (size_t)(a0 + i) + 2] = B.z[a0 + i];
+        }
+        if (F.dsum && lane == 0) F.dsum[l] = __longlong_as_double(0x7ff8000000000000ll);
+        return;
+    }
+    const int nm = F.nmax;
+    char *wb = sm + (size_t)warp * flat_warp_bytes(nm);
+    float *Xx = (float *)wb, *Xy = Xx + nm, *Xz = Xy + nm;
+    int *par = (int *)(wb + lg_align16(12 * nm));
+    float4 *circ = (float4 *)(wb + lg_align16(12 * nm) + lg_align16(4 * nm));  // [nm][3]: (p, r2), e1, e2
+    float4 *chunk = circ + 3 * nm;                                              // [32] (C, A2, B2, checked)
+    const int r0 = B.rot_off[l], R = B.rot_off[l + 1] - r0;
+    const double cx = F.centroid[3 * l], cy = F.centroid[3 * l + 1], cz = F.centroid[3 * l + 2];
+    for (int i = lane; i < N; i += 32) {
+        Xx[i] = (float)((double)B.x[a0 + i] - cx);
+        Xy[i] = (float)((double)B.y[a0 + i] - cy);
+        Xz[i] = (float)((double)B.z[a0 + i] - cz);
+        par[i] = B.parent[a0 + i];
+    }
+    __syncwarp();
+    const bool two = lane < LG_ANGLE_STEPS - 32;
+    const float c0 = c_cos[lane], s0 = c_sin[lane];
+    const float c1 = two ? c_cos[32 + lane] : 1.0f, s1 = two ? c_sin[32 + lane] : 0.0f;
+    for (int ps = 0; ps < F.P; ++ps)
+        for (int k = 0; k < R; ++k) {
+            const int b = B.rot_child[r0 + k], a = par[b], e = F.rot_end[(size_t)l * F.rmax_lim + k];
+            const float xbx = Xx[b], xby = Xy[b], xbz = Xz[b];
+            const float3 u = unit_axis(make_float4(xbx - Xx[a], xby - Xy[a], xbz - Xz[a], 0.0f));
+            for (int i = b + 1 + lane; i < e; i += 32) {
+                const Circle C = make_circle(Xx[i], Xy[i], Xz[i], xbx, xby, xbz, u, 0.0f, 0.0f);
+                circ[3 * i] = make_float4(C.px, C.py, C.pz, C.r2);
+                circ[3 * i + 1] = make_float4(C.e1x, C.e1y, C.e1z, 0.0f);
+                circ[3 * i + 2] = make_float4(C.e2x, C.e2y, C.e2z, 0.0f);
+            }
+            __syncwarp();
+            const int m = e - b - 1, nf = N - (e - b);
+            const int total = m * nf;
+            double D0 = 0.0, D1 = 0.0;
+            float m0 = INFINITY, m1 = INFINITY;
+            for (int q0 = 0; q0 < total; q0 += 32) {
+                const int q = q0 + lane;
+                if (q < total) {
+                    const int i = b + 1 + q / nf, jj = q - (q / nf) * nf;
+                    const int j = jj < b ? jj : jj + (e - b);
+                    const float4 pc = circ[3 * i], e1 = circ[3 * i + 1], e2 = circ[3 * i + 2];
+                    const PairC pq = pair_coeffs(pc.x, pc.y, pc.z, e1.x, e1.y, e1.z, e2.x, e2.y, e2.z, pc.w, Xx[j], Xy[j],
+                                                 Xz[j], F.dc2);
+                    const bool checked = !(j == a && par[i] == b);  // the one pair closer than 3 bonds
+                    chunk[lane] = make_float4(pq.C, pq.A2, pq.B2, checked ? 1.0f : 0.0f);
+                }
+                __syncwarp();
+                const int n = min(32, total - q0);
+                float acc0 = 0.0f, acc1 = 0.0f;
+                for (int t = 0; t < n; ++t) {
+                    const float4 cf = chunk[t];
+                    const float d0 = fmaf(cf.z, s0, fmaf(cf.y, c0, cf.x));
+                    acc0 += sqrtf(fmaxf(d0, 0.0f));
+                    if (cf.w != 0.0f) m0 = fminf(m0, d0);
+                    if (two) {
+                        const float d1 = fmaf(cf.z, s1, fmaf(cf.y, c1, cf.x));
+                        acc1 += sqrtf(fmaxf(d1, 0.0f));
+                        if (cf.w != 0.0f) m1 = fminf(m1, d1);
+                    }
+                }
+                D0 += (double)acc0;
+                D1 += (double)acc1;
+                __syncwarp();
+            }
+            // best admissible step of the lane, then of the warp (larger sum, then lower step)
+            double bd = (lane == 0 || m0 >= F.dc2) ? D0 : -INFINITY;
+            int bt = lane;
+            if (two && m1 >= F.dc2 && D1 > bd) {
+                bd = D1;
+                bt = 32 + lane;
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const double od = __shfl_xor_sync(LG_FULL, bd, o);
+                const int ot = __shfl_xor_sync(LG_FULL, bt, o);
+                if (od > bd || (od == bd && ot < bt)) {
+                    bd = od;
+                    bt = ot;
+                }
+            }
+            if (F.tors && lane == 0) F.tors[(size_t)F.P * r0 + ps * R + k] = (uint8_t)bt;
+            if (bt != 0) {
+                const float c = c_cos[bt], sn = c_sin[bt];
+                for (int i = b + 1 + lane; i < e; i += 32) {
+                    const float4 pc = circ[3 * i], e1 = circ[3 * i + 1], e2 = circ[3 * i + 2];
+                    Xx[i] = fmaf(e2.x, sn, fmaf(e1.x, c, pc.x));
+                    Xy[i] = fmaf(e2.y, sn, fmaf(e1.y, c, pc.y));
+                    Xz[i] = fmaf(e2.z, sn, fmaf(e1.z, c, pc.z));
+                }
+            }
+            __syncwarp();
+        }
+    // outputs: coordinates in the input frame and the final sum of distances
+    for (int i = lane; i < N; i += 32) {
+        F.xyz[3 * (size_t)(a0 + i)] = (float)((double)Xx[i] + cx);
+        F.xyz[3 * (size_t)(a0 + i) + 1] = (float)((double)Xy[i] + cy);
+        F.xyz[3 * (size_t)(a0 + i) + 2] = (float)((double)Xz[i] + cz);
+    }
+    if (F.dsum) {
+        double D = 0.0;
+        for (int i = lane; i < N; i += 32)
+            for (int j = i + 1; j < N; ++j) {
+                const float dx = Xx[i] - Xx[j], dy = Xy[i] - Xy[j], dz = Xz[i] - Xz[j];
+                D += (double)sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+            }
+        D = warp_sum_d(D);
+        if (lane == 0) F.dsum[l] = D;
     }
 }
 
@@ -1201,6 +1331,14 @@ cudaError_t launch_dock_multi(const DockArgs &a, const MultiDev &m, int grid, in
         k_dock_multi<true><<<grid, 32 * a.ly.W, smem, s>>>(a, m);
     else
         k_dock_multi<false><<<grid, 32 * a.ly.W, smem, s>>>(a, m);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_flatten(const FlatArgs &f, int L, cudaStream_t s) {
+    const int smem = kFlatWarps * flat_warp_bytes(f.nmax);
+    cudaError_t e = cudaFuncSetAttribute(k_flatten, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    k_flatten<<<(L + kFlatWarps - 1) / kFlatWarps, 32 * kFlatWarps, smem, s>>>(f);
     return cudaGetLastError();
 }
 

@@ -52,21 +52,15 @@ extern "C" int lg_dock_multi(lg_ctx *c, const int32_t *pocket_ids, int32_t n_poc
     std::vector<OutDev> od(n_pockets);
     for (int k = 0; k < n_pockets; k++)
         if ((rc = resolve_out(c, c->multi_out[k], b, &outs[k], S, P, s, &A, &R, &od[k]))) return rc;
-    // pocket and output descriptors for the kernel
-    const size_t o_out = (sizeof(PocketDev) * n_pockets + 255) & ~(size_t)255;
-    const size_t bytes = o_out + sizeof(OutDev) * n_pockets;
-    if (c->multi_desc.ensure(bytes)) return fail(LG_ENOMEM, "descriptor allocation failed");
-    std::vector<char> img(bytes);
-    memcpy(img.data(), pk.data(), sizeof(PocketDev) * n_pockets);
-    memcpy(img.data() + o_out, od.data(), sizeof(OutDev) * n_pockets);
-    // pageable source: the call returns once the bytes have left `img`
-    cudaError_t e = cudaMemcpyAsync(c->multi_desc.p, img.data(), bytes, cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return fail(LG_ECUDA, std::string("descriptor upload: ") + cudaGetErrorString(e));
     MultiDev m;
+    memset(&m, 0, sizeof(m));
     m.np = n_pockets;
     m.pocket_major = c->multi_pocket_major;
-    m.pk = (const PocketDev *)c->multi_desc.p;
-    m.out = (const OutDev *)((char *)c->multi_desc.p + o_out);
+    for (int k = 0; k < n_pockets; k++) {
+        m.pk[k] = pk[k];
+        m.out[k] = od[k];
+    }
+    cudaError_t e;
     cudaEvent_t *tev = next_timing_events(c);
     if ((rc = dock_device(c, pk[0], bd, od[0], p, nmax, rmax, c->scratch, s, &c->stats, tev, &m))) return rc;
     if (omem == LG_MEM_HOST)

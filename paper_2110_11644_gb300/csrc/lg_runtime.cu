@@ -473,7 +473,7 @@ void lg_destroy(lg_ctx *c) {
     c->out_buf.release();
     c->scratch.release();
     for (auto &m : c->multi_out) m.release();
-    c->multi_desc.release();
+    c->flat_buf.release();
     for (auto s : c->plain_streams) cudaStreamDestroy(s);
     for (auto ev : c->join_events) cudaEventDestroy(ev);
     for (int i = 0; i < 3; i++)

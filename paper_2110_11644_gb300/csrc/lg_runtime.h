@@ -70,7 +70,7 @@ struct lg_ctx {
     lg::Server *server = nullptr;
     // several pockets in one launch (lg_dock_multi)
     std::vector<lg::DevBuf> multi_out;
-    lg::DevBuf multi_desc;
+    lg::DevBuf flat_buf;  // lg_flatten_batch: host-output staging and the preparation's unused outputs
     int multi_pocket_major = 1;
 };
 

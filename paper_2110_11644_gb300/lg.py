@@ -51,6 +51,15 @@ class lg_dock_result(ctypes.Structure):
                 ("restart_geo", _P)]
 
 
+class lg_flatten_params(ctypes.Structure):
+    _fields_ = [("passes", ctypes.c_int32), ("angle_steps", ctypes.c_int32), ("d_clash", ctypes.c_float),
+                ("max_atoms", ctypes.c_int32), ("max_rot", ctypes.c_int32)]
+
+
+class lg_flatten_result(ctypes.Structure):
+    _fields_ = [("mem", ctypes.c_int32), ("xyz", _P), ("tors", _P), ("dsum", _P), ("status", _P)]
+
+
 class lg_pose_batch(ctypes.Structure):
     _fields_ = [("L", ctypes.c_int32), ("mem", ctypes.c_int32), ("atom_off", _P), ("xyz", _P), ("q", _P),
                 ("type", _P)]
@@ -65,7 +74,7 @@ class lg_stats(ctypes.Structure):
 # Every symbol include/lg.h declares (checked by the ABI test).
 EXPORTS = ("lg_create", "lg_destroy", "lg_last_error", "lg_pocket_load", "lg_pocket_unload", "lg_dock_batch",
            "lg_score_poses", "lg_stream_submit", "lg_stream_poll", "lg_stream_wait", "lg_get_stats", "lg_set_option",
-           "lg_diag_philox", "lg_dock_batch_noalloc", "lg_dock_multi")
+           "lg_diag_philox", "lg_dock_batch_noalloc", "lg_dock_multi", "lg_flatten_batch")
 
 _lib = None
 _lock = threading.Lock()
@@ -105,6 +114,8 @@ def load():
                                                   c.POINTER(lg_dock_result), V]
             lib.lg_dock_multi.argtypes = [V, c.POINTER(c.c_int32), c.c_int32, c.POINTER(lg_ligand_batch),
                                           c.POINTER(lg_dock_params), c.POINTER(lg_dock_result), V]
+            lib.lg_flatten_batch.argtypes = [V, c.POINTER(lg_ligand_batch), c.POINTER(lg_flatten_params),
+                                             c.POINTER(lg_flatten_result), V]
             for name in EXPORTS:
                 if name not in ("lg_destroy", "lg_last_error"):
                     getattr(lib, name).restype = c.c_int
@@ -167,6 +178,17 @@ def lg_dock_multi(h, pids, batch: lg_ligand_batch, params: lg_dock_params, outs,
     ids = (ctypes.c_int32 * n)(*[int(p) for p in pids])
     res = (lg_dock_result * n)(*outs)
     _check(h, load().lg_dock_multi(h, ids, n, ctypes.byref(batch), ctypes.byref(params), res, stream))
+
+
+def lg_flatten_batch(h, batch: lg_ligand_batch, params: lg_flatten_params, out: lg_flatten_result, stream=None):
+    _check(h, load().lg_flatten_batch(h, ctypes.byref(batch), ctypes.byref(params), ctypes.byref(out), stream))
+
+
+def make_flatten_params(passes, d_clash=2.0, max_atoms=0, max_rot=0):
+    p = lg_flatten_params()
+    p.passes, p.angle_steps, p.d_clash = int(passes), LG_ANGLE_STEPS, float(d_clash)
+    p.max_atoms, p.max_rot = int(max_atoms), int(max_rot)
+    return p
 
 
 def lg_score_poses(h, pid, poses: lg_pose_batch, energies_ptr, stream=None):
@@ -410,6 +432,38 @@ class Context:
                 outs = {k: (v.cpu().numpy() if v is not None else None) for k, v in outs.items()}
             out.append({k: (v[:n[k]] if v is not None else None) for k, v in outs.items()})
         return out
+
+    def flatten(self, batch, passes, d_clash=2.0, *, device_io=False, stream=None):
+        """Flatten a CSR batch; returns numpy xyz (flat, 3*atom_off), tors,
+        dsum and status."""
+        L = len(batch.atom_off) - 1
+        A, R = int(batch.atom_off[-1]), int(batch.rot_off[-1])
+        arrs = device_batch_arrays(batch) if device_io else host_batch_arrays(batch)
+        b = make_batch_struct(arrs, L)
+        p = make_flatten_params(passes, d_clash)
+        if device_io:
+            import torch
+            z = lambda n, dt: torch.zeros(max(n, 1), dtype=dt, device="cuda")
+            outs = dict(xyz=z(3 * A, torch.float32), tors=z(passes * R, torch.uint8), dsum=z(L, torch.float64),
+                        status=z(L, torch.int32))
+        else:
+            z = lambda n, dt: np.zeros(max(n, 1), dt)
+            outs = dict(xyz=z(3 * A, np.float32), tors=z(passes * R, np.uint8), dsum=z(L, np.float64),
+                        status=z(L, np.int32))
+        r = lg_flatten_result()
+        r.mem = LG_MEM_DEVICE if device_io else LG_MEM_HOST
+        for k, v in outs.items():
+            setattr(r, k, _ptr(v))
+        if device_io:
+            import torch
+            s = torch.cuda.current_stream()
+            lg_flatten_batch(self.h, b, p, r, s.cuda_stream if stream is None else stream)
+            s.synchronize()
+            outs = {k: v.cpu().numpy() for k, v in outs.items()}
+        else:
+            lg_flatten_batch(self.h, b, p, r, stream)
+        n = dict(xyz=3 * A, tors=passes * R, dsum=L, status=L)
+        return {k: v[:n[k]] for k, v in outs.items()}
 
     def score_poses(self, pid, atom_off, xyz, q, type_):
         atom_off = np.ascontiguousarray(atom_off, np.int32)

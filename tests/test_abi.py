@@ -41,22 +41,26 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(lg.lg_dock_result) == 8 + 10 * 8
     assert ctypes.sizeof(lg.lg_pose_batch) == 8 + 4 * 8
     assert ctypes.sizeof(lg.lg_stats) == 40
+    assert ctypes.sizeof(lg.lg_flatten_params) == 20
+    assert ctypes.sizeof(lg.lg_flatten_result) == 8 + 4 * 8
 
 
 def test_struct_layout_against_compiled_c(tmp_path):
     # compile a tiny C program against include/lg.h and compare sizeof/offsetof
     prog = tmp_path / "lay.c"
-    prog.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "lg.h"\nint main(){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\\n",'
+    prog.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "lg.h"\nint main(){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n",'
                     'sizeof(lg_pocket_desc), sizeof(lg_ligand_batch), sizeof(lg_dock_params), sizeof(lg_dock_result),'
                     'sizeof(lg_pose_batch), sizeof(lg_stats), offsetof(lg_dock_params, seed),'
-                    'offsetof(lg_dock_params, rescore_top), offsetof(lg_dock_result, restart_geo));return 0;}\n')
+                    'offsetof(lg_dock_params, rescore_top), offsetof(lg_dock_result, restart_geo),'
+                    'sizeof(lg_flatten_params), sizeof(lg_flatten_result));return 0;}\n')
     exe = tmp_path / "lay"
     import subprocess
     subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)])
     got = [int(v) for v in subprocess.check_output([str(exe)]).split()]
     want = [ctypes.sizeof(lg.lg_pocket_desc), ctypes.sizeof(lg.lg_ligand_batch), ctypes.sizeof(lg.lg_dock_params),
             ctypes.sizeof(lg.lg_dock_result), ctypes.sizeof(lg.lg_pose_batch), ctypes.sizeof(lg.lg_stats),
-            lg.lg_dock_params.seed.offset, lg.lg_dock_params.rescore_top.offset, lg.lg_dock_result.restart_geo.offset]
+            lg.lg_dock_params.seed.offset, lg.lg_dock_params.rescore_top.offset, lg.lg_dock_result.restart_geo.offset,
+            ctypes.sizeof(lg.lg_flatten_params), ctypes.sizeof(lg.lg_flatten_result)]
     assert got == want
 
 
