@@ -53,7 +53,7 @@ class _Pocket(ctypes.Structure):
 class _Params(ctypes.Structure):
     _fields_ = [("restarts", ctypes.c_int32), ("passes", ctypes.c_int32), ("angle_steps", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("d_clash", ctypes.c_double), ("cluster_rmsd", ctypes.c_double),
-                ("rescore_top", ctypes.c_int32)]
+                ("rescore_top", ctypes.c_int32), ("rigid_steps", ctypes.c_int32), ("rigid_shift", ctypes.c_double)]
 
 
 def _load():
@@ -73,10 +73,12 @@ def _load():
             lib.or_topology.argtypes = [i32, P, P]
             lib.or_topology.restype = ctypes.c_int
             lib.or_dock_ligand.restype = ctypes.c_int
-            lib.or_dock_batch.argtypes = [P, P, i32] + [P] * 10 + [P] * 11 + [P, P, P, i32]
+            lib.or_dock_batch.argtypes = [P, P, i32] + [P] * 10 + [P] * 11 + [P, P, P] + [P] * 4 + [i32]
             lib.or_rank_poses.argtypes = [P, i32, i32, P, P, d, i32, P, P, P, P, P]
             lib.or_dock_batch.restype = ctypes.c_int
             lib.or_score_poses.argtypes = [P, i32, P, P, P, P, P, P]
+            lib.or_rigid_candidate.argtypes = [i32, P, i32, d, d, P]
+            lib.or_rigid_candidate.restype = None
             lib.or_flatten_batch.argtypes = [i32, P, P, P, P, P, P, P, P, i32, i32, d] + [P] * 8 + [i32]
             lib.or_flatten_batch.restype = ctypes.c_int
             _lib = lib
@@ -125,6 +127,8 @@ def _params(params):
     s.d_clash = float(np.float32(params.d_clash))
     s.cluster_rmsd = float(np.float32(getattr(params, "cluster_rmsd", 0.0)))
     s.rescore_top = int(getattr(params, "rescore_top", 0))
+    s.rigid_steps = int(getattr(params, "rigid_steps", 0))
+    s.rigid_shift = float(np.float32(getattr(params, "rigid_shift", 0.0)))
     return s
 
 
@@ -170,6 +174,15 @@ def rotate_about(xa, xb, c: float, s: float, x) -> np.ndarray:
     return out
 
 
+def rigid_candidate(xyz, cand: int, shift: float, angle: float) -> np.ndarray:
+    """Candidate `cand` (0..12) of a rigid move applied to the atoms xyz[N][3]."""
+    lib = _load()
+    X = np.ascontiguousarray(xyz, np.float64)
+    out = np.empty_like(X)
+    lib.or_rigid_candidate(len(X), _ptr(X), int(cand), float(shift), float(angle), _ptr(out))
+    return out
+
+
 def pose_energy(pocket, xyz, q, type_):
     lib = _load()
     op = _as_oracle_pocket(pocket)
@@ -201,13 +214,15 @@ def score_poses(pocket, atom_off, xyz, q, type_):
 
 
 # ------------------------------------------------------------------ docking
-def dock(pocket, batch, params, *, replay=None, trace=False, poses=False, nthreads=None) -> dict:
+def dock(pocket, batch, params, *, replay=None, replay_rigid=None, trace=False, poses=False, nthreads=None) -> dict:
     """Dock every ligand of a CSR batch (attributes atom_off, x, y, z, q, type,
     parent, rot_off, rot_child, uid).  Returns a dict of numpy arrays:
       best_E[L], best_r[L], status[L], restart_E[L,S], restart_Eabs[L,S],
       choice / own (flat, S*P*rot_off[l] per ligand), best_pose (flat xyz, 3*atom_off),
       and with trace=True trace_s / trace_d2 (flat, A*S*P*rot_off[l]),
-      with poses=True poses (flat, 3*S*atom_off[l])."""
+      with poses=True poses (flat, 3*S*atom_off[l]); with rigid moves
+      choice_rigid / own_rigid (flat, S*P*rigid_steps*l) and with trace=True
+      trace_G (13 per rigid decision)."""
     lib = _load()
     op = _as_oracle_pocket(pocket)
     pr = _params(params)
@@ -234,6 +249,16 @@ def dock(pocket, batch, params, *, replay=None, trace=False, poses=False, nthrea
     if ranking:
         out["rank"] = np.zeros(max(2 * S * L, 1), np.int32)
         out["geo"] = np.zeros(max(S * L, 1))
+    nrig = S * PS * pr.rigid_steps * L
+    if pr.rigid_steps > 0:
+        out["choice_rigid"] = np.zeros(max(nrig, 1), np.uint8)
+        out["own_rigid"] = np.zeros(max(nrig, 1), np.uint8)
+        if trace:
+            out["trace_G"] = np.zeros(max(13 * nrig, 1))
+    rep_rigid = None
+    if replay_rigid is not None:
+        rep_rigid = np.ascontiguousarray(replay_rigid, np.uint8)
+        assert rep_rigid.size >= nrig
     rep = None
     if replay is not None:
         rep = np.ascontiguousarray(replay, np.uint8)
@@ -245,7 +270,8 @@ def dock(pocket, batch, params, *, replay=None, trace=False, poses=False, nthrea
                       _ptr(out["restart_E"]), _ptr(out["restart_Eabs"]), _ptr(out["choice"]), _ptr(out["own"]),
                       _ptr(out.get("trace_s")), _ptr(out.get("trace_d2")), _ptr(out.get("poses")),
                       _ptr(out["best_pose"]), _ptr(out["best_r"]), _ptr(out["best_E"]), _ptr(out["status"]),
-                      _ptr(out.get("rank")), _ptr(out.get("geo")), int(nthreads))
+                      _ptr(out.get("rank")), _ptr(out.get("geo")), _ptr(rep_rigid), _ptr(out.get("choice_rigid")),
+                      _ptr(out.get("own_rigid")), _ptr(out.get("trace_G")), int(nthreads))
     out["restart_E"] = out["restart_E"].reshape(L, S)
     out["restart_Eabs"] = out["restart_Eabs"].reshape(L, S)
     if ranking:

@@ -31,6 +31,12 @@
  *           at least three bonds apart is at least d_clash apart.  The chosen
  *           step is the admissible one with the largest score, the lowest step
  *           on ties; it is applied when it is not 0.
+ *   rigid   (optional) After each torsion pass, rigid_steps greedy rigid moves of
+ *           the whole ligand: candidate 0 stays; 1..6 translate by +d, -d along
+ *           x, y, z (d = rigid_shift); 7..12 turn by +a, -a (a = 2 pi / A) about
+ *           the x, y, z axes through the ligand's centroid (right-hand rule).
+ *           The candidate with the largest geometric score G = sum over all
+ *           atoms of the overlap grid wins, the lowest candidate on ties.
  *   score   E = sum_i [ w_type(i) Vgrid(xhat_i) + q_i Egrid(xhat_i) + k_out |x_i - xhat_i| ]
  *           with xhat the position clamped to the grid box.
  *   best    The restart with the lowest E wins, the lowest restart on ties.
@@ -77,6 +83,8 @@ typedef struct {
     double d_clash;
     double cluster_rmsd; /* 0: no clustering */
     int32_t rescore_top; /* K; 0 or >= restarts: all poses */
+    int32_t rigid_steps; /* rigid greedy moves after each torsion pass (0: none) */
+    double rigid_shift;  /* translation step of a rigid move (A) */
 } or_params;
 
 /* ------------------------------------------------------------------ Philox4x32-10
@@ -304,6 +312,39 @@ void or_rank_poses(const or_pocket *P, int32_t S, int32_t N, const double *poses
     free(leads);
 }
 
+/* ------------------------------------------------------------------ rigid moves */
+#define OR_RIGID_CANDIDATES 13
+
+/* Candidate `cand` of a rigid move (see "rigid" above) applied to N atoms. */
+void or_rigid_candidate(int32_t N, const double *X, int32_t cand, double shift, double angle, double *out) {
+    double c[3] = {0.0, 0.0, 0.0};
+    for (int i = 0; i < N; i++)
+        for (int d = 0; d < 3; d++) c[d] += X[3 * i + d];
+    for (int d = 0; d < 3; d++) c[d] /= N;
+    for (int i = 0; i < N; i++) {
+        const double *x = X + 3 * i;
+        double *o = out + 3 * i;
+        o[0] = x[0]; o[1] = x[1]; o[2] = x[2];
+        if (cand >= 1 && cand <= 6) {
+            const int ax = (cand - 1) / 2;
+            o[ax] += (cand % 2 == 1) ? shift : -shift;
+        } else if (cand >= 7 && cand <= 12) {
+            const int ax = (cand - 7) / 2;
+            const double th = (cand % 2 == 1) ? angle : -angle, cs = cos(th), sn = sin(th);
+            const int j = (ax + 1) % 3, k = (ax + 2) % 3; /* (x: y, z), (y: z, x), (z: x, y) */
+            const double vj = x[j] - c[j], vk = x[k] - c[k];
+            o[j] = c[j] + cs * vj - sn * vk;
+            o[k] = c[k] + sn * vj + cs * vk;
+        }
+    }
+}
+
+static double or_geometric_score(const or_pocket *P, int32_t N, const double *X) {
+    double g = 0.0;
+    for (int i = 0; i < N; i++) g += or_trilinear(P, P->phi_o, X + 3 * i);
+    return g;
+}
+
 /* ------------------------------------------------------------------ docking */
 /* Outputs (any may be NULL except restart_E):
  *   restart_E[S], restart_Eabs[S]      score and sum of |per-atom terms| per restart
@@ -315,6 +356,10 @@ void or_rank_poses(const or_pocket *P, int32_t S, int32_t N, const double *poses
  *   best_pose[N][3]                    final pose of the best restart
  *   rank_out[2S] (with ranking)        ranked restarts, then each restart's leader
  *   geo_out[S] (with ranking)          geometric score of every restart
+ *   choice_rigid / own_rigid[S][P][rigid_steps], trace_G[...][13]: rigid
+ *                                      moves applied / chosen by the oracle,
+ *                                      and every candidate's geometric score
+ * replay_rigid (optional): apply these rigid moves instead.
  * replay[S][P][R] (optional): apply these steps instead of the oracle's own,
  * still recording what the oracle would have chosen. */
 int or_dock_ligand(const or_pocket *P, const or_params *prm, int32_t N, const float *x, const float *y,
@@ -322,7 +367,8 @@ int or_dock_ligand(const or_pocket *P, const or_params *prm, int32_t N, const fl
                    const int16_t *rot_child, uint64_t uid, const uint8_t *replay, double *restart_E,
                    double *restart_Eabs, uint8_t *choice, uint8_t *own, double *trace_s, double *trace_d2,
                    double *poses, double *best_pose, int32_t *best_r, double *best_E, int32_t *rank_out,
-                   double *geo_out) {
+                   double *geo_out, const uint8_t *replay_rigid, uint8_t *choice_rigid, uint8_t *own_rigid,
+                   double *trace_G) {
     int32_t end[OR_MAXN];
     if (or_validate(N, parent, type, R, rot_child, end) != 0) return -1;
     const int S = prm->restarts, PS = prm->passes, A = prm->angle_steps;
@@ -388,6 +434,26 @@ int or_dock_ligand(const or_pocket *P, const or_params *prm, int32_t N, const fl
                     }
                 }
             }
+            /* rigid greedy moves of the whole ligand */
+            for (int j = 0; j < prm->rigid_steps; j++) {
+                const size_t dec = ((size_t)r * PS + ps) * prm->rigid_steps + j;
+                int own_c = 0;
+                double own_g = -INFINITY;
+                for (int cand = 0; cand < OR_RIGID_CANDIDATES; cand++) {
+                    or_rigid_candidate(N, &X[0][0], cand, prm->rigid_shift, 2.0 * M_PI / A, &T[0][0]);
+                    double g = or_geometric_score(P, N, &T[0][0]);
+                    if (trace_G) trace_G[dec * OR_RIGID_CANDIDATES + cand] = g;
+                    if (g > own_g) { own_g = g; own_c = cand; }
+                }
+                int ch = replay_rigid ? replay_rigid[dec] : own_c;
+                if (ch < 0 || ch >= OR_RIGID_CANDIDATES) return -2;
+                if (own_rigid) own_rigid[dec] = (uint8_t)own_c;
+                if (choice_rigid) choice_rigid[dec] = (uint8_t)ch;
+                if (ch != 0) {
+                    or_rigid_candidate(N, &X[0][0], ch, prm->rigid_shift, 2.0 * M_PI / A, &T[0][0]);
+                    memcpy(X, T, sizeof(double) * 3 * N);
+                }
+            }
         }
         double eabs;
         double E = or_pose_energy(P, N, &X[0][0], q, type, &eabs);
@@ -425,13 +491,15 @@ int or_dock_ligand(const or_pocket *P, const or_params *prm, int32_t N, const fl
 /* Batch in CSR layout (see the generator for the layout).  Per-ligand output
  * offsets: restart arrays l*S; decisions S*P*rot_off[l]; traces A*S*P*rot_off[l];
  * poses 3*S*atom_off[l]; best poses 3*atom_off[l]; rankings 2*S*l; geometric
- * scores S*l.  status[l] = 0 or -1. */
+ * scores S*l; rigid decisions S*P*rigid_steps*l (traces 13 times that).
+ * status[l] = 0 or -1. */
 int or_dock_batch(const or_pocket *P, const or_params *prm, int32_t L, const int32_t *atom_off, const float *x,
                   const float *y, const float *z, const float *q, const uint8_t *type, const int16_t *parent,
                   const int32_t *rot_off, const int16_t *rot_child, const uint64_t *uid, const uint8_t *replay,
                   double *restart_E, double *restart_Eabs, uint8_t *choice, uint8_t *own, double *trace_s,
                   double *trace_d2, double *poses, double *best_pose, int32_t *best_r, double *best_E,
-                  int32_t *status, int32_t *rank_out, double *geo_out, int32_t nthreads) {
+                  int32_t *status, int32_t *rank_out, double *geo_out, const uint8_t *replay_rigid,
+                  uint8_t *choice_rigid, uint8_t *own_rigid, double *trace_G, int32_t nthreads) {
     const int S = prm->restarts, PS = prm->passes, A = prm->angle_steps;
     int bad = 0;
 #pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads > 0 ? nthreads : 1) reduction(+ : bad)
@@ -439,13 +507,16 @@ int or_dock_batch(const or_pocket *P, const or_params *prm, int32_t L, const int
         const int a0 = atom_off[l], N = atom_off[l + 1] - a0;
         const int r0 = rot_off[l], Rl = rot_off[l + 1] - r0;
         const size_t d0 = (size_t)S * PS * r0;
+        const size_t rd0 = (size_t)S * PS * prm->rigid_steps * l;
         int rc = or_dock_ligand(
             P, prm, N, x + a0, y + a0, z + a0, q + a0, type + a0, parent + a0, Rl, rot_child + r0, uid[l],
             replay ? replay + d0 : NULL, restart_E + (size_t)l * S, restart_Eabs ? restart_Eabs + (size_t)l * S : NULL,
             choice ? choice + d0 : NULL, own ? own + d0 : NULL, trace_s ? trace_s + d0 * A : NULL,
             trace_d2 ? trace_d2 + d0 * A : NULL, poses ? poses + (size_t)3 * S * a0 : NULL,
             best_pose ? best_pose + (size_t)3 * a0 : NULL, best_r + l, best_E + l,
-            rank_out ? rank_out + (size_t)2 * S * l : NULL, geo_out ? geo_out + (size_t)S * l : NULL);
+            rank_out ? rank_out + (size_t)2 * S * l : NULL, geo_out ? geo_out + (size_t)S * l : NULL,
+            replay_rigid ? replay_rigid + rd0 : NULL, choice_rigid ? choice_rigid + rd0 : NULL,
+            own_rigid ? own_rigid + rd0 : NULL, trace_G ? trace_G + rd0 * OR_RIGID_CANDIDATES : NULL);
         status[l] = rc;
         if (rc != 0) bad++;
     }

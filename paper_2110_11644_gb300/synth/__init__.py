@@ -265,6 +265,8 @@ class DockParams:
     d_clash: float = 2.0
     cluster_rmsd: float = 0.0   # 0: no clustering
     rescore_top: int = 0        # 0: rescore every pose
+    rigid_steps: int = 0        # rigid greedy moves after each torsion pass (0: none)
+    rigid_shift: float = 0.375  # translation step of a rigid move (A)
 
 
 CONFIG_SEEDS = {1: 0, 2: 2, 3: 3, 4: 4, 5: 5}
