@@ -168,7 +168,17 @@ typedef struct {
  *                every restart's final pose in device scratch (12 bytes per
  *                atom and restart for each ligand docked at once) and needs
  *                shared memory growing as restarts^2 / 16 bytes (68 KB at
- *                1,024 restarts), which can lower the kernels' occupancy. */
+ *                1,024 restarts), which can lower the kernels' occupancy.
+ *   rigid_steps, rigid_shift  rigid greedy refinement (the paper's greedy
+ *                optimisation read broadly, Sec. 3.1), off when rigid_steps =
+ *                0: after each torsion pass, rigid_steps (0..LG_MAX_RIGID_STEPS)
+ *                moves of the whole ligand, each the best of 13 candidates by
+ *                the total overlap of all atoms (lowest candidate on ties):
+ *                0 stay; 1..6 shift by +rigid_shift, -rigid_shift (A, >= 0)
+ *                along x, y, z; 7..12 turn by +10, -10 degrees about the x, y, z
+ *                axes through the ligand's centroid.  Candidate sums are FP64
+ *                over FP32 lookups. */
+#define LG_MAX_RIGID_STEPS 16
 typedef struct {
     int32_t restarts;
     int32_t passes;
@@ -181,6 +191,8 @@ typedef struct {
     int32_t max_rot;
     float cluster_rmsd;
     int32_t rescore_top;
+    int32_t rigid_steps;
+    float rigid_shift;
 } lg_dock_params;
 
 /* Caller-owned outputs (all with the location given by `mem`).
@@ -195,7 +207,10 @@ typedef struct {
  *                      restarts*passes*rot_off[l] + (r*passes + pass)*R_l + k
  *   rank, leader, restart_geo  optional, with pose ranking on: the ranked
  *                      restarts (l*restarts + position), each restart's cluster
- *                      leader and geometric score (l*restarts + r) */
+ *                      leader and geometric score (l*restarts + r)
+ *   restart_rigid      optional, with rigid refinement on: the candidate taken
+ *                      at every rigid move of every restart,
+ *                      ((l*restarts + r)*passes + pass)*rigid_steps + j */
 typedef struct {
     int32_t mem;
     double *score;
@@ -208,6 +223,7 @@ typedef struct {
     int32_t *rank;
     int32_t *leader;
     double *restart_geo;
+    uint8_t *restart_rigid;
 } lg_dock_result;
 
 /* Dock and score a batch of ligands against one pocket (paper Sec. 3.1).

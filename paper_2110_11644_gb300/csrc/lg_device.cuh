@@ -262,6 +262,45 @@ __device__ __forceinline__ float3 rotate_point(float x, float y, float z, float 
                        fmaf(e2z, s, fmaf(e1z, c, fmaf(w, u.z, xbz))));
 }
 
+// Rigid moves of the whole ligand: candidate 0 stays; 1..6 shift by +d, -d
+// along x, y, z; 7..12 turn by +a, -a about the x, y, z axes through the
+// centroid (cx, cy, cz) (right-hand rule; (ca, sa) = (cos a, sin a)).
+constexpr int kRigidCandidates = 13;
+
+__device__ __forceinline__ float3 rigid_candidate(int cand, float x, float y, float z, float cx, float cy, float cz,
+                                                  float d, float ca, float sa) {
+    float3 r = make_float3(x, y, z);
+    if (cand >= 1 && cand <= 6) {
+        const float dd = (cand & 1) ? d : -d;
+        if (cand <= 2) r.x += dd;
+        else if (cand <= 4) r.y += dd;
+        else r.z += dd;
+    } else if (cand >= 7) {
+        const float s = (cand & 1) ? sa : -sa;
+        if (cand <= 8) {         // about x: (y, z)
+            const float vj = y - cy, vk = z - cz;
+            r.y = cy + fmaf(ca, vj, -s * vk);
+            r.z = cz + fmaf(s, vj, ca * vk);
+        } else if (cand <= 10) { // about y: (z, x)
+            const float vj = z - cz, vk = x - cx;
+            r.z = cz + fmaf(ca, vj, -s * vk);
+            r.x = cx + fmaf(s, vj, ca * vk);
+        } else {                 // about z: (x, y)
+            const float vj = x - cx, vk = y - cy;
+            r.x = cx + fmaf(ca, vj, -s * vk);
+            r.y = cy + fmaf(s, vj, ca * vk);
+        }
+    }
+    return r;
+}
+
+// A direction under candidate `cand` (turns only; shifts leave it unchanged).
+__device__ __forceinline__ float4 rigid_candidate_vec(int cand, float4 v, float ca, float sa) {
+    if (cand < 7) return v;
+    const float3 r = rigid_candidate(cand, v.x, v.y, v.z, 0.0f, 0.0f, 0.0f, 0.0f, ca, sa);
+    return make_float4(r.x, r.y, r.z, v.w);
+}
+
 // Rotate a vector about the unit axis u by (c, s) (Rodrigues).
 __device__ __forceinline__ float4 rotate_vec(float4 v, float3 u, float c, float s) {
     const float uv = fmaf(u.x, v.x, fmaf(u.y, v.y, u.z * v.z));

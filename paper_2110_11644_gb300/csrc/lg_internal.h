@@ -57,6 +57,7 @@ struct OutDev {
     int32_t *rank;
     int32_t *leader;
     double *restart_geo;
+    uint8_t *restart_rigid;
 };
 
 // Shared-memory layout of one docking CTA: a part shared by the CTA (the
@@ -172,6 +173,8 @@ struct DockArgs {
     uint32_t seed_lo, seed_hi;
     float dc2g;                // d_clash^2 in grid units
     int nmax_lim, rmax_lim;    // per-ligand maxima (declared and within the layout)
+    int rigid_steps;           // rigid greedy moves after each torsion pass
+    float rigid_shift_g;       // their translation step in grid units
     int ranking;               // pose ranking on
     float thr2g;               // cluster RMSD^2 in grid units
     int rescore_top;           // K (0 = all)
@@ -229,8 +232,8 @@ cudaError_t launch_diag_philox(int n, const uint32_t *ctr, const uint32_t *key, 
                                cudaStream_t s);
 cudaError_t launch_dock_multi(const DockArgs &a, const MultiDev &m, int grid, int smem, cudaStream_t s);
 cudaError_t launch_flatten(const FlatArgs &f, int L, cudaStream_t s);
-cudaError_t dock_kernel_attributes(int W, int smem, int *ctas_per_sm, bool ranking);
-cudaError_t multi_kernel_attributes(int W, int smem, int *ctas_per_sm, bool ranking);
+cudaError_t dock_kernel_attributes(int W, int smem, int *ctas_per_sm, bool ranking, bool rigid);
+cudaError_t multi_kernel_attributes(int W, int smem, int *ctas_per_sm, bool ranking, bool rigid);
 cudaError_t plain_kernel_attributes(int smem);
 
 }  // namespace lg

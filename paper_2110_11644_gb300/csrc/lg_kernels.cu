@@ -470,6 +470,66 @@ __device__ int sweep_bond_plain(const DockArgs &A, const GridK &G, const CtaView
     return t;
 }
 
+// Rigid greedy moves of the warp's restart (plain form): lane c scores
+// candidate c (same arithmetic and order as the restart-tiled form, so both
+// forms choose and move identically).
+__device__ __forceinline__ void rigid_moves_plain(const DockArgs &A, const GridK &Go, const OutDev &O,
+                                                  const WarpView &wv, int l, int r, int ps, int N, int R, int lane) {
+    const float c0 = 0.5f * Go.gmax, dg = A.rigid_shift_g, ca = c_cos[1], sa = c_sin[1];
+    for (int j = 0; j < A.rigid_steps; ++j) {
+        float sx = 0.0f, sy = 0.0f, sz = 0.0f;
+        if (lane < 4)
+            for (int i = lane; i < N; i += 4) {
+                sx += wv.Xx[i];
+                sy += wv.Xy[i];
+                sz += wv.Xz[i];
+            }
+        sx += __shfl_xor_sync(LG_FULL, sx, 1);
+        sy += __shfl_xor_sync(LG_FULL, sy, 1);
+        sz += __shfl_xor_sync(LG_FULL, sz, 1);
+        sx += __shfl_xor_sync(LG_FULL, sx, 2);
+        sy += __shfl_xor_sync(LG_FULL, sy, 2);
+        sz += __shfl_xor_sync(LG_FULL, sz, 2);
+        sx = __shfl_sync(LG_FULL, sx, 0);
+        sy = __shfl_sync(LG_FULL, sy, 0);
+        sz = __shfl_sync(LG_FULL, sz, 0);
+        const float cx = sx / (float)N, cy = sy / (float)N, cz = sz / (float)N;
+        double bG = -INFINITY;
+        int bC = kRigidCandidates;
+        if (lane < kRigidCandidates) {
+            double G = 0.0;
+            for (int i = 0; i < N; ++i) {
+                const float3 y = rigid_candidate(lane, wv.Xx[i], wv.Xy[i], wv.Xz[i], cx, cy, cz, dg, ca, sa);
+                G += (double)lookup_clamped(Go, y.x + c0, y.y + c0, y.z + c0);
+            }
+            bG = G;
+            bC = lane;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double oG = __shfl_xor_sync(LG_FULL, bG, o);
+            const int oC = __shfl_xor_sync(LG_FULL, bC, o);
+            if (oG > bG || (oG == bG && oC < bC)) {
+                bG = oG;
+                bC = oC;
+            }
+        }
+        if (lane == 0 && O.restart_rigid)
+            O.restart_rigid[(((size_t)l * A.S + r) * A.P + ps) * A.rigid_steps + j] = (uint8_t)bC;
+        __syncwarp();
+        if (bC != 0) {
+            for (int i = lane; i < N; i += 32) {
+                const float3 y = rigid_candidate(bC, wv.Xx[i], wv.Xy[i], wv.Xz[i], cx, cy, cz, dg, ca, sa);
+                wv.Xx[i] = y.x;
+                wv.Xy[i] = y.y;
+                wv.Xz[i] = y.z;
+            }
+            for (int k = lane; k < R; k += 32) wv.axis[k] = rigid_candidate_vec(bC, wv.axis[k], ca, sa);
+        }
+        __syncwarp();
+    }
+}
+
 __global__ void __launch_bounds__(1024) k_dock_plain(const __grid_constant__ DockArgs A, int l, int slot) {
     extern __shared__ __align__(16) char sm[];
     if (A.out.status[l] != LG_OK) return;  // rejected by the preparation kernel
@@ -509,11 +569,13 @@ __global__ void __launch_bounds__(1024) k_dock_plain(const __grid_constant__ Doc
             wv.axis[k] = make_float4(w.x, w.y, w.z, 0.0f);
         }
         __syncwarp();
-        for (int ps = 0; ps < P; ++ps)
+        for (int ps = 0; ps < P; ++ps) {
             for (int k = 0; k < R; ++k) {
                 const int t = sweep_bond_plain(A, Go, cv, wv, N, R, k, lane, cl, sl, ct, st);
                 if (lane == 0) wv.tcur[ps * R + k] = (uint8_t)t;
             }
+            if (A.rigid_steps > 0) rigid_moves_plain(A, Go, A.out, wv, l, r, ps, N, R, lane);
+        }
         // pose score: FP32 per-atom terms; FP64 sums s_g over atoms i = g (mod 4)
         // in order, combined as (s0 + s1) + (s2 + s3)
         for (int i = lane; i < N; i += 32) {
@@ -765,9 +827,72 @@ __device__ __forceinline__ int sweep_bond_rt(const DockArgs &A, const GridK &G, 
     return t;
 }
 
-// kRank: pose ranking on (a separate instantiation, so the plain best-restart
-// form carries none of its code)
-template <bool kRank>
+// Rigid greedy moves of the tile's restarts after torsion pass ps: the 4
+// lanes of a restart share its 13 candidates (lane g: g, g+4, g+8, g+12); a
+// candidate's score is the FP64 sum, in atom order, of the FP32 overlap
+// lookups of all atoms at their moved positions; the best (highest score,
+// lowest candidate) moves the atoms and turns the bond axes.
+__device__ __forceinline__ void rigid_moves_rt(const DockArgs &A, const GridK &Go, const OutDev &O, const RtView &v,
+                                               int l, int r, int ps, int N, int R, int rs, int g, bool valid) {
+    const float c0 = 0.5f * Go.gmax, dg = A.rigid_shift_g, ca = c_cos[1], sa = c_sin[1];
+    for (int j = 0; j < A.rigid_steps; ++j) {
+        float sx = 0.0f, sy = 0.0f, sz = 0.0f;  // centroid: sums over atoms i = g (mod 4), (s0 + s1) + (s2 + s3)
+        for (int i = g; i < N; i += kLanesPerRestart) {
+            sx += v.Xx[i * kTile + rs];
+            sy += v.Xy[i * kTile + rs];
+            sz += v.Xz[i * kTile + rs];
+        }
+        sx += __shfl_xor_sync(LG_FULL, sx, 1);
+        sy += __shfl_xor_sync(LG_FULL, sy, 1);
+        sz += __shfl_xor_sync(LG_FULL, sz, 1);
+        sx += __shfl_xor_sync(LG_FULL, sx, 2);
+        sy += __shfl_xor_sync(LG_FULL, sy, 2);
+        sz += __shfl_xor_sync(LG_FULL, sz, 2);
+        const float cx = sx / (float)N, cy = sy / (float)N, cz = sz / (float)N;
+        double bG = -INFINITY;
+        int bC = kRigidCandidates;
+        for (int cand = g; cand < kRigidCandidates; cand += kLanesPerRestart) {
+            double G = 0.0;
+            for (int i = 0; i < N; ++i) {
+                const float3 y = rigid_candidate(cand, v.Xx[i * kTile + rs], v.Xy[i * kTile + rs], v.Xz[i * kTile + rs],
+                                                 cx, cy, cz, dg, ca, sa);
+                G += (double)lookup_clamped(Go, y.x + c0, y.y + c0, y.z + c0);
+            }
+            if (G > bG) {  // ascending candidates: ties keep the lower one
+                bG = G;
+                bC = cand;
+            }
+        }
+#pragma unroll
+        for (int o = 1; o < kLanesPerRestart; o <<= 1) {
+            const double oG = __shfl_xor_sync(LG_FULL, bG, o);
+            const int oC = __shfl_xor_sync(LG_FULL, bC, o);
+            if (oG > bG || (oG == bG && oC < bC)) {
+                bG = oG;
+                bC = oC;
+            }
+        }
+        if (valid && g == 0 && O.restart_rigid)
+            O.restart_rigid[(((size_t)l * A.S + r) * A.P + ps) * A.rigid_steps + j] = (uint8_t)bC;
+        __syncwarp();
+        if (bC != 0) {
+            for (int i = g; i < N; i += kLanesPerRestart) {
+                const float3 y = rigid_candidate(bC, v.Xx[i * kTile + rs], v.Xy[i * kTile + rs], v.Xz[i * kTile + rs],
+                                                 cx, cy, cz, dg, ca, sa);
+                v.Xx[i * kTile + rs] = y.x;
+                v.Xy[i * kTile + rs] = y.y;
+                v.Xz[i * kTile + rs] = y.z;
+            }
+            for (int k = g; k < R; k += kLanesPerRestart)
+                v.axis[k * kTile + rs] = rigid_candidate_vec(bC, v.axis[k * kTile + rs], ca, sa);
+        }
+        __syncwarp();
+    }
+}
+
+// kRank: pose ranking on; kRigid: rigid refinement on (separate
+// instantiations, so the plain best-restart form carries none of their code)
+template <bool kRank, bool kRigid>
 __device__ __forceinline__ void dock_ligand_rt(const DockArgs &A, const PocketDev &Pk, const OutDev &O, int l, char *sm) {
     if (O.status[l] != LG_OK) return;  // rejected by the preparation kernel (uniform)
     const Layout &Ly = A.ly;
@@ -814,11 +939,13 @@ __device__ __forceinline__ void dock_ligand_rt(const DockArgs &A, const PocketDe
         }
         __syncwarp();
         // 2. greedy torsion sweep
-        for (int ps = 0; ps < P; ++ps)
+        for (int ps = 0; ps < P; ++ps) {
             for (int k = 0; k < R; ++k) {
                 const int t = sweep_bond_rt(A, Go, cv, v, N, R, k, rs, g, valid, cs, sn);
                 if (g == 0) v.tcur[(ps * R + k) * kTile + rs] = (uint8_t)t;
             }
+            if (kRigid) rigid_moves_rt(A, Go, O, v, l, r, ps, N, R, rs, g, valid);
+        }
         __syncwarp();
         // 3. pose score: FP32 per-atom terms; FP64 sums s_g over atoms i = g
         //    (mod 4) in order, combined as (s0 + s1) + (s2 + s3)
@@ -896,7 +1023,7 @@ __device__ __forceinline__ void dock_ligand_rt(const DockArgs &A, const PocketDe
 #ifndef LG_RT_MIN_BLOCKS
 #define LG_RT_MIN_BLOCKS 4
 #endif
-template <bool kRank>
+template <bool kRank, bool kRigid>
 __global__ void __launch_bounds__(128, LG_RT_MIN_BLOCKS) k_dock_batched(const __grid_constant__ DockArgs A) {
     extern __shared__ __align__(16) char sm[];
     __shared__ int s_item;
@@ -906,7 +1033,7 @@ __global__ void __launch_bounds__(128, LG_RT_MIN_BLOCKS) k_dock_batched(const __
         const int item = s_item;
         __syncthreads();
         if (item >= A.batch.L) break;
-        dock_ligand_rt<kRank>(A, A.pocket, A.out, A.order ? A.order[item] : item, sm);
+        dock_ligand_rt<kRank, kRigid>(A, A.pocket, A.out, A.order ? A.order[item] : item, sm);
     }
 }
 
@@ -915,7 +1042,7 @@ __global__ void __launch_bounds__(128, LG_RT_MIN_BLOCKS) k_dock_batched(const __
 // The preparation kernel validated every ligand once and wrote its status to
 // the first pocket's outputs; the other pockets' outputs get the same status
 // here.
-template <bool kRank>
+template <bool kRank, bool kRigid>
 __global__ void __launch_bounds__(128, LG_RT_MIN_BLOCKS) k_dock_multi(const __grid_constant__ DockArgs A,
                                                                        const __grid_constant__ MultiDev M) {
     extern __shared__ __align__(16) char sm[];
@@ -935,7 +1062,7 @@ __global__ void __launch_bounds__(128, LG_RT_MIN_BLOCKS) k_dock_multi(const __gr
             }
             __syncthreads();
         }
-        dock_ligand_rt<kRank>(A, M.pk[p], O, l, sm);
+        dock_ligand_rt<kRank, kRigid>(A, M.pk[p], O, l, sm);
         __syncthreads();
     };
     for (;;) {
@@ -1283,14 +1410,20 @@ static cudaError_t kernel_attributes(K kernel, int W, int smem, int *ctas_per_sm
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, kernel, 32 * W, smem);
 }
 
-cudaError_t dock_kernel_attributes(int W, int smem, int *ctas_per_sm, bool ranking) {
-    return ranking ? kernel_attributes(k_dock_batched<true>, W, smem, ctas_per_sm)
-                   : kernel_attributes(k_dock_batched<false>, W, smem, ctas_per_sm);
+cudaError_t dock_kernel_attributes(int W, int smem, int *ctas_per_sm, bool ranking, bool rigid) {
+    if (ranking)
+        return rigid ? kernel_attributes(k_dock_batched<true, true>, W, smem, ctas_per_sm)
+                     : kernel_attributes(k_dock_batched<true, false>, W, smem, ctas_per_sm);
+    return rigid ? kernel_attributes(k_dock_batched<false, true>, W, smem, ctas_per_sm)
+                 : kernel_attributes(k_dock_batched<false, false>, W, smem, ctas_per_sm);
 }
 
-cudaError_t multi_kernel_attributes(int W, int smem, int *ctas_per_sm, bool ranking) {
-    return ranking ? kernel_attributes(k_dock_multi<true>, W, smem, ctas_per_sm)
-                   : kernel_attributes(k_dock_multi<false>, W, smem, ctas_per_sm);
+cudaError_t multi_kernel_attributes(int W, int smem, int *ctas_per_sm, bool ranking, bool rigid) {
+    if (ranking)
+        return rigid ? kernel_attributes(k_dock_multi<true, true>, W, smem, ctas_per_sm)
+                     : kernel_attributes(k_dock_multi<true, false>, W, smem, ctas_per_sm);
+    return rigid ? kernel_attributes(k_dock_multi<false, true>, W, smem, ctas_per_sm)
+                 : kernel_attributes(k_dock_multi<false, false>, W, smem, ctas_per_sm);
 }
 
 cudaError_t plain_kernel_attributes(int smem) {
@@ -1319,18 +1452,28 @@ cudaError_t launch_dock_plain(const DockArgs &a, int ligand, int slot, cudaStrea
 }
 
 cudaError_t launch_dock_batched(const DockArgs &a, int grid, int smem, cudaStream_t s) {
-    if (a.ranking)
-        k_dock_batched<true><<<grid, 32 * a.ly.W, smem, s>>>(a);
+    const bool rigid = a.rigid_steps > 0;
+    if (a.ranking && rigid)
+        k_dock_batched<true, true><<<grid, 32 * a.ly.W, smem, s>>>(a);
+    else if (a.ranking)
+        k_dock_batched<true, false><<<grid, 32 * a.ly.W, smem, s>>>(a);
+    else if (rigid)
+        k_dock_batched<false, true><<<grid, 32 * a.ly.W, smem, s>>>(a);
     else
-        k_dock_batched<false><<<grid, 32 * a.ly.W, smem, s>>>(a);
+        k_dock_batched<false, false><<<grid, 32 * a.ly.W, smem, s>>>(a);
     return cudaGetLastError();
 }
 
 cudaError_t launch_dock_multi(const DockArgs &a, const MultiDev &m, int grid, int smem, cudaStream_t s) {
-    if (a.ranking)
-        k_dock_multi<true><<<grid, 32 * a.ly.W, smem, s>>>(a, m);
+    const bool rigid = a.rigid_steps > 0;
+    if (a.ranking && rigid)
+        k_dock_multi<true, true><<<grid, 32 * a.ly.W, smem, s>>>(a, m);
+    else if (a.ranking)
+        k_dock_multi<true, false><<<grid, 32 * a.ly.W, smem, s>>>(a, m);
+    else if (rigid)
+        k_dock_multi<false, true><<<grid, 32 * a.ly.W, smem, s>>>(a, m);
     else
-        k_dock_multi<false><<<grid, 32 * a.ly.W, smem, s>>>(a, m);
+        k_dock_multi<false, false><<<grid, 32 * a.ly.W, smem, s>>>(a, m);
     return cudaGetLastError();
 }
 

@@ -51,7 +51,7 @@ extern "C" int lg_dock_multi(lg_ctx *c, const int32_t *pocket_ids, int32_t n_poc
     if ((int)c->multi_out.size() < n_pockets) c->multi_out.resize(n_pockets);
     std::vector<OutDev> od(n_pockets);
     for (int k = 0; k < n_pockets; k++)
-        if ((rc = resolve_out(c, c->multi_out[k], b, &outs[k], S, P, s, &A, &R, &od[k]))) return rc;
+        if ((rc = resolve_out(c, c->multi_out[k], b, &outs[k], S, P, p->rigid_steps, s, &A, &R, &od[k]))) return rc;
     MultiDev m;
     memset(&m, 0, sizeof(m));
     m.np = n_pockets;
@@ -65,7 +65,7 @@ extern "C" int lg_dock_multi(lg_ctx *c, const int32_t *pocket_ids, int32_t n_poc
     if ((rc = dock_device(c, pk[0], bd, od[0], p, nmax, rmax, c->scratch, s, &c->stats, tev, &m))) return rc;
     if (omem == LG_MEM_HOST)
         for (int k = 0; k < n_pockets; k++)
-            if ((rc = fetch_out(od[k], &outs[k], L, S, P, A, R, s))) return rc;
+            if ((rc = fetch_out(od[k], &outs[k], L, S, P, A, R, p->rigid_steps, s))) return rc;
     if (b->mem == LG_MEM_HOST || omem == LG_MEM_HOST) {
         e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return fail(LG_ECUDA, std::string("docking: ") + cudaGetErrorString(e));

@@ -71,6 +71,9 @@ int check_params(const lg_dock_params *p) {
     if (!(p->cluster_rmsd >= 0.0f) || !std::isfinite(p->cluster_rmsd))
         return fail(LG_EINVAL, "cluster_rmsd must be finite and >= 0");
     if (p->rescore_top < 0) return fail(LG_EINVAL, "rescore_top must be >= 0");
+    if (p->rigid_steps < 0 || p->rigid_steps > LG_MAX_RIGID_STEPS) return fail(LG_EINVAL, "rigid_steps out of range");
+    if (!(p->rigid_shift >= 0.0f) || !std::isfinite(p->rigid_shift))
+        return fail(LG_EINVAL, "rigid_shift must be finite and >= 0");
     return LG_OK;
 }
 
@@ -135,7 +138,7 @@ int stage_batch(DevBuf &buf, const lg_ligand_batch *b, int64_t A, int64_t R, Bat
 }
 
 // Device output buffers for a host result; fills `d`.
-int stage_out(DevBuf &buf, const lg_dock_result *o, int L, int S, int P, int64_t A, int64_t R, OutDev *d) {
+int stage_out(DevBuf &buf, const lg_dock_result *o, int L, int S, int P, int64_t A, int64_t R, int Rs, OutDev *d) {
     Carve c;
     const size_t o_s = c.take(8 * (size_t)L), o_b = c.take(4 * (size_t)L), o_st = c.take(4 * (size_t)L);
     const size_t o_t = o->tors_idx ? c.take((size_t)P * R + 1) : 0;
@@ -145,6 +148,8 @@ int stage_out(DevBuf &buf, const lg_dock_result *o, int L, int S, int P, int64_t
     const size_t o_rk = o->rank ? c.take(4 * (size_t)L * S) : 0;
     const size_t o_ld = o->leader ? c.take(4 * (size_t)L * S) : 0;
     const size_t o_g = o->restart_geo ? c.take(8 * (size_t)L * S) : 0;
+    const size_t n_rig = (size_t)L * S * P * Rs;
+    const size_t o_rg = o->restart_rigid ? c.take(n_rig + 1) : 0;
     if (buf.ensure(c.off)) return fail(LG_ENOMEM, "device output allocation failed");
     char *base = (char *)buf.p;
     d->score = (double *)(base + o_s);
@@ -157,10 +162,12 @@ int stage_out(DevBuf &buf, const lg_dock_result *o, int L, int S, int P, int64_t
     d->rank = o->rank ? (int32_t *)(base + o_rk) : nullptr;
     d->leader = o->leader ? (int32_t *)(base + o_ld) : nullptr;
     d->restart_geo = o->restart_geo ? (double *)(base + o_g) : nullptr;
+    d->restart_rigid = o->restart_rigid ? (uint8_t *)(base + o_rg) : nullptr;
     return LG_OK;
 }
 
-int fetch_out(const OutDev &d, const lg_dock_result *o, int L, int S, int P, int64_t A, int64_t R, cudaStream_t s) {
+int fetch_out(const OutDev &d, const lg_dock_result *o, int L, int S, int P, int64_t A, int64_t R, int Rs,
+              cudaStream_t s) {
     cudaError_t e = cudaSuccess;
     auto cp = [&](void *dst, const void *src, size_t n) {
         if (e == cudaSuccess && n) e = cudaMemcpyAsync(dst, src, n, cudaMemcpyDeviceToHost, s);
@@ -175,6 +182,7 @@ int fetch_out(const OutDev &d, const lg_dock_result *o, int L, int S, int P, int
     if (o->rank) cp(o->rank, d.rank, 4 * (size_t)L * S);
     if (o->leader) cp(o->leader, d.leader, 4 * (size_t)L * S);
     if (o->restart_geo) cp(o->restart_geo, d.restart_geo, 8 * (size_t)L * S);
+    if (o->restart_rigid) cp(o->restart_rigid, d.restart_rigid, (size_t)L * S * P * Rs);
     if (e != cudaSuccess) return fail(LG_ECUDA, std::string("result download: ") + cudaGetErrorString(e));
     return LG_OK;
 }
@@ -223,6 +231,8 @@ int dock_device(lg_ctx *ctx, const PocketDev &pk, const BatchDev &bd, const OutD
     const int L = bd.L;
     const bool plain = p->mode == LG_MODE_PLAIN;
     if (plain && multi) return fail(LG_EINVAL, "several pockets run in the batched mode only");
+    a.rigid_steps = p->rigid_steps;
+    a.rigid_shift_g = (float)((double)p->rigid_shift / h);
     a.ranking = ranking_on(p) ? 1 : 0;
     a.thr2g = (float)((double)p->cluster_rmsd * p->cluster_rmsd / (h * h));
     a.rescore_top = p->rescore_top;
@@ -279,7 +289,8 @@ int dock_device(lg_ctx *ctx, const PocketDev &pk, const BatchDev &bd, const OutD
         a.ly = make_layout(nmax, rmax, a.P, W, want_pose);
         a.lrt = make_layout_rt(nmax, rmax, a.P, want_pose);
         smem = std::max(a.ly.cta_bytes + W * a.lrt.warp_bytes, a.ly.cta_bytes + rank_smem);
-        e = multi ? multi_kernel_attributes(W, smem, &occ, a.ranking) : dock_kernel_attributes(W, smem, &occ, a.ranking);
+        e = multi ? multi_kernel_attributes(W, smem, &occ, a.ranking, a.rigid_steps > 0)
+                  : dock_kernel_attributes(W, smem, &occ, a.ranking, a.rigid_steps > 0);
         if (e != cudaSuccess)
             return fail(LG_ECUDA, std::string("dock kernel attributes: ") + cudaGetErrorString(e));
         if (occ > 0 || W == 1) break;
@@ -339,8 +350,8 @@ int resolve_batch(lg_ctx *c, const lg_ligand_batch *b, const lg_dock_params *p, 
 
 // Device view of a result: device buffers from `buf` for host results (the
 // totals of a device batch are read back first), as given for device results.
-int resolve_out(lg_ctx *c, DevBuf &buf, const lg_ligand_batch *b, const lg_dock_result *o, int S, int P, cudaStream_t s,
-                int64_t *A, int64_t *R, OutDev *od) {
+int resolve_out(lg_ctx *c, DevBuf &buf, const lg_ligand_batch *b, const lg_dock_result *o, int S, int P, int Rs,
+                cudaStream_t s, int64_t *A, int64_t *R, OutDev *od) {
     (void)c;
     const int L = b->L;
     if (o->mem == LG_MEM_HOST) {
@@ -353,7 +364,7 @@ int resolve_out(lg_ctx *c, DevBuf &buf, const lg_ligand_batch *b, const lg_dock_
             *A = tot[0];
             *R = tot[1];
         }
-        return stage_out(buf, o, L, S, P, *A, *R, od);
+        return stage_out(buf, o, L, S, P, *A, *R, Rs, od);
     }
     od->score = o->score;
     od->best_restart = o->best_restart;
@@ -365,6 +376,7 @@ int resolve_out(lg_ctx *c, DevBuf &buf, const lg_ligand_batch *b, const lg_dock_
     od->rank = o->rank;
     od->leader = o->leader;
     od->restart_geo = o->restart_geo;
+    od->restart_rigid = o->restart_rigid;
     return LG_OK;
 }
 
@@ -596,11 +608,11 @@ int lg_dock_batch(lg_ctx *c, int32_t pid, const lg_ligand_batch *b, const lg_doc
     BatchDev bd;
     if ((rc = resolve_batch(c, b, p, s, &bd, &A, &R, &nmax, &rmax))) return rc;
     OutDev od;
-    if ((rc = resolve_out(c, c->out_buf, b, o, S, P, s, &A, &R, &od))) return rc;
+    if ((rc = resolve_out(c, c->out_buf, b, o, S, P, p->rigid_steps, s, &A, &R, &od))) return rc;
     cudaEvent_t *tev = next_timing_events(c);
     if ((rc = dock_device(c, pk->dev, bd, od, p, nmax, rmax, c->scratch, s, &c->stats, tev))) return rc;
     if (o->mem == LG_MEM_HOST) {
-        if ((rc = fetch_out(od, o, L, S, P, A, R, s))) return rc;
+        if ((rc = fetch_out(od, o, L, S, P, A, R, p->rigid_steps, s))) return rc;
     }
     if (b->mem == LG_MEM_HOST || o->mem == LG_MEM_HOST) {
         cudaError_t e = cudaStreamSynchronize(s);

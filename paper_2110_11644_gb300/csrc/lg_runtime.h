@@ -32,15 +32,16 @@ bool ranking_on(const lg_dock_params *p);
 int check_params(const lg_dock_params *p);
 int host_batch_shape(const lg_ligand_batch *b, int64_t *A, int64_t *R, int *nmax, int *rmax);
 int stage_batch(DevBuf &buf, const lg_ligand_batch *b, int64_t A, int64_t R, BatchDev *d, cudaStream_t s);
-int stage_out(DevBuf &buf, const lg_dock_result *o, int L, int S, int P, int64_t A, int64_t R, OutDev *d);
-int fetch_out(const OutDev &d, const lg_dock_result *o, int L, int S, int P, int64_t A, int64_t R, cudaStream_t s);
+int stage_out(DevBuf &buf, const lg_dock_result *o, int L, int S, int P, int64_t A, int64_t R, int Rs, OutDev *d);
+int fetch_out(const OutDev &d, const lg_dock_result *o, int L, int S, int P, int64_t A, int64_t R, int Rs,
+              cudaStream_t s);
 int dock_device(lg_ctx *ctx, const PocketDev &pk, const BatchDev &bd, const OutDev &od, const lg_dock_params *p,
                 int nmax, int rmax, DevBuf &scratch, cudaStream_t s, lg_stats *st, cudaEvent_t *tev,
                 const MultiDev *multi = nullptr);
 int resolve_batch(lg_ctx *c, const lg_ligand_batch *b, const lg_dock_params *p, cudaStream_t s, BatchDev *bd,
                   int64_t *A, int64_t *R, int *nmax, int *rmax);
-int resolve_out(lg_ctx *c, DevBuf &buf, const lg_ligand_batch *b, const lg_dock_result *o, int S, int P, cudaStream_t s,
-                int64_t *A, int64_t *R, OutDev *od);
+int resolve_out(lg_ctx *c, DevBuf &buf, const lg_ligand_batch *b, const lg_dock_result *o, int S, int P, int Rs,
+                cudaStream_t s, int64_t *A, int64_t *R, OutDev *od);
 cudaEvent_t *next_timing_events(lg_ctx *c);
 void harvest_timing(lg_ctx *c);
 void serve_stop(lg_ctx *c);

@@ -104,14 +104,16 @@ static bool same_kind(const Request &a, const Request &b) {
            a.params.cluster_rmsd == b.params.cluster_rmsd && a.params.rescore_top == b.params.rescore_top &&
            (a.out.rank != nullptr) == (b.out.rank != nullptr) &&
            (a.out.leader != nullptr) == (b.out.leader != nullptr) &&
-           (a.out.restart_geo != nullptr) == (b.out.restart_geo != nullptr);
+           (a.out.restart_geo != nullptr) == (b.out.restart_geo != nullptr) &&
+           a.params.rigid_steps == b.params.rigid_steps && a.params.rigid_shift == b.params.rigid_shift &&
+           (a.out.restart_rigid != nullptr) == (b.out.restart_rigid != nullptr);
 }
 
 // Concatenate the requests into the slot's pinned buffer and launch them.
 static int launch_slot(Server *sv, Slot &sl) {
     lg_ctx *c = sv->ctx;
     const Request &r0 = *sl.reqs[0];
-    const int S = r0.params.restarts, P = r0.params.passes;
+    const int S = r0.params.restarts, P = r0.params.passes, Rs = r0.params.rigid_steps;
     int L = 0, nmax = 1, rmax = 1;
     int64_t A = 0, R = 0;
     for (auto &r : sl.reqs) {
@@ -173,11 +175,12 @@ static int launch_slot(Server *sv, Slot &sl) {
     size_t ob = 8 * (size_t)L + 4 * (size_t)L + 4 * (size_t)L;
     const bool want_t = r0.out.tors_idx, want_p = r0.out.pose, want_rs = r0.out.restart_score,
                want_rt = r0.out.restart_tors, want_rk = r0.out.rank, want_ld = r0.out.leader,
-               want_g = r0.out.restart_geo;
+               want_g = r0.out.restart_geo, want_rg = r0.out.restart_rigid;
     ob += want_rk ? 4 * (size_t)L * S : 0;
     ob += want_ld ? 4 * (size_t)L * S : 0;
     ob += want_g ? 8 * (size_t)L * S : 0;
     ob += want_t ? (size_t)P * R : 0;
+    ob += want_rg ? (size_t)L * S * P * Rs : 0;
     ob += want_p ? 12 * (size_t)A : 0;
     ob += want_rs ? 8 * (size_t)L * S : 0;
     ob += want_rt ? (size_t)S * P * R : 0;
@@ -192,19 +195,20 @@ static int launch_slot(Server *sv, Slot &sl) {
     if (want_ld) { hr.leader = (int32_t *)o; o += 4 * (size_t)L * S; }
     if (want_p) { hr.pose = (float *)o; o += 12 * (size_t)A; }
     if (want_t) { hr.tors_idx = (uint8_t *)o; o += (size_t)P * R; }
-    if (want_rt) { hr.restart_tors = (uint8_t *)o; }
+    if (want_rt) { hr.restart_tors = (uint8_t *)o; o += (size_t)S * P * R; }
+    if (want_rg) { hr.restart_rigid = (uint8_t *)o; }
 
     cudaSetDevice(c->device);
     BatchDev bd;
     OutDev od;
     int rc2;
     if ((rc2 = stage_batch(sl.in, &mb, A, R, &bd, sl.stream))) return rc2;
-    if ((rc2 = stage_out(sl.out, &hr, L, S, P, A, R, &od))) return rc2;
+    if ((rc2 = stage_out(sl.out, &hr, L, S, P, A, R, Rs, &od))) return rc2;
     lg_dock_params p = r0.params;
     p.mode = LG_MODE_BATCHED;
     lg_stats st{};
     if ((rc2 = dock_device(c, r0.pocket, bd, od, &p, nmax, rmax, sl.scratch, sl.stream, &st, nullptr))) return rc2;
-    if ((rc2 = fetch_out(od, &hr, L, S, P, A, R, sl.stream))) return rc2;
+    if ((rc2 = fetch_out(od, &hr, L, S, P, A, R, Rs, sl.stream))) return rc2;
     if (cudaEventRecord(sl.done, sl.stream) != cudaSuccess) return fail(LG_ECUDA, "event record failed");
     return LG_OK;
 }
@@ -231,6 +235,10 @@ static void finish_slot(Slot &sl, bool ok) {
             if (r->out.leader) memcpy(r->out.leader, hr.leader + (size_t)S * l0, 4 * (size_t)S * r->L);
             if (r->out.restart_geo)
                 memcpy(r->out.restart_geo, hr.restart_geo + (size_t)S * l0, 8 * (size_t)S * r->L);
+            if (r->out.restart_rigid) {
+                const size_t per = (size_t)S * P * r->params.rigid_steps;
+                memcpy(r->out.restart_rigid, hr.restart_rigid + per * l0, per * r->L);
+            }
         }
         l0 += r->L;
         a0 += r->A;
@@ -255,7 +263,8 @@ static size_t request_device_bytes(const Request &r) {
     return 40 * (size_t)r.L + 19 * (size_t)r.A + 2 * (size_t)r.R + (r.out.pose ? 12 * (size_t)r.A : 0) +
            (r.out.tors_idx ? P * r.R : 0) + (r.out.restart_score ? 8 * S * r.L : 0) +
            (r.out.restart_tors ? S * P * r.R : 0) + (r.out.rank ? 4 * S * r.L : 0) +
-           (r.out.leader ? 4 * S * r.L : 0) + (r.out.restart_geo ? 8 * S * r.L : 0) + 8 * (size_t)r.L + 4096;
+           (r.out.leader ? 4 * S * r.L : 0) + (r.out.restart_geo ? 8 * S * r.L : 0) +
+           (r.out.restart_rigid ? S * P * r.params.rigid_steps * r.L : 0) + 8 * (size_t)r.L + 4096;
 }
 
 static void worker(Server *sv) {

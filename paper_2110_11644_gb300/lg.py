@@ -42,13 +42,14 @@ class lg_dock_params(ctypes.Structure):
     _fields_ = [("restarts", ctypes.c_int32), ("passes", ctypes.c_int32), ("angle_steps", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("d_clash", ctypes.c_float), ("mode", ctypes.c_int32),
                 ("plain_streams", ctypes.c_int32), ("max_atoms", ctypes.c_int32), ("max_rot", ctypes.c_int32),
-                ("cluster_rmsd", ctypes.c_float), ("rescore_top", ctypes.c_int32)]
+                ("cluster_rmsd", ctypes.c_float), ("rescore_top", ctypes.c_int32),
+                ("rigid_steps", ctypes.c_int32), ("rigid_shift", ctypes.c_float)]
 
 
 class lg_dock_result(ctypes.Structure):
     _fields_ = [("mem", ctypes.c_int32), ("score", _P), ("best_restart", _P), ("tors_idx", _P), ("pose", _P),
                 ("status", _P), ("restart_score", _P), ("restart_tors", _P), ("rank", _P), ("leader", _P),
-                ("restart_geo", _P)]
+                ("restart_geo", _P), ("restart_rigid", _P)]
 
 
 class lg_flatten_params(ctypes.Structure):
@@ -281,7 +282,7 @@ def make_batch_struct(arrs: dict, L: int) -> lg_ligand_batch:
 
 
 def make_params(restarts, passes, seed, d_clash=2.0, mode=LG_MODE_BATCHED, plain_streams=0, max_atoms=0, max_rot=0,
-                cluster_rmsd=0.0, rescore_top=0):
+                cluster_rmsd=0.0, rescore_top=0, rigid_steps=0, rigid_shift=0.375):
     p = lg_dock_params()
     p.restarts, p.passes, p.angle_steps = int(restarts), int(passes), LG_ANGLE_STEPS
     p.seed = int(seed)
@@ -290,11 +291,12 @@ def make_params(restarts, passes, seed, d_clash=2.0, mode=LG_MODE_BATCHED, plain
     p.plain_streams = int(plain_streams)
     p.max_atoms, p.max_rot = int(max_atoms), int(max_rot)
     p.cluster_rmsd, p.rescore_top = float(cluster_rmsd), int(rescore_top)
+    p.rigid_steps, p.rigid_shift = int(rigid_steps), float(rigid_shift)
     return p
 
 
 def alloc_result(L, A, R, S, P, device=False, pose=True, tors=True, restart_score=False, restart_tors=False,
-                 ranking=False):
+                 ranking=False, rigid_steps=0):
     """Output arrays for a batch: numpy (host) or CUDA torch tensors (device)."""
     if device:
         import torch
@@ -304,7 +306,8 @@ def alloc_result(L, A, R, S, P, device=False, pose=True, tors=True, restart_scor
                     restart_score=z(L * S, torch.float64) if restart_score else None,
                     restart_tors=z(S * P * R, torch.uint8) if restart_tors else None,
                     rank=z(L * S, torch.int32) if ranking else None, leader=z(L * S, torch.int32) if ranking else None,
-                    restart_geo=z(L * S, torch.float64) if ranking else None)
+                    restart_geo=z(L * S, torch.float64) if ranking else None,
+                    restart_rigid=z(L * S * P * rigid_steps, torch.uint8) if rigid_steps else None)
     else:
         z = lambda n, dt: np.zeros(max(n, 1), dt)
         arrs = dict(score=z(L, np.float64), best_restart=z(L, np.int32), status=z(L, np.int32),
@@ -312,7 +315,8 @@ def alloc_result(L, A, R, S, P, device=False, pose=True, tors=True, restart_scor
                     restart_score=z(L * S, np.float64) if restart_score else None,
                     restart_tors=z(S * P * R, np.uint8) if restart_tors else None,
                     rank=z(L * S, np.int32) if ranking else None, leader=z(L * S, np.int32) if ranking else None,
-                    restart_geo=z(L * S, np.float64) if ranking else None)
+                    restart_geo=z(L * S, np.float64) if ranking else None,
+                    restart_rigid=z(L * S * P * rigid_steps, np.uint8) if rigid_steps else None)
     r = lg_dock_result()
     r.mem = LG_MEM_DEVICE if device else LG_MEM_HOST
     for k, v in arrs.items():
@@ -373,7 +377,8 @@ class Context:
         return lg_get_stats(self.h)
 
     def dock(self, pid, batch, params, *, mode=LG_MODE_BATCHED, device_io=False, pose=True, tors=True,
-             restart_score=False, restart_tors=False, stream=None, plain_streams=0, max_atoms=0, max_rot=0):
+             restart_score=False, restart_tors=False, restart_rigid=False, stream=None, plain_streams=0, max_atoms=0,
+             max_rot=0):
         """Dock a CSR batch (numpy attributes).  With device_io=True the batch is
         copied to the GPU first and the results come back from device buffers;
         otherwise the library stages host memory itself.  Returns numpy arrays.
@@ -387,9 +392,11 @@ class Context:
         thr = float(getattr(params, "cluster_rmsd", 0.0))
         K = int(getattr(params, "rescore_top", 0))
         ranking = thr > 0.0 or 0 < K < S
-        p = make_params(S, P, params.seed, params.d_clash, mode, plain_streams, max_atoms, max_rot, thr, K)
+        Rs = int(getattr(params, "rigid_steps", 0))
+        p = make_params(S, P, params.seed, params.d_clash, mode, plain_streams, max_atoms, max_rot, thr, K, Rs,
+                        float(getattr(params, "rigid_shift", 0.375)))
         r, outs = alloc_result(L, A, R, S, P, device=device_io, pose=pose, tors=tors, restart_score=restart_score,
-                               restart_tors=restart_tors, ranking=ranking)
+                               restart_tors=restart_tors, ranking=ranking, rigid_steps=Rs if restart_rigid else 0)
         if device_io:
             import torch
             s = torch.cuda.current_stream()
@@ -399,11 +406,11 @@ class Context:
         else:
             lg_dock_batch(self.h, pid, b, p, r, stream)
         n = dict(score=L, best_restart=L, status=L, tors_idx=P * R, pose=3 * A, restart_score=L * S,
-                 restart_tors=S * P * R, rank=L * S, leader=L * S, restart_geo=L * S)
+                 restart_tors=S * P * R, rank=L * S, leader=L * S, restart_geo=L * S, restart_rigid=L * S * P * Rs)
         return {k: (v[:n[k]] if v is not None else None) for k, v in outs.items()}
 
     def dock_multi(self, pids, batch, params, *, device_io=False, pose=True, tors=True, restart_score=False,
-                   restart_tors=False, stream=None, max_atoms=0, max_rot=0):
+                   restart_tors=False, restart_rigid=False, stream=None, max_atoms=0, max_rot=0):
         """Dock a CSR batch against several pockets in one launch; returns one
         dict of numpy arrays per pocket (as dock())."""
         L = len(batch.atom_off) - 1
@@ -412,11 +419,14 @@ class Context:
         thr = float(getattr(params, "cluster_rmsd", 0.0))
         K = int(getattr(params, "rescore_top", 0))
         ranking = thr > 0.0 or 0 < K < S
+        Rs = int(getattr(params, "rigid_steps", 0))
         arrs = device_batch_arrays(batch) if device_io else host_batch_arrays(batch)
         b = make_batch_struct(arrs, L)
-        p = make_params(S, P, params.seed, params.d_clash, LG_MODE_BATCHED, 0, max_atoms, max_rot, thr, K)
+        p = make_params(S, P, params.seed, params.d_clash, LG_MODE_BATCHED, 0, max_atoms, max_rot, thr, K, Rs,
+                        float(getattr(params, "rigid_shift", 0.375)))
         res = [alloc_result(L, A, R, S, P, device=device_io, pose=pose, tors=tors, restart_score=restart_score,
-                            restart_tors=restart_tors, ranking=ranking) for _ in pids]
+                            restart_tors=restart_tors, ranking=ranking, rigid_steps=Rs if restart_rigid else 0)
+               for _ in pids]
         if device_io:
             import torch
             s = torch.cuda.current_stream()
@@ -425,7 +435,7 @@ class Context:
         else:
             lg_dock_multi(self.h, pids, b, p, [r for r, _ in res], stream)
         n = dict(score=L, best_restart=L, status=L, tors_idx=P * R, pose=3 * A, restart_score=L * S,
-                 restart_tors=S * P * R, rank=L * S, leader=L * S, restart_geo=L * S)
+                 restart_tors=S * P * R, rank=L * S, leader=L * S, restart_geo=L * S, restart_rigid=L * S * P * Rs)
         out = []
         for _, outs in res:
             if device_io:

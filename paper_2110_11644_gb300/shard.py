@@ -82,14 +82,17 @@ def clash_pairs_per_ligand(batch) -> np.ndarray:
     return out
 
 
-def ligand_flops(batch, restarts: int, passes: int) -> np.ndarray:
-    """Algorithmic FLOPs of docking each ligand (see the module docstring)."""
+def ligand_flops(batch, restarts: int, passes: int, rigid_steps: int = 0) -> np.ndarray:
+    """Algorithmic FLOPs of docking each ligand (see the module docstring);
+    rigid refinement adds, per pass and rigid move, 13 candidates of N rotated
+    atoms and lookups."""
     N = np.diff(batch.atom_off).astype(np.float64)
     m, pairs, rl, L = _bond_counts(batch)
     per_bond = 36.0 * m * (C_ROT + C_TRI) + C_PAIR * pairs.astype(np.float64)
     sweep = np.zeros(L)
     np.add.at(sweep, rl, per_bond)
-    return restarts * (C_POSE_ATOM * N + C_RESTART + passes * sweep + C_FIN * N)
+    rigid = rigid_steps * 13.0 * N * (C_ROT + C_TRI)
+    return restarts * (C_POSE_ATOM * N + C_RESTART + passes * (sweep + rigid) + C_FIN * N)
 
 
 def ligand_flops_circle(batch, restarts: int, passes: int) -> np.ndarray:

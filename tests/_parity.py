@@ -15,7 +15,9 @@ would have chosen itself, its FP64 scores and clash distances, and then:
      relative to max(|E|, sum |e_i|);
   3. the best restart is the oracle's argmin, or within TOL_SCORE of it;
   4. the best pose matches the replayed FP64 pose to RMSD <= TOL_RMSD A;
-  5. tors_idx equals the best restart's decisions.
+  5. tors_idx equals the best restart's decisions;
+  6. with rigid refinement, every rigid move the GPU took that differs from
+     the oracle's own choice scores within TOL_TIE of the oracle's best.
 
 Tolerances (from the accuracy target): score gap 1e-5 relative, clash margin
 1e-5 relative to d_clash^2, scores 1e-5 relative, pose RMSD 1e-3 A.
@@ -61,7 +63,22 @@ def check(pocket, batch, params, gpu, report=None):
     restart_tors (flat numpy arrays as the C-ABI lays them out)."""
     S, P = params.restarts, params.passes
     dc2 = float(np.float32(params.d_clash)) ** 2
-    rep = oracle.dock(pocket, batch, params, replay=gpu["restart_tors"], trace=True, poses=True)
+    Rs = int(getattr(params, "rigid_steps", 0))
+    rigid = gpu.get("restart_rigid") if Rs > 0 else None
+    if Rs > 0:
+        assert rigid is not None, "rigid refinement needs the GPU's restart_rigid decisions"
+    rep = oracle.dock(pocket, batch, params, replay=gpu["restart_tors"], replay_rigid=rigid, trace=True, poses=True)
+    n_rig = n_rig_dev = 0
+    if Rs > 0:
+        tg = rep["trace_G"].reshape(-1, 13)
+        for d in range(len(rigid)):
+            g, o = int(rigid[d]), int(rep["own_rigid"][d])
+            n_rig += 1
+            if g != o:
+                n_rig_dev += 1
+                assert tg[d, g] >= tg[d, o] - TOL_TIE * max(abs(tg[d, o]), 1e-30), \
+                    f"rigid decision {d}: GPU candidate {g} vs oracle {o}, G={tg[d, [g, o]]}"
+
     L = batch.L
     aoff, roff = batch.atom_off, batch.rot_off
     n_dec = n_dev = 0
@@ -105,7 +122,7 @@ def check(pocket, batch, params, gpu, report=None):
         worst_rmsd = max(worst_rmsd, rmsd)
         assert rmsd <= TOL_RMSD, f"ligand {l}: pose RMSD {rmsd:.3g}"
     out = dict(decisions=n_dec, deviations=n_dev, worst_score_rel=worst_score, worst_rmsd=worst_rmsd,
-               best_restart_near_ties=best_r_near)
+               best_restart_near_ties=best_r_near, rigid_decisions=n_rig, rigid_deviations=n_rig_dev)
     if report is not None:
         report.update(out)
     return out

@@ -216,3 +216,43 @@ def test_bad_arguments_raise(ctx, cfg1, pocket1):
     with pytest.raises(lg.LgError) as e:
         ctx.dock(pocket1, batch.subset([0]), synth.DockParams(restarts=0, passes=1))
     assert e.value.code == lg.LG_EINVAL
+
+
+# ----------------------------------------------------------------------------- rigid refinement
+def test_rigid_refinement_matches_oracle(ctx, cfg1, pocket1):
+    import dataclasses
+    pocket, batch, params = cfg1
+    prm = dataclasses.replace(params, rigid_steps=2)
+    sub = batch.subset(range(96))
+    g = ctx.dock(pocket1, sub, prm, restart_score=True, restart_tors=True, restart_rigid=True)
+    assert np.all(g["status"] == 0)
+    rep = check(pocket, sub, prm, g)
+    assert rep["rigid_decisions"] == sub.L * prm.restarts * prm.passes * prm.rigid_steps
+    assert rep["rigid_deviations"] <= 0.01 * rep["rigid_decisions"] + 2, rep
+    # rigid moves are taken, and the result differs from the torsion-only method
+    assert np.any(g["restart_rigid"] != 0)
+    base = ctx.dock(pocket1, sub, params)
+    assert not np.array_equal(base["score"], g["score"])
+
+
+def test_rigid_refinement_plain_equals_batched(ctx, cfg1, pocket1):
+    import dataclasses
+    _, batch, params = cfg1
+    prm = dataclasses.replace(params, rigid_steps=3, rigid_shift=0.5)
+    sub = batch.subset(range(40))
+    a = ctx.dock(pocket1, sub, prm, restart_score=True, restart_tors=True, restart_rigid=True)
+    b = ctx.dock(pocket1, sub, prm, restart_score=True, restart_tors=True, restart_rigid=True,
+                 mode=lg.LG_MODE_PLAIN)
+    for k in ("score", "best_restart", "tors_idx", "pose", "restart_score", "restart_tors", "restart_rigid"):
+        assert np.array_equal(a[k], b[k]), k
+
+
+def test_rigid_refinement_throughput_ligands(ctx, cfg2_pocket):
+    import dataclasses
+    sub = synth.config_ligands(2, 48)
+    prm = dataclasses.replace(synth.config_params(2), rigid_steps=1)
+    pid = ctx.load_pocket(cfg2_pocket)
+    g = ctx.dock(pid, sub, prm, restart_score=True, restart_tors=True, restart_rigid=True)
+    ctx.unload_pocket(pid)
+    rep = check(cfg2_pocket, sub, prm, g)
+    assert rep["rigid_deviations"] <= 0.01 * rep["rigid_decisions"] + 2, rep
