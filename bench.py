@@ -321,6 +321,94 @@ def multi_pocket_leg(ctx, dev, n_lig, steps, peak_tflops):
             **out, "per_pocket": per}
 
 
+def heavy_tailed_leg(ctx, pid, dev, n_lig, steps, peak_tflops):
+    """The heavy-tailed library (atoms lognormal, median 28, 10-100; torsions
+    up to 20) on the throughput pocket: one lg_dock_batch per step, split into
+    size classes with autotuned warps per CTA, device-resident inputs, L2
+    flushed before each step; the same with the tuner off (4 warps per CTA)
+    for comparison."""
+    import torch
+    from paper_2110_11644_gb300 import lg, synth
+    batch = synth.config_ligands(3, n_lig, uid_base=2 << 40)
+    params = synth.config_params(3)
+    L, S, P = batch.L, params.restarts, params.passes
+    A, R = int(batch.atom_off[-1]), int(batch.rot_off[-1])
+    darr = lg.device_batch_arrays(batch, f"cuda:{dev}")
+    b = lg.make_batch_struct(darr, L)
+    p = lg.make_params(S, P, params.seed, params.d_clash, lg.LG_MODE_BATCHED, 0, int(batch.n_atoms().max()),
+                       max(1, int(batch.n_rot().max())))
+    r, outs = lg.alloc_result(L, A, R, S, P, device=True, pose=True, tors=True)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{dev}")
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream
+
+    def timed(n):
+        lg.lg_dock_batch(ctx.h, pid, b, p, r, sh)   # warm-up (and, the first time, the autotuner's trials)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ms = 0.0
+        for _ in range(n):
+            flush.fill_(1)
+            e0.record(stream)
+            lg.lg_dock_batch(ctx.h, pid, b, p, r, sh)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1) / n
+        return ms
+
+    ms = timed(steps)
+    st = ctx.stats()
+    scores = outs["score"][:L].cpu().numpy().copy()
+    ctx.set_option("autotune", 0)
+    ctx.set_option("warps_per_cta", 4)
+    ms4 = timed(1)
+    assert np.array_equal(outs["score"][:L].cpu().numpy(), scores), "results depend on the launch configuration"
+    ctx.set_option("size_classes", 0)
+    ms1 = timed(1)
+    ctx.set_option("size_classes", 1)
+    ctx.set_option("warps_per_cta", 0)
+    ctx.set_option("autotune", 1)
+    assert np.array_equal(outs["score"][:L].cpu().numpy(), scores), "results depend on the launch configuration"
+    assert int((outs["status"][:L] != 0).sum()) == 0
+    F = algorithmic_flops(batch, S, P)
+    return {"ligands": L, "value": L / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": steps,
+            "frac": F / (ms / 1e3) / 1e12 / peak_tflops, "launches_per_step": st.launches,
+            "untuned_4_warps": {"value": L / (ms4 / 1e3), "ms_per_step": ms4},
+            "one_launch_4_warps": {"value": L / (ms1 / 1e3), "ms_per_step": ms1},
+            "sample": f"{L} ligands: atoms lognormal (median 28, 10-100), torsions ~0.2 N (0-20), {S} restarts, "
+                      f"{P} passes, 64^3 pocket"}
+
+
+def small_batch_leg(ctx, pid, dev, n_lig, calls):
+    """Per-call latency of small device-resident batches (the serving regime):
+    direct launches against a captured CUDA graph replayed per call."""
+    import torch
+    from paper_2110_11644_gb300 import lg, synth
+    batch = synth.config_ligands(2, n_lig, uid_base=3 << 40)
+    params = synth.config_params(2)
+    L, S, P = batch.L, params.restarts, params.passes
+    A, R = int(batch.atom_off[-1]), int(batch.rot_off[-1])
+    darr = lg.device_batch_arrays(batch, f"cuda:{dev}")
+    b = lg.make_batch_struct(darr, L)
+    p = lg.make_params(S, P, params.seed, params.d_clash, lg.LG_MODE_BATCHED, 0, int(batch.n_atoms().max()),
+                       max(1, int(batch.n_rot().max())))
+    r, outs = lg.alloc_result(L, A, R, S, P, device=True, pose=True, tors=True)
+    side = torch.cuda.Stream(device=dev)
+    res = {}
+    for name, g in (("direct", 0), ("graph", 1)):
+        ctx.set_option("graphs", g)
+        for _ in range(3):
+            lg.lg_dock_batch(ctx.h, pid, b, p, r, side.cuda_stream)
+        side.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(calls):
+            lg.lg_dock_batch(ctx.h, pid, b, p, r, side.cuda_stream)
+        side.synchronize()
+        res[name] = {"us_per_call": (time.perf_counter() - t0) / calls * 1e6, "graph_mode": ctx.stats().graph}
+    ctx.set_option("graphs", 0)
+    return {"ligands": L, "calls": calls, **res}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -335,6 +423,8 @@ def main():
     ap.add_argument("--serve-loads", default="0.5", help="comma-separated offered loads for the serving leg")
     ap.add_argument("--multi-ligands", type=int, default=20000,
                     help="ligands of the 15-pocket leg (0 = off)")
+    ap.add_argument("--heavy-ligands", type=int, default=1_000_000,
+                    help="ligands of the heavy-tailed leg (0 = off)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -522,6 +612,12 @@ def main():
             serving = [serving_leg(ctx, pid, batch, params, value / world, float(ld), args.serve_seconds)
                        for ld in args.serve_loads.split(",")]
 
+        small = small_batch_leg(ctx, pid, dev, 64, 200) if world == 1 else None
+
+        heavy = None
+        if args.heavy_ligands > 0 and world == 1:
+            heavy = heavy_tailed_leg(ctx, pid, dev, args.heavy_ligands, 2, roofline["peak"])
+
         multi = None
         if args.multi_ligands > 0 and world == 1:
             multi = multi_pocket_leg(ctx, dev, args.multi_ligands, 3, roofline["peak"])
@@ -535,7 +631,8 @@ def main():
                            "warps_per_cta": st.warps_per_cta, "ctas_per_sm": st.ctas_per_sm, "grid": st.grid},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "clocks": clk, "gpu_launches": launches_per_step * args.steps, "plain": plain,
-                "serving": serving, "multi_pocket": multi, "flatten": flatten}
+                "serving": serving, "multi_pocket": multi, "flatten": flatten, "heavy_tailed": heavy,
+                "small_batch": small}
         print(json.dumps(line), flush=True)
     ctx.close()
     if dist:

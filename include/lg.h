@@ -402,12 +402,24 @@ typedef struct {
     int32_t warps_per_cta;
     int32_t ctas_per_sm;
     int32_t smem_bytes;   /* dynamic shared memory per CTA */
+    int32_t graph;        /* last call: 2 captured a CUDA graph, 1 replayed one, 0 launched directly */
 } lg_stats;
 
 int lg_get_stats(lg_ctx *ctx, lg_stats *out);
 
-/* Context options: "timing" (0/1, default 0), "warps_per_cta" (0 = autotune,
- * else 1..32), "serve_max_inflight" (requests on the device at once, default 8),
+/* Context options: "timing" (0/1, default 0), "warps_per_cta" (0 = the
+ * autotuner's or the default choice, else 1..4 for every batched launch),
+ * "autotune" (0/1, default 1; setting it clears the tuned choices: with it on,
+ * the first batched call of a (size class, restarts, passes, atom and torsion
+ * maxima, features) combination times 4, 2 and 1 warps per CTA on up to 4,096
+ * ligands of that class and keeps the fastest; results do not depend on the
+ * choice), "graphs" (0/1, default 0: an lg_dock_batch call with device
+ * batch and result on a non-default stream is captured, preparation and
+ * docking kernels together, as a CUDA graph and replayed when a later call
+ * has the same arguments; with timing on, such a call's device time then
+ * spans the preparation kernels too), "size_classes" (0/1, default 1: a batch whose atom maximum exceeds
+ * 64 is docked by one launch per size class -- atoms <= 32, <= 64, more --
+ * each with shared memory for its own maximum), "serve_max_inflight" (requests on the device at once, default 8),
  * "serve_mem_reserve_mb" (free device memory the server leaves untouched,
  * default 1024), "multi_order" (lg_dock_multi's visiting order: 0 =
  * pocket-major, the default; 1 = ligand-major, a CTA docks one ligand against

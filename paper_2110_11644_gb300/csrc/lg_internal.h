@@ -180,9 +180,24 @@ struct DockArgs {
     int rescore_top;           // K (0 = all)
     const int32_t *order;      // batched mode: ligand visiting order (NULL = identity)
     int32_t *work_counter;     // batched mode: next item of the persistent loop
+    const int32_t *cls_off;    // batched mode: class boundaries in `order` (NULL = the whole batch)
+    int cls;                   // with cls_off: the size class this launch docks
+    int item_cap;              // > 0: dock only the first item_cap items (autotuning trials)
+    int sort_classes;          // preparation: 1 = size class major, then cost; 0 = cost only
 };
 
-constexpr int kSortBuckets = 128;
+// Cost order of the batched kernels: ligands are filed by size class (atoms
+// <= 32, <= 64, more) and, within a class, by estimated cost (2 buckets per
+// octave); the sort visits the largest class first, costliest first.
+constexpr int kCostBuckets = 64;
+constexpr int kSizeClasses = 3;
+constexpr int kSortBuckets = kSizeClasses * kCostBuckets;
+// scratch ints after the histogram: one work counter per launch unit (each
+// size class, then the whole batch) and the class boundaries in the order
+// (start of class 2, class 1, class 0, then L)
+constexpr int kHistInts = kSortBuckets + 2 * (kSizeClasses + 1);
+__host__ __device__ inline int size_class(int n) { return n <= 32 ? 0 : (n <= 64 ? 1 : 2); }
+__host__ __device__ inline int class_bound(int c) { return c == 0 ? 32 : (c == 1 ? 64 : LG_MAX_ATOMS); }
 
 // Ligand flattening (one warp per ligand; see k_flatten).
 struct FlatArgs {

@@ -1026,14 +1026,23 @@ __device__ __forceinline__ void dock_ligand_rt(const DockArgs &A, const PocketDe
 template <bool kRank, bool kRigid>
 __global__ void __launch_bounds__(128, LG_RT_MIN_BLOCKS) k_dock_batched(const __grid_constant__ DockArgs A) {
     extern __shared__ __align__(16) char sm[];
-    __shared__ int s_item;
+    __shared__ int s_lig;
     for (;;) {
-        if (threadIdx.x == 0) s_item = atomicAdd(A.work_counter, 1);
+        if (threadIdx.x == 0) {  // next ligand of the launch's range of the cost order, or -1
+            int first = 0, count = A.batch.L;
+            if (A.cls_off) {  // one size class
+                first = A.cls_off[2 - A.cls];
+                count = A.cls_off[3 - A.cls] - first;
+            }
+            if (A.item_cap > 0) count = min(count, A.item_cap);
+            const int item = atomicAdd(A.work_counter, 1);
+            s_lig = item < count ? (A.order ? A.order[first + item] : first + item) : -1;
+        }
         __syncthreads();
-        const int item = s_item;
+        const int l = s_lig;
         __syncthreads();
-        if (item >= A.batch.L) break;
-        dock_ligand_rt<kRank, kRigid>(A, A.pocket, A.out, A.order ? A.order[item] : item, sm);
+        if (l < 0) break;
+        dock_ligand_rt<kRank, kRigid>(A, A.pocket, A.out, l, sm);
     }
 }
 
@@ -1225,7 +1234,9 @@ __global__ void __launch_bounds__(32 * kFlatWarps) k_flatten(const __grid_consta
 // ascending in [1, N-1]), writes the end of every torsional child's subtree,
 // the centroid (FP64) and the ligand's status; with `sort` it also files the
 // ligand into a log-scale cost bucket (4 per octave) of
-//   cost ~ restarts * (passes * 36 * sum of moving atoms + 8 * atoms + 64).
+//   cost ~ restarts * (passes * 36 * sum of moving atoms + 8 * atoms + 64):
+// 4 buckets per octave, or (sort_classes) the size class and 2 buckets per
+// octave within it (rejected ligands: class 0).
 __global__ void k_prep(const __grid_constant__ DockArgs A, int sort) {
     __shared__ int sh[kSortBuckets];
     if (sort)
@@ -1286,8 +1297,13 @@ __global__ void k_prep(const __grid_constant__ DockArgs A, int sort) {
         }
         if (sort) {
             const double cost = ok ? (double)A.S * ((double)A.P * 36.0 * (double)msum + 8.0 * N + 64.0) : 1.0;
-            int key = (int)(4.0 * log2(cost));
-            key = max(0, min(kSortBuckets - 1, key));
+            int key;
+            if (A.sort_classes) {  // size class, then 2 buckets per octave of cost
+                const int cb = max(0, min(kCostBuckets - 1, (int)(2.0 * log2(cost)) - 16));
+                key = size_class(ok ? N : 1) * kCostBuckets + cb;
+            } else {  // 4 buckets per octave of cost
+                key = max(0, min(kSortBuckets - 1, (int)(4.0 * log2(cost)) - 32));
+            }
             A.scr.keys[l] = key;
             atomicAdd(&sh[key], 1);
         }
@@ -1299,7 +1315,7 @@ __global__ void k_prep(const __grid_constant__ DockArgs A, int sort) {
 }
 
 // Exclusive offsets of the buckets in descending key order (one warp).
-__global__ void k_sort_scan(int32_t *hist) {
+__global__ void k_sort_scan(int32_t *hist, int L) {
     const int lane = threadIdx.x;
     constexpr int per = kSortBuckets / 32;
     int v[per];
@@ -1320,6 +1336,12 @@ __global__ void k_sort_scan(int32_t *hist) {
     for (int j = 0; j < per; j++) {
         hist[kSortBuckets - 1 - (lane * per + j)] = run;
         run += v[j];
+    }
+    __syncwarp();
+    if (lane == 0) {  // class boundaries: a class starts at the offset of its costliest bucket
+        int32_t *co = hist + kSortBuckets + kSizeClasses + 1;
+        for (int c = kSizeClasses - 1; c >= 0; --c) co[kSizeClasses - 1 - c] = hist[c * kCostBuckets + kCostBuckets - 1];
+        co[kSizeClasses] = L;
     }
 }
 
@@ -1365,7 +1387,7 @@ static size_t al256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 size_t scratch_bytes(int L, int rmax, int rank_slots, int S, int P, int nmax) {
     rmax = rmax > 0 ? rmax : 1;
-    size_t b = al256(4 * (kSortBuckets + 1)) + 2 * al256(4 * (size_t)L) + al256(24 * (size_t)L) +
+    size_t b = al256(4 * kHistInts) + 2 * al256(4 * (size_t)L) + al256(24 * (size_t)L) +
                al256(2 * (size_t)L * rmax);
     if (rank_slots > 0) {
         const size_t nm = (size_t)((nmax + 3) & ~3);
@@ -1380,7 +1402,7 @@ Scratch carve_scratch(void *base, int L, int rmax, int rank_slots, int S, int P,
     char *p = (char *)base;
     Scratch s;
     s.hist = (int32_t *)p;
-    p += al256(4 * (kSortBuckets + 1));
+    p += al256(4 * kHistInts);
     s.keys = (int32_t *)p;
     p += al256(4 * (size_t)L);
     s.order = (int32_t *)p;
@@ -1436,7 +1458,7 @@ cudaError_t launch_prep(const DockArgs &a, bool sort, cudaStream_t s, int *launc
     k_prep<<<blocks, 256, 0, s>>>(a, sort ? 1 : 0);
     *launches += 1;
     if (sort) {
-        k_sort_scan<<<1, 32, 0, s>>>(a.scr.hist);
+        k_sort_scan<<<1, 32, 0, s>>>(a.scr.hist, L);
         k_sort_scatter<<<blocks, 256, 0, s>>>(L, a.scr.keys, a.scr.hist, a.scr.order);
         *launches += 2;
     }

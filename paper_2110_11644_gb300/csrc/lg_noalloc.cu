@@ -138,7 +138,7 @@ extern "C" int lg_dock_batch_noalloc(lg_ctx *c, int32_t pid, const lg_ligand_bat
     a.order = a.scr.order;
     // the array keeps the previous call's contents: clear the bucket counters
     // and the work counter
-    if ((e = cudaMemsetAsync(a.scr.hist, 0, 4 * (kSortBuckets + 1), s)) != cudaSuccess)
+    if ((e = cudaMemsetAsync(a.scr.hist, 0, 4 * kHistInts, s)) != cudaSuccess)
         return fail(LG_ECUDA, std::string("scratch clear: ") + cudaGetErrorString(e));
     int launches = 0;
     if ((e = launch_prep(a, true, s, &launches)) != cudaSuccess)

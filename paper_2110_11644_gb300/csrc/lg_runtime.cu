@@ -201,9 +201,33 @@ int choose_warps(int S, int opt) {
 // Launch the docking of a device-resident batch on stream s: the preparation
 // kernel (validation, subtree ends, centroids; cost sort in batched mode),
 // then the persistent docking kernel or one plain launch per ligand.
+// Size classes present in a host batch (bit c: class c).
+unsigned host_class_mask(const lg_ligand_batch *b) {
+    unsigned m = 0;
+    for (int l = 0; l < b->L; l++) m |= 1u << size_class(std::max(1, b->atom_off[l + 1] - b->atom_off[l]));
+    return m;
+}
+
+// Warps per CTA of a batched launch unit: the context option, else the
+// autotuner's cached choice, else the restart-tile heuristic.
+static int tuned_warps(lg_ctx *c, const std::array<int, 8> &key, int S, bool *cached) {
+    *cached = false;
+    if (c->warps_opt > 0) {
+        *cached = true;
+        return std::min(c->warps_opt, 4);
+    }
+    std::lock_guard<std::mutex> g(c->tune_mu);
+    auto it = c->tune.find(key);
+    if (it != c->tune.end()) {
+        *cached = true;
+        return it->second;
+    }
+    return choose_warps(S, 0);
+}
+
 int dock_device(lg_ctx *ctx, const PocketDev &pk, const BatchDev &bd, const OutDev &od, const lg_dock_params *p,
                 int nmax, int rmax, DevBuf &scratch, cudaStream_t s, lg_stats *st, cudaEvent_t *tev,
-                const MultiDev *multi) {
+                const MultiDev *multi, unsigned class_mask, bool allow_graph) {
     const bool timed = tev != nullptr;
     DockArgs a;
     memset(&a, 0, sizeof(a));
@@ -244,7 +268,7 @@ int dock_device(lg_ctx *ctx, const PocketDev &pk, const BatchDev &bd, const OutD
         if (scratch.ensure(scratch_bytes(L, rmax, a.ranking ? slots : 0, a.S, a.P, a.ly.nmax)))
             return fail(LG_ENOMEM, "scratch allocation failed");
         a.scr = carve_scratch(scratch.p, L, rmax, a.ranking ? slots : 0, a.S, a.P, a.ly.nmax);
-        if (!plain && (e = cudaMemsetAsync(a.scr.hist, 0, 4 * (kSortBuckets + 1), s)) != cudaSuccess)
+        if (!plain && (e = cudaMemsetAsync(a.scr.hist, 0, 4 * kHistInts, s)) != cudaSuccess)
             return fail(LG_ECUDA, std::string("scratch clear: ") + cudaGetErrorString(e));
         if ((e = launch_prep(a, !plain, s, &launches)) != cudaSuccess)
             return fail(LG_ECUDA, std::string("preparation launch: ") + cudaGetErrorString(e));
@@ -282,35 +306,193 @@ int dock_device(lg_ctx *ctx, const PocketDev &pk, const BatchDev &bd, const OutD
         st->smem_bytes = psmem;
         return LG_OK;
     }
-    // batched: cost-ordered persistent launch of restart-tiled warps
-    int W = choose_warps(a.S, ctx_warps_opt(ctx));
-    int occ = 0, smem = 0;
-    for (;;) {
-        a.ly = make_layout(nmax, rmax, a.P, W, want_pose);
-        a.lrt = make_layout_rt(nmax, rmax, a.P, want_pose);
-        smem = std::max(a.ly.cta_bytes + W * a.lrt.warp_bytes, a.ly.cta_bytes + rank_smem);
-        e = multi ? multi_kernel_attributes(W, smem, &occ, a.ranking, a.rigid_steps > 0)
-                  : dock_kernel_attributes(W, smem, &occ, a.ranking, a.rigid_steps > 0);
-        if (e != cudaSuccess)
-            return fail(LG_ECUDA, std::string("dock kernel attributes: ") + cudaGetErrorString(e));
-        if (occ > 0 || W == 1) break;
-        W = std::max(1, W / 2);
+    // batched: cost-ordered persistent launches of restart-tiled warps, one
+    // per size class when the batch's atom maximum exceeds 64 (each class
+    // with shared memory for its own maximum, so small ligands keep a high
+    // occupancy), else one for the whole batch
+    struct Unit {
+        int cls, nmax, W, occ, smem, grid;
+        bool tuned;
+        std::array<int, 8> key;
+    };
+    std::vector<Unit> units;
+    const bool split = !multi && ctx->size_classes && nmax > class_bound(1);
+    auto configure = [&](Unit &u) -> int {
+        for (;;) {
+            a.ly = make_layout(u.nmax, rmax, a.P, u.W, want_pose);
+            a.lrt = make_layout_rt(u.nmax, rmax, a.P, want_pose);
+            u.smem = std::max(a.ly.cta_bytes + u.W * a.lrt.warp_bytes, a.ly.cta_bytes + rank_smem);
+            e = multi ? multi_kernel_attributes(u.W, u.smem, &u.occ, a.ranking, a.rigid_steps > 0)
+                      : dock_kernel_attributes(u.W, u.smem, &u.occ, a.ranking, a.rigid_steps > 0);
+            if (e != cudaSuccess) return fail(LG_ECUDA, std::string("dock kernel attributes: ") + cudaGetErrorString(e));
+            if (u.occ > 0 || u.W == 1) break;
+            u.W = std::max(1, u.W / 2);
+        }
+        if (u.occ <= 0) return fail(LG_EINVAL, "docking kernel does not fit on an SM");
+        const long items = multi && multi->pocket_major ? (long)L * multi->np : (long)L;
+        u.grid = (int)std::max(1L, std::min((long)ctx_num_sms(ctx) * u.occ, items));
+        return LG_OK;
+    };
+    for (int c = kSizeClasses - 1; c >= -1; --c) {
+        if (split ? (c < 0 || !((class_mask >> c) & 1u)) : c >= 0) continue;
+        Unit u;
+        u.cls = c;
+        u.nmax = c < 0 ? nmax : std::min(nmax, class_bound(c));
+        u.key = {c, a.S, a.P, u.nmax, rmax, a.ranking, a.rigid_steps > 0 ? 1 : 0, want_pose + 2 * (multi ? 1 : 0)};
+        u.W = tuned_warps(ctx, u.key, a.S, &u.tuned);
+        if (int rc = configure(u)) return rc;
+        units.push_back(u);
     }
-    if (occ <= 0) return fail(LG_EINVAL, "docking kernel does not fit on an SM");
-    const long items = multi && multi->pocket_major ? (long)L * multi->np : (long)L;
-    const int grid = (int)std::max(1L, std::min((long)ctx_num_sms(ctx) * occ, items));
-    if (int rc = setup_scratch(grid)) return rc;
-    a.work_counter = a.scr.hist + kSortBuckets;
+    a.sort_classes = split ? 1 : 0;
+    int slots = 1;
+    for (const Unit &u : units) slots = std::max(slots, u.grid);
+    bool need_tune = false;  // tuning trials run eagerly on the sorted batch: no graph for this call
+    for (const Unit &u : units) need_tune = need_tune || (ctx->autotune && !multi && !u.tuned);
+    const bool graph = allow_graph && ctx->graphs && !multi && s != nullptr && !need_tune;
+    if (!graph) {
+        if (int rc = setup_scratch(slots)) return rc;
+    } else {  // the preparation goes into the graph with the docking launches
+        if (scratch.ensure(scratch_bytes(L, rmax, a.ranking ? slots : 0, a.S, a.P, a.ly.nmax)))
+            return fail(LG_ENOMEM, "scratch allocation failed");
+        a.scr = carve_scratch(scratch.p, L, rmax, a.ranking ? slots : 0, a.S, a.P, a.ly.nmax);
+    }
     a.order = a.scr.order;
+    int32_t *counters = a.scr.hist + kSortBuckets;
+    // the kernels' shared-memory limit is per function: the largest of the units
+    auto set_limit = [&]() -> cudaError_t {
+        int big = 0, occ = 0;
+        for (const Unit &u : units) big = std::max(big, u.smem);
+        return multi ? multi_kernel_attributes(units.front().W, big, &occ, a.ranking, a.rigid_steps > 0)
+                     : dock_kernel_attributes(units.front().W, big, &occ, a.ranking, a.rigid_steps > 0);
+    };
+    auto launch_unit = [&](const Unit &u, int cap) -> cudaError_t {
+        a.ly = make_layout(u.nmax, rmax, a.P, u.W, want_pose);
+        a.lrt = make_layout_rt(u.nmax, rmax, a.P, want_pose);
+        a.cls = u.cls;
+        a.cls_off = u.cls >= 0 ? counters + kSizeClasses + 1 : nullptr;
+        a.work_counter = counters + (u.cls >= 0 ? u.cls : kSizeClasses);
+        a.item_cap = cap;
+        return multi ? launch_dock_multi(a, *multi, u.grid, u.smem, s) : launch_dock_batched(a, u.grid, u.smem, s);
+    };
+    // autotuning: a unit without a cached choice times every candidate on the
+    // first ligands of its class (same order, same ligands), keeps the fastest
+    // and re-clears its work counter; the results do not depend on the choice
+    if (ctx->autotune && !multi)
+        for (Unit &u : units) {
+            if (u.tuned) continue;
+            static const int kCand[3] = {4, 2, 1};
+            constexpr int kTuneCap = 4096;
+            float best = INFINITY;
+            Unit keep = u;
+            cudaEvent_t t0 = nullptr, t1 = nullptr;
+            if ((e = cudaEventCreate(&t0)) != cudaSuccess || (e = cudaEventCreate(&t1)) != cudaSuccess) {
+                if (t0) cudaEventDestroy(t0);
+                return fail(LG_ECUDA, std::string("autotuning events: ") + cudaGetErrorString(e));
+            }
+            for (int w : kCand) {
+                Unit v = u;
+                v.W = w;
+                if (configure(v) != LG_OK || v.W != w) continue;
+                if (v.grid > slots) continue;  // ranking slots are sized for the launches above
+                if ((e = cudaMemsetAsync(counters + (u.cls >= 0 ? u.cls : kSizeClasses), 0, 4, s)) != cudaSuccess ||
+                    (e = cudaEventRecord(t0, s)) != cudaSuccess || (e = launch_unit(v, kTuneCap)) != cudaSuccess ||
+                    (e = cudaEventRecord(t1, s)) != cudaSuccess || (e = cudaEventSynchronize(t1)) != cudaSuccess) {
+                    cudaEventDestroy(t0);
+                    cudaEventDestroy(t1);
+                    return fail(LG_ECUDA, std::string("autotuning: ") + cudaGetErrorString(e));
+                }
+                float ms = 0.0f;
+                cudaEventElapsedTime(&ms, t0, t1);
+                launches++;
+                if (ms < best) {
+                    best = ms;
+                    keep = v;
+                }
+            }
+            cudaEventDestroy(t0);
+            cudaEventDestroy(t1);
+            u = keep;
+            {
+                std::lock_guard<std::mutex> g(ctx->tune_mu);
+                ctx->tune[u.key] = u.W;
+            }
+            if ((e = cudaMemsetAsync(counters + (u.cls >= 0 ? u.cls : kSizeClasses), 0, 4, s)) != cudaSuccess)
+                return fail(LG_ECUDA, std::string("autotuning: ") + cudaGetErrorString(e));
+        }
+    if ((e = set_limit()) != cudaSuccess)
+        return fail(LG_ECUDA, std::string("dock kernel attributes: ") + cudaGetErrorString(e));
+    if (graph) {
+        // key: the launch arguments after carving, the units and the stream
+        std::vector<char> key(sizeof(DockArgs) + units.size() * 6 * sizeof(int) + sizeof(void *));
+        memcpy(key.data(), &a, sizeof(DockArgs));
+        char *kp = key.data() + sizeof(DockArgs);
+        for (const Unit &u : units) {
+            const int v[6] = {u.cls, u.nmax, u.W, u.smem, u.grid, u.occ};
+            memcpy(kp, v, sizeof(v));
+            kp += sizeof(v);
+        }
+        memcpy(kp, &s, sizeof(void *));
+        auto &cache = ctx->graph_cache;
+        int hit = -1;
+        for (int i = 0; i < (int)cache.size(); i++)
+            if (cache[i].key == key) hit = i;
+        if (hit < 0) {
+            const int before = launches;
+            cudaGraph_t g = nullptr;
+            if ((e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+                return fail(LG_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+            cudaError_t ec = cudaMemsetAsync(a.scr.hist, 0, 4 * kHistInts, s);
+            if (ec == cudaSuccess) ec = launch_prep(a, true, s, &launches);
+            for (const Unit &u : units)
+                if (ec == cudaSuccess) ec = launch_unit(u, 0);
+            e = cudaStreamEndCapture(s, &g);
+            if (ec != cudaSuccess || e != cudaSuccess) {
+                if (g) cudaGraphDestroy(g);
+                return fail(LG_ECUDA, std::string("graph capture: ") + cudaGetErrorString(ec != cudaSuccess ? ec : e));
+            }
+            lg_ctx::GraphRec rec;
+            rec.key = std::move(key);
+            rec.launches = launches - before + (int)units.size();
+            e = cudaGraphInstantiate(&rec.exec, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) return fail(LG_ECUDA, std::string("graph instantiation: ") + cudaGetErrorString(e));
+            if (cache.size() >= 8) {
+                cudaGraphExecDestroy(cache.front().exec);
+                cache.erase(cache.begin());
+            }
+            cache.push_back(std::move(rec));
+            hit = (int)cache.size() - 1;
+            st->graph = 2;
+        } else {
+            lg_ctx::GraphRec rec = std::move(cache[hit]);  // most recently used last
+            cache.erase(cache.begin() + hit);
+            cache.push_back(std::move(rec));
+            hit = (int)cache.size() - 1;
+            st->graph = 1;
+        }
+        if (timed) cudaEventRecord(tev[0], s);
+        if ((e = cudaGraphLaunch(cache[hit].exec, s)) != cudaSuccess)
+            return fail(LG_ECUDA, std::string("graph launch: ") + cudaGetErrorString(e));
+        if (timed) cudaEventRecord(tev[1], s);
+        const Unit &u0 = units.front();
+        st->launches = cache[hit].launches;
+        st->grid = u0.grid;
+        st->warps_per_cta = u0.W;
+        st->ctas_per_sm = u0.occ;
+        st->smem_bytes = u0.smem;
+        return LG_OK;
+    }
     if (timed) cudaEventRecord(tev[0], s);
-    if ((e = multi ? launch_dock_multi(a, *multi, grid, smem, s) : launch_dock_batched(a, grid, smem, s)) != cudaSuccess)
-        return fail(LG_ECUDA, std::string("dock launch: ") + cudaGetErrorString(e));
+    for (const Unit &u : units)
+        if ((e = launch_unit(u, 0)) != cudaSuccess)
+            return fail(LG_ECUDA, std::string("dock launch: ") + cudaGetErrorString(e));
     if (timed) cudaEventRecord(tev[1], s);
-    st->launches = launches + 1;
-    st->grid = grid;
-    st->warps_per_cta = W;
-    st->ctas_per_sm = occ;
-    st->smem_bytes = smem;
+    const Unit &u0 = units.front();
+    st->launches = launches + (int)units.size();
+    st->grid = u0.grid;
+    st->warps_per_cta = u0.W;
+    st->ctas_per_sm = u0.occ;
+    st->smem_bytes = u0.smem;
     return LG_OK;
 }
 
@@ -485,6 +667,7 @@ void lg_destroy(lg_ctx *c) {
     c->out_buf.release();
     c->scratch.release();
     for (auto &m : c->multi_out) m.release();
+    for (auto &g : c->graph_cache) cudaGraphExecDestroy(g.exec);
     c->flat_buf.release();
     for (auto s : c->plain_streams) cudaStreamDestroy(s);
     for (auto ev : c->join_events) cudaEventDestroy(ev);
@@ -610,7 +793,11 @@ int lg_dock_batch(lg_ctx *c, int32_t pid, const lg_ligand_batch *b, const lg_doc
     OutDev od;
     if ((rc = resolve_out(c, c->out_buf, b, o, S, P, p->rigid_steps, s, &A, &R, &od))) return rc;
     cudaEvent_t *tev = next_timing_events(c);
-    if ((rc = dock_device(c, pk->dev, bd, od, p, nmax, rmax, c->scratch, s, &c->stats, tev))) return rc;
+    const unsigned cmask = b->mem == LG_MEM_HOST ? host_class_mask(b) : (1u << kSizeClasses) - 1;
+    const bool graph_ok = b->mem == LG_MEM_DEVICE && o->mem == LG_MEM_DEVICE;
+    if ((rc = dock_device(c, pk->dev, bd, od, p, nmax, rmax, c->scratch, s, &c->stats, tev, nullptr, cmask,
+                          graph_ok)))
+        return rc;
     if (o->mem == LG_MEM_HOST) {
         if ((rc = fetch_out(od, o, L, S, P, A, R, p->rigid_steps, s))) return rc;
     }
@@ -696,6 +883,17 @@ int lg_set_option(lg_ctx *c, const char *key, int64_t v) {
     } else if (!strcmp(key, "serve_max_inflight")) {
         if (v < 1 || v > 64) return fail(LG_EINVAL, "serve_max_inflight must be in [1, 64]");
         c->serve_max_inflight = (int)v;
+    } else if (!strcmp(key, "graphs")) {
+        cudaSetDevice(c->device);
+        c->graphs = v != 0;
+        for (auto &g : c->graph_cache) cudaGraphExecDestroy(g.exec);
+        c->graph_cache.clear();
+    } else if (!strcmp(key, "size_classes")) {
+        c->size_classes = v != 0;
+    } else if (!strcmp(key, "autotune")) {
+        c->autotune = v != 0;
+        std::lock_guard<std::mutex> tg(c->tune_mu);
+        c->tune.clear();
     } else if (!strcmp(key, "multi_order")) {
         if (v != 0 && v != 1) return fail(LG_EINVAL, "multi_order must be 0 or 1");
         c->multi_pocket_major = v == 0 ? 1 : 0;

@@ -3,6 +3,8 @@
 
 #include <cuda_runtime.h>
 
+#include <array>
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -37,7 +39,9 @@ int fetch_out(const OutDev &d, const lg_dock_result *o, int L, int S, int P, int
               cudaStream_t s);
 int dock_device(lg_ctx *ctx, const PocketDev &pk, const BatchDev &bd, const OutDev &od, const lg_dock_params *p,
                 int nmax, int rmax, DevBuf &scratch, cudaStream_t s, lg_stats *st, cudaEvent_t *tev,
-                const MultiDev *multi = nullptr);
+                const MultiDev *multi = nullptr, unsigned class_mask = (1u << kSizeClasses) - 1,
+                bool allow_graph = false);
+unsigned host_class_mask(const lg_ligand_batch *b);
 int resolve_batch(lg_ctx *c, const lg_ligand_batch *b, const lg_dock_params *p, cudaStream_t s, BatchDev *bd,
                   int64_t *A, int64_t *R, int *nmax, int *rmax);
 int resolve_out(lg_ctx *c, DevBuf &buf, const lg_ligand_batch *b, const lg_dock_result *o, int S, int P, int Rs,
@@ -71,6 +75,20 @@ struct lg_ctx {
     lg::Server *server = nullptr;
     // several pockets in one launch (lg_dock_multi)
     std::vector<lg::DevBuf> multi_out;
+    // autotuner: warps per CTA chosen by timing, per (size class, restarts,
+    // passes, atoms, torsions, features) of the batched kernel
+    bool autotune = true;
+    bool size_classes = true;  // one batched launch per size class when the atom maximum exceeds 64
+    // captured CUDA graphs of device-resident lg_dock_batch calls (most recent last)
+    bool graphs = false;
+    struct GraphRec {
+        std::vector<char> key;
+        cudaGraphExec_t exec = nullptr;
+        int launches = 0;
+    };
+    std::vector<GraphRec> graph_cache;
+    std::mutex tune_mu;
+    std::map<std::array<int, 8>, int> tune;
     lg::DevBuf flat_buf;  // lg_flatten_batch: host-output staging and the preparation's unused outputs
     int multi_pocket_major = 1;
 };
