@@ -129,3 +129,37 @@ def test_many_small_requests_latency_recorded(served):
         lg.lg_stream_wait(ctx.h, t, 60000)
     lats = [lg.lg_stream_poll(ctx.h, t)[1] for t in tickets]
     assert all(0.0 <= x <= time.perf_counter() - t0 + 1e-3 for x in lats)
+
+
+def test_requests_with_rigid_moves_and_ranking(served):
+    # requests with rigid refinement and pose ranking are merged only with
+    # requests of the same kind; each result equals the direct call
+    import dataclasses
+    ctx, pid = served
+    base = synth.config_params(1)
+    kinds = [base, dataclasses.replace(base, rigid_steps=1),
+             dataclasses.replace(base, rigid_steps=2, cluster_rmsd=3.0, rescore_top=4)]
+    full = synth.config_ligands(1)
+    reqs, tickets = [], []
+    for k in range(9):
+        prm = kinds[k % 3]
+        sub = full.subset(range(20 * k, 20 * k + 20))
+        arrs = lg.host_batch_arrays(sub)
+        b = lg.make_batch_struct(arrs, sub.L)
+        p = lg.make_params(prm.restarts, prm.passes, prm.seed, prm.d_clash, cluster_rmsd=prm.cluster_rmsd,
+                           rescore_top=prm.rescore_top, rigid_steps=prm.rigid_steps, rigid_shift=prm.rigid_shift)
+        ranking = prm.cluster_rmsd > 0
+        r, outs = lg.alloc_result(sub.L, int(sub.atom_off[-1]), int(sub.rot_off[-1]), prm.restarts, prm.passes,
+                                  restart_tors=True, ranking=ranking, rigid_steps=prm.rigid_steps)
+        reqs.append((sub, prm, arrs, b, p, r, outs))
+        tickets.append(lg.lg_stream_submit(ctx.h, pid, b, p, r))
+    for t in tickets:
+        assert lg.lg_stream_wait(ctx.h, t, 60000) == lg.LG_OK
+    for sub, prm, _, _, _, _, outs in reqs:
+        d = ctx.dock(pid, sub, prm, restart_tors=True, restart_rigid=True)
+        S, P, R = prm.restarts, prm.passes, int(sub.rot_off[-1])
+        n = dict(score=sub.L, best_restart=sub.L, pose=3 * int(sub.atom_off[-1]), restart_tors=S * P * R,
+                 restart_rigid=sub.L * S * P * prm.rigid_steps, rank=sub.L * S, leader=sub.L * S)
+        for k, m in n.items():
+            if outs.get(k) is not None and m:
+                assert np.array_equal(outs[k][:m], d[k][:m]), (prm, k)
