@@ -173,13 +173,14 @@ def contiguous_request(pool, start, size):
     return arrs, size, a1 - a0, r1 - r0
 
 
-def serving_leg(ctx, pid, pool, params, rate_evals, load, duration_s, seed=5, max_size=4096):
+def serving_leg(ctx, pids, pool, params, rate_evals, load, duration_s, seed=5, max_size=4096):
     """Poisson arrivals of requests of floor(exp(U(0, ln max_size))) ligands at
-    `load` times `rate_evals` ligands/s for `duration_s` seconds, submitted to
-    the library's serving loop; latency is submit-to-done as the library
-    measures it."""
+    `load` times `rate_evals` ligands/s for `duration_s` seconds, each aimed at
+    a pocket drawn uniformly from `pids`, submitted to the library's serving
+    loop; latency is submit-to-done as the library measures it."""
     from paper_2110_11644_gb300 import lg
     rng = np.random.default_rng(seed)
+    target = rng.integers(0, len(pids), size=1 << 20)
     mean_size = (max_size - 1) / np.log(max_size)
     lam = load * rate_evals / mean_size
     n = int(lam * duration_s) + 1
@@ -200,7 +201,7 @@ def serving_leg(ctx, pid, pool, params, rate_evals, load, duration_s, seed=5, ma
             cursor += size
             b = lg.make_batch_struct(arrs, L)
             r, outs = lg.alloc_result(L, A, R, params.restarts, params.passes, device=False, pose=False, tors=False)
-            t = lg.lg_stream_submit(ctx.h, pid, b, p, r)
+            t = lg.lg_stream_submit(ctx.h, pids[int(target[i % len(target)])], b, p, r)
             live[t] = (arrs, outs, L)
             pending.append(t)
             i += 1
@@ -222,7 +223,8 @@ def serving_leg(ctx, pid, pool, params, rate_evals, load, duration_s, seed=5, ma
     return {"offered_load": load, "offered_evals_per_s": load * rate_evals, "duration_s": round(wall, 2),
             "requests": len(lat), "ligands": ligs, "sustained_evals_per_s": ligs / wall,
             "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
-            "request_sizes": f"floor(exp(U(0, ln {max_size}))) ligands, Poisson arrivals"}
+            "pockets": len(pids),
+            "request_sizes": f"floor(exp(U(0, ln {max_size}))) ligands, Poisson arrivals, uniform pocket"}
 
 
 def run_reference(args):
@@ -314,11 +316,9 @@ def multi_pocket_leg(ctx, dev, n_lig, steps, peak_tflops):
                     "ms": round(ms, 3), "evals_per_s": L / (ms / 1e3),
                     "frac": F / (dock_ms / 1e3) / 1e12 / peak_tflops})
     ctx.set_option("timing", 0)
-    for pid in pids:
-        ctx.unload_pocket(pid)
     return {"pockets": n_p, "ligands": L, "evals_per_step": L * n_p, "unit": UNIT, "restarts": S, "passes": P,
             "sample": f"{L} ligands of the throughput workload's generator against all {n_p} pockets",
-            **out, "per_pocket": per}
+            **out, "per_pocket": per}, pids
 
 
 def heavy_tailed_leg(ctx, pid, dev, n_lig, steps, peak_tflops):
@@ -419,8 +419,9 @@ def main():
     ap.add_argument("--plain-sample", type=int, default=4096)
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--serve-seconds", type=float, default=4.0, help="serving leg at 50%% of the measured peak (0 = off)")
-    ap.add_argument("--serve-loads", default="0.5", help="comma-separated offered loads for the serving leg")
+    ap.add_argument("--serve-seconds", type=float, default=3.0, help="seconds per offered load of the serving leg (0 = off)")
+    ap.add_argument("--serve-loads", default="0.25,0.5,0.9",
+                    help="comma-separated offered loads (fractions of the measured batched rate)")
     ap.add_argument("--multi-ligands", type=int, default=20000,
                     help="ligands of the 15-pocket leg (0 = off)")
     ap.add_argument("--heavy-ligands", type=int, default=1_000_000,
@@ -607,10 +608,6 @@ def main():
             cpu = {"value": rate, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
                    "sample": f"first {n_done} ligands of the workload, FP64 oracle, {secs:.1f} s"}
 
-        serving = None
-        if args.serve_seconds > 0:
-            serving = [serving_leg(ctx, pid, batch, params, value / world, float(ld), args.serve_seconds)
-                       for ld in args.serve_loads.split(",")]
 
         small = small_batch_leg(ctx, pid, dev, 64, 200) if world == 1 else None
 
@@ -618,9 +615,18 @@ def main():
         if args.heavy_ligands > 0 and world == 1:
             heavy = heavy_tailed_leg(ctx, pid, dev, args.heavy_ligands, 2, roofline["peak"])
 
-        multi = None
+        multi, mp_pids = None, []
         if args.multi_ligands > 0 and world == 1:
-            multi = multi_pocket_leg(ctx, dev, args.multi_ligands, 3, roofline["peak"])
+            multi, mp_pids = multi_pocket_leg(ctx, dev, args.multi_ligands, 3, roofline["peak"])
+
+        # serving: requests aimed at a random pocket of the 15-pocket set when it
+        # is loaded, else at the throughput pocket
+        serving = None
+        if args.serve_seconds > 0:
+            serving = [serving_leg(ctx, mp_pids or [pid], batch, params, value / world, float(ld), args.serve_seconds)
+                       for ld in args.serve_loads.split(",")]
+        for q in mp_pids:
+            ctx.unload_pocket(q)
 
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
