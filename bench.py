@@ -623,6 +623,8 @@ def main():
         # is loaded, else at the throughput pocket
         serving = None
         if args.serve_seconds > 0:
+            # warm-up (not reported): the serving slots grow their buffers once
+            serving_leg(ctx, mp_pids or [pid], batch, params, value / world, 0.9, 1.0, seed=4)
             serving = [serving_leg(ctx, mp_pids or [pid], batch, params, value / world, float(ld), args.serve_seconds)
                        for ld in args.serve_loads.split(",")]
         for q in mp_pids:

@@ -421,7 +421,10 @@ int lg_get_stats(lg_ctx *ctx, lg_stats *out);
  * 64 is docked by one launch per size class -- atoms <= 32, <= 64, more --
  * each with shared memory for its own maximum), "serve_max_inflight" (requests on the device at once, default 8),
  * "serve_mem_reserve_mb" (free device memory the server leaves untouched,
- * default 1024), "multi_order" (lg_dock_multi's visiting order: 0 =
+ * default 1024), "serve_max_merge" (ligands per merged batch, default 4,096),
+ * "serve_cross_pocket" (0/1, default 0: merge requests aimed at different
+ * pockets into one launch, each ligand docked against its own request's
+ * pocket), "multi_order" (lg_dock_multi's visiting order: 0 =
  * pocket-major, the default; 1 = ligand-major, a CTA docks one ligand against
  * every pocket in turn).  Errors: LG_EINVAL. */
 int lg_set_option(lg_ctx *ctx, const char *key, int64_t value);

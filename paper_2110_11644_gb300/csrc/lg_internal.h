@@ -230,6 +230,10 @@ struct MultiDev {
     int pocket_major;
     PocketDev pk[LG_MAX_MULTI_POCKETS];
     OutDev out[LG_MAX_MULTI_POCKETS];  // out[0] receives the preparation's status
+    // per-ligand mode (merged serving requests aimed at different pockets):
+    // ligand l is docked once, against pk[lig_pocket[l]], into the launch's
+    // own outputs; `out` is unused
+    const int32_t *lig_pocket;
 };
 
 // Byte size of the scratch of a launch, and its carving.

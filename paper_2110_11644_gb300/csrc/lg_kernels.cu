@@ -1057,7 +1057,7 @@ __global__ void __launch_bounds__(128, LG_RT_MIN_BLOCKS) k_dock_multi(const __gr
     extern __shared__ __align__(16) char sm[];
     __shared__ int s_item;
     const int L = A.batch.L;
-    const int items = M.pocket_major ? M.np * L : L;
+    const int items = (M.pocket_major && !M.lig_pocket) ? M.np * L : L;
     auto dock_one = [&](int p, int l) {
         const OutDev &O = M.out[p];
         if (p > 0) {
@@ -1080,7 +1080,11 @@ __global__ void __launch_bounds__(128, LG_RT_MIN_BLOCKS) k_dock_multi(const __gr
         const int item = s_item;
         __syncthreads();
         if (item >= items) break;
-        if (M.pocket_major) {
+        if (M.lig_pocket) {  // one pocket per ligand
+            const int l = A.order ? A.order[item] : item;
+            dock_ligand_rt<kRank, kRigid>(A, M.pk[M.lig_pocket[l]], A.out, l, sm);
+            __syncthreads();
+        } else if (M.pocket_major) {
             const int p = item / L, i = item - p * L;
             dock_one(p, A.order ? A.order[i] : i);
         } else {

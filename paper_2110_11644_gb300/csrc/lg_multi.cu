@@ -56,6 +56,7 @@ extern "C" int lg_dock_multi(lg_ctx *c, const int32_t *pocket_ids, int32_t n_poc
     memset(&m, 0, sizeof(m));
     m.np = n_pockets;
     m.pocket_major = c->multi_pocket_major;
+    m.lig_pocket = nullptr;
     for (int k = 0; k < n_pockets; k++) {
         m.pk[k] = pk[k];
         m.out[k] = od[k];

@@ -270,7 +270,10 @@ int dock_device(lg_ctx *ctx, const PocketDev &pk, const BatchDev &bd, const OutD
         a.scr = carve_scratch(scratch.p, L, rmax, a.ranking ? slots : 0, a.S, a.P, a.ly.nmax);
         if (!plain && (e = cudaMemsetAsync(a.scr.hist, 0, 4 * kHistInts, s)) != cudaSuccess)
             return fail(LG_ECUDA, std::string("scratch clear: ") + cudaGetErrorString(e));
-        if ((e = launch_prep(a, !plain, s, &launches)) != cudaSuccess)
+        // merged requests for several pockets keep their pocket-grouped order
+        // (one pocket's grids in L2 at a time), so no cost sort
+        const bool sort = !plain && !(multi && multi->lig_pocket);
+        if ((e = launch_prep(a, sort, s, &launches)) != cudaSuccess)
             return fail(LG_ECUDA, std::string("preparation launch: ") + cudaGetErrorString(e));
         return LG_OK;
     };
@@ -329,7 +332,7 @@ int dock_device(lg_ctx *ctx, const PocketDev &pk, const BatchDev &bd, const OutD
             u.W = std::max(1, u.W / 2);
         }
         if (u.occ <= 0) return fail(LG_EINVAL, "docking kernel does not fit on an SM");
-        const long items = multi && multi->pocket_major ? (long)L * multi->np : (long)L;
+        const long items = multi && multi->pocket_major && !multi->lig_pocket ? (long)L * multi->np : (long)L;
         u.grid = (int)std::max(1L, std::min((long)ctx_num_sms(ctx) * u.occ, items));
         return LG_OK;
     };
@@ -356,7 +359,7 @@ int dock_device(lg_ctx *ctx, const PocketDev &pk, const BatchDev &bd, const OutD
             return fail(LG_ENOMEM, "scratch allocation failed");
         a.scr = carve_scratch(scratch.p, L, rmax, a.ranking ? slots : 0, a.S, a.P, a.ly.nmax);
     }
-    a.order = a.scr.order;
+    a.order = (multi && multi->lig_pocket) ? nullptr : a.scr.order;
     int32_t *counters = a.scr.hist + kSortBuckets;
     // the kernels' shared-memory limit is per function: the largest of the units
     auto set_limit = [&]() -> cudaError_t {
@@ -880,6 +883,11 @@ int lg_set_option(lg_ctx *c, const char *key, int64_t v) {
     } else if (!strcmp(key, "warps_per_cta")) {
         if (v < 0 || v > 32) return fail(LG_EINVAL, "warps_per_cta must be in [0, 32]");
         c->warps_opt = (int)v;
+    } else if (!strcmp(key, "serve_max_merge")) {
+        if (v < 1 || v > (1 << 20)) return fail(LG_EINVAL, "serve_max_merge must be in [1, 2^20]");
+        c->serve_max_merge = (int)v;
+    } else if (!strcmp(key, "serve_cross_pocket")) {
+        c->serve_cross_pocket = v != 0;
     } else if (!strcmp(key, "serve_max_inflight")) {
         if (v < 1 || v > 64) return fail(LG_EINVAL, "serve_max_inflight must be in [1, 64]");
         c->serve_max_inflight = (int)v;

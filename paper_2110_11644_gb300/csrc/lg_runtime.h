@@ -70,6 +70,8 @@ struct lg_ctx {
     int tev_head = 0, tev_pending = 0;
     int warps_opt = 0;
     int serve_max_inflight = 8;
+    int serve_max_merge = 4096;  // ligands per merged batch
+    bool serve_cross_pocket = false;  // merge requests aimed at different pockets
     int64_t serve_reserve_mb = 1024;
     std::mutex serve_mu;  // guards `server` creation
     lg::Server *server = nullptr;

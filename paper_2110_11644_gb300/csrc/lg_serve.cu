@@ -4,13 +4,16 @@
 // asynchronous reader -> docker -> writer pipeline whose stages talk through
 // thread-safe queues (Sec. 3.2).  Here one worker thread per context takes
 // requests from a host queue, merges the queued requests that share a pocket
-// and parameters into one batch, and keeps up to `serve_max_inflight` such
+// and parameters into one batch (with the option serve_cross_pocket, requests
+// aimed at different pockets too: each ligand is then docked against its own
+// request's pocket in the same launch), and keeps up to `serve_max_inflight` such
 // batches on the device at once, each on its own stream (continuous batching:
 // a request that arrives while others run is admitted as soon as a slot and
 // enough free device memory are there).  Results are per ligand, so a
 // ligand's result does not depend on which requests it was merged with.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -71,8 +74,8 @@ struct Slot {
     bool busy = false;
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
-    DevBuf in, out, scratch;
-    PinnedBuf hin, hout;
+    DevBuf in, out, scratch, lp;  // lp: pocket slot of every merged ligand
+    PinnedBuf hin, hout, hlp;
     std::vector<std::shared_ptr<Request>> reqs;
     int L = 0;
     int64_t A = 0, R = 0;
@@ -91,13 +94,16 @@ struct Server {
     uint64_t next_ticket = 1;
     std::vector<Slot> slots;
     static constexpr size_t kMaxQueued = 1 << 16;
-    static constexpr int kMaxMerge = 1 << 16;  // ligands per merged batch
 };
 
-static bool same_kind(const Request &a, const Request &b) {
-    return a.pocket.cell_o == b.pocket.cell_o && a.params.restarts == b.params.restarts &&
+// Requests that can share one launch: same parameters and the same optional
+// outputs, and the same pocket unless cross-pocket merging is on (each ligand
+// is then docked against its own request's pocket).
+static bool same_kind(const Request &a, const Request &b, bool cross_pocket) {
+    return (cross_pocket || a.pocket.cell_o == b.pocket.cell_o) && a.params.restarts == b.params.restarts &&
            a.params.passes == b.params.passes && a.params.seed == b.params.seed &&
-           a.params.d_clash == b.params.d_clash && (a.out.pose != nullptr) == (b.out.pose != nullptr) &&
+           a.params.d_clash == b.params.d_clash && a.params.max_atoms == b.params.max_atoms &&
+           a.params.max_rot == b.params.max_rot && (a.out.pose != nullptr) == (b.out.pose != nullptr) &&
            (a.out.tors_idx != nullptr) == (b.out.tors_idx != nullptr) &&
            (a.out.restart_score != nullptr) == (b.out.restart_score != nullptr) &&
            (a.out.restart_tors != nullptr) == (b.out.restart_tors != nullptr) &&
@@ -207,7 +213,36 @@ static int launch_slot(Server *sv, Slot &sl) {
     lg_dock_params p = r0.params;
     p.mode = LG_MODE_BATCHED;
     lg_stats st{};
-    if ((rc2 = dock_device(c, r0.pocket, bd, od, &p, nmax, rmax, sl.scratch, sl.stream, &st, nullptr))) return rc2;
+    // distinct pockets of the merged requests (the merge keeps them <= LG_MAX_MULTI_POCKETS)
+    std::vector<PocketDev> pks;
+    std::vector<int> slot_of;
+    for (auto &r : sl.reqs) {
+        int k = 0;
+        while (k < (int)pks.size() && pks[k].cell_o != r->pocket.cell_o) k++;
+        if (k == (int)pks.size()) pks.push_back(r->pocket);
+        slot_of.push_back(k);
+    }
+    if (pks.size() == 1) {
+        if ((rc2 = dock_device(c, r0.pocket, bd, od, &p, nmax, rmax, sl.scratch, sl.stream, &st, nullptr))) return rc2;
+    } else {
+        if (sl.hlp.ensure(4 * (size_t)L) || sl.lp.ensure(4 * (size_t)L))
+            return fail(LG_ENOMEM, "pocket index allocation failed");
+        int32_t *hl = (int32_t *)sl.hlp.p;
+        int l0 = 0;
+        for (size_t q = 0; q < sl.reqs.size(); q++) {
+            for (int l = 0; l < sl.reqs[q]->L; l++) hl[l0 + l] = slot_of[q];
+            l0 += sl.reqs[q]->L;
+        }
+        if (cudaMemcpyAsync(sl.lp.p, hl, 4 * (size_t)L, cudaMemcpyHostToDevice, sl.stream) != cudaSuccess)
+            return fail(LG_ECUDA, "pocket index upload failed");
+        std::unique_ptr<MultiDev> m(new MultiDev());
+        memset(m.get(), 0, sizeof(MultiDev));
+        m->np = (int)pks.size();
+        for (int k = 0; k < m->np; k++) m->pk[k] = pks[k];
+        m->lig_pocket = (const int32_t *)sl.lp.p;
+        if ((rc2 = dock_device(c, pks[0], bd, od, &p, nmax, rmax, sl.scratch, sl.stream, &st, nullptr, m.get())))
+            return rc2;
+    }
     if ((rc2 = fetch_out(od, &hr, L, S, P, A, R, Rs, sl.stream))) return rc2;
     if (cudaEventRecord(sl.done, sl.stream) != cudaSuccess) return fail(LG_ECUDA, "event record failed");
     return LG_OK;
@@ -296,18 +331,23 @@ static void worker(Server *sv) {
             if (!free_sl) break;
             // merge queued requests of the same kind, in arrival order
             std::vector<std::shared_ptr<Request>> take;
+            std::vector<const float4 *> pockets;  // distinct pockets of the merged batch
+            const int max_merge = c->serve_max_merge;
             int Lm = 0;
             size_t bytes = 0;
             for (auto it = sv->queue.begin(); it != sv->queue.end();) {
-                if (!take.empty() && (!same_kind(*take[0], **it) || Lm + (*it)->L > Server::kMaxMerge)) {
+                const bool known = std::find(pockets.begin(), pockets.end(), (*it)->pocket.cell_o) != pockets.end();
+                if (!take.empty() && (!same_kind(*take[0], **it, c->serve_cross_pocket) || Lm + (*it)->L > max_merge ||
+                                      (!known && (int)pockets.size() >= LG_MAX_MULTI_POCKETS))) {
                     ++it;
                     continue;
                 }
+                if (!known) pockets.push_back((*it)->pocket.cell_o);
                 take.push_back(*it);
                 Lm += (*it)->L;
                 bytes += request_device_bytes(**it);
                 it = sv->queue.erase(it);
-                if (Lm >= Server::kMaxMerge) break;
+                if (Lm >= max_merge) break;
             }
             // admission by free device memory (always admit when the device is idle)
             size_t fr = 0, tot = 0;
@@ -319,6 +359,12 @@ static void worker(Server *sv) {
                 for (auto it = take.rbegin(); it != take.rend(); ++it) sv->queue.push_front(*it);
                 break;
             }
+            // requests for the same pocket side by side: the merged batch is
+            // docked in this order, one pocket's grids in L2 at a time
+            std::stable_sort(take.begin(), take.end(),
+                             [](const std::shared_ptr<Request> &x, const std::shared_ptr<Request> &y) {
+                                 return (uintptr_t)x->pocket.cell_o < (uintptr_t)y->pocket.cell_o;
+                             });
             for (auto &r : take) r->state = LG_REQ_RUNNING;
             free_sl->reqs = take;
             free_sl->busy = true;
@@ -382,8 +428,10 @@ void serve_stop(lg_ctx *c) {
         sl.in.release();
         sl.out.release();
         sl.scratch.release();
+        sl.lp.release();
         sl.hin.release();
         sl.hout.release();
+        sl.hlp.release();
         cudaStreamDestroy(sl.stream);
         cudaEventDestroy(sl.done);
     }

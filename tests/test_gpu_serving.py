@@ -163,3 +163,35 @@ def test_requests_with_rigid_moves_and_ranking(served):
         for k, m in n.items():
             if outs.get(k) is not None and m:
                 assert np.array_equal(outs[k][:m], d[k][:m]), (prm, k)
+
+
+def test_requests_for_different_pockets_share_launches():
+    # requests aimed at three pockets are merged into one launch (one pocket per
+    # ligand); every result equals docking the request alone against its pocket
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    ctx = lg.Context(0)
+    try:
+        ctx.set_option("serve_max_inflight", 1)  # one slot: everything queued is merged
+        ctx.set_option("serve_cross_pocket", 1)
+        pockets = [synth.config_pocket(1), synth.config_pocket(4, 0), synth.config_pocket(4, 3)]
+        pids = [ctx.load_pocket(p) for p in pockets]
+        params = synth.config_params(1)
+        full = synth.config_ligands(2, 400)
+        reqs, tickets = [], []
+        for k in range(18):
+            sub = full.subset(range(20 * k, 20 * k + 20))
+            req = _request(sub, params)
+            pid = pids[k % 3]
+            reqs.append((sub, pid, req))
+            tickets.append(lg.lg_stream_submit(ctx.h, pid, req["b"], req["p"], req["r"]))
+        for t in tickets:
+            assert lg.lg_stream_wait(ctx.h, t, 60000) == lg.LG_OK
+        for sub, pid, req in reqs:
+            alone = ctx.dock(pid, sub, params)
+            got = _trim(req, params.passes)
+            for k in got:
+                assert np.array_equal(got[k], alone[k][:len(got[k])]), k
+    finally:
+        ctx.close()
