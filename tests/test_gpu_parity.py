@@ -256,3 +256,42 @@ def test_rigid_refinement_throughput_ligands(ctx, cfg2_pocket):
     ctx.unload_pocket(pid)
     rep = check(cfg2_pocket, sub, prm, g)
     assert rep["rigid_deviations"] <= 0.01 * rep["rigid_decisions"] + 2, rep
+
+
+# ----------------------------------------------------------------------------- full sizes
+def _slice_outputs(batch, gpu, idx, S, P):
+    """The outputs of ligands idx of a docked batch, laid out as for batch.subset(idx)."""
+    aoff, roff = batch.atom_off, batch.rot_off
+    out = {k: [] for k in ("score", "best_restart", "status", "tors_idx", "pose", "restart_score", "restart_tors")}
+    for l in idx:
+        a0, a1, r0, r1 = int(aoff[l]), int(aoff[l + 1]), int(roff[l]), int(roff[l + 1])
+        out["score"].append(gpu["score"][l:l + 1])
+        out["best_restart"].append(gpu["best_restart"][l:l + 1])
+        out["status"].append(gpu["status"][l:l + 1])
+        out["tors_idx"].append(gpu["tors_idx"][P * r0:P * r1])
+        out["pose"].append(gpu["pose"][3 * a0:3 * a1])
+        out["restart_score"].append(gpu["restart_score"][S * l:S * (l + 1)])
+        out["restart_tors"].append(gpu["restart_tors"][S * P * r0:S * P * r1])
+    return {k: np.concatenate(v) for k, v in out.items()}
+
+
+@pytest.mark.parametrize("cfg,L", [(2, 100_000), (3, 1_000_000)])
+def test_full_size_launch_sampled_against_oracle(ctx, cfg2_pocket, cfg, L):
+    # the throughput (100,000 ligands) and heavy-tailed (1,000,000 ligands)
+    # workloads in the bench's launch configuration: device-resident batch,
+    # declared maxima, one persistent launch (per size class); sampled ligands
+    # are replayed in the oracle
+    pid = ctx.load_pocket(cfg2_pocket)
+    params = synth.config_params(cfg)
+    batch = synth.config_ligands(cfg, L)
+    S, P = params.restarts, params.passes
+    gpu = ctx.dock(pid, batch, params, device_io=True, restart_score=True, restart_tors=True,
+                   max_atoms=int(batch.n_atoms().max()), max_rot=max(1, int(batch.n_rot().max())))
+    ctx.unload_pocket(pid)
+    assert np.all(gpu["status"] == 0)
+    rng = np.random.default_rng(cfg)
+    idx = np.sort(rng.choice(L, size=48, replace=False))
+    idx = np.concatenate([idx, [int(np.argmax(batch.n_atoms()))]])  # and the largest ligand
+    sub = batch.subset(idx)
+    rep = check(cfg2_pocket, sub, params, _slice_outputs(batch, gpu, idx, S, P))
+    assert rep["deviations"] <= 0.01 * rep["decisions"] + 2, rep
