@@ -252,7 +252,10 @@ typedef struct {
  * Memory: if the batch and result are device memory the call is asynchronous
  * on `stream` and the caller keeps every buffer alive until the stream
  * reaches the end of the call; otherwise the library stages through its own
- * device buffers and returns after the results are in host memory.
+ * device buffers and returns after the results are in host memory.  Calls on
+ * one context share its scratch buffers: the library makes each call's stream
+ * wait for the previous call's device work, so asynchronous calls on
+ * different streams run one after the other on the device.
  * Errors: LG_EINVAL (bad parameters or sizes; per-ligand problems go to
  * status[] instead), LG_ENOPOCKET, LG_ENOMEM, LG_ECUDA. */
 int lg_dock_batch(lg_ctx *ctx, int32_t pocket_id, const lg_ligand_batch *batch, const lg_dock_params *params,

@@ -89,6 +89,7 @@ extern "C" int lg_flatten_batch(lg_ctx *c, const lg_ligand_batch *b, const lg_fl
     a.rmax_lim = rmax;
     a.scr = carve_scratch(c->scratch.p, L, rmax);
     int launches = 0;
+    if (scratch_acquire(c, s) != cudaSuccess) return fail(LG_ECUDA, "stream wait failed");
     cudaError_t e = launch_prep(a, false, s, &launches);
     if (e != cudaSuccess) return fail(LG_ECUDA, std::string("preparation launch: ") + cudaGetErrorString(e));
     FlatArgs f;
@@ -104,8 +105,10 @@ extern "C" int lg_flatten_batch(lg_ctx *c, const lg_ligand_batch *b, const lg_fl
     f.tors = tors;
     f.dsum = dsum;
     f.status = status;
-    if ((e = launch_flatten(f, L, s)) != cudaSuccess)
-        return fail(LG_ECUDA, std::string("flattening launch: ") + cudaGetErrorString(e));
+    e = launch_flatten(f, L, s);
+    const cudaError_t er = scratch_release(c, s);
+    if (e != cudaSuccess) return fail(LG_ECUDA, std::string("flattening launch: ") + cudaGetErrorString(e));
+    if (er != cudaSuccess) return fail(LG_ECUDA, "event record failed");
     if (host_out) {
         auto cp = [&](void *dst, const void *src, size_t n) {
             if (e == cudaSuccess && n) e = cudaMemcpyAsync(dst, src, n, cudaMemcpyDeviceToHost, s);

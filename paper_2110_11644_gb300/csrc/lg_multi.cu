@@ -63,7 +63,10 @@ extern "C" int lg_dock_multi(lg_ctx *c, const int32_t *pocket_ids, int32_t n_poc
     }
     cudaError_t e;
     cudaEvent_t *tev = next_timing_events(c);
-    if ((rc = dock_device(c, pk[0], bd, od[0], p, nmax, rmax, c->scratch, s, &c->stats, tev, &m))) return rc;
+    if (scratch_acquire(c, s) != cudaSuccess) return fail(LG_ECUDA, "stream wait failed");
+    rc = dock_device(c, pk[0], bd, od[0], p, nmax, rmax, c->scratch, s, &c->stats, tev, &m);
+    if (scratch_release(c, s) != cudaSuccess && rc == LG_OK) rc = fail(LG_ECUDA, "event record failed");
+    if (rc) return rc;
     if (omem == LG_MEM_HOST)
         for (int k = 0; k < n_pockets; k++)
             if ((rc = fetch_out(od[k], &outs[k], L, S, P, A, R, p->rigid_steps, s))) return rc;

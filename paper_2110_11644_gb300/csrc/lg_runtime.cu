@@ -212,9 +212,10 @@ unsigned host_class_mask(const lg_ligand_batch *b) {
 // autotuner's cached choice, else the restart-tile heuristic.
 static int tuned_warps(lg_ctx *c, const std::array<int, 8> &key, int S, bool *cached) {
     *cached = false;
-    if (c->warps_opt > 0) {
+    const int opt = c->warps_opt.load();
+    if (opt > 0) {
         *cached = true;
-        return std::min(c->warps_opt, 4);
+        return std::min(opt, 4);
     }
     std::lock_guard<std::mutex> g(c->tune_mu);
     auto it = c->tune.find(key);
@@ -642,6 +643,7 @@ int lg_create(int device, lg_ctx **out) {
         return fail(LG_ECUDA, std::string("device setup: ") + cudaGetErrorString(e));
     }
     for (int i = 0; i < 3; i++) cudaEventCreate(&c->ev[i]);
+    cudaEventCreateWithFlags(&c->scratch_ev, cudaEventDisableTiming);
     for (int i = 0; i < lg_ctx::kTimingRing; i++)
         for (int j = 0; j < 2; j++) cudaEventCreate(&c->tev[i][j]);
     float cs[LG_ANGLE_STEPS], sn[LG_ANGLE_STEPS];
@@ -676,6 +678,7 @@ void lg_destroy(lg_ctx *c) {
     for (auto ev : c->join_events) cudaEventDestroy(ev);
     for (int i = 0; i < 3; i++)
         if (c->ev[i]) cudaEventDestroy(c->ev[i]);
+    if (c->scratch_ev) cudaEventDestroy(c->scratch_ev);
     for (int i = 0; i < lg_ctx::kTimingRing; i++)
         for (int j = 0; j < 2; j++)
             if (c->tev[i][j]) cudaEventDestroy(c->tev[i][j]);
@@ -798,9 +801,10 @@ int lg_dock_batch(lg_ctx *c, int32_t pid, const lg_ligand_batch *b, const lg_doc
     cudaEvent_t *tev = next_timing_events(c);
     const unsigned cmask = b->mem == LG_MEM_HOST ? host_class_mask(b) : (1u << kSizeClasses) - 1;
     const bool graph_ok = b->mem == LG_MEM_DEVICE && o->mem == LG_MEM_DEVICE;
-    if ((rc = dock_device(c, pk->dev, bd, od, p, nmax, rmax, c->scratch, s, &c->stats, tev, nullptr, cmask,
-                          graph_ok)))
-        return rc;
+    if (scratch_acquire(c, s) != cudaSuccess) return fail(LG_ECUDA, "stream wait failed");
+    rc = dock_device(c, pk->dev, bd, od, p, nmax, rmax, c->scratch, s, &c->stats, tev, nullptr, cmask, graph_ok);
+    if (scratch_release(c, s) != cudaSuccess && rc == LG_OK) rc = fail(LG_ECUDA, "event record failed");
+    if (rc) return rc;
     if (o->mem == LG_MEM_HOST) {
         if ((rc = fetch_out(od, o, L, S, P, A, R, p->rigid_steps, s))) return rc;
     }

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <array>
+#include <atomic>
 #include <map>
 #include <mutex>
 #include <string>
@@ -68,10 +69,11 @@ struct lg_ctx {
     static constexpr int kTimingRing = 64;
     cudaEvent_t tev[kTimingRing][2] = {};
     int tev_head = 0, tev_pending = 0;
-    int warps_opt = 0;
-    int serve_max_inflight = 8;
-    int serve_max_merge = 4096;  // ligands per merged batch
-    bool serve_cross_pocket = false;  // merge requests aimed at different pockets
+    // options read by the serving worker too (lg_set_option writes them)
+    std::atomic<int> warps_opt{0};
+    int serve_max_inflight = 8;  // read when the server starts
+    std::atomic<int> serve_max_merge{4096};        // ligands per merged batch
+    std::atomic<bool> serve_cross_pocket{false};   // merge requests aimed at different pockets
     int64_t serve_reserve_mb = 1024;
     std::mutex serve_mu;  // guards `server` creation
     lg::Server *server = nullptr;
@@ -79,10 +81,10 @@ struct lg_ctx {
     std::vector<lg::DevBuf> multi_out;
     // autotuner: warps per CTA chosen by timing, per (size class, restarts,
     // passes, atoms, torsions, features) of the batched kernel
-    bool autotune = true;
-    bool size_classes = true;  // one batched launch per size class when the atom maximum exceeds 64
+    std::atomic<bool> autotune{true};
+    std::atomic<bool> size_classes{true};  // one batched launch per size class when the atom maximum exceeds 64
     // captured CUDA graphs of device-resident lg_dock_batch calls (most recent last)
-    bool graphs = false;
+    std::atomic<bool> graphs{false};
     struct GraphRec {
         std::vector<char> key;
         cudaGraphExec_t exec = nullptr;
@@ -93,11 +95,17 @@ struct lg_ctx {
     std::map<std::array<int, 8>, int> tune;
     lg::DevBuf flat_buf;  // lg_flatten_batch: host-output staging and the preparation's unused outputs
     int multi_pocket_major = 1;
+    // orders the calls that share `scratch` (and `flat_buf`) on the device: a
+    // call's stream waits for the previous such call's work to finish
+    cudaEvent_t scratch_ev = nullptr;
 };
 
 namespace lg {
 
 inline int ctx_num_sms(lg_ctx *c) { return c->num_sms; }
+// Bracket the device work of a call that uses the context's scratch buffers.
+inline cudaError_t scratch_acquire(lg_ctx *c, cudaStream_t s) { return cudaStreamWaitEvent(s, c->scratch_ev, 0); }
+inline cudaError_t scratch_release(lg_ctx *c, cudaStream_t s) { return cudaEventRecord(c->scratch_ev, s); }
 inline int ctx_warps_opt(lg_ctx *c) { return c->warps_opt; }
 inline bool ctx_timing(lg_ctx *c) { return c->timing; }
 inline cudaEvent_t ctx_event(lg_ctx *c, int i) { return c->ev[i]; }

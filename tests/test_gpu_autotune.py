@@ -125,3 +125,28 @@ def test_graph_capture_and_replay(ctx, cfg1):
     finally:
         ctx.set_option("graphs", 0)
         ctx.unload_pocket(pid)
+
+
+def test_async_calls_on_two_streams_share_scratch_safely(ctx, cfg1):
+    # two device-memory calls issued back to back on different streams use the
+    # same context scratch; the library orders them on the device
+    import torch
+    pocket, full, params = cfg1
+    pid = ctx.load_pocket(pocket)
+    a_b, b_b = full.subset(range(0, 128)), full.subset(range(128, 256))
+    res = []
+    for batch in (a_b, b_b):
+        L, A, R = batch.L, int(batch.atom_off[-1]), int(batch.rot_off[-1])
+        darr = lg.device_batch_arrays(batch)
+        res.append((batch, darr, lg.make_batch_struct(darr, L),
+                    lg.alloc_result(L, A, R, params.restarts, params.passes, device=True)))
+    p = lg.make_params(params.restarts, params.passes, params.seed, params.d_clash)
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    for (batch, _, b, (r, _)), s in zip(res, (s1, s2)):
+        lg.lg_dock_batch(ctx.h, pid, b, p, r, s.cuda_stream)
+    torch.cuda.synchronize()
+    for batch, _, _, (_, outs) in res:
+        ref = ctx.dock(pid, batch, params)
+        assert np.array_equal(outs["score"][:batch.L].cpu().numpy(), ref["score"])
+        assert np.array_equal(outs["best_restart"][:batch.L].cpu().numpy(), ref["best_restart"])
+    ctx.unload_pocket(pid)
