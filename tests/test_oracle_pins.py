@@ -219,6 +219,66 @@ def test_energy_at_nodes_equals_direct_pairwise_sum(cfg1):
         assert np.all(np.abs(E - want) <= 2e-6 * scale)
 
 
+def test_interpolation_error_within_second_derivative_bound(cfg1):
+    # off the nodes, the oracle's trilinear lookup of the generator's grids
+    # equals the direct pairwise sum up to the textbook interpolation bound
+    # (h^2/8) * sum_i max |d^2 f / dx_i^2| over the cell.  Atoms whose cutoff
+    # sphere crosses the cell make the field jump there; their terms enter the
+    # reference as the trilinear interpolation of their values at the 8 nodes.
+    # (Caught by it: transposed or shifted grids, a wrong interpolation order.)
+    from paper_2110_11644_gb300.synth import (COULOMB_CUT, COULOMB_K, COULOMB_RMIN, LJ_CAP, LJ_CUT, LJ_EPS,
+                                              LJ_R0, LJ_RMIN)
+    pocket = cfg1[0]
+    h, n = float(pocket.h), pocket.n
+    atoms, qa = pocket.atoms_xyz, pocket.atoms_q
+    rng = np.random.default_rng(21)
+    g = rng.uniform(1, n - 2, size=(4000, 3))
+    pts = pocket.origin + h * g
+    dmin = np.linalg.norm(pts[:, None] - atoms[None], axis=-1).min(1)
+    pts, g = pts[dmin > 3.5][:300], g[dmin > 3.5][:300]
+    assert len(pts) >= 100
+    e_int = oracle.trilinear(pocket, "e", pts)
+    v_int = oracle.trilinear(pocket, "v", pts)
+    corner = np.array([[c, b, a] for a in (0, 1) for b in (0, 1) for c in (0, 1)], np.float64)  # x fastest
+
+    def coul(d):
+        r = np.maximum(d, COULOMB_RMIN)
+        return np.where(d < COULOMB_CUT, COULOMB_K / (4 * r * r), 0.0)
+
+    def lj(d):
+        x = LJ_R0 / np.maximum(d, LJ_RMIN)
+        return np.where(d < LJ_CUT, LJ_EPS * (x ** 12 - 2 * x ** 6), 0.0)
+
+    checked_v = 0
+    for k in range(len(pts)):
+        f = g[k] - np.floor(g[k])
+        cxyz = pocket.origin + h * (np.floor(g[k]) + corner)
+        w = np.prod(np.where(corner == 1, f, 1 - f), axis=1)           # trilinear weights of the nodes
+        dc = np.linalg.norm(cxyz[:, None] - atoms[None], axis=-1)     # [8, na]
+        dp = np.linalg.norm(pts[k] - atoms, axis=-1)
+        r_lo = np.maximum(dc.min(0) - h * np.sqrt(3.0), 1e-3)          # lower bound of r over the cell
+        r_hi = dc.max(0)
+        # electrostatics: f = K q / (4 r^2), sum_i |f_ii| <= 18 K |q| / (4 r^4)
+        cross = (r_lo < COULOMB_CUT) & (r_hi >= COULOMB_CUT)
+        smooth = (r_hi < COULOMB_CUT) & ~cross
+        ref = np.sum(qa[smooth] * coul(dp[smooth])) + np.sum(qa[cross] * (w @ coul(dc[:, cross])))
+        bound = (h * h / 8) * np.sum(18 * COULOMB_K * np.abs(qa[smooth]) / (4 * r_lo[smooth] ** 4))
+        assert abs(e_int[k] - ref) <= bound + 1e-6 * (abs(ref) + 1), (k, e_int[k], ref, bound)
+        # vdW-like: |f''| + 2 |f'| / r bounds sum_i |f_ii|; only where the cap is not reached
+        if (lj(dc).sum(1) >= LJ_CAP).any() or lj(dp).sum() >= LJ_CAP:
+            continue
+        cross = (r_lo < LJ_CUT) & (r_hi >= LJ_CUT)
+        smooth = (r_hi < LJ_CUT) & ~cross
+        r = r_lo[smooth]
+        f1 = LJ_EPS * (12 * LJ_R0 ** 12 / r ** 13 + 12 * LJ_R0 ** 6 / r ** 7)
+        f2 = LJ_EPS * (156 * LJ_R0 ** 12 / r ** 14 + 84 * LJ_R0 ** 6 / r ** 8)
+        ref = np.sum(lj(dp[smooth])) + np.sum(w @ lj(dc[:, cross]))
+        bound = (h * h / 8) * np.sum(f2 + 2 * f1 / r)
+        assert abs(v_int[k] - ref) <= bound + 1e-6 * (abs(ref) + 1), (k, v_int[k], ref, bound)
+        checked_v += 1
+    assert checked_v >= 100
+
+
 def test_energy_outside_box_adds_linear_penalty(cfg1):
     pocket = cfg1[0]
     hi = pocket.origin + pocket.h * (pocket.n - 1)
