@@ -295,3 +295,52 @@ def test_full_size_launch_sampled_against_oracle(ctx, cfg2_pocket, cfg, L):
     sub = batch.subset(idx)
     rep = check(cfg2_pocket, sub, params, _slice_outputs(batch, gpu, idx, S, P))
     assert rep["deviations"] <= 0.01 * rep["decisions"] + 2, rep
+
+
+# ----------------------------------------------------------------------------- invariants of GPU poses
+def _bond_distance(parent):
+    N = len(parent)
+    adj = [[] for _ in range(N)]
+    for i in range(1, N):
+        adj[i].append(int(parent[i]))
+        adj[int(parent[i])].append(i)
+    D = np.full((N, N), 10 ** 6)
+    for s in range(N):
+        D[s, s] = 0
+        front = [s]
+        while front:
+            nxt = []
+            for v in front:
+                for w in adj[v]:
+                    if D[s, w] > D[s, v] + 1:
+                        D[s, w] = D[s, v] + 1
+                        nxt.append(w)
+            front = nxt
+    return D
+
+
+def test_gpu_poses_keep_geometry_and_are_clash_free(ctx, cfg2_pocket):
+    # the GPU's best poses: every bond length equals the input's to 1e-5 A
+    # (measured: 3e-6 A after 3 passes of FP32 moves), and no pair three or
+    # more bonds apart is closer than d_clash (up to the near-tie margin)
+    pid = ctx.load_pocket(cfg2_pocket)
+    params = synth.config_params(2)
+    batch = synth.config_ligands(2, 200)
+    g = ctx.dock(pid, batch, params)
+    ctx.unload_pocket(pid)
+    worst_bond = 0.0
+    dc2 = float(np.float32(params.d_clash)) ** 2
+    for l in range(batch.L):
+        a0, a1 = int(batch.atom_off[l]), int(batch.atom_off[l + 1])
+        par = batch.parent[a0:a1].astype(int)
+        X0 = np.stack([batch.x[a0:a1], batch.y[a0:a1], batch.z[a0:a1]], 1).astype(np.float64)
+        X = g["pose"][3 * a0:3 * a1].reshape(-1, 3).astype(np.float64)
+        b0 = np.linalg.norm(X0[1:] - X0[par[1:]], axis=1)
+        b1 = np.linalg.norm(X[1:] - X[par[1:]], axis=1)
+        worst_bond = max(worst_bond, float(np.abs(b1 - b0).max(initial=0.0)))
+        D = _bond_distance(par)
+        i, j = np.nonzero(np.triu(D >= 3))
+        d2 = ((X[i] - X[j]) ** 2).sum(1)
+        assert np.all(d2 >= dc2 * (1 - 1e-4)), (l, float(d2.min()))
+    assert worst_bond <= 1e-5, worst_bond
+    print("worst bond-length change (A):", worst_bond)
