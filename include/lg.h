@@ -414,9 +414,9 @@ int lg_get_stats(lg_ctx *ctx, lg_stats *out);
  * autotuner's or the default choice, else 1..4 for every batched launch),
  * "autotune" (0/1, default 1; setting it clears the tuned choices: with it on,
  * the first batched call of a (size class, restarts, passes, atom and torsion
- * maxima, features) combination times 4, 2 and 1 warps per CTA on up to 4,096
- * ligands of that class and keeps the fastest; results do not depend on the
- * choice), "graphs" (0/1, default 0: an lg_dock_batch call with device
+ * maxima, features) combination times 4, 2 and 1 warps per CTA on the same
+ * even sample of that class's ligands (16 waves of the widest grid, at least
+ * 4,096) and keeps the fastest; results do not depend on the choice), "graphs" (0/1, default 0: an lg_dock_batch call with device
  * batch and result on a non-default stream is captured, preparation and
  * docking kernels together, as a CUDA graph and replayed when a later call
  * has the same arguments; with timing on, such a call's device time then

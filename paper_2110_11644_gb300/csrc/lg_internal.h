@@ -182,7 +182,7 @@ struct DockArgs {
     int32_t *work_counter;     // batched mode: next item of the persistent loop
     const int32_t *cls_off;    // batched mode: class boundaries in `order` (NULL = the whole batch)
     int cls;                   // with cls_off: the size class this launch docks
-    int item_cap;              // > 0: dock only the first item_cap items (autotuning trials)
+    int item_cap;              // > 0: dock only item_cap items evenly spread over the range (autotuning trials)
     int sort_classes;          // preparation: 1 = size class major, then cost; 0 = cost only
 };
 

@@ -832,9 +832,10 @@ __device__ __forceinline__ int sweep_bond_rt(const DockArgs &A, const GridK &G, 
 // candidate's score is the FP64 sum, in atom order, of the FP32 overlap
 // lookups of all atoms at their moved positions; the best (highest score,
 // lowest candidate) moves the atoms and turns the bond axes.
-__device__ __forceinline__ void rigid_moves_rt(const DockArgs &A, const GridK &Go, const OutDev &O, const RtView &v,
+__device__ __forceinline__ bool rigid_moves_rt(const DockArgs &A, const GridK &Go, const OutDev &O, const RtView &v,
                                                int l, int r, int ps, int N, int R, int rs, int g, bool valid) {
     const float c0 = 0.5f * Go.gmax, dg = A.rigid_shift_g, ca = c_cos[1], sa = c_sin[1];
+    bool moved = false;
     for (int j = 0; j < A.rigid_steps; ++j) {
         float sx = 0.0f, sy = 0.0f, sz = 0.0f;  // centroid: sums over atoms i = g (mod 4), (s0 + s1) + (s2 + s3)
         for (int i = g; i < N; i += kLanesPerRestart) {
@@ -875,6 +876,7 @@ __device__ __forceinline__ void rigid_moves_rt(const DockArgs &A, const GridK &G
         if (valid && g == 0 && O.restart_rigid)
             O.restart_rigid[(((size_t)l * A.S + r) * A.P + ps) * A.rigid_steps + j] = (uint8_t)bC;
         __syncwarp();
+        moved = moved || bC != 0;
         if (bC != 0) {
             for (int i = g; i < N; i += kLanesPerRestart) {
                 const float3 y = rigid_candidate(bC, v.Xx[i * kTile + rs], v.Xy[i * kTile + rs], v.Xz[i * kTile + rs],
@@ -888,6 +890,7 @@ __device__ __forceinline__ void rigid_moves_rt(const DockArgs &A, const GridK &G
         }
         __syncwarp();
     }
+    return moved;
 }
 
 // kRank: pose ranking on; kRigid: rigid refinement on (separate
@@ -940,11 +943,23 @@ __device__ __forceinline__ void dock_ligand_rt(const DockArgs &A, const PocketDe
         __syncwarp();
         // 2. greedy torsion sweep
         for (int ps = 0; ps < P; ++ps) {
+            bool moved = false;
             for (int k = 0; k < R; ++k) {
                 const int t = sweep_bond_rt(A, Go, cv, v, N, R, k, rs, g, valid, cs, sn);
                 if (g == 0) v.tcur[(ps * R + k) * kTile + rs] = (uint8_t)t;
+                moved = moved || t != 0;
             }
-            if (kRigid) rigid_moves_rt(A, Go, O, v, l, r, ps, N, R, rs, g, valid);
+            if (kRigid) moved = rigid_moves_rt(A, Go, O, v, l, r, ps, N, R, rs, g, valid) || moved;
+            // a pass in which no restart of the tile moved leaves every state as
+            // it found it, so each later pass would repeat it move for move:
+            // record their decisions (all step 0) without running them
+            if (ps + 1 < P && !__any_sync(LG_FULL, valid && moved)) {
+                for (int q = (ps + 1) * R + g; q < P * R; q += kLanesPerRestart) v.tcur[q * kTile + rs] = 0;
+                if (kRigid && valid && g == 0 && O.restart_rigid)
+                    for (int q = (ps + 1) * A.rigid_steps; q < P * A.rigid_steps; ++q)
+                        O.restart_rigid[((size_t)l * A.S + r) * A.P * A.rigid_steps + q] = 0;
+                break;
+            }
         }
         __syncwarp();
         // 3. pose score: FP32 per-atom terms; FP64 sums s_g over atoms i = g
@@ -1034,9 +1049,14 @@ __global__ void __launch_bounds__(128, LG_RT_MIN_BLOCKS) k_dock_batched(const __
                 first = A.cls_off[2 - A.cls];
                 count = A.cls_off[3 - A.cls] - first;
             }
-            if (A.item_cap > 0) count = min(count, A.item_cap);
+            int stride = 1;
+            if (A.item_cap > 0 && count > A.item_cap) {  // autotuning trial: an even sample of the range
+                stride = count / A.item_cap;
+                count = A.item_cap;
+            }
             const int item = atomicAdd(A.work_counter, 1);
-            s_lig = item < count ? (A.order ? A.order[first + item] : first + item) : -1;
+            const int at = first + item * stride;
+            s_lig = item < count ? (A.order ? A.order[at] : at) : -1;
         }
         __syncthreads();
         const int l = s_lig;

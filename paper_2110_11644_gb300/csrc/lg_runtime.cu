@@ -348,10 +348,18 @@ int dock_device(lg_ctx *ctx, const PocketDev &pk, const BatchDev &bd, const OutD
         units.push_back(u);
     }
     a.sort_classes = split ? 1 : 0;
+    static const int kCand[3] = {4, 2, 1};  // autotuning candidates (warps per CTA)
     int slots = 1;
     for (const Unit &u : units) slots = std::max(slots, u.grid);
     bool need_tune = false;  // tuning trials run eagerly on the sorted batch: no graph for this call
     for (const Unit &u : units) need_tune = need_tune || (ctx->autotune && !multi && !u.tuned);
+    if (need_tune)  // ranking slots for every candidate's grid
+        for (const Unit &u : units)
+            for (int w : kCand) {
+                Unit v = u;
+                v.W = w;
+                if (!u.tuned && configure(v) == LG_OK) slots = std::max(slots, v.grid);
+            }
     const bool graph = allow_graph && ctx->graphs && !multi && s != nullptr && !need_tune;
     if (!graph) {
         if (int rc = setup_scratch(slots)) return rc;
@@ -384,8 +392,15 @@ int dock_device(lg_ctx *ctx, const PocketDev &pk, const BatchDev &bd, const OutD
     if (ctx->autotune && !multi)
         for (Unit &u : units) {
             if (u.tuned) continue;
-            static const int kCand[3] = {4, 2, 1};
-            constexpr int kTuneCap = 4096;
+            // the same ligands for every candidate: an even sample of the
+            // class's cost order, 16 waves of the widest candidate's grid (at
+            // least 4,096)
+            int cap = 4096;
+            for (int w : kCand) {
+                Unit v = u;
+                v.W = w;
+                if (configure(v) == LG_OK && v.W == w) cap = std::max(cap, 16 * v.grid);
+            }
             float best = INFINITY;
             Unit keep = u;
             cudaEvent_t t0 = nullptr, t1 = nullptr;
@@ -399,7 +414,7 @@ int dock_device(lg_ctx *ctx, const PocketDev &pk, const BatchDev &bd, const OutD
                 if (configure(v) != LG_OK || v.W != w) continue;
                 if (v.grid > slots) continue;  // ranking slots are sized for the launches above
                 if ((e = cudaMemsetAsync(counters + (u.cls >= 0 ? u.cls : kSizeClasses), 0, 4, s)) != cudaSuccess ||
-                    (e = cudaEventRecord(t0, s)) != cudaSuccess || (e = launch_unit(v, kTuneCap)) != cudaSuccess ||
+                    (e = cudaEventRecord(t0, s)) != cudaSuccess || (e = launch_unit(v, cap)) != cudaSuccess ||
                     (e = cudaEventRecord(t1, s)) != cudaSuccess || (e = cudaEventSynchronize(t1)) != cudaSuccess) {
                     cudaEventDestroy(t0);
                     cudaEventDestroy(t1);
