@@ -261,14 +261,16 @@ typedef struct {
 int lg_dock_batch(lg_ctx *ctx, int32_t pocket_id, const lg_ligand_batch *batch, const lg_dock_params *params,
                   lg_dock_result *out, void *stream);
 
-/* Dock one batch against several loaded pockets in one launch: the
- * screening campaign's pattern, a ligand library against every binding site
- * (paper Sec. 1 and 4: 15 binding sites).  Results are those of n_pockets
- * lg_dock_batch calls, bit for bit: outs[k] receives the results for
- * pocket_ids[k].  The per-ligand preparation (validation, subtree ends,
- * centroid, cost order) runs once for all pockets; the docking kernel visits
- * (pocket, ligand) pairs pocket-major (context option "multi_order"), so the
- * grids of one pocket at a time need to be in L2.
+/* Dock one batch against several loaded pockets: the screening campaign's
+ * pattern, a ligand library against every binding site (paper Sec. 1 and 4:
+ * 15 binding sites).  Results are those of n_pockets lg_dock_batch calls, bit
+ * for bit: outs[k] receives the results for pocket_ids[k].  The per-ligand
+ * preparation (validation, subtree ends, centroid, cost order) runs once for
+ * all pockets.  Visiting order (context option "multi_order"): pocket-major,
+ * the default, docks the batch against each pocket in turn with one
+ * persistent launch per pocket, so only one pocket's grids need to be in L2;
+ * ligand-major is one launch in which a CTA docks its ligand against every
+ * pocket.
  *   - Batched mode only (params->mode = LG_MODE_BATCHED).
  *   - Every outs[k] has the same mem and the same set of optional outputs.
  *   - Memory and errors as lg_dock_batch.  1 <= n_pockets <= 64. */

@@ -1077,7 +1077,14 @@ __global__ void __launch_bounds__(128, LG_RT_MIN_BLOCKS) k_dock_multi(const __gr
     extern __shared__ __align__(16) char sm[];
     __shared__ int s_item;
     const int L = A.batch.L;
-    const int items = (M.pocket_major && !M.lig_pocket) ? M.np * L : L;
+    int items = (M.pocket_major && !M.lig_pocket) ? M.np * L : L;
+    int stride = 1;
+    if (A.item_cap > 0) {  // autotuning trial: an even sample of the ligands (of the first pocket when
+                           // pocket-major, as the full launch keeps one pocket's grids in L2 at a time)
+        const int span = min(items, L);
+        stride = max(1, span / A.item_cap);
+        items = min(A.item_cap, span);
+    }
     auto dock_one = [&](int p, int l) {
         const OutDev &O = M.out[p];
         if (p > 0) {
@@ -1100,15 +1107,16 @@ __global__ void __launch_bounds__(128, LG_RT_MIN_BLOCKS) k_dock_multi(const __gr
         const int item = s_item;
         __syncthreads();
         if (item >= items) break;
+        const int at = item * stride;
         if (M.lig_pocket) {  // one pocket per ligand
-            const int l = A.order ? A.order[item] : item;
+            const int l = A.order ? A.order[at] : at;
             dock_ligand_rt<kRank, kRigid>(A, M.pk[M.lig_pocket[l]], A.out, l, sm);
             __syncthreads();
         } else if (M.pocket_major) {
-            const int p = item / L, i = item - p * L;
+            const int p = at / L, i = at - p * L;
             dock_one(p, A.order ? A.order[i] : i);
         } else {
-            const int l = A.order ? A.order[item] : item;
+            const int l = A.order ? A.order[at] : at;
             for (int p = 0; p < M.np; ++p) dock_one(p, l);
         }
     }

@@ -64,7 +64,34 @@ extern "C" int lg_dock_multi(lg_ctx *c, const int32_t *pocket_ids, int32_t n_poc
     cudaError_t e;
     cudaEvent_t *tev = next_timing_events(c);
     if (scratch_acquire(c, s) != cudaSuccess) return fail(LG_ECUDA, "stream wait failed");
-    rc = dock_device(c, pk[0], bd, od[0], p, nmax, rmax, c->scratch, s, &c->stats, tev, &m);
+    if (m.pocket_major) {
+        // pocket-major: one persistent launch per pocket, all on the preparation
+        // and cost order of the first (pockets in turn keep one pocket's grids
+        // in L2; measured faster than one launch over all (pocket, ligand) items)
+        if (tev) cudaEventRecord(tev[0], s);
+        for (int k = 0; k < n_pockets && rc == LG_OK; k++) {
+            if (k > 0) {  // the preparation's per-ligand status (and the results of rejected ligands)
+                e = cudaMemcpyAsync(od[k].status, od[0].status, 4 * (size_t)L, cudaMemcpyDeviceToDevice, s);
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(od[k].score, od[0].score, 8 * (size_t)L, cudaMemcpyDeviceToDevice, s);
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(od[k].best_restart, od[0].best_restart, 4 * (size_t)L,
+                                        cudaMemcpyDeviceToDevice, s);
+                if (e != cudaSuccess) {
+                    rc = fail(LG_ECUDA, std::string("status copy: ") + cudaGetErrorString(e));
+                    break;
+                }
+            }
+            lg_stats st = c->stats;
+            rc = dock_device(c, pk[k], bd, od[k], p, nmax, rmax, c->scratch, s, &st, nullptr, nullptr,
+                             (1u << kSizeClasses) - 1, false, k > 0);
+            if (k == 0) c->stats = st;
+            else c->stats.launches += st.launches;
+        }
+        if (tev) cudaEventRecord(tev[1], s);
+    } else {
+        rc = dock_device(c, pk[0], bd, od[0], p, nmax, rmax, c->scratch, s, &c->stats, tev, &m);
+    }
     if (scratch_release(c, s) != cudaSuccess && rc == LG_OK) rc = fail(LG_ECUDA, "event record failed");
     if (rc) return rc;
     if (omem == LG_MEM_HOST)

@@ -228,7 +228,7 @@ static int tuned_warps(lg_ctx *c, const std::array<int, 8> &key, int S, bool *ca
 
 int dock_device(lg_ctx *ctx, const PocketDev &pk, const BatchDev &bd, const OutDev &od, const lg_dock_params *p,
                 int nmax, int rmax, DevBuf &scratch, cudaStream_t s, lg_stats *st, cudaEvent_t *tev,
-                const MultiDev *multi, unsigned class_mask, bool allow_graph) {
+                const MultiDev *multi, unsigned class_mask, bool allow_graph, bool reuse_prep) {
     const bool timed = tev != nullptr;
     DockArgs a;
     memset(&a, 0, sizeof(a));
@@ -342,7 +342,9 @@ int dock_device(lg_ctx *ctx, const PocketDev &pk, const BatchDev &bd, const OutD
         Unit u;
         u.cls = c;
         u.nmax = c < 0 ? nmax : std::min(nmax, class_bound(c));
-        u.key = {c, a.S, a.P, u.nmax, rmax, a.ranking, a.rigid_steps > 0 ? 1 : 0, want_pose + 2 * (multi ? 1 : 0)};
+        // launch kind: one pocket; several pockets ligand-major, pocket-major, or one pocket per ligand
+        const int kind = !multi ? 0 : (multi->lig_pocket ? 3 : (multi->pocket_major ? 2 : 1));
+        u.key = {c, a.S, a.P, u.nmax, rmax, a.ranking, a.rigid_steps > 0 ? 1 : 0, want_pose + 2 * kind};
         u.W = tuned_warps(ctx, u.key, a.S, &u.tuned);
         if (int rc = configure(u)) return rc;
         units.push_back(u);
@@ -352,7 +354,7 @@ int dock_device(lg_ctx *ctx, const PocketDev &pk, const BatchDev &bd, const OutD
     int slots = 1;
     for (const Unit &u : units) slots = std::max(slots, u.grid);
     bool need_tune = false;  // tuning trials run eagerly on the sorted batch: no graph for this call
-    for (const Unit &u : units) need_tune = need_tune || (ctx->autotune && !multi && !u.tuned);
+    for (const Unit &u : units) need_tune = need_tune || (ctx->autotune && !u.tuned);
     if (need_tune)  // ranking slots for every candidate's grid
         for (const Unit &u : units)
             for (int w : kCand) {
@@ -360,8 +362,14 @@ int dock_device(lg_ctx *ctx, const PocketDev &pk, const BatchDev &bd, const OutD
                 v.W = w;
                 if (!u.tuned && configure(v) == LG_OK) slots = std::max(slots, v.grid);
             }
-    const bool graph = allow_graph && ctx->graphs && !multi && s != nullptr && !need_tune;
-    if (!graph) {
+    const bool graph = allow_graph && ctx->graphs && !multi && s != nullptr && !need_tune && !reuse_prep;
+    if (reuse_prep) {  // the same batch was prepared and sorted by the previous call: clear the work counters
+        if (scratch.ensure(scratch_bytes(L, rmax, a.ranking ? slots : 0, a.S, a.P, a.ly.nmax)))
+            return fail(LG_ENOMEM, "scratch allocation failed");
+        a.scr = carve_scratch(scratch.p, L, rmax, a.ranking ? slots : 0, a.S, a.P, a.ly.nmax);
+        if ((e = cudaMemsetAsync(a.scr.hist + kSortBuckets, 0, 4 * (kSizeClasses + 1), s)) != cudaSuccess)
+            return fail(LG_ECUDA, std::string("scratch clear: ") + cudaGetErrorString(e));
+    } else if (!graph) {
         if (int rc = setup_scratch(slots)) return rc;
     } else {  // the preparation goes into the graph with the docking launches
         if (scratch.ensure(scratch_bytes(L, rmax, a.ranking ? slots : 0, a.S, a.P, a.ly.nmax)))
@@ -389,7 +397,7 @@ int dock_device(lg_ctx *ctx, const PocketDev &pk, const BatchDev &bd, const OutD
     // autotuning: a unit without a cached choice times every candidate on the
     // first ligands of its class (same order, same ligands), keeps the fastest
     // and re-clears its work counter; the results do not depend on the choice
-    if (ctx->autotune && !multi)
+    if (ctx->autotune)
         for (Unit &u : units) {
             if (u.tuned) continue;
             // the same ligands for every candidate: an even sample of the

@@ -41,7 +41,7 @@ int fetch_out(const OutDev &d, const lg_dock_result *o, int L, int S, int P, int
 int dock_device(lg_ctx *ctx, const PocketDev &pk, const BatchDev &bd, const OutDev &od, const lg_dock_params *p,
                 int nmax, int rmax, DevBuf &scratch, cudaStream_t s, lg_stats *st, cudaEvent_t *tev,
                 const MultiDev *multi = nullptr, unsigned class_mask = (1u << kSizeClasses) - 1,
-                bool allow_graph = false);
+                bool allow_graph = false, bool reuse_prep = false);
 unsigned host_class_mask(const lg_ligand_batch *b);
 int resolve_batch(lg_ctx *c, const lg_ligand_batch *b, const lg_dock_params *p, cudaStream_t s, BatchDev *bd,
                   int64_t *A, int64_t *R, int *nmax, int *rmax);
