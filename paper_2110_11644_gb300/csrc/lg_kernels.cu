@@ -942,13 +942,27 @@ __device__ __forceinline__ void dock_ligand_rt(const DockArgs &A, const PocketDe
         }
         __syncwarp();
         // 2. greedy torsion sweep
-        for (int ps = 0; ps < P; ++ps) {
+        // Once a restart has made R decisions in a row without a move (one
+        // round over every bond), its state is the one those decisions saw, so
+        // every later decision repeats one of them: step 0.  When all restarts
+        // of the tile are there, the remaining decisions are recorded as step
+        // 0 without running them (with rigid moves, whole passes are the unit).
+        int zrun = 0;  // decisions in a row without a move (this lane's restart)
+        bool converged = false;
+        for (int ps = 0; ps < P && !converged; ++ps) {
             bool moved = false;
             for (int k = 0; k < R; ++k) {
                 const int t = sweep_bond_rt(A, Go, cv, v, N, R, k, rs, g, valid, cs, sn);
                 if (g == 0) v.tcur[(ps * R + k) * kTile + rs] = (uint8_t)t;
                 moved = moved || t != 0;
+                zrun = t != 0 ? 0 : zrun + 1;
+                if (!kRigid && !__any_sync(LG_FULL, valid && zrun < R)) {
+                    for (int q = ps * R + k + 1 + g; q < P * R; q += kLanesPerRestart) v.tcur[q * kTile + rs] = 0;
+                    converged = true;
+                    break;
+                }
             }
+            if (converged) break;
             if (kRigid) moved = rigid_moves_rt(A, Go, O, v, l, r, ps, N, R, rs, g, valid) || moved;
             // a pass in which no restart of the tile moved leaves every state as
             // it found it, so each later pass would repeat it move for move:
