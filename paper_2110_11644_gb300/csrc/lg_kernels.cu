@@ -473,9 +473,10 @@ __device__ int sweep_bond_plain(const DockArgs &A, const GridK &G, const CtaView
 // Rigid greedy moves of the warp's restart (plain form): lane c scores
 // candidate c (same arithmetic and order as the restart-tiled form, so both
 // forms choose and move identically).
-__device__ __forceinline__ void rigid_moves_plain(const DockArgs &A, const GridK &Go, const OutDev &O,
+__device__ __forceinline__ bool rigid_moves_plain(const DockArgs &A, const GridK &Go, const OutDev &O,
                                                   const WarpView &wv, int l, int r, int ps, int N, int R, int lane) {
     const float c0 = 0.5f * Go.gmax, dg = A.rigid_shift_g, ca = c_cos[1], sa = c_sin[1];
+    bool moved = false;
     for (int j = 0; j < A.rigid_steps; ++j) {
         float sx = 0.0f, sy = 0.0f, sz = 0.0f;
         if (lane < 4)
@@ -517,6 +518,7 @@ __device__ __forceinline__ void rigid_moves_plain(const DockArgs &A, const GridK
         if (lane == 0 && O.restart_rigid)
             O.restart_rigid[(((size_t)l * A.S + r) * A.P + ps) * A.rigid_steps + j] = (uint8_t)bC;
         __syncwarp();
+        moved = moved || bC != 0;
         if (bC != 0) {
             for (int i = lane; i < N; i += 32) {
                 const float3 y = rigid_candidate(bC, wv.Xx[i], wv.Xy[i], wv.Xz[i], cx, cy, cz, dg, ca, sa);
@@ -528,6 +530,7 @@ __device__ __forceinline__ void rigid_moves_plain(const DockArgs &A, const GridK
         }
         __syncwarp();
     }
+    return moved;
 }
 
 __global__ void __launch_bounds__(1024) k_dock_plain(const __grid_constant__ DockArgs A, int l, int slot) {
@@ -569,13 +572,35 @@ __global__ void __launch_bounds__(1024) k_dock_plain(const __grid_constant__ Doc
             wv.axis[k] = make_float4(w.x, w.y, w.z, 0.0f);
         }
         __syncwarp();
-        for (int ps = 0; ps < P; ++ps) {
+        // the same exact stops as the restart-tiled form, per restart: R
+        // decisions in a row without a move (torsions only), or a pass without
+        // a move (with rigid moves); the remaining decisions are step 0
+        int zrun = 0;
+        bool converged = false;
+        for (int ps = 0; ps < P && !converged; ++ps) {
+            bool moved = false;
             for (int k = 0; k < R; ++k) {
                 const int t = sweep_bond_plain(A, Go, cv, wv, N, R, k, lane, cl, sl, ct, st);
                 if (lane == 0) wv.tcur[ps * R + k] = (uint8_t)t;
+                moved = moved || t != 0;
+                zrun = t != 0 ? 0 : zrun + 1;
+                if (A.rigid_steps == 0 && zrun >= R) {
+                    for (int q = ps * R + k + 1 + lane; q < P * R; q += 32) wv.tcur[q] = 0;
+                    converged = true;
+                    break;
+                }
             }
-            if (A.rigid_steps > 0) rigid_moves_plain(A, Go, A.out, wv, l, r, ps, N, R, lane);
+            if (converged) break;
+            if (A.rigid_steps > 0) moved = rigid_moves_plain(A, Go, A.out, wv, l, r, ps, N, R, lane) || moved;
+            if (ps + 1 < P && !moved) {
+                for (int q = (ps + 1) * R + lane; q < P * R; q += 32) wv.tcur[q] = 0;
+                if (A.rigid_steps > 0 && lane == 0 && A.out.restart_rigid)
+                    for (int q = (ps + 1) * A.rigid_steps; q < P * A.rigid_steps; ++q)
+                        A.out.restart_rigid[((size_t)l * S + r) * P * A.rigid_steps + q] = 0;
+                break;
+            }
         }
+        __syncwarp();
         // pose score: FP32 per-atom terms; FP64 sums s_g over atoms i = g (mod 4)
         // in order, combined as (s0 + s1) + (s2 + s3)
         for (int i = lane; i < N; i += 32) {
