@@ -1207,7 +1207,12 @@ __global__ void __launch_bounds__(32 * kFlatWarps) k_flatten(const __grid_consta
     const bool two = lane < LG_ANGLE_STEPS - 32;
     const float c0 = c_cos[lane], s0 = c_sin[lane];
     const float c1 = two ? c_cos[32 + lane] : 1.0f, s1 = two ? c_sin[32 + lane] : 0.0f;
-    for (int ps = 0; ps < F.P; ++ps)
+    // R decisions in a row without a move (one round over every bond) leave
+    // the state as they saw it: every later decision repeats one of them, so
+    // the sweep stops and records step 0 for the rest (exact)
+    int zrun = 0;
+    bool converged = false;
+    for (int ps = 0; ps < F.P && !converged; ++ps)
         for (int k = 0; k < R; ++k) {
             const int b = B.rot_child[r0 + k], a = par[b], e = F.rot_end[(size_t)l * F.rmax_lim + k];
             const float xbx = Xx[b], xby = Xy[b], xbz = Xz[b];
@@ -1279,6 +1284,13 @@ __global__ void __launch_bounds__(32 * kFlatWarps) k_flatten(const __grid_consta
                 }
             }
             __syncwarp();
+            zrun = bt != 0 ? 0 : zrun + 1;
+            if (zrun >= R) {
+                if (F.tors)
+                    for (int q = ps * R + k + 1 + lane; q < F.P * R; q += 32) F.tors[(size_t)F.P * r0 + q] = 0;
+                converged = true;
+                break;
+            }
         }
     // outputs: coordinates in the input frame and the final sum of distances
     for (int i = lane; i < N; i += 32) {
