@@ -1204,9 +1204,14 @@ __global__ void __launch_bounds__(32 * kFlatWarps) k_flatten(const __grid_consta
         par[i] = B.parent[a0 + i];
     }
     __syncwarp();
-    const bool two = lane < LG_ANGLE_STEPS - 32;
-    const float c0 = c_cos[lane], s0 = c_sin[lane];
-    const float c1 = two ? c_cos[32 + lane] : 1.0f, s1 = two ? c_sin[32 + lane] : 0.0f;
+    // lanes: 4 step groups (g: steps g, g+4, ..., g+32) x 8 pair groups (pg)
+    const int g = lane & 3, pg = lane >> 2;
+    float cs[kStepsPerLane], sn[kStepsPerLane];
+#pragma unroll
+    for (int j = 0; j < kStepsPerLane; ++j) {
+        cs[j] = c_cos[4 * j + g];
+        sn[j] = c_sin[4 * j + g];
+    }
     // R decisions in a row without a move (one round over every bond) leave
     // the state as they saw it: every later decision repeats one of them, so
     // the sweep stops and records step 0 for the rest (exact)
@@ -1226,8 +1231,13 @@ __global__ void __launch_bounds__(32 * kFlatWarps) k_flatten(const __grid_consta
             __syncwarp();
             const int m = e - b - 1, nf = N - (e - b);
             const int total = m * nf;
-            double D0 = 0.0, D1 = 0.0;
-            float m0 = INFINITY, m1 = INFINITY;
+            double D[kStepsPerLane];
+            float mn[kStepsPerLane];
+#pragma unroll
+            for (int j = 0; j < kStepsPerLane; ++j) {
+                D[j] = 0.0;
+                mn[j] = INFINITY;
+            }
             for (int q0 = 0; q0 < total; q0 += 32) {
                 const int q = q0 + lane;
                 if (q < total) {
@@ -1241,31 +1251,41 @@ __global__ void __launch_bounds__(32 * kFlatWarps) k_flatten(const __grid_consta
                 }
                 __syncwarp();
                 const int n = min(32, total - q0);
-                float acc0 = 0.0f, acc1 = 0.0f;
-                for (int t = 0; t < n; ++t) {
+                float acc[kStepsPerLane];
+#pragma unroll
+                for (int j = 0; j < kStepsPerLane; ++j) acc[j] = 0.0f;
+                for (int t = pg; t < n; t += 8) {  // the lane's pairs of the chunk, its 9 steps each
                     const float4 cf = chunk[t];
-                    const float d0 = fmaf(cf.z, s0, fmaf(cf.y, c0, cf.x));
-                    acc0 += sqrtf(fmaxf(d0, 0.0f));
-                    if (cf.w != 0.0f) m0 = fminf(m0, d0);
-                    if (two) {
-                        const float d1 = fmaf(cf.z, s1, fmaf(cf.y, c1, cf.x));
-                        acc1 += sqrtf(fmaxf(d1, 0.0f));
-                        if (cf.w != 0.0f) m1 = fminf(m1, d1);
+#pragma unroll
+                    for (int j = 0; j < kStepsPerLane; ++j) {
+                        const float d = fmaf(cf.z, sn[j], fmaf(cf.y, cs[j], cf.x));
+                        acc[j] += sqrtf(fmaxf(d, 0.0f));
+                        if (cf.w != 0.0f) mn[j] = fminf(mn[j], d);
                     }
                 }
-                D0 += (double)acc0;
-                D1 += (double)acc1;
+#pragma unroll
+                for (int j = 0; j < kStepsPerLane; ++j) D[j] += (double)acc[j];
                 __syncwarp();
             }
-            // best admissible step of the lane, then of the warp (larger sum, then lower step)
-            double bd = (lane == 0 || m0 >= F.dc2) ? D0 : -INFINITY;
-            int bt = lane;
-            if (two && m1 >= F.dc2 && D1 > bd) {
-                bd = D1;
-                bt = 32 + lane;
+            // totals over the 8 pair groups, then the best admissible step of
+            // the lane and of the warp (larger sum, then lower step)
+            double bd = -INFINITY;
+            int bt = 1024;
+#pragma unroll
+            for (int j = 0; j < kStepsPerLane; ++j) {
+#pragma unroll
+                for (int o = 4; o < 32; o <<= 1) {
+                    D[j] += __shfl_xor_sync(LG_FULL, D[j], o);
+                    mn[j] = fminf(mn[j], __shfl_xor_sync(LG_FULL, mn[j], o));
+                }
+                const int t = 4 * j + g;
+                if ((t == 0 || mn[j] >= F.dc2) && D[j] > bd) {
+                    bd = D[j];
+                    bt = t;
+                }
             }
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
+            for (int o = 1; o < 4; o <<= 1) {
                 const double od = __shfl_xor_sync(LG_FULL, bd, o);
                 const int ot = __shfl_xor_sync(LG_FULL, bt, o);
                 if (od > bd || (od == bd && ot < bt)) {
