@@ -944,114 +944,137 @@ __device__ __forceinline__ void dock_ligand_rt(const DockArgs &A, const PocketDe
     const uint64_t uid = B.uid[l];
     const uint2 key = make_uint2(A.seed_lo, A.seed_hi);
     const GridK Go = grid_k(Pk, Pk.cell_o), Gve = grid_k(Pk, Pk.cell_ve);
-    const int ntiles = (S + kTile - 1) / kTile;
-
+    // Restart streaming: warp w owns restarts w, w + W, w + 2W, ... and runs
+    // them through its 8 restart slots.  All slots take the same bond at the
+    // same time, pass after pass; a slot whose restart has finished (P passes,
+    // or converged: R decisions in a row without a move, or with rigid moves a
+    // pass without one -- every later decision would repeat step 0) is emptied
+    // at the end of the pass and refilled with the warp's next restart, which
+    // starts its first pass with the others' next one.  A restart's arithmetic
+    // does not depend on its slot, so results are those of restarts run alone.
+    int r = warp + W * rs;  // this slot's restart (-1: idle)
+    if (r >= S) r = -1;
+    int qnext = kTile;      // next index into the warp's restart list (uniform)
+    int pc = 0;             // passes this slot's restart has completed
+    int zrun = 0;           // its decisions in a row without a move
+    bool movedp = true;     // whether it moved in its last pass
+    bool fresh = true;      // slot needs its restart's initial pose (an idle slot takes restart 0's, never used)
     double bestE = INFINITY;
     int bestR = -1;
-    for (int tile = warp; tile < ntiles; tile += W) {
-        const int r = tile * kTile + rs;
-        const bool valid = r < S;
-        // 1. restart poses (the 4 lanes of a restart split its atoms and bonds)
-        const Pose pose = restart_pose(uid, (uint32_t)r, key, Pk.n_pp);
-        const float4 pp = __ldg(Pk.pp + pose.pp);
-        for (int i = g; i < N; i += kLanesPerRestart) {
-            const float3 x = rot_add(pose.R, cv.d0x[i], cv.d0y[i], cv.d0z[i], pp.x, pp.y, pp.z);
-            v.Xx[i * kTile + rs] = x.x;
-            v.Xy[i * kTile + rs] = x.y;
-            v.Xz[i * kTile + rs] = x.z;
-        }
-        for (int k = g; k < R; k += kLanesPerRestart) {
-            const float4 d = cv.dv[k];
-            const float3 w = rot_vec(pose.R, d.x, d.y, d.z);
-            v.axis[k * kTile + rs] = make_float4(w.x, w.y, w.z, 0.0f);
+    for (;;) {
+        // 1. initial pose of newly filled slots (the 4 lanes of a slot split atoms and bonds)
+        if (fresh) {
+            const Pose pose = restart_pose(uid, (uint32_t)(r >= 0 ? r : 0), key, Pk.n_pp);
+            const float4 pp = __ldg(Pk.pp + pose.pp);
+            for (int i = g; i < N; i += kLanesPerRestart) {
+                const float3 x = rot_add(pose.R, cv.d0x[i], cv.d0y[i], cv.d0z[i], pp.x, pp.y, pp.z);
+                v.Xx[i * kTile + rs] = x.x;
+                v.Xy[i * kTile + rs] = x.y;
+                v.Xz[i * kTile + rs] = x.z;
+            }
+            for (int k = g; k < R; k += kLanesPerRestart) {
+                const float4 d = cv.dv[k];
+                const float3 w = rot_vec(pose.R, d.x, d.y, d.z);
+                v.axis[k * kTile + rs] = make_float4(w.x, w.y, w.z, 0.0f);
+            }
+            fresh = false;
         }
         __syncwarp();
-        // 2. greedy torsion sweep
-        // Once a restart has made R decisions in a row without a move (one
-        // round over every bond), its state is the one those decisions saw, so
-        // every later decision repeats one of them: step 0.  When all restarts
-        // of the tile are there, the remaining decisions are recorded as step
-        // 0 without running them (with rigid moves, whole passes are the unit).
-        int zrun = 0;  // decisions in a row without a move (this lane's restart)
-        bool converged = false;
-        for (int ps = 0; ps < P && !converged; ++ps) {
-            bool moved = false;
-            for (int k = 0; k < R; ++k) {
-                const int t = sweep_bond_rt(A, Go, cv, v, N, R, k, rs, g, valid, cs, sn);
-                if (g == 0) v.tcur[(ps * R + k) * kTile + rs] = (uint8_t)t;
-                moved = moved || t != 0;
-                zrun = t != 0 ? 0 : zrun + 1;
-                if (!kRigid && !__any_sync(LG_FULL, valid && zrun < R)) {
-                    for (int q = ps * R + k + 1 + g; q < P * R; q += kLanesPerRestart) v.tcur[q * kTile + rs] = 0;
-                    converged = true;
-                    break;
+        // 2. finished restarts: remaining decisions are step 0; score, outputs, best
+        const bool active = r >= 0;
+        const bool conv = kRigid ? (pc > 0 && !movedp) : (zrun >= R);
+        const bool done = active && (pc >= P || conv);
+        if (__any_sync(LG_FULL, done)) {
+            if (done) {
+                for (int q = pc * R + g; q < PR; q += kLanesPerRestart) v.tcur[q * kTile + rs] = 0;
+                if (kRigid && g == 0 && O.restart_rigid)
+                    for (int q = pc * A.rigid_steps; q < P * A.rigid_steps; ++q)
+                        O.restart_rigid[((size_t)l * S + r) * P * A.rigid_steps + q] = 0;
+            }
+            __syncwarp();
+            // pose score: FP32 per-atom terms; FP64 sums s_g over atoms i = g
+            // (mod 4) in order, combined as (s0 + s1) + (s2 + s3)
+            double E = 0.0;
+            if (done)
+                for (int i = g; i < N; i += kLanesPerRestart) {
+                    const float2 wq = cv.wq[i];
+                    E += (double)atom_energy(Pk, Gve, v.Xx[i * kTile + rs], v.Xy[i * kTile + rs], v.Xz[i * kTile + rs],
+                                             wq.x, wq.y);
+                }
+            E += __shfl_xor_sync(LG_FULL, E, 1);
+            E += __shfl_xor_sync(LG_FULL, E, 2);
+            if (done) {
+                if (O.restart_score && g == 0) O.restart_score[(size_t)l * S + r] = E;
+                if (O.restart_tors)
+                    for (int t = g; t < PR; t += kLanesPerRestart)
+                        O.restart_tors[(size_t)S * P * r0 + (size_t)r * PR + t] = v.tcur[t * kTile + rs];
+                if (kRank) {  // keep the restart for the ranking step
+                    float *x = A.scr.rk_pose + rk_pose_off(A, blockIdx.x, r);
+                    for (int i = g; i < N; i += kLanesPerRestart) {
+                        x[3 * i] = v.Xx[i * kTile + rs];
+                        x[3 * i + 1] = v.Xy[i * kTile + rs];
+                        x[3 * i + 2] = v.Xz[i * kTile + rs];
+                    }
+                    for (int t = g; t < PR; t += kLanesPerRestart)
+                        A.scr.rk_tors[((size_t)blockIdx.x * S + r) * P * Ly.rmax + t] = v.tcur[t * kTile + rs];
+                    if (g == 0) A.scr.rk_E[(size_t)blockIdx.x * S + r] = E;
                 }
             }
-            if (converged) break;
-            if (kRigid) moved = rigid_moves_rt(A, Go, O, v, l, r, ps, N, R, rs, g, valid) || moved;
-            // a pass in which no restart of the tile moved leaves every state as
-            // it found it, so each later pass would repeat it move for move:
-            // record their decisions (all step 0) without running them
-            if (ps + 1 < P && !__any_sync(LG_FULL, valid && moved)) {
-                for (int q = (ps + 1) * R + g; q < P * R; q += kLanesPerRestart) v.tcur[q * kTile + rs] = 0;
-                if (kRigid && valid && g == 0 && O.restart_rigid)
-                    for (int q = (ps + 1) * A.rigid_steps; q < P * A.rigid_steps; ++q)
-                        O.restart_rigid[((size_t)l * A.S + r) * A.P * A.rigid_steps + q] = 0;
+            // best of the finished restarts (lowest E, then lowest restart), then of the warp
+            double te = done ? E : INFINITY;
+            int tr = done ? r : 0x7fffffff, ts = rs;
+#pragma unroll
+            for (int o = kLanesPerRestart; o < 32; o <<= 1) {
+                const double oe = __shfl_xor_sync(LG_FULL, te, o);
+                const int orr = __shfl_xor_sync(LG_FULL, tr, o), os = __shfl_xor_sync(LG_FULL, ts, o);
+                if (oe < te || (oe == te && orr < tr)) {
+                    te = oe;
+                    tr = orr;
+                    ts = os;
+                }
+            }
+            if (tr != 0x7fffffff && (bestR < 0 || te < bestE || (te == bestE && tr < bestR))) {
+                bestE = te;
+                bestR = tr;
+                for (int t = lane; t < PR; t += 32) v.tbest[t] = v.tcur[t * kTile + ts];
+                if (Ly.want_pose)
+                    for (int i = lane; i < N; i += 32) {
+                        v.Bx[i] = v.Xx[i * kTile + ts];
+                        v.By[i] = v.Xy[i * kTile + ts];
+                        v.Bz[i] = v.Xz[i * kTile + ts];
+                    }
+            }
+            __syncwarp();
+            // refill the finished slots, in slot order, from the warp's restart list
+            const unsigned dm = __ballot_sync(LG_FULL, done && g == 0);
+            if (done) {
+                const int j = qnext + __popc(dm & ((1u << (kLanesPerRestart * rs)) - 1u));
+                const int rn = warp + W * j;
+                r = rn < S ? rn : -1;
+                pc = 0;
+                zrun = 0;
+                movedp = true;
+                fresh = r >= 0;
+            }
+            qnext += __popc(dm);
+            continue;  // initial poses first
+        }
+        if (!__any_sync(LG_FULL, active)) break;
+        // 3. one greedy pass over the torsional bonds for every active slot
+        movedp = false;
+        for (int k = 0; k < R; ++k) {
+            const int t = sweep_bond_rt(A, Go, cv, v, N, R, k, rs, g, active, cs, sn);
+            if (active && g == 0) v.tcur[(pc * R + k) * kTile + rs] = (uint8_t)t;
+            movedp = movedp || t != 0;
+            zrun = t != 0 ? 0 : zrun + 1;
+            if (!kRigid && !__any_sync(LG_FULL, active && zrun < R)) {  // every active restart converged
+                if (active)
+                    for (int q = pc * R + k + 1 + g; q < (pc + 1) * R; q += kLanesPerRestart) v.tcur[q * kTile + rs] = 0;
                 break;
             }
         }
-        __syncwarp();
-        // 3. pose score: FP32 per-atom terms; FP64 sums s_g over atoms i = g
-        //    (mod 4) in order, combined as (s0 + s1) + (s2 + s3)
-        double E = 0.0;
-        for (int i = g; i < N; i += kLanesPerRestart) {
-            const float2 wq = cv.wq[i];
-            E += (double)atom_energy(Pk, Gve, v.Xx[i * kTile + rs], v.Xy[i * kTile + rs], v.Xz[i * kTile + rs], wq.x,
-                                     wq.y);
-        }
-        E += __shfl_xor_sync(LG_FULL, E, 1);
-        E += __shfl_xor_sync(LG_FULL, E, 2);
-        if (valid) {
-            if (O.restart_score && g == 0) O.restart_score[(size_t)l * S + r] = E;
-            if (O.restart_tors)
-                for (int t = g; t < PR; t += kLanesPerRestart)
-                    O.restart_tors[(size_t)S * P * r0 + (size_t)r * PR + t] = v.tcur[t * kTile + rs];
-            if (kRank) {  // keep the restart for the ranking step
-                float *x = A.scr.rk_pose + rk_pose_off(A, blockIdx.x, r);
-                for (int i = g; i < N; i += kLanesPerRestart) {
-                    x[3 * i] = v.Xx[i * kTile + rs];
-                    x[3 * i + 1] = v.Xy[i * kTile + rs];
-                    x[3 * i + 2] = v.Xz[i * kTile + rs];
-                }
-                for (int t = g; t < PR; t += kLanesPerRestart)
-                    A.scr.rk_tors[((size_t)blockIdx.x * S + r) * P * Ly.rmax + t] = v.tcur[t * kTile + rs];
-                if (g == 0) A.scr.rk_E[(size_t)blockIdx.x * S + r] = E;
-            }
-        }
-        // 4. best restart of the tile (lowest E, then lowest restart)
-        double te = valid ? E : INFINITY;
-        int tr = valid ? r : 0x7fffffff;
-#pragma unroll
-        for (int o = kLanesPerRestart; o < 32; o <<= 1) {
-            const double oe = __shfl_xor_sync(LG_FULL, te, o);
-            const int orr = __shfl_xor_sync(LG_FULL, tr, o);
-            if (oe < te || (oe == te && orr < tr)) {
-                te = oe;
-                tr = orr;
-            }
-        }
-        if (tr != 0x7fffffff && (bestR < 0 || te < bestE)) {  // later tiles hold higher restarts
-            bestE = te;
-            bestR = tr;
-            const int ws = tr - tile * kTile;
-            for (int t = lane; t < PR; t += 32) v.tbest[t] = v.tcur[t * kTile + ws];
-            if (Ly.want_pose)
-                for (int i = lane; i < N; i += 32) {
-                    v.Bx[i] = v.Xx[i * kTile + ws];
-                    v.By[i] = v.Xy[i * kTile + ws];
-                    v.Bz[i] = v.Xz[i * kTile + ws];
-                }
-        }
+        if (kRigid) movedp = rigid_moves_rt(A, Go, O, v, l, r, pc, N, R, rs, g, active) || movedp;
+        if (active) pc++;
         __syncwarp();
     }
     if (kRank) {
