@@ -120,14 +120,14 @@ def cpu_cores() -> int:
     return len(os.sched_getaffinity(0))
 
 
-def oracle_rate(pocket, batch, params, budget_s: float, chunk: int = 256, max_ligands: int = 8192):
+def oracle_rate(pocket, batch, params, budget_s: float, chunk: int = 256, max_ligands: int = 65536, threads=None):
     """Oracle throughput on the first ligands of the workload, in chunks until
     the time budget is spent.  Returns (evals/s, ligands, seconds)."""
     import oracle
     done, t0 = 0, time.perf_counter()
     while done < max_ligands:
         sub = batch.subset(range(done, min(done + chunk, batch.L)))
-        oracle.dock(pocket, sub, params, nthreads=cpu_cores())
+        oracle.dock(pocket, sub, params, nthreads=threads or cpu_cores())
         done += sub.L
         if time.perf_counter() - t0 >= budget_s or done >= batch.L:
             break
@@ -605,8 +605,11 @@ def main():
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
             rate, n_done, secs = oracle_rate(pocket, batch, params, args.cpu_budget)
+            rate1, n1, secs1 = oracle_rate(pocket, batch, params, args.cpu_budget / 4, chunk=64, threads=1)
             cpu = {"value": rate, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
-                   "sample": f"first {n_done} ligands of the workload, FP64 oracle, {secs:.1f} s"}
+                   "sample": f"first {n_done} ligands of the workload, FP64 oracle, {secs:.1f} s",
+                   "single_core": {"value": rate1, "unit": UNIT, "cores": 1,
+                                   "sample": f"first {n1} ligands, {secs1:.1f} s"}}
 
 
         small = small_batch_leg(ctx, pid, dev, 64, 200) if world == 1 else None

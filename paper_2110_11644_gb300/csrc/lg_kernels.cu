@@ -744,7 +744,7 @@ __device__ __forceinline__ int sweep_bond_rt(const DockArgs &A, const GridK &G, 
 #ifndef LG_RT_INSIDE_PATH
 #define LG_RT_INSIDE_PATH 1
 #endif
-    const bool all_in = LG_RT_INSIDE_PATH && __all_sync(LG_FULL, ball_in);
+    const bool all_in = LG_RT_INSIDE_PATH && __all_sync(LG_FULL, ball_in || !valid);
 
     // Fixed atoms farther than rho + d_clash from xb can never come within
     // d_clash of a moving atom: each restart keeps a list of the others.
@@ -791,14 +791,16 @@ __device__ __forceinline__ int sweep_bond_rt(const DockArgs &A, const GridK &G, 
     };
 
     // Overlap scores of the lane's 9 steps over the moving atoms (in order),
-    // and each atom's clash pairs while its cell loads are in flight.
+    // and each atom's clash pairs while its cell loads are in flight.  Lanes
+    // of an idle slot issue no loads.
     float acc[kStepsPerLane];
 #pragma unroll
     for (int j = 0; j < kStepsPerLane; ++j) acc[j] = 0.0f;
     for (int i = b + 1; i < e; ++i) {
         const Circle C = make_circle(v.Xx[i * kTile + rs], v.Xy[i * kTile + rs], v.Xz[i * kTile + rs], xbx, xby, xbz, u,
                                      c0, G.gmax);
-        if (all_in) {
+        if (!valid) {
+        } else if (all_in) {
 #pragma unroll
             for (int j = 0; j < kStepsPerLane; ++j) {
                 const float3 q = circle_index(C.Px, C.Py, C.Pz, C.e1x, C.e1y, C.e1z, C.e2x, C.e2y, C.e2z, cs[j], sn[j]);
@@ -1063,7 +1065,9 @@ __device__ __forceinline__ void dock_ligand_rt(const DockArgs &A, const PocketDe
         // 3. one greedy pass over the torsional bonds for every active slot
         movedp = false;
         for (int k = 0; k < R; ++k) {
-            const int t = sweep_bond_rt(A, Go, cv, v, N, R, k, rs, g, active, cs, sn);
+            // a restart R zero decisions in a row into the pass sequence repeats
+            // them from here on (step 0, no move): its lanes skip the work
+            const int t = sweep_bond_rt(A, Go, cv, v, N, R, k, rs, g, active && (kRigid || zrun < R), cs, sn);
             if (active && g == 0) v.tcur[(pc * R + k) * kTile + rs] = (uint8_t)t;
             movedp = movedp || t != 0;
             zrun = t != 0 ? 0 : zrun + 1;
