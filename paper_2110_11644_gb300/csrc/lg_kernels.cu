@@ -731,13 +731,27 @@ __device__ __forceinline__ int sweep_bond_rt(const DockArgs &A, const GridK &G, 
     // Every moving atom stays at its distance from xb, so the subtree's circles
     // lie in the ball of radius max |x_i - xb| about xb: when that ball is in
     // the grid box for all 8 restarts, no lookup of this decision needs clamping.
-    float rho2 = 0.0f;
+    // The same loop bounds the subtree in cylindrical coordinates about the
+    // axis: axial t = (x - xb).u in [tlo, thi], squared radius in [q2lo, q2hi].
+    float rho2 = 0.0f, tlo = INFINITY, thi = -INFINITY, q2lo = INFINITY, q2hi = 0.0f;
     for (int i = b + 1 + g; i < e; i += kLanesPerRestart) {
         const float dx = v.Xx[i * kTile + rs] - xbx, dy = v.Xy[i * kTile + rs] - xby, dz = v.Xz[i * kTile + rs] - xbz;
-        rho2 = fmaxf(rho2, fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+        const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz)), t = fmaf(u.x, dx, fmaf(u.y, dy, u.z * dz));
+        const float q2 = fmaf(-t, t, d2);
+        rho2 = fmaxf(rho2, d2);
+        tlo = fminf(tlo, t);
+        thi = fmaxf(thi, t);
+        q2lo = fminf(q2lo, q2);
+        q2hi = fmaxf(q2hi, q2);
     }
-    rho2 = fmaxf(rho2, __shfl_xor_sync(LG_FULL, rho2, 1));
-    rho2 = fmaxf(rho2, __shfl_xor_sync(LG_FULL, rho2, 2));
+#pragma unroll
+    for (int o = 1; o < kLanesPerRestart; o <<= 1) {
+        rho2 = fmaxf(rho2, __shfl_xor_sync(LG_FULL, rho2, o));
+        tlo = fminf(tlo, __shfl_xor_sync(LG_FULL, tlo, o));
+        thi = fmaxf(thi, __shfl_xor_sync(LG_FULL, thi, o));
+        q2lo = fminf(q2lo, __shfl_xor_sync(LG_FULL, q2lo, o));
+        q2hi = fmaxf(q2hi, __shfl_xor_sync(LG_FULL, q2hi, o));
+    }
     const float rho = sqrtf(rho2) + 1e-2f, lo = 1e-2f, hi = G.gmax - 1e-2f;
     const bool ball_in = xbx + c0 - rho >= lo && xbx + c0 + rho <= hi && xby + c0 - rho >= lo &&
                          xby + c0 + rho <= hi && xbz + c0 - rho >= lo && xbz + c0 + rho <= hi;
@@ -747,8 +761,18 @@ __device__ __forceinline__ int sweep_bond_rt(const DockArgs &A, const GridK &G, 
     const bool all_in = LG_RT_INSIDE_PATH && __all_sync(LG_FULL, ball_in || !valid);
 
     // Fixed atoms farther than rho + d_clash from xb can never come within
-    // d_clash of a moving atom: each restart keeps a list of the others.
-    const float rlim = sqrtf(rho2) + sqrtf(dc2) + 1e-3f, rlim2 = rlim * rlim;
+    // d_clash of a moving atom, and neither can those whose cylindrical
+    // coordinates lie outside the subtree's range widened by d_clash: a
+    // fixed point's distance to a coaxial circle is at least the distance
+    // between the two in the (t, radius) plane.  Each restart keeps a list of
+    // the others (the 0.05 A margin covers rounding; dropped atoms have no
+    // step within d_clash).
+    const float dm = sqrtf(dc2) + 0.05f, rlim = sqrtf(rho2) + dm, rlim2 = rlim * rlim;
+    tlo -= dm;
+    thi += dm;
+    const float rlo = fmaxf(sqrtf(fmaxf(q2lo, 0.0f)) - dm, 0.0f), rhi = sqrtf(q2hi) + dm;
+    q2lo = rlo > 0.0f ? rlo * rlo : -INFINITY;  // atoms on the axis (rounding may make q2 < 0) stay in
+    q2hi = rhi * rhi;
     int ncnt = 0;  // near fixed atoms of this restart (same in its 4 lanes)
     for (int jb = 0; jb < nF; jb += kLanesPerRestart) {
         const int jj = jb + g;
@@ -757,7 +781,9 @@ __device__ __forceinline__ int sweep_bond_rt(const DockArgs &A, const GridK &G, 
         if (valid && jj < nF) {
             j = jj < b ? jj : jj + (e - b);
             const float dx = v.Xx[j * kTile + rs] - xbx, dy = v.Xy[j * kTile + rs] - xby, dz = v.Xz[j * kTile + rs] - xbz;
-            nr = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < rlim2;
+            const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz)), t = fmaf(u.x, dx, fmaf(u.y, dy, u.z * dz));
+            const float q2 = fmaf(-t, t, d2);
+            nr = d2 < rlim2 && t > tlo && t < thi && q2 > q2lo && q2 < q2hi;
         }
         const unsigned bal = __ballot_sync(LG_FULL, nr);
         if (nr) v.near[rs * v.nstride + ncnt + __popc(bal & gmask & below)] = (uint8_t)j;
