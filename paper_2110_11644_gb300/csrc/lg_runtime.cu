@@ -349,6 +349,26 @@ int dock_device(lg_ctx *ctx, const PocketDev &pk, const BatchDev &bd, const OutD
         if (int rc = configure(u)) return rc;
         units.push_back(u);
     }
+    // A batch too small to fill the GPU gets wider CTAs unless the context
+    // fixes the width: when every item fits in one wave of 4 (or 2) warps per
+    // CTA, all run at once and each ligand's restarts spread over more warps
+    // (no more warps than restart tiles), which shortens the call; the tuned
+    // width is for full batches and is neither used nor tuned here
+    if (ctx->warps_opt.load() <= 0) {
+        const long items = multi && multi->pocket_major && !multi->lig_pocket ? (long)L * multi->np : (long)L;
+        const int wcap = std::min(4, (a.S + kTile - 1) / kTile);
+        for (Unit &u : units)
+            for (int w : {4, 2}) {
+                if (w > wcap) continue;
+                Unit v = u;
+                v.W = w;
+                if (configure(v) == LG_OK && v.W == w && items <= (long)ctx_num_sms(ctx) * v.occ) {
+                    if (w > u.W) u = v;
+                    u.tuned = true;
+                    break;
+                }
+            }
+    }
     a.sort_classes = split ? 1 : 0;
     static const int kCand[3] = {4, 2, 1};  // autotuning candidates (warps per CTA)
     int slots = 1;

@@ -65,16 +65,40 @@ def test_results_do_not_depend_on_warps_or_tuning(ctx, cfg2_pocket, heavy):
 def test_autotuner_caches_its_choice(ctx, cfg2_pocket, heavy):
     pid = ctx.load_pocket(cfg2_pocket)
     params = synth.config_params(3)
-    sub = heavy.subset(range(600))
     ctx.set_option("autotune", 1)  # clears the cache
-    _dock(ctx, pid, sub, params)
+    _dock(ctx, pid, heavy, params)   # 3,000 ligands: more than one wave of 2-warp CTAs
     first = ctx.stats().launches
-    _dock(ctx, pid, sub, params)
+    _dock(ctx, pid, heavy, params)
     second = ctx.stats().launches
     ctx.unload_pocket(pid)
     # prep + sort (3) + one launch per class (3); the first call adds the timing trials
     assert second == 6
     assert first > second
+
+
+def test_small_batches_take_wide_ctas_untuned(ctx, cfg1, cfg2_pocket):
+    # a batch that fits in one wave of 4-warp CTAs runs at one CTA per ligand
+    # with its restart tiles over up to 4 warps, without tuning; results as
+    # at any width
+    pocket, full, params = cfg1
+    pid = ctx.load_pocket(pocket)
+    ctx.set_option("autotune", 1)
+    small = full.subset(range(64))
+    out = _dock(ctx, pid, small, params)
+    st = ctx.stats()
+    assert st.warps_per_cta == 2 and st.launches == 4  # 16 restarts: 2 tiles; prep + sort (2) + one launch
+    ctx.set_option("warps_per_cta", 1)
+    try:
+        ref = _dock(ctx, pid, small, params)
+    finally:
+        ctx.set_option("warps_per_cta", 0)
+    for k in KEYS:
+        assert np.array_equal(out[k], ref[k]), k
+    ctx.unload_pocket(pid)
+    pid = ctx.load_pocket(cfg2_pocket)
+    _dock(ctx, pid, synth.config_ligands(2, 64), synth.config_params(2))
+    assert ctx.stats().warps_per_cta == 4  # 30 restarts: 4 tiles
+    ctx.unload_pocket(pid)
 
 
 def test_heavy_tailed_split_matches_oracle(ctx, cfg2_pocket, heavy):
