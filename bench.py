@@ -520,8 +520,8 @@ def main():
                 "kernel": "k_dock_batched", "dock_ms_per_launch": dock_ms, "flop_per_launch": F,
                 "flop_per_launch_circle_form": circle_form_flops(batch, S, P),
                 "peak_basis": f"{sm_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max_mhz:.0f} MHz",
-                "limiter": "L1 data pipe ~62% (scattered 32-byte trilinear-cell gathers plus shared-memory "
-                           "wavefronts), L1->L2 requests ~59%, issue ~56% at 16 warps/SM; "
+                "limiter": "L1 data pipe ~59% (scattered 32-byte trilinear-cell gathers plus shared-memory "
+                           "wavefronts), L1->L2 requests ~53%, issue ~56% at 16 warps/SM; "
                            "see profiles/dock_batched_ncu_small.md"}
 
     # end to end through the public API with host buffers (pinned)
