@@ -379,6 +379,55 @@ def heavy_tailed_leg(ctx, pid, dev, n_lig, steps, peak_tflops):
                       f"{P} passes, 64^3 pocket"}
 
 
+def stages_leg(ctx, pid, dev, n_lig, steps=2):
+    """Throughput of the optional stages on the throughput workload's first
+    n_lig ligands (device-resident, L2 flushed before each call): the plain
+    best-restart docking, with pose ranking (3 A clustering, first 30
+    rescored), with rigid refinement (2 greedy rigid moves after each torsion
+    pass), with both; and the paper's setting of 256 restarts with ranking on
+    a quarter of the ligands."""
+    import torch
+    from paper_2110_11644_gb300 import lg, synth
+    params = synth.config_params(2)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{dev}")
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream
+    res = {}
+    cases = (("best_restart", 30, n_lig, {}), ("ranking", 30, n_lig, dict(cluster_rmsd=3.0, rescore_top=30)),
+             ("rigid", 30, n_lig, dict(rigid_steps=2)),
+             ("ranking_rigid", 30, n_lig, dict(cluster_rmsd=3.0, rescore_top=30, rigid_steps=2)),
+             ("paper_256_restarts_ranking", 256, max(1, n_lig // 4), dict(cluster_rmsd=3.0, rescore_top=30)))
+    for name, S, n, kw in cases:
+        batch = synth.config_ligands(2, n, uid_base=4 << 40)
+        L, P = batch.L, params.passes
+        A, R = int(batch.atom_off[-1]), int(batch.rot_off[-1])
+        darr = lg.device_batch_arrays(batch, f"cuda:{dev}")
+        b = lg.make_batch_struct(darr, L)
+        p = lg.make_params(S, P, params.seed, params.d_clash, lg.LG_MODE_BATCHED, 0, int(batch.n_atoms().max()),
+                           max(1, int(batch.n_rot().max())), **kw)
+        ranking = "cluster_rmsd" in kw
+        r, outs = lg.alloc_result(L, A, R, S, P, device=True, pose=True, tors=True, ranking=ranking,
+                                  rigid_steps=kw.get("rigid_steps", 0))
+        lg.lg_dock_batch(ctx.h, pid, b, p, r, sh)  # warm-up (and the autotuner's trials)
+        torch.cuda.synchronize()
+        ms = 0.0
+        for _ in range(steps):
+            flush.fill_(1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            lg.lg_dock_batch(ctx.h, pid, b, p, r, sh)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1) / steps
+        assert int((outs["status"][:L] != 0).sum()) == 0
+        res[name] = {"ligands": L, "restarts": S, "ms": round(ms, 3), "evals_per_s": L / (ms / 1e3)}
+        del outs, r, darr
+    base = res["best_restart"]["evals_per_s"]
+    for name in res:
+        res[name]["relative_to_best_restart"] = res[name]["evals_per_s"] / base
+    return res
+
+
 def small_batch_leg(ctx, pid, dev, n_lig, calls):
     """Per-call latency of small device-resident batches (the serving regime):
     direct launches against a captured CUDA graph replayed per call."""
@@ -422,6 +471,8 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=3.0, help="seconds per offered load of the serving leg (0 = off)")
     ap.add_argument("--serve-loads", default="0.25,0.5,0.9",
                     help="comma-separated offered loads (fractions of the measured batched rate)")
+    ap.add_argument("--stage-ligands", type=int, default=20000,
+                    help="ligands of the optional-stages leg (ranking, rigid refinement; 0 = off)")
     ap.add_argument("--multi-ligands", type=int, default=20000,
                     help="ligands of the 15-pocket leg (0 = off)")
     ap.add_argument("--heavy-ligands", type=int, default=1_000_000,
@@ -613,6 +664,7 @@ def main():
 
 
         small = small_batch_leg(ctx, pid, dev, 64, 200) if world == 1 else None
+        stages = stages_leg(ctx, pid, dev, args.stage_ligands) if world == 1 and args.stage_ligands > 0 else None
 
         heavy = None
         if args.heavy_ligands > 0 and world == 1:
@@ -643,7 +695,7 @@ def main():
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "clocks": clk, "gpu_launches": launches_per_step * args.steps, "plain": plain,
                 "serving": serving, "multi_pocket": multi, "flatten": flatten, "heavy_tailed": heavy,
-                "small_batch": small}
+                "small_batch": small, "stages": stages}
         print(json.dumps(line), flush=True)
     ctx.close()
     if dist:
