@@ -495,20 +495,26 @@ __device__ __forceinline__ bool rigid_moves_plain(const DockArgs &A, const GridK
         sy = __shfl_sync(LG_FULL, sy, 0);
         sz = __shfl_sync(LG_FULL, sz, 0);
         const float cx = sx / (float)N, cy = sy / (float)N, cz = sz / (float)N;
-        double bG = -INFINITY;
+        // lane c scores candidate c: FP32 sums s_g over atoms i = g (mod 4) in
+        // order, combined as (s0 + s1) + (s2 + s3) (the batched form's order)
+        float bG = -INFINITY;
         int bC = kRigidCandidates;
         if (lane < kRigidCandidates) {
-            double G = 0.0;
-            for (int i = 0; i < N; ++i) {
-                const float3 y = rigid_candidate(lane, wv.Xx[i], wv.Xy[i], wv.Xz[i], cx, cy, cz, dg, ca, sa);
-                G += (double)lookup_clamped(Go, y.x + c0, y.y + c0, y.z + c0);
+            float s4[kLanesPerRestart];
+#pragma unroll
+            for (int g = 0; g < kLanesPerRestart; ++g) {
+                s4[g] = 0.0f;
+                for (int i = g; i < N; i += kLanesPerRestart) {
+                    const float3 y = rigid_candidate(lane, wv.Xx[i], wv.Xy[i], wv.Xz[i], cx, cy, cz, dg, ca, sa);
+                    s4[g] += lookup_clamped(Go, y.x + c0, y.y + c0, y.z + c0);
+                }
             }
-            bG = G;
+            bG = (s4[0] + s4[1]) + (s4[2] + s4[3]);
             bC = lane;
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            const double oG = __shfl_xor_sync(LG_FULL, bG, o);
+            const float oG = __shfl_xor_sync(LG_FULL, bG, o);
             const int oC = __shfl_xor_sync(LG_FULL, bC, o);
             if (oG > bG || (oG == bG && oC < bC)) {
                 bG = oG;
@@ -880,11 +886,11 @@ __device__ __forceinline__ int sweep_bond_rt(const DockArgs &A, const GridK &G, 
     return t;
 }
 
-// Rigid greedy moves of the tile's restarts after torsion pass ps: the 4
-// lanes of a restart share its 13 candidates (lane g: g, g+4, g+8, g+12); a
-// candidate's score is the FP64 sum, in atom order, of the FP32 overlap
-// lookups of all atoms at their moved positions; the best (highest score,
-// lowest candidate) moves the atoms and turns the bond axes.
+// Rigid greedy moves of the tile's restarts after torsion pass ps: lane g of
+// a restart scores all 13 candidates on atoms i = g (mod 4), in order, with
+// FP32 sums s_g; a candidate's score is (s0 + s1) + (s2 + s3) of the FP32
+// overlap lookups of the atoms at their moved positions; the best (highest
+// score, lowest candidate) moves the atoms and turns the bond axes.
 __device__ __forceinline__ bool rigid_moves_rt(const DockArgs &A, const GridK &Go, const OutDev &O, const RtView &v,
                                                int l, int r, int ps, int N, int R, int rs, int g, bool valid) {
     const float c0 = 0.5f * Go.gmax, dg = A.rigid_shift_g, ca = c_cos[1], sa = c_sin[1];
@@ -903,27 +909,28 @@ __device__ __forceinline__ bool rigid_moves_rt(const DockArgs &A, const GridK &G
         sy += __shfl_xor_sync(LG_FULL, sy, 2);
         sz += __shfl_xor_sync(LG_FULL, sz, 2);
         const float cx = sx / (float)N, cy = sy / (float)N, cz = sz / (float)N;
-        double bG = -INFINITY;
-        int bC = kRigidCandidates;
-        for (int cand = g; cand < kRigidCandidates; cand += kLanesPerRestart) {
-            double G = 0.0;
-            for (int i = 0; i < N; ++i) {
-                const float3 y = rigid_candidate(cand, v.Xx[i * kTile + rs], v.Xy[i * kTile + rs], v.Xz[i * kTile + rs],
-                                                 cx, cy, cz, dg, ca, sa);
-                G += (double)lookup_clamped(Go, y.x + c0, y.y + c0, y.z + c0);
+        float Gc[kRigidCandidates];
+#pragma unroll
+        for (int c = 0; c < kRigidCandidates; ++c) Gc[c] = 0.0f;
+        if (valid)  // idle slots issue no loads
+            for (int i = g; i < N; i += kLanesPerRestart) {
+                const float x = v.Xx[i * kTile + rs], y = v.Xy[i * kTile + rs], z = v.Xz[i * kTile + rs];
+#pragma unroll
+                for (int c = 0; c < kRigidCandidates; ++c) {
+                    const float3 q = rigid_candidate(c, x, y, z, cx, cy, cz, dg, ca, sa);
+                    Gc[c] += lookup_clamped(Go, q.x + c0, q.y + c0, q.z + c0);
+                }
             }
+        float bG = -INFINITY;
+        int bC = kRigidCandidates;
+#pragma unroll
+        for (int c = 0; c < kRigidCandidates; ++c) {
+            float G = Gc[c];
+            G += __shfl_xor_sync(LG_FULL, G, 1);
+            G += __shfl_xor_sync(LG_FULL, G, 2);
             if (G > bG) {  // ascending candidates: ties keep the lower one
                 bG = G;
-                bC = cand;
-            }
-        }
-#pragma unroll
-        for (int o = 1; o < kLanesPerRestart; o <<= 1) {
-            const double oG = __shfl_xor_sync(LG_FULL, bG, o);
-            const int oC = __shfl_xor_sync(LG_FULL, bC, o);
-            if (oG > bG || (oG == bG && oC < bC)) {
-                bG = oG;
-                bC = oC;
+                bC = c;
             }
         }
         if (valid && g == 0 && O.restart_rigid)
