@@ -47,6 +47,12 @@ __device__ __forceinline__ double warp_sum_d(double v) {
     return v;
 }
 
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(LG_FULL, v, o);
+    return v;
+}
+
 // ------------------------------------------------------------------ the ligand of a CTA
 struct CtaView {
     float4 *dv;
@@ -174,7 +180,7 @@ __device__ void rank_finish(const DockArgs &A, const PocketDev &Pk, const OutDev
     char *q = rbase;
     double *sG = (double *)q;
     q += lg_align16(8 * S);
-    double *cen = (double *)q;  // [S][3], by restart
+    float *cen = (float *)q;    // [S][3], by restart
     q += lg_align16(24 * S);
     int *ord = (int *)q;        // restart at each geometric position
     q += lg_align16(4 * S);
@@ -190,28 +196,30 @@ __device__ void rank_finish(const DockArgs &A, const PocketDev &Pk, const OutDev
     const size_t pstride = (size_t)A.ly.nmax * 3;
     const bool cluster = A.thr2g > 0.0f;
 
-    // 1. geometric scores (and centroids for the clustering bound)
+    // 1. geometric scores (and centroids for the clustering bound): FP32
+    // lookups summed in FP32 over lanes' atoms, then across lanes in a fixed
+    // tree (the torsion steps' overlap sums are FP32 too)
     for (int r = warp; r < S; r += W) {
         const float *x = pose0 + pstride * r;
-        double g = 0.0, cx = 0.0, cy = 0.0, cz = 0.0;
+        float g = 0.0f, cx = 0.0f, cy = 0.0f, cz = 0.0f;
         for (int i = lane; i < N; i += 32) {
             const float px = x[3 * i], py = x[3 * i + 1], pz = x[3 * i + 2];
-            g += (double)lookup_clamped(Go, px + Pk.c0, py + Pk.c0, pz + Pk.c0);
+            g += lookup_clamped(Go, px + Pk.c0, py + Pk.c0, pz + Pk.c0);
             cx += px;
             cy += py;
             cz += pz;
         }
-        g = warp_sum_d(g);
+        g = warp_sum_f(g);
         if (cluster) {
-            cx = warp_sum_d(cx);
-            cy = warp_sum_d(cy);
-            cz = warp_sum_d(cz);
+            cx = warp_sum_f(cx);
+            cy = warp_sum_f(cy);
+            cz = warp_sum_f(cz);
         }
         if (lane == 0) {
-            sG[r] = g;
-            cen[3 * r] = cx / N;
-            cen[3 * r + 1] = cy / N;
-            cen[3 * r + 2] = cz / N;
+            sG[r] = (double)g;
+            cen[3 * r] = cx / (float)N;
+            cen[3 * r + 1] = cy / (float)N;
+            cen[3 * r + 2] = cz / (float)N;
         }
     }
     __syncthreads();
@@ -229,28 +237,37 @@ __device__ void rank_finish(const DockArgs &A, const PocketDev &Pk, const OutDev
     // 3a. pairs within the threshold: bit q of row p for positions q < p
     const float lim = A.thr2g * (float)N;
     if (cluster) {
-        const double cut = (double)A.thr2g * (1.0 + 1e-4);
+        // the 1e-3 margin covers the FP32 rounding of the centroids (at most
+        // ~1e-4 of the squared threshold for 100 atoms in the box)
+        const float cut = A.thr2g * (1.0f + 1e-3f);
         for (int p = warp; p < S; p += W) {
             const int rp = ord[p];
             const float *x = pose0 + pstride * rp;
-            const double px = cen[3 * rp], py = cen[3 * rp + 1], pz = cen[3 * rp + 2];
+            const float px = cen[3 * rp], py = cen[3 * rp + 1], pz = cen[3 * rp + 2];
             for (int w = 0; 32 * w < p; ++w) {
+                // pairs of this word that pass the centroid bound, then each
+                // pair's sum of squared displacements by the whole warp
+                // (coalesced: lane i takes coordinates i, i + 32, ...; FP32
+                // lane sums combined in a fixed tree)
                 const int qq = 32 * w + lane;
-                bool within = false;
+                bool cand = false;
                 if (qq < p) {
                     const int rq = ord[qq];
-                    const double dx = cen[3 * rq] - px, dy = cen[3 * rq + 1] - py, dz = cen[3 * rq + 2] - pz;
-                    if (dx * dx + dy * dy + dz * dz <= cut) {
-                        const float *y = pose0 + pstride * rq;
-                        float ss = 0.0f;
-                        for (int i = 0; i < 3 * N; ++i) {
-                            const float d = x[i] - y[i];
-                            ss = fmaf(d, d, ss);
-                        }
-                        within = ss <= lim;
-                    }
+                    const float dx = cen[3 * rq] - px, dy = cen[3 * rq + 1] - py, dz = cen[3 * rq + 2] - pz;
+                    cand = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) <= cut;
                 }
-                const unsigned word = __ballot_sync(LG_FULL, within);
+                unsigned todo = __ballot_sync(LG_FULL, cand), word = 0u;
+                while (todo) {
+                    const int bq = __ffs(todo) - 1;
+                    todo &= todo - 1u;
+                    const float *y = pose0 + pstride * ord[32 * w + bq];
+                    float ss = 0.0f;
+                    for (int i = lane; i < 3 * N; i += 32) {
+                        const float d = x[i] - y[i];
+                        ss = fmaf(d, d, ss);
+                    }
+                    if (warp_sum_f(ss) <= lim) word |= 1u << bq;
+                }
                 if (lane == 0) bits[rank_row_off(p) + w] = word;
             }
         }
