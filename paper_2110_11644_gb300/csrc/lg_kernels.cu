@@ -10,11 +10,12 @@
 //    of 32 (the paper's CUDA design works in bundles of 32 atoms, Sec. 3.1).
 //
 //  * k_dock_batched -- persistent, ligands in descending estimated cost.  One
-//    CTA docks one ligand; each warp runs a tile of 8 restarts at once with 4
+//    CTA docks one ligand; each warp holds 8 restart slots at once with 4
 //    lanes per restart, each lane owning 9 of the 36 steps, so the work that is
 //    paid once per decision (circle set-up, argmax, moves) is shared by 8
 //    restarts, the 9 steps of a lane (every 4th step) are straight-line code,
-//    and the argmax needs 2 shuffles.
+//    and the argmax needs 2 shuffles; a slot whose restart has finished takes
+//    the warp's next restart at the next pass boundary.
 //
 // Every moving atom traces a circle about the bond axis,
 //     x(theta) = p + e1 cos(theta) + e2 sin(theta),
@@ -24,7 +25,10 @@
 //     |x_i(theta) - x_j|^2 = C + 2a cos(theta) + 2b sin(theta),
 // whose minimum over the circle is C - 2 sqrt(a^2 + b^2).  Pairs that stay
 // clear of d_clash at every step are dropped with one test; the others are
-// evaluated step by step.
+// evaluated step by step.  Fixed atoms outside the moving subtree's range of
+// axial and radial coordinates about the bond (widened by d_clash) are never
+// paired: a point's distance to a coaxial circle is at least the distance
+// between the two in the (axial, radial) plane.
 //
 // Positions live in centred grid units (see lg_internal.h).
 #include <curand_philox4x32_x.h>

@@ -187,7 +187,7 @@ int fetch_out(const OutDev &d, const lg_dock_result *o, int L, int S, int P, int
     return LG_OK;
 }
 
-// Warps per CTA for the batched kernel: restart tiles of 8 are spread over
+// Warps per CTA for the batched kernel: restart tiles (8 slots each) are spread over
 // the CTA's warps; up to 4 warps, dividing the tile count when possible,
 // unless the context option fixes the count.
 int choose_warps(int S, int opt) {
