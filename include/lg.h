@@ -210,7 +210,16 @@ typedef struct {
  *                      leader and geometric score (l*restarts + r)
  *   restart_rigid      optional, with rigid refinement on: the candidate taken
  *                      at every rigid move of every restart,
- *                      ((l*restarts + r)*passes + pass)*rigid_steps + j */
+ *                      ((l*restarts + r)*passes + pass)*rigid_steps + j
+ *   decision_rank      optional (not with the serving loop nor lg_dock_multi's
+ *                      ligand-major order: LG_EINVAL): for every torsion
+ *                      decision of every restart (the layout of restart_tors),
+ *                      1 + the number of steps ranked before the chosen one by
+ *                      overlap score (higher score, or equal score and lower
+ *                      step): the steps whose clash check a method cannot skip.
+ *                      Decisions skipped after convergence repeat the bond's
+ *                      previous decision and its rank; a bond that moves no
+ *                      atom ranks 1.  For accounting (work per decision). */
 typedef struct {
     int32_t mem;
     double *score;
@@ -224,6 +233,7 @@ typedef struct {
     int32_t *leader;
     double *restart_geo;
     uint8_t *restart_rigid;
+    uint8_t *decision_rank;
 } lg_dock_result;
 
 /* Dock and score a batch of ligands against one pocket (paper Sec. 3.1).

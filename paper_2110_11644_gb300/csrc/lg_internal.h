@@ -58,6 +58,7 @@ struct OutDev {
     int32_t *leader;
     double *restart_geo;
     uint8_t *restart_rigid;
+    uint8_t *decision_rank;
 };
 
 // Shared-memory layout of one docking CTA: a part shared by the CTA (the
@@ -251,7 +252,7 @@ cudaError_t launch_diag_philox(int n, const uint32_t *ctr, const uint32_t *key, 
                                cudaStream_t s);
 cudaError_t launch_dock_multi(const DockArgs &a, const MultiDev &m, int grid, int smem, cudaStream_t s);
 cudaError_t launch_flatten(const FlatArgs &f, int L, cudaStream_t s);
-cudaError_t dock_kernel_attributes(int W, int smem, int *ctas_per_sm, bool ranking, bool rigid);
+cudaError_t dock_kernel_attributes(int W, int smem, int *ctas_per_sm, bool ranking, bool rigid, bool trace);
 cudaError_t multi_kernel_attributes(int W, int smem, int *ctas_per_sm, bool ranking, bool rigid);
 cudaError_t plain_kernel_attributes(int smem);
 

@@ -388,9 +388,10 @@ __device__ __forceinline__ WarpView warp_view(char *sm, const Layout &L, int w) 
 //   q0 = (P.x, P.y, P.z, e1.x), q1 = (e1.y, e1.z, e2.x, e2.y),
 //   q2 = (e2.z, r2, inside, 0), q3 = (p.x, p.y, p.z, 0).
 __device__ int sweep_bond_plain(const DockArgs &A, const GridK &G, const CtaView &cv, const WarpView &wv, int N,
-                                int R, int k, int lane, float cl, float sl, float ct, float st) {
+                                int R, int k, int lane, float cl, float sl, float ct, float st, int &jr) {
     const int b = cv.rch[k], a = cv.par[b], e = cv.rend[k];
     const int m = e - b - 1;
+    jr = 1;
     if (m <= 0) return 0;  // nothing moves: every step scores 0, step 0 wins
 
     const float xbx = wv.Xx[b], xby = wv.Xy[b], xbz = wv.Xz[b];
@@ -475,8 +476,15 @@ __device__ int sweep_bond_plain(const DockArgs &A, const GridK &G, const CtaView
             ba = oa;
         }
     }
-    const int t = __shfl_sync(LG_FULL, ba, 0);  // lane 0's copy keeps control flow warp-uniform
-    if (t <= 0 || t >= LG_ANGLE_STEPS) return 0;
+    const int t0 = __shfl_sync(LG_FULL, ba, 0);  // lane 0's copy keeps control flow warp-uniform
+    const int t = (t0 > 0 && t0 < LG_ANGLE_STEPS) ? t0 : 0;
+    if (A.out.decision_rank) {  // steps ranked before the chosen one, admissible or not
+        const float bsu = __shfl_sync(LG_FULL, bs, 0);
+        const unsigned lo = __ballot_sync(LG_FULL, acc > bsu || (acc == bsu && lane < t));
+        const unsigned hi = __ballot_sync(LG_FULL, lane < 4 && (acc_t > bsu || (acc_t == bsu && 32 + lane < t)));
+        jr = 1 + __popc(lo) + __popc(hi);
+    }
+    if (t == 0) return 0;
 
     const float c = c_cos[t], s = c_sin[t];
     for (int i = b + 1 + lane; i < e; i += 32) {
@@ -602,17 +610,24 @@ __global__ void __launch_bounds__(1024) k_dock_plain(const __grid_constant__ Doc
         // the same exact stops as the restart-tiled form, per restart: R
         // decisions in a row without a move (torsions only), or a pass without
         // a move (with rigid moves); the remaining decisions are step 0
+        uint8_t *dr = A.out.decision_rank ? A.out.decision_rank + (size_t)S * P * r0 + (size_t)r * PR : nullptr;
         int zrun = 0;
         bool converged = false;
         for (int ps = 0; ps < P && !converged; ++ps) {
             bool moved = false;
             for (int k = 0; k < R; ++k) {
-                const int t = sweep_bond_plain(A, Go, cv, wv, N, R, k, lane, cl, sl, ct, st);
-                if (lane == 0) wv.tcur[ps * R + k] = (uint8_t)t;
+                int jr;
+                const int t = sweep_bond_plain(A, Go, cv, wv, N, R, k, lane, cl, sl, ct, st, jr);
+                if (lane == 0) {
+                    wv.tcur[ps * R + k] = (uint8_t)t;
+                    if (dr) dr[ps * R + k] = (uint8_t)jr;
+                }
                 moved = moved || t != 0;
                 zrun = t != 0 ? 0 : zrun + 1;
                 if (A.rigid_steps == 0 && zrun >= R) {
                     for (int q = ps * R + k + 1 + lane; q < P * R; q += 32) wv.tcur[q] = 0;
+                    if (dr && lane == 0)  // skipped decisions repeat the bond's previous one
+                        for (int q = ps * R + k + 1; q < P * R; ++q) dr[q] = dr[q - R];
                     converged = true;
                     break;
                 }
@@ -621,6 +636,8 @@ __global__ void __launch_bounds__(1024) k_dock_plain(const __grid_constant__ Doc
             if (A.rigid_steps > 0) moved = rigid_moves_plain(A, Go, A.out, wv, l, r, ps, N, R, lane) || moved;
             if (ps + 1 < P && !moved) {
                 for (int q = (ps + 1) * R + lane; q < P * R; q += 32) wv.tcur[q] = 0;
+                if (dr && lane == 0)
+                    for (int q = (ps + 1) * R; q < P * R; ++q) dr[q] = dr[q - R];
                 if (A.rigid_steps > 0 && lane == 0 && A.out.restart_rigid)
                     for (int q = (ps + 1) * A.rigid_steps; q < P * A.rigid_steps; ++q)
                         A.out.restart_rigid[((size_t)l * S + r) * P * A.rigid_steps + q] = 0;
@@ -743,9 +760,10 @@ __device__ __forceinline__ void flush_pool(const RtView &v, int rs, int g, int &
 // of a restart score neighbouring steps in the same instruction.  Returns the
 // step chosen for the lane's restart.
 __device__ __forceinline__ int sweep_bond_rt(const DockArgs &A, const GridK &G, const CtaView &cv, const RtView &v, int N, int R, int k,
-                             int rs, int g, bool valid, const float *cs, const float *sn) {
+                             int rs, int g, bool valid, const float *cs, const float *sn, bool want_rank, int &jr) {
     const int b = cv.rch[k], a = cv.par[b], e = cv.rend[k];
     const int m = e - b - 1;
+    jr = 1;
     if (m <= 0) return 0;  // nothing moves: every step scores 0, step 0 wins
 
     const float xbx = v.Xx[b * kTile + rs], xby = v.Xy[b * kTile + rs], xbz = v.Xz[b * kTile + rs];
@@ -891,6 +909,15 @@ __device__ __forceinline__ int sweep_bond_rt(const DockArgs &A, const GridK &G, 
         }
     }
     const int t = (bt > 0 && bt < LG_ANGLE_STEPS) ? bt : 0;
+    if (want_rank) {  // steps ranked before the chosen one, admissible or not
+        int cnt = 0;
+#pragma unroll
+        for (int j = 0; j < kStepsPerLane; ++j)
+            cnt += (acc[j] > bs || (acc[j] == bs && kLanesPerRestart * j + g < t)) ? 1 : 0;
+        cnt += __shfl_xor_sync(LG_FULL, cnt, 1);
+        cnt += __shfl_xor_sync(LG_FULL, cnt, 2);
+        jr = 1 + cnt;
+    }
     if (t != 0) {
         const float c = c_cos[t], s = c_sin[t];
         for (int i = b + 1 + g; i < e; i += kLanesPerRestart) {
@@ -974,9 +1001,10 @@ __device__ __forceinline__ bool rigid_moves_rt(const DockArgs &A, const GridK &G
     return moved;
 }
 
-// kRank: pose ranking on; kRigid: rigid refinement on (separate
-// instantiations, so the plain best-restart form carries none of their code)
-template <bool kRank, bool kRigid>
+// kRank: pose ranking on; kRigid: rigid refinement on; kTrace: decision
+// ranks recorded (separate instantiations, so the plain best-restart form
+// carries none of their code)
+template <bool kRank, bool kRigid, bool kTrace = false>
 __device__ __forceinline__ void dock_ligand_rt(const DockArgs &A, const PocketDev &Pk, const OutDev &O, int l, char *sm) {
     if (O.status[l] != LG_OK) return;  // rejected by the preparation kernel (uniform)
     const Layout &Ly = A.ly;
@@ -1043,6 +1071,10 @@ __device__ __forceinline__ void dock_ligand_rt(const DockArgs &A, const PocketDe
         if (__any_sync(LG_FULL, done)) {
             if (done) {
                 for (int q = pc * R + g; q < PR; q += kLanesPerRestart) v.tcur[q * kTile + rs] = 0;
+                if (kTrace && g == 0) {  // skipped passes repeat the last one
+                    uint8_t *dr = O.decision_rank + (size_t)S * P * r0 + (size_t)r * PR;
+                    for (int q = pc * R; q < PR; ++q) dr[q] = dr[q - R];
+                }
                 if (kRigid && g == 0 && O.restart_rigid)
                     for (int q = pc * A.rigid_steps; q < P * A.rigid_steps; ++q)
                         O.restart_rigid[((size_t)l * S + r) * P * A.rigid_steps + q] = 0;
@@ -1121,13 +1153,25 @@ __device__ __forceinline__ void dock_ligand_rt(const DockArgs &A, const PocketDe
         for (int k = 0; k < R; ++k) {
             // a restart R zero decisions in a row into the pass sequence repeats
             // them from here on (step 0, no move): its lanes skip the work
-            const int t = sweep_bond_rt(A, Go, cv, v, N, R, k, rs, g, active && (kRigid || zrun < R), cs, sn);
-            if (active && g == 0) v.tcur[(pc * R + k) * kTile + rs] = (uint8_t)t;
+            const bool sv = kRigid || zrun < R;
+            int jr;
+            const int t = sweep_bond_rt(A, Go, cv, v, N, R, k, rs, g, active && sv, cs, sn, kTrace, jr);
+            if (active && g == 0) {
+                v.tcur[(pc * R + k) * kTile + rs] = (uint8_t)t;
+                if (kTrace) {  // a skipped decision repeats the bond's previous one
+                    uint8_t *dr = O.decision_rank + (size_t)S * P * r0 + (size_t)r * PR + pc * R + k;
+                    *dr = sv ? (uint8_t)jr : dr[-R];
+                }
+            }
             movedp = movedp || t != 0;
             zrun = t != 0 ? 0 : zrun + 1;
             if (!kRigid && !__any_sync(LG_FULL, active && zrun < R)) {  // every active restart converged
                 if (active)
                     for (int q = pc * R + k + 1 + g; q < (pc + 1) * R; q += kLanesPerRestart) v.tcur[q * kTile + rs] = 0;
+                if (kTrace && active && g == 0) {
+                    uint8_t *dr = O.decision_rank + (size_t)S * P * r0 + (size_t)r * PR;
+                    for (int q = pc * R + k + 1; q < (pc + 1) * R; ++q) dr[q] = dr[q - R];
+                }
                 break;
             }
         }
@@ -1158,7 +1202,7 @@ __device__ __forceinline__ void dock_ligand_rt(const DockArgs &A, const PocketDe
 #ifndef LG_RT_MIN_BLOCKS
 #define LG_RT_MIN_BLOCKS 4
 #endif
-template <bool kRank, bool kRigid>
+template <bool kRank, bool kRigid, bool kTrace>
 __global__ void __launch_bounds__(128, LG_RT_MIN_BLOCKS) k_dock_batched(const __grid_constant__ DockArgs A) {
     extern __shared__ __align__(16) char sm[];
     __shared__ int s_lig;
@@ -1182,7 +1226,7 @@ __global__ void __launch_bounds__(128, LG_RT_MIN_BLOCKS) k_dock_batched(const __
         const int l = s_lig;
         __syncthreads();
         if (l < 0) break;
-        dock_ligand_rt<kRank, kRigid>(A, A.pocket, A.out, l, sm);
+        dock_ligand_rt<kRank, kRigid, kTrace>(A, A.pocket, A.out, l, sm);
     }
 }
 
@@ -1616,12 +1660,19 @@ static cudaError_t kernel_attributes(K kernel, int W, int smem, int *ctas_per_sm
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, kernel, 32 * W, smem);
 }
 
-cudaError_t dock_kernel_attributes(int W, int smem, int *ctas_per_sm, bool ranking, bool rigid) {
-    if (ranking)
-        return rigid ? kernel_attributes(k_dock_batched<true, true>, W, smem, ctas_per_sm)
-                     : kernel_attributes(k_dock_batched<true, false>, W, smem, ctas_per_sm);
-    return rigid ? kernel_attributes(k_dock_batched<false, true>, W, smem, ctas_per_sm)
-                 : kernel_attributes(k_dock_batched<false, false>, W, smem, ctas_per_sm);
+// The batched kernel of a feature set, called with the launch's arguments.
+template <typename F>
+static cudaError_t with_batched(bool ranking, bool rigid, bool trace, F &&f) {
+    if (ranking) {
+        if (rigid) return trace ? f(k_dock_batched<true, true, true>) : f(k_dock_batched<true, true, false>);
+        return trace ? f(k_dock_batched<true, false, true>) : f(k_dock_batched<true, false, false>);
+    }
+    if (rigid) return trace ? f(k_dock_batched<false, true, true>) : f(k_dock_batched<false, true, false>);
+    return trace ? f(k_dock_batched<false, false, true>) : f(k_dock_batched<false, false, false>);
+}
+
+cudaError_t dock_kernel_attributes(int W, int smem, int *ctas_per_sm, bool ranking, bool rigid, bool trace) {
+    return with_batched(ranking, rigid, trace, [&](auto kernel) { return kernel_attributes(kernel, W, smem, ctas_per_sm); });
 }
 
 cudaError_t multi_kernel_attributes(int W, int smem, int *ctas_per_sm, bool ranking, bool rigid) {
@@ -1658,16 +1709,10 @@ cudaError_t launch_dock_plain(const DockArgs &a, int ligand, int slot, cudaStrea
 }
 
 cudaError_t launch_dock_batched(const DockArgs &a, int grid, int smem, cudaStream_t s) {
-    const bool rigid = a.rigid_steps > 0;
-    if (a.ranking && rigid)
-        k_dock_batched<true, true><<<grid, 32 * a.ly.W, smem, s>>>(a);
-    else if (a.ranking)
-        k_dock_batched<true, false><<<grid, 32 * a.ly.W, smem, s>>>(a);
-    else if (rigid)
-        k_dock_batched<false, true><<<grid, 32 * a.ly.W, smem, s>>>(a);
-    else
-        k_dock_batched<false, false><<<grid, 32 * a.ly.W, smem, s>>>(a);
-    return cudaGetLastError();
+    return with_batched(a.ranking, a.rigid_steps > 0, a.out.decision_rank != nullptr, [&](auto kernel) {
+        kernel<<<grid, 32 * a.ly.W, smem, s>>>(a);
+        return cudaGetLastError();
+    });
 }
 
 cudaError_t launch_dock_multi(const DockArgs &a, const MultiDev &m, int grid, int smem, cudaStream_t s) {

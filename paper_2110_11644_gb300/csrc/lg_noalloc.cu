@@ -109,6 +109,7 @@ extern "C" int lg_dock_batch_noalloc(lg_ctx *c, int32_t pid, const lg_ligand_bat
     a.out.pose = o->pose;
     a.out.restart_score = o->restart_score;
     a.out.restart_tors = o->restart_tors;
+    a.out.decision_rank = o->decision_rank;
     a.out.restart_rigid = o->restart_rigid;
     a.S = p->restarts;
     a.P = p->passes;
@@ -128,7 +129,7 @@ extern "C" int lg_dock_batch_noalloc(lg_ctx *c, int32_t pid, const lg_ligand_bat
         a.ly = make_layout(nmax, rmax, a.P, W, want_pose);
         a.lrt = make_layout_rt(nmax, rmax, a.P, want_pose);
         smem = a.ly.cta_bytes + W * a.lrt.warp_bytes;
-        if ((e = dock_kernel_attributes(W, smem, &occ, false, a.rigid_steps > 0)) != cudaSuccess)
+        if ((e = dock_kernel_attributes(W, smem, &occ, false, a.rigid_steps > 0, a.out.decision_rank != nullptr)) != cudaSuccess)
             return fail(LG_ECUDA, std::string("dock kernel attributes: ") + cudaGetErrorString(e));
         if (occ > 0 || W == 1) break;
         W = std::max(1, W / 2);

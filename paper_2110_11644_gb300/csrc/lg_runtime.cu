@@ -150,6 +150,7 @@ int stage_out(DevBuf &buf, const lg_dock_result *o, int L, int S, int P, int64_t
     const size_t o_g = o->restart_geo ? c.take(8 * (size_t)L * S) : 0;
     const size_t n_rig = (size_t)L * S * P * Rs;
     const size_t o_rg = o->restart_rigid ? c.take(n_rig + 1) : 0;
+    const size_t o_dr = o->decision_rank ? c.take((size_t)S * P * R + 1) : 0;
     if (buf.ensure(c.off)) return fail(LG_ENOMEM, "device output allocation failed");
     char *base = (char *)buf.p;
     d->score = (double *)(base + o_s);
@@ -163,6 +164,7 @@ int stage_out(DevBuf &buf, const lg_dock_result *o, int L, int S, int P, int64_t
     d->leader = o->leader ? (int32_t *)(base + o_ld) : nullptr;
     d->restart_geo = o->restart_geo ? (double *)(base + o_g) : nullptr;
     d->restart_rigid = o->restart_rigid ? (uint8_t *)(base + o_rg) : nullptr;
+    d->decision_rank = o->decision_rank ? (uint8_t *)(base + o_dr) : nullptr;
     return LG_OK;
 }
 
@@ -183,6 +185,7 @@ int fetch_out(const OutDev &d, const lg_dock_result *o, int L, int S, int P, int
     if (o->leader) cp(o->leader, d.leader, 4 * (size_t)L * S);
     if (o->restart_geo) cp(o->restart_geo, d.restart_geo, 8 * (size_t)L * S);
     if (o->restart_rigid) cp(o->restart_rigid, d.restart_rigid, (size_t)L * S * P * Rs);
+    if (o->decision_rank) cp(o->decision_rank, d.decision_rank, (size_t)S * P * R);
     if (e != cudaSuccess) return fail(LG_ECUDA, std::string("result download: ") + cudaGetErrorString(e));
     return LG_OK;
 }
@@ -256,6 +259,10 @@ int dock_device(lg_ctx *ctx, const PocketDev &pk, const BatchDev &bd, const OutD
     const int L = bd.L;
     const bool plain = p->mode == LG_MODE_PLAIN;
     if (plain && multi) return fail(LG_EINVAL, "several pockets run in the batched mode only");
+    if (multi)
+        for (int k = 0; k < multi->np; ++k)
+            if (multi->out[k].decision_rank)
+                return fail(LG_EINVAL, "decision_rank needs one launch per pocket (the pocket-major order)");
     a.rigid_steps = p->rigid_steps;
     a.rigid_shift_g = (float)((double)p->rigid_shift / h);
     a.ranking = ranking_on(p) ? 1 : 0;
@@ -327,7 +334,7 @@ int dock_device(lg_ctx *ctx, const PocketDev &pk, const BatchDev &bd, const OutD
             a.lrt = make_layout_rt(u.nmax, rmax, a.P, want_pose);
             u.smem = std::max(a.ly.cta_bytes + u.W * a.lrt.warp_bytes, a.ly.cta_bytes + rank_smem);
             e = multi ? multi_kernel_attributes(u.W, u.smem, &u.occ, a.ranking, a.rigid_steps > 0)
-                      : dock_kernel_attributes(u.W, u.smem, &u.occ, a.ranking, a.rigid_steps > 0);
+                      : dock_kernel_attributes(u.W, u.smem, &u.occ, a.ranking, a.rigid_steps > 0, a.out.decision_rank != nullptr);
             if (e != cudaSuccess) return fail(LG_ECUDA, std::string("dock kernel attributes: ") + cudaGetErrorString(e));
             if (u.occ > 0 || u.W == 1) break;
             u.W = std::max(1, u.W / 2);
@@ -403,7 +410,7 @@ int dock_device(lg_ctx *ctx, const PocketDev &pk, const BatchDev &bd, const OutD
         int big = 0, occ = 0;
         for (const Unit &u : units) big = std::max(big, u.smem);
         return multi ? multi_kernel_attributes(units.front().W, big, &occ, a.ranking, a.rigid_steps > 0)
-                     : dock_kernel_attributes(units.front().W, big, &occ, a.ranking, a.rigid_steps > 0);
+                     : dock_kernel_attributes(units.front().W, big, &occ, a.ranking, a.rigid_steps > 0, a.out.decision_rank != nullptr);
     };
     auto launch_unit = [&](const Unit &u, int cap) -> cudaError_t {
         a.ly = make_layout(u.nmax, rmax, a.P, u.W, want_pose);
@@ -606,6 +613,7 @@ int resolve_out(lg_ctx *c, DevBuf &buf, const lg_ligand_batch *b, const lg_dock_
     od->leader = o->leader;
     od->restart_geo = o->restart_geo;
     od->restart_rigid = o->restart_rigid;
+    od->decision_rank = o->decision_rank;
     return LG_OK;
 }
 

@@ -454,6 +454,7 @@ int lg_stream_submit(lg_ctx *c, int32_t pid, const lg_ligand_batch *b, const lg_
     if (b->L > 0 && (!b->atom_off || !b->x || !b->y || !b->z || !b->q || !b->type || !b->parent || !b->rot_off || !b->uid))
         return fail(LG_EINVAL, "null batch array");
     if (!o->score || !o->best_restart || !o->status) return fail(LG_EINVAL, "score, best_restart and status are required");
+    if (o->decision_rank) return fail(LG_EINVAL, "decision_rank is not served (use lg_dock_batch)");
     auto r = std::make_shared<Request>();
     {
         std::lock_guard<std::mutex> g(c->mu);

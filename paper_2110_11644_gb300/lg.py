@@ -49,7 +49,7 @@ class lg_dock_params(ctypes.Structure):
 class lg_dock_result(ctypes.Structure):
     _fields_ = [("mem", ctypes.c_int32), ("score", _P), ("best_restart", _P), ("tors_idx", _P), ("pose", _P),
                 ("status", _P), ("restart_score", _P), ("restart_tors", _P), ("rank", _P), ("leader", _P),
-                ("restart_geo", _P), ("restart_rigid", _P)]
+                ("restart_geo", _P), ("restart_rigid", _P), ("decision_rank", _P)]
 
 
 class lg_flatten_params(ctypes.Structure):
@@ -297,7 +297,7 @@ def make_params(restarts, passes, seed, d_clash=2.0, mode=LG_MODE_BATCHED, plain
 
 
 def alloc_result(L, A, R, S, P, device=False, pose=True, tors=True, restart_score=False, restart_tors=False,
-                 ranking=False, rigid_steps=0):
+                 ranking=False, rigid_steps=0, decision_rank=False):
     """Output arrays for a batch: numpy (host) or CUDA torch tensors (device)."""
     if device:
         import torch
@@ -308,7 +308,8 @@ def alloc_result(L, A, R, S, P, device=False, pose=True, tors=True, restart_scor
                     restart_tors=z(S * P * R, torch.uint8) if restart_tors else None,
                     rank=z(L * S, torch.int32) if ranking else None, leader=z(L * S, torch.int32) if ranking else None,
                     restart_geo=z(L * S, torch.float64) if ranking else None,
-                    restart_rigid=z(L * S * P * rigid_steps, torch.uint8) if rigid_steps else None)
+                    restart_rigid=z(L * S * P * rigid_steps, torch.uint8) if rigid_steps else None,
+                    decision_rank=z(S * P * R, torch.uint8) if decision_rank else None)
     else:
         z = lambda n, dt: np.zeros(max(n, 1), dt)
         arrs = dict(score=z(L, np.float64), best_restart=z(L, np.int32), status=z(L, np.int32),
@@ -317,7 +318,8 @@ def alloc_result(L, A, R, S, P, device=False, pose=True, tors=True, restart_scor
                     restart_tors=z(S * P * R, np.uint8) if restart_tors else None,
                     rank=z(L * S, np.int32) if ranking else None, leader=z(L * S, np.int32) if ranking else None,
                     restart_geo=z(L * S, np.float64) if ranking else None,
-                    restart_rigid=z(L * S * P * rigid_steps, np.uint8) if rigid_steps else None)
+                    restart_rigid=z(L * S * P * rigid_steps, np.uint8) if rigid_steps else None,
+                    decision_rank=z(S * P * R, np.uint8) if decision_rank else None)
     r = lg_dock_result()
     r.mem = LG_MEM_DEVICE if device else LG_MEM_HOST
     for k, v in arrs.items():
@@ -379,7 +381,7 @@ class Context:
 
     def dock(self, pid, batch, params, *, mode=LG_MODE_BATCHED, device_io=False, pose=True, tors=True,
              restart_score=False, restart_tors=False, restart_rigid=False, stream=None, plain_streams=0, max_atoms=0,
-             max_rot=0):
+             max_rot=0, decision_rank=False):
         """Dock a CSR batch (numpy attributes).  With device_io=True the batch is
         copied to the GPU first and the results come back from device buffers;
         otherwise the library stages host memory itself.  Returns numpy arrays.
@@ -397,7 +399,8 @@ class Context:
         p = make_params(S, P, params.seed, params.d_clash, mode, plain_streams, max_atoms, max_rot, thr, K, Rs,
                         float(getattr(params, "rigid_shift", 0.375)))
         r, outs = alloc_result(L, A, R, S, P, device=device_io, pose=pose, tors=tors, restart_score=restart_score,
-                               restart_tors=restart_tors, ranking=ranking, rigid_steps=Rs if restart_rigid else 0)
+                               restart_tors=restart_tors, ranking=ranking, rigid_steps=Rs if restart_rigid else 0,
+                               decision_rank=decision_rank)
         if device_io:
             import torch
             s = torch.cuda.current_stream()
@@ -407,11 +410,12 @@ class Context:
         else:
             lg_dock_batch(self.h, pid, b, p, r, stream)
         n = dict(score=L, best_restart=L, status=L, tors_idx=P * R, pose=3 * A, restart_score=L * S,
-                 restart_tors=S * P * R, rank=L * S, leader=L * S, restart_geo=L * S, restart_rigid=L * S * P * Rs)
+                 restart_tors=S * P * R, rank=L * S, leader=L * S, restart_geo=L * S, restart_rigid=L * S * P * Rs,
+                 decision_rank=S * P * R)
         return {k: (v[:n[k]] if v is not None else None) for k, v in outs.items()}
 
     def dock_multi(self, pids, batch, params, *, device_io=False, pose=True, tors=True, restart_score=False,
-                   restart_tors=False, restart_rigid=False, stream=None, max_atoms=0, max_rot=0):
+                   restart_tors=False, restart_rigid=False, stream=None, max_atoms=0, max_rot=0, decision_rank=False):
         """Dock a CSR batch against several pockets in one launch; returns one
         dict of numpy arrays per pocket (as dock())."""
         L = len(batch.atom_off) - 1
@@ -426,7 +430,8 @@ class Context:
         p = make_params(S, P, params.seed, params.d_clash, LG_MODE_BATCHED, 0, max_atoms, max_rot, thr, K, Rs,
                         float(getattr(params, "rigid_shift", 0.375)))
         res = [alloc_result(L, A, R, S, P, device=device_io, pose=pose, tors=tors, restart_score=restart_score,
-                            restart_tors=restart_tors, ranking=ranking, rigid_steps=Rs if restart_rigid else 0)
+                            restart_tors=restart_tors, ranking=ranking, rigid_steps=Rs if restart_rigid else 0,
+                               decision_rank=decision_rank)
                for _ in pids]
         if device_io:
             import torch
@@ -436,7 +441,8 @@ class Context:
         else:
             lg_dock_multi(self.h, pids, b, p, [r for r, _ in res], stream)
         n = dict(score=L, best_restart=L, status=L, tors_idx=P * R, pose=3 * A, restart_score=L * S,
-                 restart_tors=S * P * R, rank=L * S, leader=L * S, restart_geo=L * S, restart_rigid=L * S * P * Rs)
+                 restart_tors=S * P * R, rank=L * S, leader=L * S, restart_geo=L * S, restart_rigid=L * S * P * Rs,
+                 decision_rank=S * P * R)
         out = []
         for _, outs in res:
             if device_io:

@@ -14,10 +14,13 @@ with N the atoms, m_k the atoms torsional bond k moves and Pi_k the clash
 pairs of bond k (moving atom, atom outside the child's subtree, three or more
 bonds apart).  Per step and moving atom: 21 to rotate it about the bond,
 30 for a trilinear lookup; per restart 21 N + 40 for the rigid pose and 64 per
-atom for the final score.  A clash pair costs 8 and is credited once per
-decision (the chosen step's check, the least any method needs); clash checks
-of the other steps are not credited.  ligand_flops_circle counts the lower
-figure of the circle form the kernels evaluate.
+atom for the final score.  A clash pair costs 8 and is credited j* times per
+decision, j* = 1 + the number of steps ranked before the chosen one by overlap
+score: a method must clash-check those steps (each was rejected) and the
+chosen one, and no others.  ligand_flops takes j* = 1, a lower bound;
+ligand_flops_ranked takes each decision's j* from the docking run's own
+decisions (lg_dock_result.decision_rank).  ligand_flops_circle counts the
+lower figure of the circle form the kernels evaluate.
 """
 from __future__ import annotations
 
@@ -93,6 +96,25 @@ def ligand_flops(batch, restarts: int, passes: int, rigid_steps: int = 0) -> np.
     np.add.at(sweep, rl, per_bond)
     rigid = rigid_steps * 13.0 * N * (C_ROT + C_TRI)
     return restarts * (C_POSE_ATOM * N + C_RESTART + passes * (sweep + rigid) + C_FIN * N)
+
+
+def ligand_flops_ranked(batch, restarts: int, passes: int, decision_rank, rigid_steps: int = 0) -> np.ndarray:
+    """ligand_flops with each decision's clash pairs credited j* times:
+    decision_rank holds j* for every decision of every restart in the layout
+    of lg_dock_result.restart_tors (restarts*passes*rot_off[l] + (r*passes +
+    pass)*R_l + k)."""
+    _, pairs, rl, L = _bond_counts(batch)
+    roff = batch.rot_off.astype(np.int64)
+    nrot = np.diff(roff)
+    per = restarts * passes * nrot                      # decisions per ligand
+    ranks = np.asarray(decision_rank, np.float64)[: int(per.sum())]
+    lig = np.repeat(np.arange(L), per)
+    local = np.arange(ranks.size) - np.repeat(np.cumsum(per) - per, per)
+    bond = roff[lig] + local % np.maximum(nrot[lig], 1)
+    jsum = np.bincount(bond, weights=ranks, minlength=int(roff[-1]))  # sum of j* per bond
+    extra = np.zeros(L)
+    np.add.at(extra, rl, C_PAIR * (jsum - restarts * passes) * pairs)
+    return ligand_flops(batch, restarts, passes, rigid_steps) + extra
 
 
 def ligand_flops_circle(batch, restarts: int, passes: int) -> np.ndarray:

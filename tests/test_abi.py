@@ -38,7 +38,7 @@ def test_struct_layouts_match_header():
     # sizes of the ctypes mirrors against the C layout rules (LP64)
     assert ctypes.sizeof(lg.lg_ligand_batch) == 8 + 10 * 8
     assert ctypes.sizeof(lg.lg_dock_params) == 64
-    assert ctypes.sizeof(lg.lg_dock_result) == 8 + 11 * 8
+    assert ctypes.sizeof(lg.lg_dock_result) == 8 + 12 * 8
     assert ctypes.sizeof(lg.lg_pose_batch) == 8 + 4 * 8
     assert ctypes.sizeof(lg.lg_stats) == 40
     assert ctypes.sizeof(lg.lg_flatten_params) == 20

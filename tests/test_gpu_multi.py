@@ -118,5 +118,16 @@ def test_multi_bad_arguments(multi):
         lg.lg_dock_multi(ctx.h, pids, b, p, [r] * len(pids))
     with pytest.raises(lg.LgError):
         lg.lg_dock_multi(ctx.h, [], b, lg.make_params(16, 2, 1), [])
+    # decision ranks: per-pocket launches only (pocket-major); ligand-major refuses
+    pm = ctx.dock_multi(pids, batch, _params(), restart_tors=True, decision_rank=True)
+    for pid, g in zip(pids, pm):
+        want = ctx.dock(pid, batch, _params(), restart_tors=True, decision_rank=True)
+        assert np.array_equal(g["decision_rank"], want["decision_rank"])
+    ctx.set_option("multi_order", 1)
+    try:
+        with pytest.raises(lg.LgError):
+            ctx.dock_multi(pids, batch, _params(), decision_rank=True)
+    finally:
+        ctx.set_option("multi_order", 0)
     # the context stays usable
     assert all(np.all(g["status"] == 0) for g in ctx.dock_multi(pids, batch, _params()))

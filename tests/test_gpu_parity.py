@@ -95,6 +95,55 @@ def test_plain_and_batched_forms_agree_bitwise(ctx, cfg1, pocket1):
         assert np.array_equal(a[k], b[k]), k
 
 
+def _oracle_rank_bounds(trace_s, choice):
+    """Per decision, the least and largest 1 + (steps ranked before the
+    chosen one by overlap score, ties to the lower step) over orderings that
+    may swap scores within the 1e-5 near-tie tolerance."""
+    s = trace_s.reshape(-1, 36)
+    c = choice.astype(int)
+    sc = s[np.arange(len(c)), c]
+    tol = 1e-5 * np.maximum(np.abs(s).max(1), 1e-30)
+    other = np.arange(36)[None, :] != c[:, None]
+    exact = 1 + ((s > sc[:, None]) | ((s == sc[:, None]) & (np.arange(36)[None, :] < c[:, None]))).sum(1)
+    lo = 1 + ((s > (sc + tol)[:, None]) & other).sum(1)
+    hi = 1 + ((s >= (sc - tol)[:, None]) & other).sum(1)
+    return exact, lo, hi
+
+
+def test_decision_ranks_match_oracle_and_both_forms(ctx, cfg1, pocket1, cfg2_pocket):
+    # decision_rank: 1 + the steps ranked before the chosen one; the oracle
+    # replays the GPU's choices and ranks the same steps in FP64
+    pocket, batch, params = cfg1
+    sub = batch.subset(range(96))
+    a = _dock(ctx, pocket1, sub, params, decision_rank=True)
+    b = _dock(ctx, pocket1, sub, params, decision_rank=True, mode=lg.LG_MODE_PLAIN, plain_streams=4)
+    c = _dock(ctx, pocket1, sub, params, decision_rank=True, device_io=True)
+    assert np.array_equal(a["decision_rank"], b["decision_rank"])
+    assert np.array_equal(a["decision_rank"], c["decision_rank"])
+    plain = _dock(ctx, pocket1, sub, params)
+    for k in plain:  # asking for the ranks changes nothing else
+        if plain[k] is not None:
+            assert np.array_equal(plain[k], a[k]), k
+    rep = oracle.dock(pocket, sub, params, replay=a["restart_tors"], trace=True)
+    exact, lo, hi = _oracle_rank_bounds(rep["trace_s"], a["restart_tors"])
+    g = a["decision_rank"].astype(int)
+    assert np.all((g >= lo) & (g <= hi))
+    assert np.mean(g == exact) > 0.99
+    assert g.min() >= 1 and g.max() <= 36 and g.mean() > 1.0
+    # throughput ligands, whose convergence stops skip decisions: the skipped
+    # ones repeat the bond's previous rank, as the oracle's full sweep finds
+    pid = ctx.load_pocket(cfg2_pocket)
+    prm2 = synth.config_params(2)
+    lig2 = synth.config_ligands(2, 48)
+    d = _dock(ctx, pid, lig2, prm2, decision_rank=True)
+    ctx.unload_pocket(pid)
+    rep = oracle.dock(cfg2_pocket, lig2, prm2, replay=d["restart_tors"], trace=True)
+    exact, lo, hi = _oracle_rank_bounds(rep["trace_s"], d["restart_tors"])
+    g = d["decision_rank"].astype(int)
+    assert np.all((g >= lo) & (g <= hi))
+    assert np.mean(g == exact) > 0.99
+
+
 def test_host_and_device_io_agree_and_runs_repeat(ctx, cfg1, pocket1):
     _, batch, params = cfg1
     a = _dock(ctx, pocket1, batch, params)

@@ -134,3 +134,34 @@ def test_cost_model_counts_match_brute_force():
     N = np.diff(batch.atom_off)
     want = 30 * (21 * N + 40 + 3 * (36 * 51 * m_got + 8 * p_got) + 64 * N)
     assert np.allclose(F, want, rtol=0, atol=1e-6)
+
+
+def test_ranked_flops_credit_each_decision():
+    # j* from the oracle's own decisions (1 + steps ranked before the chosen
+    # one); all ones give the lower bound; otherwise the pair term counts
+    # j* * Pi_k * 8 decision by decision
+    import oracle
+    pocket = synth.config_pocket(1)
+    batch = synth.config_ligands(1, 24)
+    params = synth.config_params(1)
+    S, P = params.restarts, params.passes
+    out = oracle.dock(pocket, batch, params, trace=True)
+    s = out["trace_s"].reshape(-1, 36)
+    ch = out["choice"].astype(int)
+    sc = s[np.arange(len(ch)), ch]
+    jstar = 1 + ((s > sc[:, None]) | ((s == sc[:, None]) & (np.arange(36)[None, :] < ch[:, None]))).sum(1)
+    assert jstar.max() > 1
+    ones = shard.ligand_flops_ranked(batch, S, P, np.ones(len(ch)))
+    assert np.allclose(ones, shard.ligand_flops(batch, S, P), rtol=0, atol=1e-6)
+    got = shard.ligand_flops_ranked(batch, S, P, jstar)
+    m, pairs, rl, _ = shard._bond_counts(batch)
+    for l in range(batch.L):
+        N = int(batch.atom_off[l + 1] - batch.atom_off[l])
+        r0, R = int(batch.rot_off[l]), int(batch.rot_off[l + 1] - batch.rot_off[l])
+        want = S * (21 * N + 40 + 64 * N)
+        for r in range(S):
+            for ps in range(P):
+                for k in range(R):
+                    d = S * P * r0 + (r * P + ps) * R + k
+                    want += 36 * 51 * m[r0 + k] + 8 * pairs[r0 + k] * jstar[d]
+        assert abs(got[l] - want) <= 1e-9 * want, l
