@@ -559,7 +559,7 @@ def main():
     # accounting call on the same batch (same decisions, bit for bit)
     F1 = algorithmic_flops(batch, S, P)
     dock_ms = st.dock_ms_total / max(st.dock_calls, 1)
-    acc_r, acc_o = lg.alloc_result(L, A, R, S, P, device=True, pose=False, tors=False, decision_rank=True)
+    acc_r, acc_o = lg.alloc_result(L, A, R, S, P, device=True, pose=True, tors=True, decision_rank=True)
     lg.lg_dock_batch(ctx.h, pid, bstruct, pstruct, acc_r, sh)
     torch.cuda.synchronize()
     ranks = acc_o["decision_rank"][:S * P * R].cpu().numpy()
