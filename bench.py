@@ -139,10 +139,15 @@ KERNEL_SOURCES = ("lg_kernels.cu", "lg_device.cuh", "lg_internal.h")
 
 
 def kernel_source_sha() -> str:
-    """Hash of the sources that define the docking kernels."""
+    """Hash of the code (comments and blank space removed) of the sources that
+    define the docking kernels."""
+    import re
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
-        h.update(open(os.path.join(ROOT, "paper_2110_11644_gb300", "csrc", f), "rb").read())
+        text = open(os.path.join(ROOT, "paper_2110_11644_gb300", "csrc", f), encoding="utf-8").read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", " ", text)
+        h.update(" ".join(text.split()).encode())
     return h.hexdigest()[:16]
 
 

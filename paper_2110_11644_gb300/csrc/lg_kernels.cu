@@ -934,7 +934,7 @@ __device__ __forceinline__ int sweep_bond_rt(const DockArgs &A, const GridK &G, 
     return t;
 }
 
-// Rigid greedy moves of the tile's restarts after torsion pass ps: lane g of
+// Rigid greedy moves of the warp's restart slots after torsion pass ps: lane g of
 // a restart scores all 13 candidates on atoms i = g (mod 4), in order, with
 // FP32 sums s_g; a candidate's score is (s0 + s1) + (s2 + s3) of the FP32
 // overlap lookups of the atoms at their moved positions; the best (highest
