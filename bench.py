@@ -254,7 +254,9 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * T / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "step": f"{sample} ligands of the workload per step (bounded sample)"},
+            "config": {"workload": WORKLOAD, "ligands_per_gpu": N_LIGANDS, "restarts": params.restarts,
+                       "passes": params.passes, "angle_steps": 36,
+                       "step": f"{sample} ligands of the workload per step (bounded sample)"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
                              "sample": f"{sample} ligands per step, {args.steps} steps"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
