@@ -216,8 +216,9 @@ struct FlatArgs {
 };
 
 constexpr int kFlatWarps = 4;
+constexpr int kFlatChunk = 128;  // pair coefficients built per round (4 per lane)
 __host__ __device__ inline int flat_warp_bytes(int nmax) {
-    return lg_align16(12 * nmax) + lg_align16(4 * nmax) + lg_align16(48 * nmax) + 32 * 16;
+    return lg_align16(12 * nmax) + lg_align16(4 * nmax) + lg_align16(48 * nmax) + kFlatChunk * 16;
 }
 
 // Several pockets in one persistent launch: work items are (pocket, ligand)

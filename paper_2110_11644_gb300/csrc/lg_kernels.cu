@@ -1293,9 +1293,9 @@ __global__ void __launch_bounds__(128, LG_RT_MIN_BLOCKS) k_dock_multi(const __gr
 // (lane t: step t, lanes 0..3 also steps 32..35).  Only the (moving, fixed)
 // pairs change with the step: their distance on the step's circle point is
 //     |x_i(theta) - x_j| = sqrt(C + A2 cos(theta) + B2 sin(theta)),
-// with the pair coefficients built once per decision, 32 pairs at a time by the
-// lanes and read back by broadcast.  Per step, distances are summed in FP32
-// within a 32-pair chunk and the chunks in FP64; the clash rule of the sweep
+// with the pair coefficients built once per decision, 128 pairs at a time by
+// the lanes and read back by broadcast.  Per step, distances are summed in FP32
+// within a 128-pair chunk and the chunks in FP64; the clash rule of the sweep
 // (pairs at least three bonds apart, at least d_clash) decides admissibility;
 // the admissible step with the largest sum wins, the lowest step on ties.
 __global__ void __launch_bounds__(32 * kFlatWarps) k_flatten(const __grid_constant__ FlatArgs F) {
@@ -1319,7 +1319,7 @@ __global__ void __launch_bounds__(32 * kFlatWarps) k_flatten(const __grid_consta
     float *Xx = (float *)wb, *Xy = Xx + nm, *Xz = Xy + nm;
     int *par = (int *)(wb + lg_align16(12 * nm));
     float4 *circ = (float4 *)(wb + lg_align16(12 * nm) + lg_align16(4 * nm));  // [nm][3]: (p, r2), e1, e2
-    float4 *chunk = circ + 3 * nm;                                              // [32] (C, A2, B2, checked)
+    float4 *chunk = circ + 3 * nm;                                              // [kFlatChunk] (C, A2, B2, checked)
     const int r0 = B.rot_off[l], R = B.rot_off[l + 1] - r0;
     const double cx = F.centroid[3 * l], cy = F.centroid[3 * l + 1], cz = F.centroid[3 * l + 2];
     for (int i = lane; i < N; i += 32) {
@@ -1363,19 +1363,22 @@ __global__ void __launch_bounds__(32 * kFlatWarps) k_flatten(const __grid_consta
                 D[j] = 0.0;
                 mn[j] = INFINITY;
             }
-            for (int q0 = 0; q0 < total; q0 += 32) {
-                const int q = q0 + lane;
-                if (q < total) {
-                    const int i = b + 1 + q / nf, jj = q - (q / nf) * nf;
-                    const int j = jj < b ? jj : jj + (e - b);
-                    const float4 pc = circ[3 * i], e1 = circ[3 * i + 1], e2 = circ[3 * i + 2];
-                    const PairC pq = pair_coeffs(pc.x, pc.y, pc.z, e1.x, e1.y, e1.z, e2.x, e2.y, e2.z, pc.w, Xx[j], Xy[j],
-                                                 Xz[j], F.dc2);
-                    const bool checked = !(j == a && par[i] == b);  // the one pair closer than 3 bonds
-                    chunk[lane] = make_float4(pq.C, pq.A2, pq.B2, checked ? 1.0f : 0.0f);
+            for (int q0 = 0; q0 < total; q0 += kFlatChunk) {
+#pragma unroll
+                for (int u = 0; u < kFlatChunk / 32; ++u) {
+                    const int q = q0 + 32 * u + lane;
+                    if (q < total) {
+                        const int i = b + 1 + q / nf, jj = q - (q / nf) * nf;
+                        const int j = jj < b ? jj : jj + (e - b);
+                        const float4 pc = circ[3 * i], e1 = circ[3 * i + 1], e2 = circ[3 * i + 2];
+                        const PairC pq = pair_coeffs(pc.x, pc.y, pc.z, e1.x, e1.y, e1.z, e2.x, e2.y, e2.z, pc.w, Xx[j],
+                                                     Xy[j], Xz[j], F.dc2);
+                        const bool checked = !(j == a && par[i] == b);  // the one pair closer than 3 bonds
+                        chunk[32 * u + lane] = make_float4(pq.C, pq.A2, pq.B2, checked ? 1.0f : 0.0f);
+                    }
                 }
                 __syncwarp();
-                const int n = min(32, total - q0);
+                const int n = min(kFlatChunk, total - q0);
                 float acc[kStepsPerLane];
 #pragma unroll
                 for (int j = 0; j < kStepsPerLane; ++j) acc[j] = 0.0f;
@@ -1384,7 +1387,10 @@ __global__ void __launch_bounds__(32 * kFlatWarps) k_flatten(const __grid_consta
 #pragma unroll
                     for (int j = 0; j < kStepsPerLane; ++j) {
                         const float d = fmaf(cf.z, sn[j], fmaf(cf.y, cs[j], cf.x));
-                        acc[j] += sqrtf(fmaxf(d, 0.0f));
+                        // d * rsqrt(d): the hardware reciprocal square root
+                        // (about 2 ulp) instead of a correctly rounded sqrt;
+                        // sums of positive terms keep that relative error
+                        acc[j] += d > 0.0f ? d * rsqrtf(d) : 0.0f;
                         if (cf.w != 0.0f) mn[j] = fminf(mn[j], d);
                     }
                 }
