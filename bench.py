@@ -135,6 +135,39 @@ def oracle_rate(pocket, batch, params, budget_s: float, chunk: int = 256, max_li
     return done / dt, done, dt
 
 
+def oracle_other_workloads(budget_s: float) -> dict:
+    """The oracle on the host cores on the other workloads: the tiny set
+    whole (48^3 pocket, 256 ligands, 16 restarts, 2 passes), the first
+    ligands of the heavy-tailed library, and the first ligands of the
+    throughput generator against the first pockets of the several-pocket set."""
+    import oracle
+    from paper_2110_11644_gb300 import synth
+    out = {}
+    p1, b1, prm1 = synth.config_pocket(1), synth.config_ligands(1), synth.config_params(1)
+    t0 = time.perf_counter()
+    oracle.dock(p1, b1, prm1, nthreads=cpu_cores())
+    dt = time.perf_counter() - t0
+    out["tiny_whole"] = {"value": b1.L / dt, "unit": UNIT, "ligands": b1.L, "seconds": round(dt, 2)}
+    b3 = synth.config_ligands(3, 2000, uid_base=2 << 40)
+    rate, n, secs = oracle_rate(synth.config_pocket(2), b3, synth.config_params(3), budget_s)
+    out["heavy_tailed"] = {"value": rate, "unit": UNIT, "ligands": n, "seconds": round(secs, 2)}
+    b4 = synth.config_ligands(2, 128, uid_base=1 << 40)
+    prm4 = synth.config_params(4)
+    dt, evals, used = 0.0, 0, []
+    for w in range(3):  # the first pockets of the set (grids built untimed)
+        pk = synth.config_pocket(4, w)
+        t0 = time.perf_counter()
+        oracle.dock(pk, b4, prm4, nthreads=cpu_cores())
+        dt += time.perf_counter() - t0
+        evals += b4.L
+        used.append(int(pk.n))
+        if dt >= budget_s:
+            break
+    out["several_pockets"] = {"value": evals / dt, "unit": UNIT, "evals": evals, "ligands_per_pocket": b4.L,
+                              "pocket_grids": used, "seconds": round(dt, 2)}
+    return out
+
+
 KERNEL_SOURCES = ("lg_kernels.cu", "lg_device.cuh", "lg_internal.h")
 
 
@@ -679,7 +712,8 @@ def main():
             cpu = {"value": rate, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
                    "sample": f"first {n_done} ligands of the workload, FP64 oracle, {secs:.1f} s",
                    "single_core": {"value": rate1, "unit": UNIT, "cores": 1,
-                                   "sample": f"first {n1} ligands, {secs1:.1f} s"}}
+                                   "sample": f"first {n1} ligands, {secs1:.1f} s"},
+                   "other_workloads": oracle_other_workloads(args.cpu_budget / 4)}
 
 
         small = small_batch_leg(ctx, pid, dev, 64, 200) if world == 1 else None
