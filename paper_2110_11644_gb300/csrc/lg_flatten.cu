@@ -38,6 +38,7 @@ extern "C" int lg_flatten_batch(lg_ctx *c, const lg_ligand_batch *b, const lg_fl
         return fail(LG_EINVAL, "null batch array");
     if (!o->xyz || !o->status) return fail(LG_EINVAL, "xyz and status are required");
     std::lock_guard<std::mutex> g(c->mu);
+    Range call("lg_flatten_batch");
     if (cudaSetDevice(c->device) != cudaSuccess) return fail(LG_ECUDA, "cudaSetDevice failed");
     cudaStream_t s = (cudaStream_t)stream;
     const int L = b->L, P = p->passes;

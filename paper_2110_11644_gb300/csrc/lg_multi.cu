@@ -35,6 +35,7 @@ extern "C" int lg_dock_multi(lg_ctx *c, const int32_t *pocket_ids, int32_t n_poc
     if (!b->atom_off || !b->x || !b->y || !b->z || !b->q || !b->type || !b->parent || !b->rot_off || !b->uid)
         return fail(LG_EINVAL, "null batch array");
     std::lock_guard<std::mutex> g(c->mu);
+    Range call("lg_dock_multi");
     if (cudaSetDevice(c->device) != cudaSuccess) return fail(LG_ECUDA, "cudaSetDevice failed");
     std::vector<PocketDev> pk(n_pockets);
     for (int k = 0; k < n_pockets; k++) {

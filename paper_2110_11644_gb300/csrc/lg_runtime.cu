@@ -232,6 +232,7 @@ static int tuned_warps(lg_ctx *c, const std::array<int, 8> &key, int S, bool *ca
 int dock_device(lg_ctx *ctx, const PocketDev &pk, const BatchDev &bd, const OutDev &od, const lg_dock_params *p,
                 int nmax, int rmax, DevBuf &scratch, cudaStream_t s, lg_stats *st, cudaEvent_t *tev,
                 const MultiDev *multi, unsigned class_mask, bool allow_graph, bool reuse_prep) {
+    Range range("dock: prepare, tune and launch");
     const bool timed = tev != nullptr;
     DockArgs a;
     memset(&a, 0, sizeof(a));
@@ -837,6 +838,7 @@ int lg_dock_batch(lg_ctx *c, int32_t pid, const lg_ligand_batch *b, const lg_doc
         return fail(LG_EINVAL, "null batch array");
     if (!o->score || !o->best_restart || !o->status) return fail(LG_EINVAL, "score, best_restart and status are required");
     std::lock_guard<std::mutex> g(c->mu);
+    Range call("lg_dock_batch");
     if (cudaSetDevice(c->device) != cudaSuccess) return fail(LG_ECUDA, "cudaSetDevice failed");
     PocketRec *pk = (pid >= 0 && pid < (int)c->pockets.size() && c->pockets[pid].live) ? &c->pockets[pid] : nullptr;
     if (!pk) return fail(LG_ENOPOCKET, "unknown pocket");
@@ -846,9 +848,12 @@ int lg_dock_batch(lg_ctx *c, int32_t pid, const lg_ligand_batch *b, const lg_doc
     int64_t A = -1, R = -1;
     int nmax, rmax;
     BatchDev bd;
-    if ((rc = resolve_batch(c, b, p, s, &bd, &A, &R, &nmax, &rmax))) return rc;
     OutDev od;
-    if ((rc = resolve_out(c, c->out_buf, b, o, S, P, p->rigid_steps, s, &A, &R, &od))) return rc;
+    {
+        Range stage("stage inputs and outputs");
+        if ((rc = resolve_batch(c, b, p, s, &bd, &A, &R, &nmax, &rmax))) return rc;
+        if ((rc = resolve_out(c, c->out_buf, b, o, S, P, p->rigid_steps, s, &A, &R, &od))) return rc;
+    }
     cudaEvent_t *tev = next_timing_events(c);
     const unsigned cmask = b->mem == LG_MEM_HOST ? host_class_mask(b) : (1u << kSizeClasses) - 1;
     const bool graph_ok = b->mem == LG_MEM_DEVICE && o->mem == LG_MEM_DEVICE;
@@ -857,9 +862,11 @@ int lg_dock_batch(lg_ctx *c, int32_t pid, const lg_ligand_batch *b, const lg_doc
     if (scratch_release(c, s) != cudaSuccess && rc == LG_OK) rc = fail(LG_ECUDA, "event record failed");
     if (rc) return rc;
     if (o->mem == LG_MEM_HOST) {
+        Range fetch("fetch outputs");
         if ((rc = fetch_out(od, o, L, S, P, A, R, p->rigid_steps, s))) return rc;
     }
     if (b->mem == LG_MEM_HOST || o->mem == LG_MEM_HOST) {
+        Range wait("wait for the stream");
         cudaError_t e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return fail(LG_ECUDA, std::string("docking: ") + cudaGetErrorString(e));
     } else {

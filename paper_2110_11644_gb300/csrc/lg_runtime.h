@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <array>
 #include <atomic>
@@ -13,6 +14,15 @@
 #include "lg_internal.h"
 
 namespace lg {
+
+// Named NVTX range around a host-side phase, for timeline profilers (a no-op
+// unless a tool is attached).
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range &) = delete;
+    Range &operator=(const Range &) = delete;
+};
 
 struct DevBuf {
     void *p = nullptr;

@@ -117,6 +117,7 @@ static bool same_kind(const Request &a, const Request &b, bool cross_pocket) {
 
 // Concatenate the requests into the slot's pinned buffer and launch them.
 static int launch_slot(Server *sv, Slot &sl) {
+    Range range("serve: merged launch");
     lg_ctx *c = sv->ctx;
     const Request &r0 = *sl.reqs[0];
     const int S = r0.params.restarts, P = r0.params.passes, Rs = r0.params.rigid_steps;
