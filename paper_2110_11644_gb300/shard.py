@@ -139,6 +139,13 @@ def partition(costs, world: int):
     return [np.array(sorted(p), np.int64) for p in parts]
 
 
+def pending(uid, done_uid) -> np.ndarray:
+    """Indices of the ligands whose uid has no result yet: a screen resumed
+    after a failure docks only these (results are keyed by uid and a re-run
+    of a uid is bit-identical, so nothing else needs saving)."""
+    return np.nonzero(~np.isin(np.asarray(uid, np.uint64), np.asarray(done_uid, np.uint64)))[0]
+
+
 def gather_ranking(uid, score, k: int, group=None):
     """Global k best (lowest score, then lowest uid) over all ranks of the
     default process group: each rank sends its own k best, rank 0 merges.

@@ -165,3 +165,32 @@ def test_ranked_flops_credit_each_decision():
                     d = S * P * r0 + (r * P + ps) * R + k
                     want += 36 * 51 * m[r0 + k] + 8 * pairs[r0 + k] * jstar[d]
         assert abs(got[l] - want) <= 1e-9 * want, l
+
+
+def test_resume_after_a_failed_rank_docks_only_the_missing_uids():
+    # a rank fails after its first chunk; the resumed run docks the pending
+    # uids only and the union equals one uninterrupted run bit for bit
+    import oracle
+    pocket = synth.config_pocket(1)
+    batch = synth.config_ligands(1, 64)
+    params = synth.config_params(1)
+    whole = oracle.dock(pocket, batch, params, nthreads=2)
+    parts = shard.partition(shard.ligand_flops(batch, params.restarts, params.passes), 2)
+    done_uid, done_E, done_r = [], [], []
+    for rank, idx in enumerate(parts):
+        chunks = np.array_split(idx, 3)
+        for c, chunk in enumerate(chunks):
+            if rank == 1 and c == 1:
+                break  # rank 1 fails here; its first chunk's results were kept
+            out = oracle.dock(pocket, batch.subset(chunk), params, nthreads=2)
+            done_uid += list(batch.uid[chunk]); done_E += list(out["best_E"]); done_r += list(out["best_r"])
+    todo = shard.pending(batch.uid, done_uid)
+    assert 0 < len(todo) < batch.L and not np.isin(batch.uid[todo], done_uid).any()
+    out = oracle.dock(pocket, batch.subset(todo), params, nthreads=2)
+    done_uid += list(batch.uid[todo]); done_E += list(out["best_E"]); done_r += list(out["best_r"])
+    order = np.argsort(np.asarray(done_uid, np.uint64))
+    want = np.argsort(batch.uid)
+    assert np.array_equal(np.asarray(done_uid, np.uint64)[order], batch.uid[want])
+    assert np.array_equal(np.asarray(done_E)[order], whole["best_E"][want])
+    assert np.array_equal(np.asarray(done_r)[order], whole["best_r"][want])
+    assert len(shard.pending(batch.uid, done_uid)) == 0
