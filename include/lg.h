@@ -444,6 +444,21 @@ int lg_get_stats(lg_ctx *ctx, lg_stats *out);
  * every pocket in turn).  Errors: LG_EINVAL. */
 int lg_set_option(lg_ctx *ctx, const char *key, int64_t value);
 
+/* The autotuner's cached choices as JSON text, to carry them to another
+ * context or process on the same kind of GPU:
+ *   {"device": "<name>", "sms": <SM count>, "entries": [[size class,
+ *    restarts, passes, atom maximum, torsion maximum, ranking, rigid,
+ *    kind, warps per CTA], ...]}
+ * lg_tune_export writes the text, NUL-terminated, into buf (cap bytes,
+ * caller-owned) and sets *len to its length without the NUL; when cap is too
+ * small it writes nothing, sets *len and returns LG_EINVAL (buf may be NULL
+ * with cap 0 to ask for the length).  lg_tune_import adds the entries of such
+ * a text to the context's cache; a text from another device name or SM
+ * count, or one that does not parse, is refused with LG_EINVAL and the cache
+ * is left unchanged.  Setting the "autotune" option clears the cache. */
+int lg_tune_export(lg_ctx *ctx, char *buf, int64_t cap, int64_t *len);
+int lg_tune_import(lg_ctx *ctx, const char *text);
+
 /* ---------------------------------------------------------------- diagnostics */
 
 /* Philox4x32-10 of n (counter, key) pairs on the device (device pointers:

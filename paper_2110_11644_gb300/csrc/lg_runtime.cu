@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -921,6 +922,92 @@ int lg_score_poses(lg_ctx *c, int32_t pid, const lg_pose_batch *b, double *E, vo
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return fail(LG_ECUDA, std::string("scoring: ") + cudaGetErrorString(e));
     }
+    return LG_OK;
+}
+
+// Device name and SM count that a tuning text belongs to.
+static std::string tune_device_name(lg_ctx *c) {
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, c->device) != cudaSuccess) return std::string();
+    std::string n;
+    for (const char *q = prop.name; *q; ++q)
+        if (*q != '"' && *q != '\\' && (unsigned char)*q >= 32) n += *q;  // nothing to escape in the text
+    return n;
+}
+
+int lg_tune_export(lg_ctx *c, char *buf, int64_t cap, int64_t *len) {
+    if (!c || !len || (cap > 0 && !buf)) return fail(LG_EINVAL, "null argument");
+    std::string t = "{\"device\": \"" + tune_device_name(c) + "\", \"sms\": " + std::to_string(ctx_num_sms(c)) +
+                    ", \"entries\": [";
+    {
+        std::lock_guard<std::mutex> g(c->tune_mu);
+        bool first = true;
+        for (const auto &kv : c->tune) {
+            t += first ? "[" : ", [";
+            first = false;
+            for (int v : kv.first) t += std::to_string(v) + ", ";
+            t += std::to_string(kv.second) + "]";
+        }
+    }
+    t += "]}";
+    *len = (int64_t)t.size();
+    if (cap < (int64_t)t.size() + 1) return fail(LG_EINVAL, "buffer too small for the tuning text");
+    memcpy(buf, t.c_str(), t.size() + 1);
+    return LG_OK;
+}
+
+int lg_tune_import(lg_ctx *c, const char *text) {
+    if (!c || !text) return fail(LG_EINVAL, "null argument");
+    const std::string t(text);
+    auto field = [&](const char *name) -> size_t {  // position after "name":
+        const size_t k = t.find(std::string("\"") + name + "\"");
+        if (k == std::string::npos) return k;
+        const size_t colon = t.find(':', k);
+        return colon == std::string::npos ? colon : colon + 1;
+    };
+    size_t k = field("device");
+    if (k == std::string::npos) return fail(LG_EINVAL, "tuning text: no device");
+    const size_t q0 = t.find('"', k), q1 = q0 == std::string::npos ? q0 : t.find('"', q0 + 1);
+    if (q1 == std::string::npos) return fail(LG_EINVAL, "tuning text: bad device");
+    if (t.substr(q0 + 1, q1 - q0 - 1) != tune_device_name(c)) return fail(LG_EINVAL, "tuning text is for another device");
+    k = field("sms");
+    if (k == std::string::npos || atoi(t.c_str() + k) != ctx_num_sms(c))
+        return fail(LG_EINVAL, "tuning text is for another SM count");
+    k = field("entries");
+    if (k == std::string::npos) return fail(LG_EINVAL, "tuning text: no entries");
+    // entries: a list of lists of 9 integers
+    std::vector<std::pair<std::array<int, 8>, int>> got;
+    std::vector<long> cur;
+    int depth = 0;
+    for (size_t i = k; i < t.size(); ++i) {
+        const char ch = t[i];
+        if (ch == '[') {
+            if (++depth > 2) return fail(LG_EINVAL, "tuning text: nesting");
+            if (depth == 2) cur.clear();
+        } else if (ch == ']') {
+            if (depth == 2) {
+                if (cur.size() != 9) return fail(LG_EINVAL, "tuning text: an entry is not 9 integers");
+                std::array<int, 8> key;
+                for (int j = 0; j < 8; ++j) key[j] = (int)cur[j];
+                const int w = (int)cur[8];
+                if (w != 1 && w != 2 && w != 4) return fail(LG_EINVAL, "tuning text: warps per CTA not 1, 2 or 4");
+                if (key[0] < -1 || key[0] >= kSizeClasses || key[1] < 1 || key[2] < 0 || key[3] < 1 || key[4] < 1)
+                    return fail(LG_EINVAL, "tuning text: bad key");
+                got.push_back({key, w});
+            }
+            if (--depth == 0) break;
+        } else if (ch == '-' || (ch >= '0' && ch <= '9')) {
+            if (depth != 2) return fail(LG_EINVAL, "tuning text: number outside an entry");
+            char *end = nullptr;
+            cur.push_back(strtol(t.c_str() + i, &end, 10));
+            i = (size_t)(end - t.c_str()) - 1;
+        } else if (ch != ',' && ch != ' ' && ch != '\n' && ch != '\t' && ch != '\r') {
+            return fail(LG_EINVAL, "tuning text: unexpected character");
+        }
+    }
+    if (depth != 0) return fail(LG_EINVAL, "tuning text: unterminated entries");
+    std::lock_guard<std::mutex> g(c->tune_mu);
+    for (const auto &e : got) c->tune[e.first] = e.second;
     return LG_OK;
 }
 

@@ -76,7 +76,8 @@ class lg_stats(ctypes.Structure):
 # Every symbol include/lg.h declares (checked by the ABI test).
 EXPORTS = ("lg_create", "lg_destroy", "lg_last_error", "lg_pocket_load", "lg_pocket_unload", "lg_dock_batch",
            "lg_score_poses", "lg_stream_submit", "lg_stream_poll", "lg_stream_wait", "lg_get_stats", "lg_set_option",
-           "lg_diag_philox", "lg_dock_batch_noalloc", "lg_dock_multi", "lg_flatten_batch")
+           "lg_diag_philox", "lg_dock_batch_noalloc", "lg_dock_multi", "lg_flatten_batch", "lg_tune_export",
+           "lg_tune_import")
 
 _lib = None
 _lock = threading.Lock()
@@ -118,6 +119,8 @@ def load():
                                           c.POINTER(lg_dock_params), c.POINTER(lg_dock_result), V]
             lib.lg_flatten_batch.argtypes = [V, c.POINTER(lg_ligand_batch), c.POINTER(lg_flatten_params),
                                              c.POINTER(lg_flatten_result), V]
+            lib.lg_tune_export.argtypes = [V, c.c_char_p, c.c_int64, c.POINTER(c.c_int64)]
+            lib.lg_tune_import.argtypes = [V, c.c_char_p]
             for name in EXPORTS:
                 if name not in ("lg_destroy", "lg_last_error"):
                     getattr(lib, name).restype = c.c_int
@@ -165,6 +168,21 @@ def lg_pocket_unload(h, pid: int):
 
 def lg_dock_batch(h, pid, batch: lg_ligand_batch, params: lg_dock_params, out: lg_dock_result, stream=None):
     _check(h, load().lg_dock_batch(h, pid, ctypes.byref(batch), ctypes.byref(params), ctypes.byref(out), stream))
+
+
+def lg_tune_export(h) -> str:
+    """The autotuner's cached choices as JSON text (see lg.h)."""
+    n = ctypes.c_int64()
+    rc = load().lg_tune_export(h, None, 0, ctypes.byref(n))
+    if rc != LG_OK and n.value <= 0:
+        _check(h, rc)
+    buf = ctypes.create_string_buffer(n.value + 1)
+    _check(h, load().lg_tune_export(h, buf, n.value + 1, ctypes.byref(n)))
+    return buf.value.decode()
+
+
+def lg_tune_import(h, text: str):
+    _check(h, load().lg_tune_import(h, text.encode()))
 
 
 def lg_dock_batch_noalloc(h, pid, batch: lg_ligand_batch, params: lg_dock_params, out: lg_dock_result, stream=None):
@@ -375,6 +393,12 @@ class Context:
 
     def set_option(self, key, value):
         lg_set_option(self.h, key, value)
+
+    def tune_export(self) -> str:
+        return lg_tune_export(self.h)
+
+    def tune_import(self, text: str):
+        lg_tune_import(self.h, text)
 
     def stats(self) -> lg_stats:
         return lg_get_stats(self.h)

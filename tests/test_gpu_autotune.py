@@ -76,6 +76,39 @@ def test_autotuner_caches_its_choice(ctx, cfg2_pocket, heavy):
     assert first > second
 
 
+def test_tuning_carries_to_another_context(ctx, cfg2_pocket, heavy):
+    # the tuned choices exported as JSON and imported by a fresh context: its
+    # first call runs no timing trials and docks identically
+    import json
+    pid = ctx.load_pocket(cfg2_pocket)
+    params = synth.config_params(3)
+    ctx.set_option("autotune", 1)  # clears the cache
+    assert json.loads(ctx.tune_export())["entries"] == []
+    ref = _dock(ctx, pid, heavy, params)
+    text = ctx.tune_export()
+    doc = json.loads(text)
+    assert doc["sms"] > 0 and len(doc["entries"]) == 3 and all(len(e) == 9 and e[8] in (1, 2, 4) for e in doc["entries"])
+    ctx.unload_pocket(pid)
+    c2 = lg.Context(0)
+    try:
+        p2 = c2.load_pocket(cfg2_pocket)
+        c2.tune_import(text)
+        got = _dock(c2, p2, heavy, params)
+        assert c2.stats().launches == 6  # prep + sort (3) + one launch per class (3): no trials
+        for k in KEYS:
+            assert np.array_equal(got[k], ref[k]), k
+        assert json.loads(c2.tune_export())["entries"] == doc["entries"]
+        # another device, or text that does not parse: refused, cache unchanged
+        other = dict(doc, device=doc["device"] + " X")
+        for bad in (json.dumps(other), json.dumps(dict(doc, sms=doc["sms"] + 1)), text.replace("]]", "]"),
+                    text.replace("[[", "[[99, ") if doc["entries"] else text + "x", "not json"):
+            with pytest.raises(lg.LgError):
+                c2.tune_import(bad)
+        assert json.loads(c2.tune_export())["entries"] == doc["entries"]
+    finally:
+        c2.close()
+
+
 def test_small_batches_take_wide_ctas_untuned(ctx, cfg1, cfg2_pocket):
     # a batch that fits in one wave of 4-warp CTAs runs at one CTA per ligand
     # with its restart tiles over up to 4 warps, without tuning; results as
