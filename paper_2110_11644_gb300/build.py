@@ -44,21 +44,34 @@ def _deps():
         [os.path.join(INCLUDE, "lg.h")]
 
 
-def needs_build() -> bool:
-    if not os.path.exists(LIB):
+# library variants: "" the product; "checked" a debug build with device-side
+# bounds checks (-DLG_CHECKS, see csrc/lg_device.cuh)
+VARIANT_FLAGS = {"": [], "checked": ["-DLG_CHECKS"]}
+
+
+def library(variant: str = "") -> str:
+    return LIB if not variant else os.path.join(HERE, f"liblgdock_{variant}.so")
+
+
+def needs_build(variant: str = "") -> bool:
+    lib = library(variant)
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return any(os.path.getmtime(f) > t for f in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, extra=()) -> str:
-    if not force and not needs_build():
-        return LIB
-    os.makedirs(BUILD_DIR, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra=(), variant: str = "") -> str:
+    lib = library(variant)
+    if not force and not needs_build(variant):
+        return lib
+    extra = [*VARIANT_FLAGS[variant], *extra]
+    build_dir = BUILD_DIR if not variant else f"{BUILD_DIR}_{variant}"
+    os.makedirs(build_dir, exist_ok=True)
     cc = nvcc()
 
     def compile_one(src):
-        obj = os.path.join(BUILD_DIR, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(build_dir, os.path.basename(src)[:-3] + ".o")
         cmd = [cc, *flags(extra), "-c", src, "-o", obj]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
@@ -72,13 +85,13 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     if verbose:
         for _, log in results:
             sys.stderr.write(log)
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [cc, *ARCH, "-shared", "-o", tmp, *[o for o, _ in results], "-lcudart_static", "-lpthread", "-ldl", "-lrt"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

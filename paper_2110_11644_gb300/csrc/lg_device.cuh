@@ -76,6 +76,37 @@ __device__ __forceinline__ float3 rot_vec(const float *R, float vx, float vy, fl
                        fmaf(R[6], vx, fmaf(R[7], vy, R[8] * vz)));
 }
 
+// ------------------------------------------------------------------ bounds checks
+// A debug build (-DLG_CHECKS) checks the computed indices of grid cells,
+// shared-memory lists and scratch slots: an index outside [0, bound) is
+// counted, the first one recorded (site, index, bound), and the access goes to
+// the nearest in-range element instead, so it stays in bounds; the host turns
+// a record into an error of the call.  Other builds compile the checks away.
+enum CheckSite {
+    kChkCell = 1,      // overlap-grid cell of a torsion-step lookup
+    kChkCellVE,        // potential-grid cell of a pose score
+    kChkNear,          // near-atom list entry
+    kChkPool,          // clash-pair pool entry
+    kChkDecision,      // decision record of a restart slot
+    kChkRankSlot,      // ranking scratch slot
+    kChkAtom,          // atom index of a moving or fixed atom
+};
+#ifdef LG_CHECKS
+__device__ int lg_check_rec[4];  // site, index, bound of the first failure; failures
+__device__ __forceinline__ long long lg_checked(long long idx, long long bound, int site) {
+    if (idx >= 0 && idx < bound) return idx;
+    if (atomicAdd(&lg_check_rec[3], 1) == 0) {
+        lg_check_rec[0] = site;
+        lg_check_rec[1] = (int)idx;
+        lg_check_rec[2] = (int)bound;
+    }
+    return idx < 0 ? 0 : bound - 1;
+}
+#define LG_IDX(idx, bound, site) lg_checked((long long)(idx), (long long)(bound), (site))
+#else
+#define LG_IDX(idx, bound, site) (idx)
+#endif
+
 // ------------------------------------------------------------------ grid lookups
 // Floor of an index-space coordinate in [0, 2^22) by adding 1.5*2^23 with
 // round-down: the integer part lands in the low mantissa bits of t and
@@ -140,7 +171,8 @@ __device__ __forceinline__ float lookup_in(const GridK &G, float gx, float gy, f
     float tx, ty, tz;
     const float fx = floor_frac(gx, tx), fy = floor_frac(gy, ty), fz = floor_frac(gz, tz);
     float4 lo, hi;
-    load_cell(G.cells + 2 * (size_t)cell_index(tx, ty, tz, G.n, G.n2, G.moff), lo, hi);
+    load_cell(G.cells + 2 * (size_t)LG_IDX(cell_index(tx, ty, tz, G.n, G.n2, G.moff), (size_t)G.n2 * G.n, kChkCell),
+              lo, hi);
     return cell_eval(lo, hi, fx, fy, fz);
 }
 
@@ -161,7 +193,8 @@ __device__ __forceinline__ float atom_energy(const PocketDev &P, const GridK &G,
     const float out = P.h * sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
     float tx, ty, tz;
     const float fx = floor_frac(cx, tx), fy = floor_frac(cy, ty), fz = floor_frac(cz, tz);
-    const float4 *p = G.cells + 4 * (size_t)cell_index(tx, ty, tz, G.n, G.n2, G.moff);
+    const float4 *p =
+        G.cells + 4 * (size_t)LG_IDX(cell_index(tx, ty, tz, G.n, G.n2, G.moff), (size_t)G.n2 * G.n, kChkCellVE);
     float4 vlo, vhi, elo, ehi;
     load_cell(p, vlo, vhi);
     load_cell(p + 2, elo, ehi);

@@ -110,6 +110,9 @@ extern "C" int lg_flatten_batch(lg_ctx *c, const lg_ligand_batch *b, const lg_fl
     const cudaError_t er = scratch_release(c, s);
     if (e != cudaSuccess) return fail(LG_ECUDA, std::string("flattening launch: ") + cudaGetErrorString(e));
     if (er != cudaSuccess) return fail(LG_ECUDA, "event record failed");
+#ifdef LG_CHECKS
+    if (int rc = checks_result(s)) return rc;
+#endif
     if (host_out) {
         auto cp = [&](void *dst, const void *src, size_t n) {
             if (e == cudaSuccess && n) e = cudaMemcpyAsync(dst, src, n, cudaMemcpyDeviceToHost, s);

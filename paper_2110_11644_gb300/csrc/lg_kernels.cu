@@ -45,6 +45,23 @@ void set_angle_tables(const float *cosv, const float *sinv) {
     cudaMemcpyToSymbol(c_sin, sinv, sizeof(float) * LG_ANGLE_STEPS);
 }
 
+// Bounds-check record of a debug build (see lg_device.cuh): waits for the
+// stream, returns the failures and fills rec (site, index, bound, failures),
+// then clears the record; 0 in other builds.
+int checks_collect(cudaStream_t s, int rec[4]) {
+#ifdef LG_CHECKS
+    if (cudaStreamSynchronize(s) != cudaSuccess) return 0;
+    cudaMemcpyFromSymbol(rec, lg_check_rec, sizeof(int) * 4);
+    const int zero[4] = {0, 0, 0, 0};
+    cudaMemcpyToSymbol(lg_check_rec, zero, sizeof(int) * 4);
+    return rec[3];
+#else
+    (void)s;
+    rec[0] = rec[1] = rec[2] = rec[3] = 0;
+    return 0;
+#endif
+}
+
 __device__ __forceinline__ double warp_sum_d(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(LG_FULL, v, o);
@@ -831,7 +848,7 @@ __device__ __forceinline__ int sweep_bond_rt(const DockArgs &A, const GridK &G, 
             nr = d2 < rlim2 && t > tlo && t < thi && q2 > q2lo && q2 < q2hi;
         }
         const unsigned bal = __ballot_sync(LG_FULL, nr);
-        if (nr) v.near[rs * v.nstride + ncnt + __popc(bal & gmask & below)] = (uint8_t)j;
+        if (nr) v.near[rs * v.nstride + LG_IDX(ncnt + __popc(bal & gmask & below), v.nstride, kChkNear)] = (uint8_t)j;
         ncnt += __popc(bal & gmask);
     }
     v.mask[lane] = 0u;
@@ -856,7 +873,7 @@ __device__ __forceinline__ int sweep_bond_rt(const DockArgs &A, const GridK &G, 
                                     v.Xy[j * kTile + rs], v.Xz[j * kTile + rs], dc2);
             }
             const unsigned bal = __ballot_sync(LG_FULL, q.near);
-            if (q.near) v.pool[pc + __popc(bal & below)] = make_float4(q.C, q.A2, q.B2, __int_as_float(rs));
+            if (q.near) v.pool[LG_IDX(pc + __popc(bal & below), kPoolCap, kChkPool)] = make_float4(q.C, q.A2, q.B2, __int_as_float(rs));
             pc += __popc(bal);
         }
     };
@@ -1157,7 +1174,7 @@ __device__ __forceinline__ void dock_ligand_rt(const DockArgs &A, const PocketDe
             int jr;
             const int t = sweep_bond_rt(A, Go, cv, v, N, R, k, rs, g, active && sv, cs, sn, kTrace, jr);
             if (active && g == 0) {
-                v.tcur[(pc * R + k) * kTile + rs] = (uint8_t)t;
+                v.tcur[LG_IDX(pc * R + k, P * Ly.rmax, kChkDecision) * kTile + rs] = (uint8_t)t;
                 if (kTrace) {  // a skipped decision repeats the bond's previous one
                     uint8_t *dr = O.decision_rank + (size_t)S * P * r0 + (size_t)r * PR + pc * R + k;
                     *dr = sv ? (uint8_t)jr : dr[-R];

@@ -230,9 +230,35 @@ static int tuned_warps(lg_ctx *c, const std::array<int, 8> &key, int S, bool *ca
     return choose_warps(S, 0);
 }
 
+static int dock_device_launch(lg_ctx *ctx, const PocketDev &pk, const BatchDev &bd, const OutDev &od,
+                              const lg_dock_params *p, int nmax, int rmax, DevBuf &scratch, cudaStream_t s, lg_stats *st,
+                              cudaEvent_t *tev, const MultiDev *multi, unsigned class_mask, bool allow_graph,
+                              bool reuse_prep);
+
+// A bounds-check record (debug builds) as the error of the call.
+int checks_result(cudaStream_t s) {
+    int rec[4];
+    if (checks_collect(s, rec) == 0) return LG_OK;
+    return fail(LG_ECUDA, "bounds check failed " + std::to_string(rec[3]) + " times; first at site " +
+                              std::to_string(rec[0]) + ": index " + std::to_string(rec[1]) + " outside [0, " +
+                              std::to_string(rec[2]) + ")");
+}
+
 int dock_device(lg_ctx *ctx, const PocketDev &pk, const BatchDev &bd, const OutDev &od, const lg_dock_params *p,
                 int nmax, int rmax, DevBuf &scratch, cudaStream_t s, lg_stats *st, cudaEvent_t *tev,
                 const MultiDev *multi, unsigned class_mask, bool allow_graph, bool reuse_prep) {
+    int rc = dock_device_launch(ctx, pk, bd, od, p, nmax, rmax, scratch, s, st, tev, multi, class_mask, allow_graph,
+                                reuse_prep);
+#ifdef LG_CHECKS
+    if (rc == LG_OK) rc = checks_result(s);
+#endif
+    return rc;
+}
+
+static int dock_device_launch(lg_ctx *ctx, const PocketDev &pk, const BatchDev &bd, const OutDev &od,
+                              const lg_dock_params *p, int nmax, int rmax, DevBuf &scratch, cudaStream_t s, lg_stats *st,
+                              cudaEvent_t *tev, const MultiDev *multi, unsigned class_mask, bool allow_graph,
+                              bool reuse_prep) {
     Range range("dock: prepare, tune and launch");
     const bool timed = tev != nullptr;
     DockArgs a;

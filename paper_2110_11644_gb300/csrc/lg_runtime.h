@@ -48,6 +48,7 @@ int stage_batch(DevBuf &buf, const lg_ligand_batch *b, int64_t A, int64_t R, Bat
 int stage_out(DevBuf &buf, const lg_dock_result *o, int L, int S, int P, int64_t A, int64_t R, int Rs, OutDev *d);
 int fetch_out(const OutDev &d, const lg_dock_result *o, int L, int S, int P, int64_t A, int64_t R, int Rs,
               cudaStream_t s);
+int checks_result(cudaStream_t s);  // a debug build's bounds-check record as the call's error
 int dock_device(lg_ctx *ctx, const PocketDev &pk, const BatchDev &bd, const OutDev &od, const lg_dock_params *p,
                 int nmax, int rmax, DevBuf &scratch, cudaStream_t s, lg_stats *st, cudaEvent_t *tev,
                 const MultiDev *multi = nullptr, unsigned class_mask = (1u << kSizeClasses) - 1,

@@ -88,11 +88,13 @@ def library_path() -> str:
 
 
 def load():
-    """Load liblgdock.so (building it first when missing or stale)."""
+    """Load liblgdock.so (building it first when missing or stale); the
+    environment variable LG_LIBRARY_VARIANT=checked loads the debug build with
+    device-side bounds checks instead."""
     global _lib
     with _lock:
         if _lib is None:
-            path = _build.build()
+            path = _build.build(variant=os.environ.get("LG_LIBRARY_VARIANT", ""))
             lib = ctypes.CDLL(path)
             c = ctypes
             V = c.c_void_p

@@ -1,0 +1,73 @@
+"""The debug build with device-side bounds checks (-DLG_CHECKS): every grid
+cell, near-atom list entry, clash-pair pool entry and decision record index
+of the docking kernels is checked, and a failure turns into an error of the
+call.  The checked library docks the parity cases (best restart, ranking,
+rigid moves, heavy-tailed size classes at every width, several pockets,
+flattening) without a failure and with results equal to the product build's
+bit for bit."""
+import os
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+from paper_2110_11644_gb300 import build, lg, synth
+
+pytestmark = pytest.mark.gpu
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+RUN = r"""
+import dataclasses, sys
+import numpy as np
+sys.path.insert(0, sys.argv[1])
+from paper_2110_11644_gb300 import lg, synth
+out = {}
+ctx = lg.Context(0)
+p1, b1, prm1 = synth.config_pocket(1), synth.config_ligands(1), synth.config_params(1)
+pid = ctx.load_pocket(p1)
+for name, prm in (("best", prm1), ("ranking", dataclasses.replace(prm1, cluster_rmsd=3.0, rescore_top=4)),
+                  ("rigid", dataclasses.replace(prm1, rigid_steps=2))):
+    r = ctx.dock(pid, b1, prm, restart_score=True, restart_tors=True, decision_rank=True)
+    for k, v in r.items():
+        if v is not None:
+            out[name + "/" + k] = v
+p2 = synth.config_pocket(2)
+pid2 = ctx.load_pocket(p2)
+heavy, prm3 = synth.config_ligands(3, 900), synth.config_params(3)
+for w in (1, 2, 4):
+    ctx.set_option("warps_per_cta", w)
+    r = ctx.dock(pid2, heavy, prm3, restart_score=True, restart_tors=True)
+    for k, v in r.items():
+        if v is not None:
+            out["heavy%d/%s" % (w, k)] = v
+ctx.set_option("warps_per_cta", 0)
+multi = ctx.dock_multi([pid, pid2], b1.subset(range(64)), prm1)
+for j, r in enumerate(multi):
+    out["multi%d/score" % j] = r["score"]
+f = ctx.flatten(synth.config_ligands(2, 300), 3)
+for k in ("xyz", "tors", "dsum"):
+    out["flatten/" + k] = f[k]
+ctx.close()
+np.savez(sys.argv[2], **out)
+"""
+
+
+def _run(tmp_path, variant):
+    path = str(tmp_path / f"res_{variant or 'product'}.npz")
+    env = dict(os.environ, LG_LIBRARY_VARIANT=variant)
+    subprocess.run([sys.executable, "-c", RUN, ROOT, path], check=True, env=env, timeout=900)
+    return np.load(path)
+
+
+def test_checked_build_docks_without_bounds_failures_and_equal_results(tmp_path):
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build(variant="checked")
+    got = _run(tmp_path, "checked")  # a bounds failure would raise in the child
+    want = _run(tmp_path, "")
+    assert set(got.files) == set(want.files)
+    for k in want.files:
+        assert np.array_equal(got[k], want[k]), k
