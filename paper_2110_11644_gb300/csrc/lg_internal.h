@@ -145,6 +145,8 @@ struct Scratch {
     float *rk_pose;
     double *rk_E;
     uint8_t *rk_tors;
+    int rk_slots;          // ranking slots
+    size_t rk_floats;      // capacity of rk_pose (floats)
 };
 
 // Ranking step: row p of the "within the RMSD threshold" bit matrix holds

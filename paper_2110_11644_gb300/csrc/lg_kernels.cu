@@ -179,6 +179,13 @@ __device__ __forceinline__ size_t rk_pose_off(const DockArgs &A, int slot, int r
     return ((size_t)slot * A.S + r) * (size_t)A.ly.nmax * 3;
 }
 
+// The ranking slot of a CTA (checked builds: within the slots the scratch
+// holds at this launch's atom maximum).
+__device__ __forceinline__ int rank_slot(const DockArgs &A, int slot) {
+    const long long fit = (long long)(A.scr.rk_floats / ((size_t)A.S * A.ly.nmax * 3));
+    return (int)LG_IDX(slot, fit < A.scr.rk_slots ? fit : A.scr.rk_slots, kChkRankSlot);
+}
+
 // Pose ranking (paper Sec. 3.1, steps 3-4) of ligand l from the restarts kept
 // in the CTA's slot, and the ligand's outputs.  All threads of the CTA call it
 // after a barrier; it reuses the warps' shared memory.
@@ -585,9 +592,10 @@ __device__ __forceinline__ bool rigid_moves_plain(const DockArgs &A, const GridK
     return moved;
 }
 
-__global__ void __launch_bounds__(1024) k_dock_plain(const __grid_constant__ DockArgs A, int l, int slot) {
+__global__ void __launch_bounds__(1024) k_dock_plain(const __grid_constant__ DockArgs A, int l, int slot_arg) {
     extern __shared__ __align__(16) char sm[];
     if (A.out.status[l] != LG_OK) return;  // rejected by the preparation kernel
+    const int slot = A.ranking ? rank_slot(A, slot_arg) : slot_arg;
     const Layout &Ly = A.ly;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
     const CtaView cv = cta_view(sm, Ly);
@@ -1114,15 +1122,16 @@ __device__ __forceinline__ void dock_ligand_rt(const DockArgs &A, const PocketDe
                     for (int t = g; t < PR; t += kLanesPerRestart)
                         O.restart_tors[(size_t)S * P * r0 + (size_t)r * PR + t] = v.tcur[t * kTile + rs];
                 if (kRank) {  // keep the restart for the ranking step
-                    float *x = A.scr.rk_pose + rk_pose_off(A, blockIdx.x, r);
+                    const int slot = rank_slot(A, blockIdx.x);
+                    float *x = A.scr.rk_pose + rk_pose_off(A, slot, r);
                     for (int i = g; i < N; i += kLanesPerRestart) {
                         x[3 * i] = v.Xx[i * kTile + rs];
                         x[3 * i + 1] = v.Xy[i * kTile + rs];
                         x[3 * i + 2] = v.Xz[i * kTile + rs];
                     }
                     for (int t = g; t < PR; t += kLanesPerRestart)
-                        A.scr.rk_tors[((size_t)blockIdx.x * S + r) * P * Ly.rmax + t] = v.tcur[t * kTile + rs];
-                    if (g == 0) A.scr.rk_E[(size_t)blockIdx.x * S + r] = E;
+                        A.scr.rk_tors[((size_t)slot * S + r) * P * Ly.rmax + t] = v.tcur[t * kTile + rs];
+                    if (g == 0) A.scr.rk_E[(size_t)slot * S + r] = E;
                 }
             }
             // best of the finished restarts (lowest E, then lowest restart), then of the warp
@@ -1198,7 +1207,7 @@ __device__ __forceinline__ void dock_ligand_rt(const DockArgs &A, const PocketDe
     }
     if (kRank) {
         __syncthreads();
-        rank_finish(A, Pk, O, l, blockIdx.x, a0, N, r0, PR, sm + Ly.cta_bytes);
+        rank_finish(A, Pk, O, l, rank_slot(A, blockIdx.x), a0, N, r0, PR, sm + Ly.cta_bytes);
         return;
     }
     if (lane == 0) {
@@ -1665,8 +1674,11 @@ Scratch carve_scratch(void *base, int L, int rmax, int rank_slots, int S, int P,
     s.rk_pose = nullptr;
     s.rk_E = nullptr;
     s.rk_tors = nullptr;
+    s.rk_slots = rank_slots > 0 ? rank_slots : 0;
+    s.rk_floats = 0;
     if (rank_slots > 0) {
         const size_t nm = (size_t)((nmax + 3) & ~3);
+        s.rk_floats = 3 * (size_t)rank_slots * S * nm;
         s.rk_pose = (float *)p;
         p += al256(12 * (size_t)rank_slots * S * nm);
         s.rk_E = (double *)p;

@@ -299,11 +299,13 @@ static int dock_device_launch(lg_ctx *ctx, const PocketDev &pk, const BatchDev &
     cudaError_t e;
     int launches = 0;
     // scratch holds one ranking slot per concurrently docked ligand: one per
-    // plain-mode stream, one per CTA of the persistent kernel
+    // plain-mode stream, one per CTA of the persistent kernel; a slot holds S
+    // poses of the largest atom maximum of the launches (size classes differ)
+    int scr_nmax = 0;
     auto setup_scratch = [&](int slots) -> int {
-        if (scratch.ensure(scratch_bytes(L, rmax, a.ranking ? slots : 0, a.S, a.P, a.ly.nmax)))
+        if (scratch.ensure(scratch_bytes(L, rmax, a.ranking ? slots : 0, a.S, a.P, scr_nmax)))
             return fail(LG_ENOMEM, "scratch allocation failed");
-        a.scr = carve_scratch(scratch.p, L, rmax, a.ranking ? slots : 0, a.S, a.P, a.ly.nmax);
+        a.scr = carve_scratch(scratch.p, L, rmax, a.ranking ? slots : 0, a.S, a.P, scr_nmax);
         if (!plain && (e = cudaMemsetAsync(a.scr.hist, 0, 4 * kHistInts, s)) != cudaSuccess)
             return fail(LG_ECUDA, std::string("scratch clear: ") + cudaGetErrorString(e));
         // merged requests for several pockets keep their pocket-grouped order
@@ -317,6 +319,7 @@ static int dock_device_launch(lg_ctx *ctx, const PocketDev &pk, const BatchDev &
     if (plain) {
         const int W = std::min(a.S, 32);
         a.ly = make_layout(nmax, rmax, a.P, W, want_pose);
+        scr_nmax = a.ly.nmax;
         const int psmem = std::max(a.ly.total, a.ly.cta_bytes + rank_smem);
         if ((e = plain_kernel_attributes(psmem)) != cudaSuccess)
             return fail(LG_ECUDA, std::string("plain kernel attributes: ") + cudaGetErrorString(e));
@@ -405,6 +408,7 @@ static int dock_device_launch(lg_ctx *ctx, const PocketDev &pk, const BatchDev &
             }
     }
     a.sort_classes = split ? 1 : 0;
+    for (const Unit &u : units) scr_nmax = std::max(scr_nmax, make_layout(u.nmax, rmax, a.P, 1, want_pose).nmax);
     static const int kCand[3] = {4, 2, 1};  // autotuning candidates (warps per CTA)
     int slots = 1;
     for (const Unit &u : units) slots = std::max(slots, u.grid);
@@ -419,17 +423,17 @@ static int dock_device_launch(lg_ctx *ctx, const PocketDev &pk, const BatchDev &
             }
     const bool graph = allow_graph && ctx->graphs && !multi && s != nullptr && !need_tune && !reuse_prep;
     if (reuse_prep) {  // the same batch was prepared and sorted by the previous call: clear the work counters
-        if (scratch.ensure(scratch_bytes(L, rmax, a.ranking ? slots : 0, a.S, a.P, a.ly.nmax)))
+        if (scratch.ensure(scratch_bytes(L, rmax, a.ranking ? slots : 0, a.S, a.P, scr_nmax)))
             return fail(LG_ENOMEM, "scratch allocation failed");
-        a.scr = carve_scratch(scratch.p, L, rmax, a.ranking ? slots : 0, a.S, a.P, a.ly.nmax);
+        a.scr = carve_scratch(scratch.p, L, rmax, a.ranking ? slots : 0, a.S, a.P, scr_nmax);
         if ((e = cudaMemsetAsync(a.scr.hist + kSortBuckets, 0, 4 * (kSizeClasses + 1), s)) != cudaSuccess)
             return fail(LG_ECUDA, std::string("scratch clear: ") + cudaGetErrorString(e));
     } else if (!graph) {
         if (int rc = setup_scratch(slots)) return rc;
     } else {  // the preparation goes into the graph with the docking launches
-        if (scratch.ensure(scratch_bytes(L, rmax, a.ranking ? slots : 0, a.S, a.P, a.ly.nmax)))
+        if (scratch.ensure(scratch_bytes(L, rmax, a.ranking ? slots : 0, a.S, a.P, scr_nmax)))
             return fail(LG_ENOMEM, "scratch allocation failed");
-        a.scr = carve_scratch(scratch.p, L, rmax, a.ranking ? slots : 0, a.S, a.P, a.ly.nmax);
+        a.scr = carve_scratch(scratch.p, L, rmax, a.ranking ? slots : 0, a.S, a.P, scr_nmax);
     }
     a.order = (multi && multi->lig_pocket) ? nullptr : a.scr.order;
     int32_t *counters = a.scr.hist + kSortBuckets;

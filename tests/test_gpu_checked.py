@@ -1,10 +1,10 @@
 """The debug build with device-side bounds checks (-DLG_CHECKS): every grid
 cell, near-atom list entry, clash-pair pool entry and decision record index
-of the docking kernels is checked, and a failure turns into an error of the
-call.  The checked library docks the parity cases (best restart, ranking,
-rigid moves, heavy-tailed size classes at every width, several pockets,
-flattening) without a failure and with results equal to the product build's
-bit for bit."""
+of the docking kernels, and every ranking scratch slot, is checked, and a
+failure turns into an error of the call.  The checked library docks the
+parity cases (best restart, ranking, rigid moves, heavy-tailed size classes
+at every width and with ranking, several pockets, flattening) without a
+failure and with results equal to the product build's bit for bit."""
 import os
 import subprocess
 import sys
@@ -43,6 +43,12 @@ for w in (1, 2, 4):
         if v is not None:
             out["heavy%d/%s" % (w, k)] = v
 ctx.set_option("warps_per_cta", 0)
+# ranking over size classes: every class's launch uses the scratch slots
+prm3r = dataclasses.replace(prm3, restarts=12, cluster_rmsd=3.0, rescore_top=4, rigid_steps=1)
+r = ctx.dock(pid2, heavy, prm3r, restart_score=True, restart_tors=True, restart_rigid=True)
+for k, v in r.items():
+    if v is not None:
+        out["heavyrank/" + k] = v
 multi = ctx.dock_multi([pid, pid2], b1.subset(range(64)), prm1)
 for j, r in enumerate(multi):
     out["multi%d/score" % j] = r["score"]

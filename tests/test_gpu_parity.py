@@ -296,6 +296,65 @@ def test_rigid_refinement_plain_equals_batched(ctx, cfg1, pocket1):
         assert np.array_equal(a[k], b[k]), k
 
 
+def test_all_stages_together_on_heavy_tailed_ligands(ctx, cfg2_pocket):
+    # ranking, rigid moves and decision ranks at once on ligands of all three
+    # size classes: the two forms agree bit for bit, at every width; the
+    # oracle replaying the GPU's torsion and rigid choices (ranking off: it
+    # changes only which restart is reported) finds only near-ties
+    import dataclasses
+    pid = ctx.load_pocket(cfg2_pocket)
+    heavy = synth.config_ligands(3, 3000)
+    n = heavy.n_atoms()
+    idx = np.sort(np.concatenate([np.nonzero(n > 64)[0][:6], np.nonzero(n <= 32)[0][:6],
+                                  np.nonzero((n > 32) & (n <= 64))[0][:6]]))
+    sub = heavy.subset(idx)
+    prm = dataclasses.replace(synth.config_params(3), restarts=12, passes=2, cluster_rmsd=3.0, rescore_top=4,
+                              rigid_steps=2)
+    kw = dict(restart_score=True, restart_tors=True, restart_rigid=True, decision_rank=True)
+    keys = ("score", "best_restart", "status", "tors_idx", "pose", "restart_score", "restart_tors", "restart_rigid",
+            "decision_rank", "rank", "leader", "restart_geo")
+    ref = ctx.dock(pid, sub, prm, mode=lg.LG_MODE_PLAIN, **kw)
+    try:
+        for w in (1, 2, 4):
+            ctx.set_option("warps_per_cta", w)
+            got = ctx.dock(pid, sub, prm, **kw)
+            for k in keys:
+                assert np.array_equal(got[k], ref[k]), (w, k)
+    finally:
+        ctx.set_option("warps_per_cta", 0)
+    prm_r = dataclasses.replace(prm, cluster_rmsd=0.0, rescore_top=0)
+    g = ctx.dock(pid, sub, prm_r, **kw)
+    ctx.unload_pocket(pid)
+    for k in ("restart_score", "restart_tors", "restart_rigid", "decision_rank"):
+        assert np.array_equal(g[k], ref[k]), k  # ranking leaves every restart as it was
+    rep = check(cfg2_pocket, sub, prm_r, g)
+    assert rep["deviations"] <= 0.01 * rep["decisions"] + 2, rep
+    assert rep["rigid_deviations"] <= 0.01 * rep["rigid_decisions"] + 2, rep
+
+
+def test_small_split_batches_take_wide_ctas(ctx, cfg2_pocket):
+    # a heavy-tailed batch small enough for one wave of 4-warp CTAs: every
+    # size class runs at 4 warps untuned, with the results of 1 warp
+    pid = ctx.load_pocket(cfg2_pocket)
+    heavy = synth.config_ligands(3, 3000)
+    n = heavy.n_atoms()
+    sub = heavy.subset(np.sort(np.concatenate([np.nonzero(n > 64)[0][:30], np.nonzero(n <= 64)[0][:170]])))
+    prm = synth.config_params(3)
+    ctx.set_option("autotune", 1)
+    a = _dock(ctx, pid, sub, prm)
+    st = ctx.stats()
+    assert st.warps_per_cta == 4 and st.launches == 6  # prep + sort (3) + one launch per class, no trials
+    ctx.set_option("warps_per_cta", 1)
+    try:
+        b = _dock(ctx, pid, sub, prm)
+    finally:
+        ctx.set_option("warps_per_cta", 0)
+    ctx.unload_pocket(pid)
+    for k in a:
+        if a[k] is not None:
+            assert np.array_equal(a[k], b[k]), k
+
+
 def test_rigid_refinement_throughput_ligands(ctx, cfg2_pocket):
     import dataclasses
     sub = synth.config_ligands(2, 48)
