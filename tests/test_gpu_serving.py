@@ -165,6 +165,36 @@ def test_requests_with_rigid_moves_and_ranking(served):
                 assert np.array_equal(outs[k][:m], d[k][:m]), (prm, k)
 
 
+def test_heavy_tailed_ranking_requests_equal_direct_calls(served):
+    # merged requests of heavy-tailed ligands (atoms up to 100: one launch
+    # per size class) with pose ranking: each result equals the direct call
+    import dataclasses
+    ctx, pid = served
+    prm = dataclasses.replace(synth.config_params(3), restarts=12, passes=2, cluster_rmsd=3.0, rescore_top=4)
+    heavy = synth.config_ligands(3, 600)
+    assert heavy.n_atoms().max() > 64
+    reqs, tickets = [], []
+    for k in range(12):
+        sub = heavy.subset(range(50 * k, 50 * k + 50))
+        arrs = lg.host_batch_arrays(sub)
+        b = lg.make_batch_struct(arrs, sub.L)
+        p = lg.make_params(prm.restarts, prm.passes, prm.seed, prm.d_clash, cluster_rmsd=prm.cluster_rmsd,
+                           rescore_top=prm.rescore_top)
+        r, outs = lg.alloc_result(sub.L, int(sub.atom_off[-1]), int(sub.rot_off[-1]), prm.restarts, prm.passes,
+                                  restart_tors=True, ranking=True)
+        reqs.append((sub, arrs, b, p, r, outs))
+        tickets.append(lg.lg_stream_submit(ctx.h, pid, b, p, r))
+    for t in tickets:
+        assert lg.lg_stream_wait(ctx.h, t, 60000) == lg.LG_OK
+    for sub, _, _, _, _, outs in reqs:
+        d = ctx.dock(pid, sub, prm, restart_tors=True)
+        S, P, R = prm.restarts, prm.passes, int(sub.rot_off[-1])
+        n = dict(score=sub.L, best_restart=sub.L, status=sub.L, pose=3 * int(sub.atom_off[-1]),
+                 restart_tors=S * P * R, rank=sub.L * S, leader=sub.L * S, restart_geo=sub.L * S)
+        for k, m in n.items():
+            assert np.array_equal(outs[k][:m], d[k][:m]), k
+
+
 def test_requests_for_different_pockets_share_launches():
     # requests aimed at three pockets are merged into one launch (one pocket per
     # ligand); every result equals docking the request alone against its pocket
