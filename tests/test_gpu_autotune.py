@@ -184,6 +184,41 @@ def test_graph_capture_and_replay(ctx, cfg1):
         ctx.unload_pocket(pid)
 
 
+def test_graph_replay_with_ranking_over_size_classes(ctx, cfg2_pocket, heavy):
+    # a captured call that launches one kernel per size class with pose
+    # ranking replays to the eager call's results
+    import dataclasses
+    import torch
+    pid = ctx.load_pocket(cfg2_pocket)
+    sub = heavy.subset(range(700))
+    prm = dataclasses.replace(synth.config_params(3), restarts=12, passes=2, cluster_rmsd=3.0, rescore_top=4)
+    L, A, R = sub.L, int(sub.atom_off[-1]), int(sub.rot_off[-1])
+    darr = lg.device_batch_arrays(sub)
+    b = lg.make_batch_struct(darr, L)
+    p = lg.make_params(prm.restarts, prm.passes, prm.seed, prm.d_clash, cluster_rmsd=prm.cluster_rmsd,
+                       rescore_top=prm.rescore_top)
+    side = torch.cuda.Stream()
+    r0, o0 = lg.alloc_result(L, A, R, prm.restarts, prm.passes, device=True, ranking=True)
+    lg.lg_dock_batch(ctx.h, pid, b, p, r0, side.cuda_stream)  # eager (tunes)
+    side.synchronize()
+    ref = {k: v.cpu().numpy() for k, v in o0.items() if v is not None}
+    ctx.set_option("graphs", 1)
+    try:
+        r1, o1 = lg.alloc_result(L, A, R, prm.restarts, prm.passes, device=True, ranking=True)
+        modes = []
+        for _ in range(3):
+            lg.lg_dock_batch(ctx.h, pid, b, p, r1, side.cuda_stream)
+            side.synchronize()
+            modes.append(ctx.stats().graph)
+            for k, v in o1.items():
+                if v is not None:
+                    assert np.array_equal(v.cpu().numpy(), ref[k]), k
+        assert modes[-1] == 1, modes
+    finally:
+        ctx.set_option("graphs", 0)
+        ctx.unload_pocket(pid)
+
+
 def test_async_calls_on_two_streams_share_scratch_safely(ctx, cfg1):
     # two device-memory calls issued back to back on different streams use the
     # same context scratch; the library orders them on the device

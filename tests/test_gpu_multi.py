@@ -105,6 +105,26 @@ def test_multi_with_ranking(multi):
             assert np.array_equal(g[k], want[k]), (pid, k)
 
 
+def test_multi_heavy_tailed_with_ranking_both_orders(multi):
+    # ligands up to 100 atoms (no size classes across pockets) with pose
+    # ranking, in both visiting orders: each pocket's results equal its own call
+    import dataclasses
+    ctx, _, pids = multi
+    batch = synth.config_ligands(3, 300)
+    assert batch.n_atoms().max() > 64
+    params = dataclasses.replace(synth.config_params(3), restarts=12, passes=2, cluster_rmsd=3.0, rescore_top=4)
+    want = [ctx.dock(pid, batch, params) for pid in pids]
+    try:
+        for order in (0, 1):
+            ctx.set_option("multi_order", order)
+            got = ctx.dock_multi(pids, batch, params)
+            for w, g in zip(want, got):
+                for k in ("score", "best_restart", "status", "rank", "leader", "restart_geo", "pose"):
+                    assert np.array_equal(g[k], w[k]), (order, k)
+    finally:
+        ctx.set_option("multi_order", 0)
+
+
 def test_multi_bad_arguments(multi):
     ctx, _, pids = multi
     batch = synth.config_ligands(2, 4)
