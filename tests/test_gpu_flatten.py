@@ -64,6 +64,15 @@ def test_flatten_matches_oracle(ctx, cfg, L, passes):
     assert rep["deviations"] <= 0.01 * rep["decisions"] + 2, rep
 
 
+def test_flatten_at_maximum_sizes(ctx):
+    # 128 atoms and 32 torsional bonds, next to small ligands
+    batch = synth.make_ligands(77, np.array([lg.LG_MAX_ATOMS, 12, 100]), np.array([lg.LG_MAX_ROT, 2, 20]))
+    gpu = ctx.flatten(batch, 2)
+    assert np.all(gpu["status"] == 0)
+    rep = check_flatten(batch, 2, gpu)
+    assert rep["deviations"] <= 0.01 * rep["decisions"] + 2, rep
+
+
 def test_flatten_device_io_equals_host(ctx):
     batch = synth.config_ligands(2, 200)
     a = ctx.flatten(batch, 2)

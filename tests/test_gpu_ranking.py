@@ -161,6 +161,22 @@ def test_ranking_max_restarts_runs(ctx, cfg1, pocket1):
         assert np.all(lead[rank[:n_lead]] == rank[:n_lead]) and np.all(lead[rank[n_lead:]] != rank[n_lead:])
 
 
+def test_ranking_at_maximum_sizes(ctx, cfg1, pocket1):
+    # the largest ligand (128 atoms, 32 torsional bonds) with 1,024 ranked
+    # restarts and rigid moves: plain and batched forms agree bitwise
+    _, _, params = cfg1
+    big = synth.make_ligands(321, np.array([lg.LG_MAX_ATOMS, 70]), np.array([lg.LG_MAX_ROT, 10]))
+    S = 1024
+    prm = dataclasses.replace(_ranked(params, 6.0, 30, restarts=S), passes=1, rigid_steps=1)
+    a = ctx.dock(pocket1, big, prm, restart_score=True, restart_tors=True, restart_rigid=True, decision_rank=True)
+    b = ctx.dock(pocket1, big, prm, restart_score=True, restart_tors=True, restart_rigid=True, decision_rank=True,
+                 mode=lg.LG_MODE_PLAIN)
+    for k in ("score", "best_restart", "status", "rank", "leader", "restart_geo", "restart_score", "restart_tors",
+              "restart_rigid", "decision_rank", "pose"):
+        assert np.array_equal(a[k], b[k]), k
+    assert np.all(a["status"] == 0)
+
+
 def test_ranking_plain_equals_batched(ctx, cfg1, pocket1):
     _, full, params = cfg1
     batch = full.subset(range(48))
