@@ -18,13 +18,14 @@ pytestmark = pytest.mark.gpu
 
 def _run(fn, ctx, pid, dev, L, A, R, params, stream):
     r, outs = lg.alloc_result(L, A, R, params.restarts, params.passes, device=True, pose=True, tors=True,
-                              restart_score=True, restart_tors=True)
+                              restart_score=True, restart_tors=True, decision_rank=True)
     b = lg.make_batch_struct(dev, L)
     p = lg.make_params(params.restarts, params.passes, params.seed, params.d_clash)
     fn(ctx.h, pid, b, p, r, stream.cuda_stream)
     stream.synchronize()
     n = dict(score=L, best_restart=L, status=L, tors_idx=params.passes * R, pose=3 * A,
-             restart_score=L * params.restarts, restart_tors=params.restarts * params.passes * R)
+             restart_score=L * params.restarts, restart_tors=params.restarts * params.passes * R,
+             decision_rank=params.restarts * params.passes * R)
     return {k: v.cpu().numpy()[:n[k]] for k, v in outs.items() if v is not None}
 
 
