@@ -1321,8 +1321,9 @@ __global__ void __launch_bounds__(128, LG_RT_MIN_BLOCKS) k_dock_multi(const __gr
 //     |x_i(theta) - x_j| = sqrt(C + A2 cos(theta) + B2 sin(theta)),
 // with the pair coefficients built once per decision, 128 pairs at a time by
 // the lanes and read back by broadcast.  Per step, distances are summed in FP32
-// within a 128-pair chunk and the chunks in FP64; the clash rule of the sweep
-// (pairs at least three bonds apart, at least d_clash) decides admissibility;
+// within a 128-pair chunk, the chunks in FP64 and the lanes' totals in FP32;
+// the clash rule of the sweep (pairs at least three bonds apart, at least
+// d_clash) decides admissibility;
 // the admissible step with the largest sum wins, the lowest step on ties.
 __global__ void __launch_bounds__(32 * kFlatWarps) k_flatten(const __grid_constant__ FlatArgs F) {
     extern __shared__ __align__(16) char sm[];
@@ -1424,26 +1425,28 @@ __global__ void __launch_bounds__(32 * kFlatWarps) k_flatten(const __grid_consta
                 for (int j = 0; j < kStepsPerLane; ++j) D[j] += (double)acc[j];
                 __syncwarp();
             }
-            // totals over the 8 pair groups, then the best admissible step of
-            // the lane and of the warp (larger sum, then lower step)
-            double bd = -INFINITY;
+            // totals over the 8 pair groups (FP32: eight terms, ~1e-7
+            // relative), then the best admissible step of the lane and of the
+            // warp (larger sum, then lower step)
+            float bd = -INFINITY;
             int bt = 1024;
 #pragma unroll
             for (int j = 0; j < kStepsPerLane; ++j) {
+                float dj = (float)D[j];
 #pragma unroll
                 for (int o = 4; o < 32; o <<= 1) {
-                    D[j] += __shfl_xor_sync(LG_FULL, D[j], o);
+                    dj += __shfl_xor_sync(LG_FULL, dj, o);
                     mn[j] = fminf(mn[j], __shfl_xor_sync(LG_FULL, mn[j], o));
                 }
                 const int t = 4 * j + g;
-                if ((t == 0 || mn[j] >= F.dc2) && D[j] > bd) {
-                    bd = D[j];
+                if ((t == 0 || mn[j] >= F.dc2) && dj > bd) {
+                    bd = dj;
                     bt = t;
                 }
             }
 #pragma unroll
             for (int o = 1; o < 4; o <<= 1) {
-                const double od = __shfl_xor_sync(LG_FULL, bd, o);
+                const float od = __shfl_xor_sync(LG_FULL, bd, o);
                 const int ot = __shfl_xor_sync(LG_FULL, bt, o);
                 if (od > bd || (od == bd && ot < bt)) {
                     bd = od;
