@@ -145,6 +145,8 @@ struct Scratch {
     float *rk_pose;
     double *rk_E;
     uint8_t *rk_tors;
+    float *rk_G;           // [slots][S] geometric score of each restart's final pose
+    float *rk_cen;         // [slots][S][3] its centroid (centred grid units)
     int rk_slots;          // ranking slots
     size_t rk_floats;      // capacity of rk_pose (floats)
 };

@@ -179,11 +179,45 @@ __device__ __forceinline__ size_t rk_pose_off(const DockArgs &A, int slot, int r
     return ((size_t)slot * A.S + r) * (size_t)A.ly.nmax * 3;
 }
 
+// The ranking step's geometric score G (the overlap grid summed over all
+// atoms) and centroid of a restart's final pose, computed when the restart
+// finishes: lane g of the 4 lanes that combine them sums atoms i = g (mod 4)
+// in order (FP32); the partials are combined as (s0 + s1) + (s2 + s3), so
+// both kernel forms produce the same numbers.
+__device__ __forceinline__ float4 rank_geo_partial(const GridK &Go, float c0, const float *Xx, const float *Xy,
+                                                   const float *Xz, int stride, int N, int g) {
+    float s = 0.0f, cx = 0.0f, cy = 0.0f, cz = 0.0f;
+    for (int i = g; i < N; i += 4) {
+        const float x = Xx[i * stride], y = Xy[i * stride], z = Xz[i * stride];
+        s += lookup_clamped(Go, x + c0, y + c0, z + c0);
+        cx += x;
+        cy += y;
+        cz += z;
+    }
+    return make_float4(s, cx, cy, cz);
+}
+
+__device__ __forceinline__ float4 rank_geo_combine(float4 q) {  // over lanes 4k .. 4k+3
+#pragma unroll
+    for (int o = 1; o < 4; o <<= 1) {
+        q.x += __shfl_xor_sync(LG_FULL, q.x, o);
+        q.y += __shfl_xor_sync(LG_FULL, q.y, o);
+        q.z += __shfl_xor_sync(LG_FULL, q.z, o);
+        q.w += __shfl_xor_sync(LG_FULL, q.w, o);
+    }
+    return q;
+}
+
 // The ranking slot of a CTA (checked builds: within the slots the scratch
 // holds at this launch's atom maximum).
 __device__ __forceinline__ int rank_slot(const DockArgs &A, int slot) {
+#ifdef LG_CHECKS
     const long long fit = (long long)(A.scr.rk_floats / ((size_t)A.S * A.ly.nmax * 3));
     return (int)LG_IDX(slot, fit < A.scr.rk_slots ? fit : A.scr.rk_slots, kChkRankSlot);
+#else
+    (void)A;
+    return slot;
+#endif
 }
 
 // Pose ranking (paper Sec. 3.1, steps 3-4) of ligand l from the restarts kept
@@ -219,36 +253,17 @@ __device__ void rank_finish(const DockArgs &A, const PocketDev &Pk, const OutDev
     unsigned *bits = (unsigned *)q;
     q += lg_align16(4 * (rank_row_off(S) + 1));
     int *bestv = (int *)q;
-    const GridK Go = grid_k(Pk, Pk.cell_o);
     const float *pose0 = A.scr.rk_pose + rk_pose_off(A, slot, 0);
     const size_t pstride = (size_t)A.ly.nmax * 3;
     const bool cluster = A.thr2g > 0.0f;
 
-    // 1. geometric scores (and centroids for the clustering bound): FP32
-    // lookups summed in FP32 over lanes' atoms, then across lanes in a fixed
-    // tree (the torsion steps' overlap sums are FP32 too)
-    for (int r = warp; r < S; r += W) {
-        const float *x = pose0 + pstride * r;
-        float g = 0.0f, cx = 0.0f, cy = 0.0f, cz = 0.0f;
-        for (int i = lane; i < N; i += 32) {
-            const float px = x[3 * i], py = x[3 * i + 1], pz = x[3 * i + 2];
-            g += lookup_clamped(Go, px + Pk.c0, py + Pk.c0, pz + Pk.c0);
-            cx += px;
-            cy += py;
-            cz += pz;
-        }
-        g = warp_sum_f(g);
-        if (cluster) {
-            cx = warp_sum_f(cx);
-            cy = warp_sum_f(cy);
-            cz = warp_sum_f(cz);
-        }
-        if (lane == 0) {
-            sG[r] = (double)g;
-            cen[3 * r] = cx / (float)N;
-            cen[3 * r + 1] = cy / (float)N;
-            cen[3 * r + 2] = cz / (float)N;
-        }
+    // 1. geometric scores and centroids, computed when each restart finished
+    for (int r = tid; r < S; r += blockDim.x) {
+        const size_t q = (size_t)slot * S + r;
+        sG[r] = (double)A.scr.rk_G[q];
+        cen[3 * r] = A.scr.rk_cen[3 * q] / (float)N;
+        cen[3 * r + 1] = A.scr.rk_cen[3 * q + 1] / (float)N;
+        cen[3 * r + 2] = A.scr.rk_cen[3 * q + 2] / (float)N;
     }
     __syncthreads();
     // 2. geometric order
@@ -694,7 +709,17 @@ __global__ void __launch_bounds__(1024) k_dock_plain(const __grid_constant__ Doc
                 x[3 * i + 2] = wv.Xz[i];
             }
             for (int t = lane; t < PR; t += 32) A.scr.rk_tors[((size_t)slot * S + r) * P * Ly.rmax + t] = wv.tcur[t];
-            if (lane == 0) A.scr.rk_E[(size_t)slot * S + r] = E;
+            float4 gq = make_float4(0.0f, 0.0f, 0.0f, 0.0f);  // lanes 0..3 as the 4 lanes of a restart slot
+            if (lane < 4) gq = rank_geo_partial(Go, Pk.c0, wv.Xx, wv.Xy, wv.Xz, 1, N, lane);
+            gq = rank_geo_combine(gq);
+            if (lane == 0) {
+                const size_t q = (size_t)slot * S + r;
+                A.scr.rk_E[q] = E;
+                A.scr.rk_G[q] = gq.x;
+                A.scr.rk_cen[3 * q] = gq.y;
+                A.scr.rk_cen[3 * q + 1] = gq.z;
+                A.scr.rk_cen[3 * q + 2] = gq.w;
+            }
         }
         if (E < bestE) {  // restarts visited in ascending order: ties keep the lower one
             bestE = E;
@@ -1132,6 +1157,18 @@ __device__ __forceinline__ void dock_ligand_rt(const DockArgs &A, const PocketDe
                     for (int t = g; t < PR; t += kLanesPerRestart)
                         A.scr.rk_tors[((size_t)slot * S + r) * P * Ly.rmax + t] = v.tcur[t * kTile + rs];
                     if (g == 0) A.scr.rk_E[(size_t)slot * S + r] = E;
+                }
+            }
+            if (kRank) {  // the restart's geometric score and centroid for the ranking step
+                float4 gq = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                if (done) gq = rank_geo_partial(Go, Pk.c0, v.Xx + rs, v.Xy + rs, v.Xz + rs, kTile, N, g);
+                gq = rank_geo_combine(gq);
+                if (done && g == 0) {
+                    const size_t q = (size_t)rank_slot(A, blockIdx.x) * S + r;
+                    A.scr.rk_G[q] = gq.x;
+                    A.scr.rk_cen[3 * q] = gq.y;
+                    A.scr.rk_cen[3 * q + 1] = gq.z;
+                    A.scr.rk_cen[3 * q + 2] = gq.w;
                 }
             }
             // best of the finished restarts (lowest E, then lowest restart), then of the warp
@@ -1655,7 +1692,8 @@ size_t scratch_bytes(int L, int rmax, int rank_slots, int S, int P, int nmax) {
     if (rank_slots > 0) {
         const size_t nm = (size_t)((nmax + 3) & ~3);
         b += al256(12 * (size_t)rank_slots * S * nm) + al256(8 * (size_t)rank_slots * S) +
-             al256((size_t)rank_slots * S * P * rmax + 1);
+             al256((size_t)rank_slots * S * P * rmax + 1) + al256(4 * (size_t)rank_slots * S) +
+             al256(12 * (size_t)rank_slots * S);
     }
     return b;
 }
@@ -1677,6 +1715,8 @@ Scratch carve_scratch(void *base, int L, int rmax, int rank_slots, int S, int P,
     s.rk_pose = nullptr;
     s.rk_E = nullptr;
     s.rk_tors = nullptr;
+    s.rk_G = nullptr;
+    s.rk_cen = nullptr;
     s.rk_slots = rank_slots > 0 ? rank_slots : 0;
     s.rk_floats = 0;
     if (rank_slots > 0) {
@@ -1687,6 +1727,10 @@ Scratch carve_scratch(void *base, int L, int rmax, int rank_slots, int S, int P,
         s.rk_E = (double *)p;
         p += al256(8 * (size_t)rank_slots * S);
         s.rk_tors = (uint8_t *)p;
+        p += al256((size_t)rank_slots * S * P * rmax + 1);
+        s.rk_G = (float *)p;
+        p += al256(4 * (size_t)rank_slots * S);
+        s.rk_cen = (float *)p;
     }
     return s;
 }
