@@ -1,8 +1,9 @@
 // Docking kernels for sm_103a (GB300): the dock-and-score step of the paper
 // (Sec. 3.1) -- restart poses, greedy torsion sweep with clash check, grid
-// scoring, best restart.  All floating-point arithmetic is in lg_device.cuh.
+// scoring, best restart.  The per-step arithmetic is in lg_device.cuh.
 //
-// Two forms share it and produce bit-identical results:
+// Two forms share it and produce bit-identical results (where a form has its
+// own loop, it sums in the same order):
 //
 //  * k_dock_plain -- one CTA per ligand, one warp per restart, one launch per
 //    ligand.  Lanes own torsion steps: lane t scores step t for every moving
