@@ -194,3 +194,11 @@ def test_resume_after_a_failed_rank_docks_only_the_missing_uids():
     assert np.array_equal(np.asarray(done_E)[order], whole["best_E"][want])
     assert np.array_equal(np.asarray(done_r)[order], whole["best_r"][want])
     assert len(shard.pending(batch.uid, done_uid)) == 0
+
+
+def test_pending_edge_cases():
+    uid = np.array([5, 3, 9, 1], np.uint64)
+    assert np.array_equal(shard.pending(uid, []), np.arange(4))
+    assert len(shard.pending(uid, uid)) == 0
+    assert np.array_equal(shard.pending(uid, np.array([9, 7], np.uint64)), np.array([0, 1, 3]))
+    assert len(shard.pending(np.zeros(0, np.uint64), uid)) == 0
