@@ -13,8 +13,8 @@ tests/test_oracle_pins.py (Philox known-answer vectors, rotation-group
 properties, exactness of trilinear interpolation on trilinear fields and
 against scipy's map_coordinates, grid energies against direct pairwise sums
 at nodes, torsion/rigid-move invariants, brute-force and exhaustive torsion
-searches on small ligands).  The end-to-end greedy docking result itself has
-no external reference beyond those pins.
+searches on small ligands), and the greedy walk across bonds and passes is
+restated step by step with scipy in tests/test_oracle_walk.py.
 """
 from __future__ import annotations
 
