@@ -339,11 +339,15 @@ def multi_pocket_leg(ctx, dev, n_lig, steps, peak_tflops):
         return ms / n
 
     out = {}
-    for name, order in (("pocket_major", 0), ("ligand_major", 1)):
-        ctx.set_option("multi_order", order)
-        ms = timed(lambda: lg.lg_dock_multi(ctx.h, pids, b, p, [r for r, _ in res], sh), steps)
-        out[name] = {"value": L * n_p / (ms / 1e3), "ms_per_step": ms}
+    for win in (1, 0):   # the pockets' L2 access-policy windows on, then off
+        ctx.set_option("l2_window", win)
+        for name, order in (("pocket_major", 0), ("ligand_major", 1)):
+            ctx.set_option("multi_order", order)
+            ms = timed(lambda: lg.lg_dock_multi(ctx.h, pids, b, p, [r for r, _ in res], sh), steps)
+            out[name if win else name + "_no_l2_window"] = {"value": L * n_p / (ms / 1e3), "ms_per_step": ms}
+    ctx.set_option("l2_window", 1)
     ctx.set_option("multi_order", 0)
+    out["l2_persist_mb"] = round(ctx.stats().l2_persist_bytes / 2 ** 20, 1)
     multi_scores = [o["score"][:L].cpu().numpy().copy() for _, o in res]
     per = []
     ctx.set_option("timing", 1)
@@ -354,7 +358,8 @@ def multi_pocket_leg(ctx, dev, n_lig, steps, peak_tflops):
         assert np.array_equal(o["score"][:L].cpu().numpy(), multi_scores[k]), "multi and single pocket disagree"
         per.append({"n": pockets[k].n, "grid_mb": round(96 * pockets[k].n ** 3 / 2 ** 20, 1),
                     "ms": round(ms, 3), "evals_per_s": L / (ms / 1e3),
-                    "frac_jstar1": F / (dock_ms / 1e3) / 1e12 / peak_tflops})
+                    "frac_jstar1": F / (dock_ms / 1e3) / 1e12 / peak_tflops,
+                    "l2_window_mb": round(ctx.stats().l2_window_bytes / 2 ** 20, 1)})
     ctx.set_option("timing", 0)
     return {"pockets": n_p, "ligands": L, "evals_per_step": L * n_p, "unit": UNIT, "restarts": S, "passes": P,
             "sample": f"{L} ligands of the throughput workload's generator against all {n_p} pockets",
@@ -498,6 +503,34 @@ def small_batch_leg(ctx, pid, dev, n_lig, calls):
     return {"ligands": L, "calls": calls, **res}
 
 
+def summary_of(line) -> dict:
+    """The headline figures of the line's legs in a few short keys (the last
+    key of the line, so a truncated tail of the output still shows them)."""
+    def r3(v):
+        return None if v is None else float("%.4g" % v)
+    rf = line.get("roofline") or {}
+    out = {"evals_per_s": r3(line["value"]), "e2e": r3((line.get("e2e") or {}).get("value")),
+           "frac": r3(rf.get("frac")), "frac_jstar1": r3(rf.get("frac_jstar1")),
+           "frac_needed": r3(rf.get("frac_needed"))}
+    if line.get("plain"):
+        out["plain"] = r3(line["plain"]["value"])
+        out["batched_over_plain"] = r3(line["plain"]["batched_over_plain"])
+    for leg in line.get("serving") or []:
+        key = "serve_%d" % round(100 * leg["offered_load"]) + ("" if leg.get("mode") == "device_loop" else "_host")
+        out[key] = [r3(leg["p50_latency_s"] * 1e3), r3(leg["p99_latency_s"] * 1e3), r3(leg["sustained_evals_per_s"])]
+    m = line.get("multi_pocket")
+    if m:
+        out["multi"] = {k: r3(v["value"]) for k, v in m.items() if isinstance(v, dict) and "value" in v}
+    h = line.get("heavy_tailed")
+    if h:
+        out["heavy"] = r3(h["value"])
+    if line.get("flatten"):
+        out["flatten"] = r3(line["flatten"]["value"])
+    if line.get("small_batch"):
+        out["small_batch_us"] = r3(line["small_batch"]["direct"]["us_per_call"])
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -508,7 +541,8 @@ def main():
     ap.add_argument("--plain-sample", type=int, default=4096)
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--serve-seconds", type=float, default=3.0, help="seconds per offered load of the serving leg (0 = off)")
+    ap.add_argument("--serve-seconds", type=float, default=60.0,
+                    help="seconds per offered load of the serving leg (0 = off)")
     ap.add_argument("--serve-loads", default="0.25,0.5,0.9",
                     help="comma-separated offered loads (fractions of the measured batched rate)")
     ap.add_argument("--stage-ligands", type=int, default=20000,
@@ -605,6 +639,9 @@ def main():
     ranks = acc_o["decision_rank"][:S * P * R].cpu().numpy()
     del acc_r, acc_o
     F = float(shard.ligand_flops_ranked(batch, S, P, ranks).sum())
+    F_needed = float(shard.ligand_flops_needed(batch, S, P, ranks).sum())
+    jstar = ranks.astype(np.int64) & shard.RANK_MASK
+    skipped = float(((ranks.astype(np.int64) & shard.RANK_SKIPPED) != 0).mean()) if ranks.size else 0.0
     props = torch.cuda.get_device_properties(dev)
     sm_count = props.multi_processor_count
     peaks = {}
@@ -619,8 +656,11 @@ def main():
                 "frac": achieved / peak_tflops, "traffic": traffic_for_current_kernel(),
                 "kernel": "k_dock_batched", "dock_ms_per_launch": dock_ms, "flop_per_launch": F,
                 "flop_basis": "cost model with per-decision j* (mean %.2f) from an untimed accounting call" %
-                              float(ranks.mean() if ranks.size else 1.0),
+                              float(jstar.mean() if jstar.size else 1.0),
                 "flop_per_launch_jstar1": F1, "frac_jstar1": F1 / (dock_ms / 1e3) / 1e12 / peak_tflops,
+                "flop_per_launch_needed": F_needed, "frac_needed": F_needed / (dock_ms / 1e3) / 1e12 / peak_tflops,
+                "needed_basis": "the same count over the decisions the run executed: %.1f%% of decisions are "
+                                "skipped by exact convergence stops and not credited" % (100 * skipped),
                 "flop_per_launch_circle_form": circle_form_flops(batch, S, P),
                 "peak_basis": f"{sm_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max_mhz:.0f} MHz",
                 "limiter": "L1 data pipe ~59% (scattered 32-byte trilinear-cell gathers plus shared-memory "
@@ -749,6 +789,7 @@ def main():
                 "clocks": clk, "gpu_launches": launches_per_step * args.steps, "plain": plain,
                 "serving": serving, "multi_pocket": multi, "flatten": flatten, "heavy_tailed": heavy,
                 "small_batch": small, "stages": stages}
+        line["summary"] = summary_of(line)  # last key: the headline figures of every leg, short
         print(json.dumps(line), flush=True)
     ctx.close()
     if dist:

@@ -218,8 +218,10 @@ typedef struct {
  *                      overlap score (higher score, or equal score and lower
  *                      step): the steps whose clash check a method cannot skip.
  *                      Decisions skipped after convergence repeat the bond's
- *                      previous decision and its rank; a bond that moves no
- *                      atom ranks 1.  For accounting (work per decision). */
+ *                      previous decision and its rank, with bit 7 (0x80) set
+ *                      to mark them skipped (the rank is the low 7 bits); a
+ *                      bond that moves no atom ranks 1.  For accounting (work
+ *                      per decision, and the work the exact stops skip). */
 typedef struct {
     int32_t mem;
     double *score;
@@ -345,9 +347,10 @@ int lg_flatten_batch(lg_ctx *ctx, const lg_ligand_batch *batch, const lg_flatten
  *     call is asynchronous on `stream` like lg_dock_batch.
  *   - The scratch needs about 32 + 2 * max_rot bytes per ligand (max_rot = 32
  *     when 0) plus 1 KiB; larger batches are rejected with LG_EINVAL.
- *   - The first call on a device looks up the array's device address (once per
- *     device, with that device current): make that first call before any
- *     stream capture.
+ *   - Every call looks up the array's device address with the context's
+ *     device current (a host-side lookup).  The first call on a device may
+ *     also load the library's device code there: make that first call before
+ *     any stream capture.
  *   - Every call shares the array and finds the previous call's contents in
  *     it; the call clears the counters that must start at zero.  Calls whose
  *     work overlaps on the GPU race on the array: order them on one stream.
@@ -418,6 +421,14 @@ typedef struct {
     int32_t ctas_per_sm;
     int32_t smem_bytes;   /* dynamic shared memory per CTA */
     int32_t graph;        /* last call: 2 captured a CUDA graph, 1 replayed one, 0 launched directly */
+    int32_t serve_loop_status;   /* device-resident serving loop: how its last launch ended (LG_OK after a
+                                    stop, LG_ETIMEOUT after its idle limit, LG_EINVAL for a bad work item;
+                                    -1 while running or never launched) */
+    int32_t reserved;
+    int64_t l2_window_bytes;     /* L2 access-policy window of the last docking launch (0: none) */
+    int64_t l2_persist_bytes;    /* persisting L2 set-aside of the context (0: none) */
+    int64_t serve_loop_launches; /* launches of the device-resident serving loop */
+    int64_t serve_loop_items;    /* ligands it has docked */
 } lg_stats;
 
 int lg_get_stats(lg_ctx *ctx, lg_stats *out);

@@ -189,6 +189,11 @@ struct DockArgs {
     int cls;                   // with cls_off: the size class this launch docks
     int item_cap;              // > 0: dock only item_cap items evenly spread over the range (autotuning trials)
     int sort_classes;          // preparation: 1 = size class major, then cost; 0 = cost only
+    // L2 access-policy window of the launch (host side only: the docking
+    // launches carry it as a launch attribute; l2_bytes = 0: none)
+    const void *l2_base;
+    size_t l2_bytes;
+    float l2_hit;
 };
 
 // Cost order of the batched kernels: ligands are filed by size class (atoms

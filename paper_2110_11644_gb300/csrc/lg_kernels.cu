@@ -39,6 +39,10 @@
 namespace lg {
 
 __constant__ float c_cos[LG_ANGLE_STEPS];
+
+// decision_rank: bit 7 marks a decision skipped by an exact convergence stop
+// (its low bits repeat the bond's previous rank)
+constexpr uint8_t kRankSkipped = 0x80;
 __constant__ float c_sin[LG_ANGLE_STEPS];
 
 void set_angle_tables(const float *cosv, const float *sinv) {
@@ -667,8 +671,8 @@ __global__ void __launch_bounds__(1024) k_dock_plain(const __grid_constant__ Doc
                 zrun = t != 0 ? 0 : zrun + 1;
                 if (A.rigid_steps == 0 && zrun >= R) {
                     for (int q = ps * R + k + 1 + lane; q < P * R; q += 32) wv.tcur[q] = 0;
-                    if (dr && lane == 0)  // skipped decisions repeat the bond's previous one
-                        for (int q = ps * R + k + 1; q < P * R; ++q) dr[q] = dr[q - R];
+                    if (dr && lane == 0)  // skipped decisions repeat the bond's previous one, marked skipped
+                        for (int q = ps * R + k + 1; q < P * R; ++q) dr[q] = dr[q - R] | kRankSkipped;
                     converged = true;
                     break;
                 }
@@ -678,7 +682,7 @@ __global__ void __launch_bounds__(1024) k_dock_plain(const __grid_constant__ Doc
             if (ps + 1 < P && !moved) {
                 for (int q = (ps + 1) * R + lane; q < P * R; q += 32) wv.tcur[q] = 0;
                 if (dr && lane == 0)
-                    for (int q = (ps + 1) * R; q < P * R; ++q) dr[q] = dr[q - R];
+                    for (int q = (ps + 1) * R; q < P * R; ++q) dr[q] = dr[q - R] | kRankSkipped;
                 if (A.rigid_steps > 0 && lane == 0 && A.out.restart_rigid)
                     for (int q = (ps + 1) * A.rigid_steps; q < P * A.rigid_steps; ++q)
                         A.out.restart_rigid[((size_t)l * S + r) * P * A.rigid_steps + q] = 0;
@@ -1122,9 +1126,9 @@ __device__ __forceinline__ void dock_ligand_rt(const DockArgs &A, const PocketDe
         if (__any_sync(LG_FULL, done)) {
             if (done) {
                 for (int q = pc * R + g; q < PR; q += kLanesPerRestart) v.tcur[q * kTile + rs] = 0;
-                if (kTrace && g == 0) {  // skipped passes repeat the last one
+                if (kTrace && g == 0) {  // skipped passes repeat the last one, marked skipped
                     uint8_t *dr = O.decision_rank + (size_t)S * P * r0 + (size_t)r * PR;
-                    for (int q = pc * R; q < PR; ++q) dr[q] = dr[q - R];
+                    for (int q = pc * R; q < PR; ++q) dr[q] = dr[q - R] | kRankSkipped;
                 }
                 if (kRigid && g == 0 && O.restart_rigid)
                     for (int q = pc * A.rigid_steps; q < P * A.rigid_steps; ++q)
@@ -1224,7 +1228,7 @@ __device__ __forceinline__ void dock_ligand_rt(const DockArgs &A, const PocketDe
                 v.tcur[LG_IDX(pc * R + k, P * Ly.rmax, kChkDecision) * kTile + rs] = (uint8_t)t;
                 if (kTrace) {  // a skipped decision repeats the bond's previous one
                     uint8_t *dr = O.decision_rank + (size_t)S * P * r0 + (size_t)r * PR + pc * R + k;
-                    *dr = sv ? (uint8_t)jr : dr[-R];
+                    *dr = sv ? (uint8_t)jr : (uint8_t)(dr[-R] | kRankSkipped);
                 }
             }
             movedp = movedp || t != 0;
@@ -1234,7 +1238,7 @@ __device__ __forceinline__ void dock_ligand_rt(const DockArgs &A, const PocketDe
                     for (int q = pc * R + k + 1 + g; q < (pc + 1) * R; q += kLanesPerRestart) v.tcur[q * kTile + rs] = 0;
                 if (kTrace && active && g == 0) {
                     uint8_t *dr = O.decision_rank + (size_t)S * P * r0 + (size_t)r * PR;
-                    for (int q = pc * R + k + 1; q < (pc + 1) * R; ++q) dr[q] = dr[q - R];
+                    for (int q = pc * R + k + 1; q < (pc + 1) * R; ++q) dr[q] = dr[q - R] | kRankSkipped;
                 }
                 break;
             }
@@ -1791,24 +1795,43 @@ cudaError_t launch_dock_plain(const DockArgs &a, int ligand, int slot, cudaStrea
     return cudaGetLastError();
 }
 
+// Launch configuration of a docking launch; with a.l2_bytes > 0 it carries the
+// pocket's L2 access-policy window (overlap-grid cells marked persisting in
+// the context's persisting L2 set-aside, other traffic streaming).
+struct DockLaunch {
+    cudaLaunchConfig_t cfg{};
+    cudaLaunchAttribute attr[1];
+    DockLaunch(const DockArgs &a, int grid, int smem, cudaStream_t s) {
+        cfg.gridDim = dim3(grid);
+        cfg.blockDim = dim3(32 * a.ly.W);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = s;
+        if (a.l2_bytes > 0) {
+            attr[0].id = cudaLaunchAttributeAccessPolicyWindow;
+            attr[0].val.accessPolicyWindow.base_ptr = const_cast<void *>(a.l2_base);
+            attr[0].val.accessPolicyWindow.num_bytes = a.l2_bytes;
+            attr[0].val.accessPolicyWindow.hitRatio = a.l2_hit;
+            attr[0].val.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+            attr[0].val.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+        }
+    }
+};
+
 cudaError_t launch_dock_batched(const DockArgs &a, int grid, int smem, cudaStream_t s) {
-    return with_batched(a.ranking, a.rigid_steps > 0, a.out.decision_rank != nullptr, [&](auto kernel) {
-        kernel<<<grid, 32 * a.ly.W, smem, s>>>(a);
-        return cudaGetLastError();
-    });
+    DockLaunch dl(a, grid, smem, s);
+    return with_batched(a.ranking, a.rigid_steps > 0, a.out.decision_rank != nullptr,
+                        [&](auto kernel) { return cudaLaunchKernelEx(&dl.cfg, kernel, a); });
 }
 
 cudaError_t launch_dock_multi(const DockArgs &a, const MultiDev &m, int grid, int smem, cudaStream_t s) {
+    DockLaunch dl(a, grid, smem, s);
     const bool rigid = a.rigid_steps > 0;
-    if (a.ranking && rigid)
-        k_dock_multi<true, true><<<grid, 32 * a.ly.W, smem, s>>>(a, m);
-    else if (a.ranking)
-        k_dock_multi<true, false><<<grid, 32 * a.ly.W, smem, s>>>(a, m);
-    else if (rigid)
-        k_dock_multi<false, true><<<grid, 32 * a.ly.W, smem, s>>>(a, m);
-    else
-        k_dock_multi<false, false><<<grid, 32 * a.ly.W, smem, s>>>(a, m);
-    return cudaGetLastError();
+    if (a.ranking && rigid) return cudaLaunchKernelEx(&dl.cfg, k_dock_multi<true, true>, a, m);
+    if (a.ranking) return cudaLaunchKernelEx(&dl.cfg, k_dock_multi<true, false>, a, m);
+    if (rigid) return cudaLaunchKernelEx(&dl.cfg, k_dock_multi<false, true>, a, m);
+    return cudaLaunchKernelEx(&dl.cfg, k_dock_multi<false, false>, a, m);
 }
 
 cudaError_t launch_flatten(const FlatArgs &f, int L, cudaStream_t s) {

@@ -29,23 +29,19 @@ namespace lg {
 // device that loads the library, held until the process exits.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[LG_NOALLOC_SCRATCH_BYTES];
 
-// Device address of the array, looked up once per device with that device
-// current.  In host code the array's name is only a host-side stand-in, so
-// kernels must be given this address.
-static void *g_scratch_addr[64];
-static std::mutex g_scratch_mu;
-
-static int noalloc_scratch(int device, void **out) {
-    if (device < 0 || device >= 64) return fail(LG_EINVAL, "device index out of range for the static scratch");
-    std::lock_guard<std::mutex> g(g_scratch_mu);
-    if (!g_scratch_addr[device]) {
-        void *p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p)
-            return fail(LG_ECUDA, std::string("static scratch address: ") + cudaGetErrorString(e));
-        g_scratch_addr[device] = p;
+// Device address of the array on the current device.  In host code the
+// array's name is only a host-side stand-in, so kernels must be given this
+// address.  It is looked up on every call (a host-side table lookup once the
+// module is loaded), so a context re-created after cudaDeviceReset never uses
+// an address of the old one; the first call on a device may load the module.
+static int noalloc_scratch(void **out) {
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+        cudaGetLastError();
+        return fail(LG_ECUDA, std::string("static scratch address: ") + cudaGetErrorString(e));
     }
-    *out = g_scratch_addr[device];
+    *out = p;
     return LG_OK;
 }
 
@@ -85,7 +81,7 @@ extern "C" int lg_dock_batch_noalloc(lg_ctx *c, int32_t pid, const lg_ligand_bat
     }
     if (cudaSetDevice(c->device) != cudaSuccess) return fail(LG_ECUDA, "cudaSetDevice failed");
     void *base = nullptr;
-    if ((rc = noalloc_scratch(c->device, &base))) return rc;
+    if ((rc = noalloc_scratch(&base))) return rc;
     cudaStream_t s = (cudaStream_t)stream;
 
     DockArgs a;
@@ -147,5 +143,8 @@ extern "C" int lg_dock_batch_noalloc(lg_ctx *c, int32_t pid, const lg_ligand_bat
     const int grid = std::max(1, std::min(c->num_sms * occ, L));
     if ((e = launch_dock_batched(a, grid, smem, s)) != cudaSuccess)
         return fail(LG_ECUDA, std::string("dock launch: ") + cudaGetErrorString(e));
+#ifdef LG_CHECKS
+    if ((rc = checks_result(s))) return rc;  // debug build: this call's bounds-check record
+#endif
     return LG_OK;
 }

@@ -284,6 +284,14 @@ static int dock_device_launch(lg_ctx *ctx, const PocketDev &pk, const BatchDev &
     st->dock_calls = keep.dock_calls;
     st->dock_ms_total = keep.dock_ms_total;
     st->dock_ms = keep.dock_ms;
+    st->serve_loop_status = keep.serve_loop_status;
+    st->serve_loop_launches = keep.serve_loop_launches;
+    st->serve_loop_items = keep.serve_loop_items;
+    // one pocket per launch: its overlap cells get the L2 window (not for
+    // launches that dock against several pockets at once)
+    if (!multi || (multi->np == 1 && !multi->lig_pocket)) l2_window_of(ctx, pk, &a.l2_base, &a.l2_bytes, &a.l2_hit);
+    st->l2_window_bytes = (int64_t)a.l2_bytes;
+    st->l2_persist_bytes = (int64_t)ctx->l2_persist_set;
     const int L = bd.L;
     const bool plain = p->mode == LG_MODE_PLAIN;
     if (plain && multi) return fail(LG_EINVAL, "several pockets run in the batched mode only");
@@ -676,6 +684,38 @@ void harvest_timing(lg_ctx *c) {
     }
 }
 
+// L2 access-policy window of a pocket's overlap cells (the lookups of every
+// torsion step): the cells, capped at the device's window limit, with the
+// share of them the persisting set-aside can hold as the hit ratio.
+void l2_window_of(lg_ctx *c, const PocketDev &pk, const void **base, size_t *bytes, float *hit) {
+    *base = nullptr;
+    *bytes = 0;
+    *hit = 0.0f;
+    if (!c->l2_window.load() || c->l2_persist_set == 0 || c->l2_window_max == 0) return;
+    const size_t n = (size_t)pk.n, cells = n * n * n * 32;
+    *base = pk.cell_o;
+    *bytes = std::min(cells, c->l2_window_max);
+    *hit = (float)std::min(1.0, (double)c->l2_persist_set / (double)*bytes);
+}
+
+// Persisting L2 set-aside for the loaded pockets: room for the largest
+// pocket's overlap cells (the pocket a launch docks against), within the
+// device's maximum.  A context limit: it ends with the context.
+static void l2_reserve(lg_ctx *c) {
+    if (c->l2_persist_max == 0) return;
+    size_t want = 0;
+    for (const auto &p : c->pockets)
+        if (p.live) want = std::max(want, (size_t)p.dev.n * p.dev.n * p.dev.n * 32);
+    want = std::min(want, c->l2_persist_max);
+    if (want == c->l2_persist_set) return;
+    if (cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, want) == cudaSuccess) {
+        c->l2_persist_set = want;
+    } else {
+        cudaGetLastError();  // no set-aside: launches then carry no window
+        c->l2_persist_set = 0;
+    }
+}
+
 // Pocket packing: trilinear coefficients per node (FP64, rounded to FP32).
 static void pack_cells(const float *g, int n, float *out, int stride, int offset) {
     auto at = [&](int i, int j, int k) -> double {
@@ -719,11 +759,23 @@ int lg_create(int device, lg_ctx **out) {
     lg_ctx *c = new (std::nothrow) lg_ctx();
     if (!c) return fail(LG_ENOMEM, "context allocation failed");
     c->device = device;
+    c->stats.serve_loop_status = -1;
     cudaError_t e;
     if ((e = cudaSetDevice(device)) != cudaSuccess ||
         (e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device)) != cudaSuccess) {
         delete c;
         return fail(LG_ECUDA, std::string("device setup: ") + cudaGetErrorString(e));
+    }
+    {
+        int pmax = 0, wmax = 0;
+        if (cudaDeviceGetAttribute(&pmax, cudaDevAttrMaxPersistingL2CacheSize, device) == cudaSuccess &&
+            cudaDeviceGetAttribute(&wmax, cudaDevAttrMaxAccessPolicyWindowSize, device) == cudaSuccess &&
+            cudaDeviceGetLimit(&c->l2_persist_prev, cudaLimitPersistingL2CacheSize) == cudaSuccess) {
+            c->l2_persist_max = (size_t)std::max(pmax, 0);
+            c->l2_window_max = (size_t)std::max(wmax, 0);
+        } else {
+            cudaGetLastError();
+        }
     }
     for (int i = 0; i < 3; i++) cudaEventCreate(&c->ev[i]);
     cudaEventCreateWithFlags(&c->scratch_ev, cudaEventDisableTiming);
@@ -751,6 +803,11 @@ void lg_destroy(lg_ctx *c) {
     cudaDeviceSynchronize();
     for (auto &p : c->pockets)
         if (p.mem) cudaFree(p.mem);
+    if (c->l2_persist_set) {  // lines marked persisting go back to normal; the limit found at creation
+        cudaCtxResetPersistingL2Cache();
+        cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, c->l2_persist_prev);
+        cudaGetLastError();
+    }
     c->in_buf.release();
     c->out_buf.release();
     c->scratch.release();
@@ -842,6 +899,7 @@ int lg_pocket_load(lg_ctx *c, const lg_pocket_desc *d, int32_t *pid) {
     } else {
         c->pockets[id] = r;
     }
+    l2_reserve(c);
     *pid = id;
     return LG_OK;
 }
@@ -853,6 +911,7 @@ int lg_pocket_unload(lg_ctx *c, int32_t pid) {
     cudaSetDevice(c->device);
     cudaFree(c->pockets[pid].mem);
     c->pockets[pid] = PocketRec();
+    l2_reserve(c);
     return LG_OK;
 }
 
@@ -1084,6 +1143,11 @@ int lg_set_option(lg_ctx *c, const char *key, int64_t v) {
     } else if (!strcmp(key, "multi_order")) {
         if (v != 0 && v != 1) return fail(LG_EINVAL, "multi_order must be 0 or 1");
         c->multi_pocket_major = v == 0 ? 1 : 0;
+    } else if (!strcmp(key, "l2_window")) {
+        c->l2_window = v != 0;
+        cudaSetDevice(c->device);
+        for (auto &g : c->graph_cache) cudaGraphExecDestroy(g.exec);  // captured launches carry the old choice
+        c->graph_cache.clear();
     } else if (!strcmp(key, "serve_mem_reserve_mb")) {
         if (v < 0) return fail(LG_EINVAL, "serve_mem_reserve_mb must be >= 0");
         c->serve_reserve_mb = v;

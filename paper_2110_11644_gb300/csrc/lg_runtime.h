@@ -62,6 +62,7 @@ cudaEvent_t *next_timing_events(lg_ctx *c);
 void harvest_timing(lg_ctx *c);
 void serve_stop(lg_ctx *c);
 int choose_warps(int S, int opt);
+void l2_window_of(lg_ctx *c, const PocketDev &pk, const void **base, size_t *bytes, float *hit);
 
 }  // namespace lg
 
@@ -106,6 +107,14 @@ struct lg_ctx {
     std::map<std::array<int, 8>, int> tune;
     lg::DevBuf flat_buf;  // lg_flatten_batch: host-output staging and the preparation's unused outputs
     int multi_pocket_major = 1;
+    // L2 residency of the pockets: the persisting set-aside (process-local
+    // context limit, sized for the largest loaded pocket's overlap cells) and
+    // the device's limits; the docking launches mark their pocket's overlap
+    // cells persisting through an access-policy window (option "l2_window")
+    size_t l2_persist_max = 0, l2_window_max = 0;
+    size_t l2_persist_prev = 0;  // the limit found at creation, restored at destruction
+    size_t l2_persist_set = 0;   // the set-aside this context asked for (0: none)
+    std::atomic<bool> l2_window{true};
     // orders the calls that share `scratch` (and `flat_buf`) on the device: a
     // call's stream waits for the previous such call's work to finish
     cudaEvent_t scratch_ev = nullptr;

@@ -303,6 +303,16 @@ static size_t request_device_bytes(const Request &r) {
            (r.out.restart_rigid ? S * P * r.params.rigid_steps * r.L : 0) + 8 * (size_t)r.L + 4096;
 }
 
+// Device scratch of a merged batch (dock_device's buffer): cost order,
+// centroids, subtree ends and, with pose ranking, one pose slot per CTA of
+// the widest launch the call may make (at most 32 CTAs per SM, and never
+// more slots than ligands).
+static size_t merged_scratch_bytes(lg_ctx *c, const Request &r, int L, int nmax, int rmax) {
+    const bool ranking = ranking_on(&r.params);
+    const int slots = ranking ? std::max(1, std::min(L, 32 * ctx_num_sms(c))) : 0;
+    return scratch_bytes(L, rmax, slots, r.params.restarts, r.params.passes, nmax);
+}
+
 static void worker(Server *sv) {
     lg_ctx *c = sv->ctx;
     cudaSetDevice(c->device);
@@ -330,36 +340,53 @@ static void worker(Server *sv) {
                     break;
                 }
             if (!free_sl) break;
-            // merge queued requests of the same kind, in arrival order
-            std::vector<std::shared_ptr<Request>> take;
-            std::vector<const float4 *> pockets;  // distinct pockets of the merged batch
-            const int max_merge = c->serve_max_merge;
-            int Lm = 0;
-            size_t bytes = 0;
-            for (auto it = sv->queue.begin(); it != sv->queue.end();) {
-                const bool known = std::find(pockets.begin(), pockets.end(), (*it)->pocket.cell_o) != pockets.end();
-                if (!take.empty() && (!same_kind(*take[0], **it, c->serve_cross_pocket) || Lm + (*it)->L > max_merge ||
-                                      (!known && (int)pockets.size() >= LG_MAX_MULTI_POCKETS))) {
-                    ++it;
-                    continue;
-                }
-                if (!known) pockets.push_back((*it)->pocket.cell_o);
-                take.push_back(*it);
-                Lm += (*it)->L;
-                bytes += request_device_bytes(**it);
-                it = sv->queue.erase(it);
-                if (Lm >= max_merge) break;
-            }
-            // admission by free device memory (always admit when the device is idle)
+            // One merged batch per kind of request: the first queued request of
+            // a kind not yet tried in this round seeds it, and the later queued
+            // requests of the same kind join it in arrival order.  A batch that
+            // does not fit in free device memory stays queued where it is (no
+            // request moves) and the next kind is tried, so a large request
+            // waiting for memory does not hold back smaller ones of other kinds.
             size_t fr = 0, tot = 0;
             cudaMemGetInfo(&fr, &tot);
             const size_t reserve = (size_t)c->serve_reserve_mb << 20;
             const size_t have = free_sl->in.cap + free_sl->out.cap + free_sl->scratch.cap;
-            const size_t need = bytes > have ? bytes - have : 0;
-            if (busy > 0 && need > 0 && need + reserve > fr) {
-                for (auto it = take.rbegin(); it != take.rend(); ++it) sv->queue.push_front(*it);
-                break;
+            const int max_merge = c->serve_max_merge;
+            std::vector<const Request *> tried;
+            std::vector<size_t> take_idx;
+            for (size_t seed = 0; seed < sv->queue.size() && take_idx.empty(); ++seed) {
+                const Request &rs = *sv->queue[seed];
+                bool seen = false;
+                for (const Request *t : tried) seen = seen || same_kind(*t, rs, c->serve_cross_pocket);
+                if (seen) continue;
+                tried.push_back(&rs);
+                std::vector<size_t> idx;
+                std::vector<const float4 *> pockets;  // distinct pockets of the merged batch
+                int Lm = 0, nm = 1, rm = 1;
+                size_t bytes = 0;
+                for (size_t i = seed; i < sv->queue.size(); ++i) {
+                    const Request &r = *sv->queue[i];
+                    const bool known = std::find(pockets.begin(), pockets.end(), r.pocket.cell_o) != pockets.end();
+                    if (!idx.empty() && (!same_kind(rs, r, c->serve_cross_pocket) || Lm + r.L > max_merge ||
+                                         (!known && (int)pockets.size() >= LG_MAX_MULTI_POCKETS)))
+                        continue;
+                    if (!known) pockets.push_back(r.pocket.cell_o);
+                    idx.push_back(i);
+                    Lm += r.L;
+                    nm = std::max(nm, r.nmax);
+                    rm = std::max(rm, r.rmax);
+                    bytes += request_device_bytes(r);
+                    if (Lm >= max_merge) break;
+                }
+                bytes += merged_scratch_bytes(c, rs, Lm, nm, rm);
+                // admission by free device memory (an idle device always admits)
+                const size_t need = bytes > have ? bytes - have : 0;
+                if (busy > 0 && need > 0 && need + reserve > fr) continue;
+                take_idx = idx;
             }
+            if (take_idx.empty()) break;  // nothing fits until a batch in flight finishes
+            std::vector<std::shared_ptr<Request>> take;
+            for (size_t i : take_idx) take.push_back(sv->queue[i]);
+            for (size_t j = take_idx.size(); j-- > 0;) sv->queue.erase(sv->queue.begin() + take_idx[j]);
             // requests for the same pocket side by side: the merged batch is
             // docked in this order, one pocket's grids in L2 at a time
             std::stable_sort(take.begin(), take.end(),

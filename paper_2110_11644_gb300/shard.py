@@ -19,8 +19,10 @@ decision, j* = 1 + the number of steps ranked before the chosen one by overlap
 score: a method must clash-check those steps (each was rejected) and the
 chosen one, and no others.  ligand_flops takes j* = 1, a lower bound;
 ligand_flops_ranked takes each decision's j* from the docking run's own
-decisions (lg_dock_result.decision_rank).  ligand_flops_circle counts the
-lower figure of the circle form the kernels evaluate.
+decisions (lg_dock_result.decision_rank).  ligand_flops_needed credits only
+the decisions the run did not skip by its exact convergence stops (the work
+the result needed); ligand_flops_circle counts the lower figure of the circle
+form the kernels evaluate.
 """
 from __future__ import annotations
 
@@ -33,6 +35,9 @@ C_ROT, C_TRI, C_PAIR, C_FIN, C_POSE_ATOM, C_RESTART = 21, 30, 8, 64, 21, 40
 # + 1 (sum) per moving atom and step; 30 per moving atom and decision for its
 # circle and the move; 21 + 44 per atom and restart
 C_LOOKUP_CIRCLE, C_BOND_CIRCLE, C_FINAL_CIRCLE = 30, 30, 44
+# decision_rank: j* in the low 7 bits; bit 7 marks a decision skipped by an
+# exact convergence stop (its rank repeats the bond's previous one)
+RANK_MASK, RANK_SKIPPED = 0x7F, 0x80
 
 
 def _bond_counts(batch):
@@ -107,7 +112,7 @@ def ligand_flops_ranked(batch, restarts: int, passes: int, decision_rank, rigid_
     roff = batch.rot_off.astype(np.int64)
     nrot = np.diff(roff)
     per = restarts * passes * nrot                      # decisions per ligand
-    ranks = np.asarray(decision_rank, np.float64)[: int(per.sum())]
+    ranks = (np.asarray(decision_rank)[: int(per.sum())].astype(np.int64) & RANK_MASK).astype(np.float64)
     lig = np.repeat(np.arange(L), per)
     local = np.arange(ranks.size) - np.repeat(np.cumsum(per) - per, per)
     bond = roff[lig] + local % np.maximum(nrot[lig], 1)
@@ -115,6 +120,29 @@ def ligand_flops_ranked(batch, restarts: int, passes: int, decision_rank, rigid_
     extra = np.zeros(L)
     np.add.at(extra, rl, C_PAIR * (jsum - restarts * passes) * pairs)
     return ligand_flops(batch, restarts, passes, rigid_steps) + extra
+
+
+def ligand_flops_needed(batch, restarts: int, passes: int, decision_rank) -> np.ndarray:
+    """The work a docking run needed: ligand_flops_ranked without the
+    decisions its exact convergence stops skipped (bit 7 of decision_rank:
+    after R decisions in a row without a move every later decision repeats
+    one of them, so neither its lookups nor its clash pairs are needed).  Per
+    restart the rigid pose and the final score stay."""
+    m, pairs, rl, L = _bond_counts(batch)
+    roff = batch.rot_off.astype(np.int64)
+    nrot = np.diff(roff)
+    per = restarts * passes * nrot
+    raw = np.asarray(decision_rank)[: int(per.sum())].astype(np.int64)
+    run = (raw & RANK_SKIPPED) == 0
+    jstar = (raw & RANK_MASK).astype(np.float64)
+    lig = np.repeat(np.arange(L), per)
+    local = np.arange(raw.size) - np.repeat(np.cumsum(per) - per, per)
+    bond = roff[lig] + local % np.maximum(nrot[lig], 1)
+    work = np.where(run, 36.0 * m[bond] * (C_ROT + C_TRI) + C_PAIR * jstar * pairs[bond], 0.0)
+    N = np.diff(batch.atom_off).astype(np.float64)
+    out = restarts * (C_POSE_ATOM * N + C_RESTART + C_FIN * N)
+    np.add.at(out, lig, work)
+    return out
 
 
 def ligand_flops_circle(batch, restarts: int, passes: int) -> np.ndarray:
@@ -149,30 +177,35 @@ def pending(uid, done_uid) -> np.ndarray:
 def gather_ranking(uid, score, k: int, group=None):
     """Global k best (lowest score, then lowest uid) over all ranks of the
     default process group: each rank sends its own k best, rank 0 merges.
-    Returns (uid, score) arrays on rank 0 and None elsewhere."""
+    Returns (uid as uint64, score) arrays on rank 0 and None elsewhere.
+
+    uids are full 64-bit values (both halves feed the restart counters), so
+    they travel as their own int64 tensor holding the uint64 bits, never
+    through a floating-point column; the tie rule compares them as uint64."""
     import torch
     import torch.distributed as dist
 
-    uid = np.asarray(uid, np.int64)
+    uid = np.asarray(uid, np.uint64)
     score = np.asarray(score, np.float64)
     ok = np.isfinite(score)
     uid, score = uid[ok], score[ok]
     order = np.lexsort((uid, score))[:k]
-    mine = torch.from_numpy(np.stack([uid[order].astype(np.float64), score[order]], 1) if len(order)
-                            else np.zeros((0, 2)))
     world = dist.get_world_size(group)
-    n = torch.tensor([mine.shape[0]], dtype=torch.int64)
+    n = torch.tensor([len(order)], dtype=torch.int64)
     counts = [torch.zeros(1, dtype=torch.int64) for _ in range(world)]
     dist.all_gather(counts, n, group=group)
     kmax = int(max(c.item() for c in counts))
-    pad = torch.full((kmax, 2), float("nan"), dtype=torch.float64)
-    pad[: mine.shape[0]] = mine
-    bufs = [torch.empty((kmax, 2), dtype=torch.float64) for _ in range(world)]
-    dist.all_gather(bufs, pad, group=group)
+    u_pad = torch.zeros(kmax, dtype=torch.int64)
+    s_pad = torch.full((kmax,), float("nan"), dtype=torch.float64)
+    u_pad[: len(order)] = torch.from_numpy(np.ascontiguousarray(uid[order]).view(np.int64))
+    s_pad[: len(order)] = torch.from_numpy(np.ascontiguousarray(score[order]))
+    u_bufs = [torch.empty(kmax, dtype=torch.int64) for _ in range(world)]
+    s_bufs = [torch.empty(kmax, dtype=torch.float64) for _ in range(world)]
+    dist.all_gather(u_bufs, u_pad, group=group)
+    dist.all_gather(s_bufs, s_pad, group=group)
     if dist.get_rank(group) != 0:
         return None
-    allv = torch.cat([b[: int(c.item())] for b, c in zip(bufs, counts)]).numpy()
-    u = allv[:, 0].astype(np.int64)
-    s = allv[:, 1]
+    u = np.concatenate([b[: int(c.item())].numpy() for b, c in zip(u_bufs, counts)]).view(np.uint64)
+    s = np.concatenate([b[: int(c.item())].numpy() for b, c in zip(s_bufs, counts)])
     order = np.lexsort((u, s))[:k]
     return u[order], s[order]

@@ -3,7 +3,8 @@ cell, near-atom list entry, clash-pair pool entry and decision record index
 of the docking kernels, and every ranking scratch slot, is checked, and a
 failure turns into an error of the call.  The checked library docks the
 parity cases (best restart, ranking, rigid moves, heavy-tailed size classes
-at every width and with ranking, several pockets, flattening) without a
+at every width and with ranking, several pockets, flattening, the
+allocation-free entry point) without a
 failure and with results equal to the product build's bit for bit."""
 import os
 import subprocess
@@ -55,6 +56,19 @@ for j, r in enumerate(multi):
 f = ctx.flatten(synth.config_ligands(2, 300), 3)
 for k in ("xyz", "tors", "dsum"):
     out["flatten/" + k] = f[k]
+# the allocation-free entry point collects its own bounds-check record
+import torch
+L, A, R = b1.L, int(b1.atom_off[-1]), int(b1.rot_off[-1])
+dev = lg.device_batch_arrays(b1)
+r, outs = lg.alloc_result(L, A, R, prm1.restarts, prm1.passes, device=True, pose=True, tors=True,
+                          restart_tors=True)
+st = torch.cuda.current_stream()
+lg.lg_dock_batch_noalloc(ctx.h, pid, lg.make_batch_struct(dev, L),
+                         lg.make_params(prm1.restarts, prm1.passes, prm1.seed, prm1.d_clash), r, st.cuda_stream)
+st.synchronize()
+for k, v in outs.items():
+    if v is not None:
+        out["noalloc/" + k] = v.cpu().numpy()
 ctx.close()
 np.savez(sys.argv[2], **out)
 """

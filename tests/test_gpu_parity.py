@@ -126,10 +126,11 @@ def test_decision_ranks_match_oracle_and_both_forms(ctx, cfg1, pocket1, cfg2_poc
             assert np.array_equal(plain[k], a[k]), k
     rep = oracle.dock(pocket, sub, params, replay=a["restart_tors"], trace=True)
     exact, lo, hi = _oracle_rank_bounds(rep["trace_s"], a["restart_tors"])
-    g = a["decision_rank"].astype(int)
+    g = a["decision_rank"].astype(int) & 0x7F  # bit 7 marks a skipped decision
     assert np.all((g >= lo) & (g <= hi))
     assert np.mean(g == exact) > 0.99
     assert g.min() >= 1 and g.max() <= 36 and g.mean() > 1.0
+    _check_skip_marks(sub, params, a)
     # throughput ligands, whose convergence stops skip decisions: the skipped
     # ones repeat the bond's previous rank, as the oracle's full sweep finds
     pid = ctx.load_pocket(cfg2_pocket)
@@ -139,9 +140,35 @@ def test_decision_ranks_match_oracle_and_both_forms(ctx, cfg1, pocket1, cfg2_poc
     ctx.unload_pocket(pid)
     rep = oracle.dock(cfg2_pocket, lig2, prm2, replay=d["restart_tors"], trace=True)
     exact, lo, hi = _oracle_rank_bounds(rep["trace_s"], d["restart_tors"])
-    g = d["decision_rank"].astype(int)
+    g = d["decision_rank"].astype(int) & 0x7F
     assert np.all((g >= lo) & (g <= hi))
     assert np.mean(g == exact) > 0.99
+    assert _check_skip_marks(lig2, prm2, d) > 0
+
+
+def _check_skip_marks(batch, params, res):
+    """Bit 7 of decision_rank marks exactly the decisions after a restart's
+    exact stop: R decisions in a row without a move, every later decision
+    repeating one of them.  Returns how many are marked."""
+    S, P = params.restarts, params.passes
+    dr = res["decision_rank"].astype(int)
+    tors = res["restart_tors"].astype(int)
+    marked = 0
+    for l in range(batch.L):
+        r0, R = int(batch.rot_off[l]), int(batch.rot_off[l + 1] - batch.rot_off[l])
+        for r in range(S):
+            d0 = S * P * r0 + r * P * R
+            zrun, stopped = 0, False
+            for q in range(P * R):
+                want = stopped
+                assert bool(dr[d0 + q] & 0x80) == want, (l, r, q)
+                marked += want
+                if not stopped:
+                    zrun = 0 if tors[d0 + q] else zrun + 1
+                    stopped = zrun >= R
+                else:
+                    assert tors[d0 + q] == 0
+    return marked
 
 
 def test_host_and_device_io_agree_and_runs_repeat(ctx, cfg1, pocket1):

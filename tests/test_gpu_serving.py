@@ -225,3 +225,57 @@ def test_requests_for_different_pockets_share_launches():
                 assert np.array_equal(got[k], alone[k][:len(got[k])]), k
     finally:
         ctx.close()
+
+
+def test_admission_holds_back_a_ranked_request_while_a_slot_is_busy():
+    # A ranked request needs pose slots in device scratch (12 B per atom,
+    # restart and slot) on top of its inputs and outputs.  With free memory
+    # minus the reserve below that need, it waits in the queue while another
+    # batch runs, and is admitted once the device is idle.
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import dataclasses
+    ctx = lg.Context(0)
+    try:
+        ctx.set_option("serve_max_inflight", 2)
+        ctx.set_option("serve_mem_reserve_mb", 0)
+        pid = ctx.load_pocket(synth.config_pocket(2))
+        lig = synth.config_ligands(2, 62_000)
+        busy_prm = dataclasses.replace(synth.config_params(2), restarts=64)
+        busy = _request(lig.subset(range(60_000)), busy_prm)
+        ranked_prm = dataclasses.replace(synth.config_params(2), restarts=256, cluster_rmsd=3.0, rescore_top=30)
+        sub = lig.subset(range(60_000, 62_000))
+        arrs = lg.host_batch_arrays(sub)
+        b = lg.make_batch_struct(arrs, sub.L)
+        p = lg.make_params(ranked_prm.restarts, ranked_prm.passes, ranked_prm.seed, ranked_prm.d_clash,
+                           cluster_rmsd=ranked_prm.cluster_rmsd, rescore_top=ranked_prm.rescore_top)
+        r, outs = lg.alloc_result(sub.L, int(sub.atom_off[-1]), int(sub.rot_off[-1]), ranked_prm.restarts,
+                                  ranked_prm.passes, ranking=True)
+        # pose slots of the ranked request: about 2,000 ligands x 256 restarts x
+        # 60 atoms x 12 B = 370 MB; its inputs and outputs alone need ~10 MB
+        t_busy = lg.lg_stream_submit(ctx.h, pid, busy["b"], busy["p"], busy["r"])
+        while lg.lg_stream_poll(ctx.h, t_busy)[0] == lg.LG_REQ_QUEUED:
+            time.sleep(1e-4)
+        free, _ = torch.cuda.mem_get_info()
+        ctx.set_option("serve_mem_reserve_mb", max(0, free // (1 << 20) - 100))
+        t_rank = lg.lg_stream_submit(ctx.h, pid, b, p, r)
+        held = 0
+        while True:
+            s_rank = lg.lg_stream_poll(ctx.h, t_rank)[0]  # the ranked request first: see below
+            s_busy = lg.lg_stream_poll(ctx.h, t_busy)[0]
+            # admitted only once the busy batch is done (its state is set
+            # before the idle device admits the next batch)
+            assert not (s_rank >= lg.LG_REQ_RUNNING and s_busy < lg.LG_REQ_DONE)
+            held += s_rank == lg.LG_REQ_QUEUED and s_busy == lg.LG_REQ_RUNNING
+            if s_busy >= lg.LG_REQ_DONE:
+                break
+            time.sleep(2e-4)
+        assert held > 0
+        assert lg.lg_stream_wait(ctx.h, t_busy, 120000) == lg.LG_OK
+        assert lg.lg_stream_wait(ctx.h, t_rank, 120000) == lg.LG_OK
+        d = ctx.dock(pid, sub, ranked_prm)
+        for k in ("score", "best_restart", "status"):
+            assert np.array_equal(outs[k][:sub.L], d[k][:sub.L]), k
+    finally:
+        ctx.close()

@@ -56,6 +56,47 @@ def test_partition_balances_and_covers():
     assert slab_loads.max() / slab_loads.mean() > loads.max() / loads.mean()
 
 
+# uids above 2^53 (not exact in FP64) and at or above 2^63 (negative as int64)
+_BIG_UIDS = np.array([2 ** 53 + 1, 2 ** 53 + 3, 2 ** 63 - 1, 2 ** 63, 2 ** 63 + 5, 2 ** 64 - 1, 7, 2 ** 53 + 2],
+                     np.uint64)
+_BIG_SCORES = np.array([-3.0, -3.0, 1.5, -3.0, 0.25, -3.0, np.nan, 1.5])
+
+
+def _gather_big(rank, world, port, q):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        mine = np.arange(rank, len(_BIG_UIDS), world)
+        top = shard.gather_ranking(_BIG_UIDS[mine], _BIG_SCORES[mine], k=6)
+        if rank == 0:
+            q.put(([int(v) for v in top[0]], top[1].tolist(), str(top[0].dtype)))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_gather_keeps_full_64_bit_uids():
+    # the gathered uids are the exact uint64 values, ordered by score, then uid
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_gather_big, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    uids, scores, dtype = q.get(timeout=300)
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    assert dtype == "uint64"
+    ok = np.isfinite(_BIG_SCORES)
+    want = sorted(zip(_BIG_SCORES[ok].tolist(), [int(u) for u in _BIG_UIDS[ok]]))[:6]
+    assert uids == [u for _, u in want]
+    assert scores == [s for s, _ in want]
+    assert uids[:4] == [2 ** 53 + 1, 2 ** 53 + 3, 2 ** 63, 2 ** 64 - 1]
+
+
 def test_ligand_flops_matches_moving_atoms():
     import oracle
     b = synth.config_ligands(2, 50)
@@ -84,8 +125,8 @@ def test_two_rank_gather_equals_single_process():
     batch = synth.config_ligands(1, 96)
     params = synth.config_params(1)
     out = oracle.dock(pocket, batch, params)
-    order = np.lexsort((batch.uid.astype(np.int64), out["best_E"]))[:20]
-    assert got[0] == batch.uid[order].astype(np.int64).tolist()
+    order = np.lexsort((batch.uid, out["best_E"]))[:20]
+    assert got[0] == batch.uid[order].tolist()
     assert np.allclose(got[1], out["best_E"][order], rtol=0, atol=0)
 
 
@@ -202,3 +243,47 @@ def test_pending_edge_cases():
     assert len(shard.pending(uid, uid)) == 0
     assert np.array_equal(shard.pending(uid, np.array([9, 7], np.uint64)), np.array([0, 1, 3]))
     assert len(shard.pending(np.zeros(0, np.uint64), uid)) == 0
+
+
+def test_needed_flops_credit_only_decisions_before_the_exact_stop():
+    # The oracle sweeps every decision.  After R decisions in a row without a
+    # move, the state repeats a full round of bonds, so every later decision
+    # of the oracle is step 0 too: the stop the kernels take is exact.  The
+    # needed count credits the decisions up to the stop (j* from the
+    # oracle's traces), and with no decision marked it equals the ranked count.
+    import oracle
+    pocket = synth.config_pocket(1)
+    batch = synth.config_ligands(1, 24)
+    params = synth.config_params(1)
+    S, P = params.restarts, params.passes
+    out = oracle.dock(pocket, batch, params, trace=True)
+    s = out["trace_s"].reshape(-1, 36)
+    ch = out["own"].astype(int)
+    sc = s[np.arange(len(ch)), ch]
+    jstar = 1 + ((s > sc[:, None]) | ((s == sc[:, None]) & (np.arange(36)[None, :] < ch[:, None]))).sum(1)
+    coded = jstar.copy()
+    m, pairs, _, _ = shard._bond_counts(batch)
+    n_skipped = 0
+    for l in range(batch.L):
+        N = int(batch.atom_off[l + 1] - batch.atom_off[l])
+        r0, R = int(batch.rot_off[l]), int(batch.rot_off[l + 1] - batch.rot_off[l])
+        want = S * (21 * N + 40 + 64 * N)
+        for r in range(S):
+            zrun, stopped = 0, False
+            for q in range(P * R):
+                d = S * P * r0 + r * P * R + q
+                if stopped:
+                    assert ch[d] == 0  # the oracle repeats step 0 after the stop
+                    coded[d] |= 0x80
+                    n_skipped += 1
+                    continue
+                want += 36 * 51 * m[r0 + q % R] + 8 * pairs[r0 + q % R] * jstar[d]
+                zrun = 0 if ch[d] else zrun + 1
+                stopped = zrun >= R
+        got = shard.ligand_flops_needed(batch, S, P, coded)[l]
+        assert abs(got - want) <= 1e-9 * want, l
+    assert n_skipped > 0
+    ranked = shard.ligand_flops_ranked(batch, S, P, jstar)
+    assert np.allclose(shard.ligand_flops_needed(batch, S, P, jstar), ranked, rtol=1e-12)
+    # the marked ranks keep their j* for the ranked count
+    assert np.allclose(shard.ligand_flops_ranked(batch, S, P, coded), ranked, rtol=1e-12)
