@@ -211,12 +211,15 @@ def contiguous_request(pool, start, size):
     return arrs, size, a1 - a0, r1 - r0
 
 
-def serving_leg(ctx, pids, pool, params, rate_evals, load, duration_s, seed=5, max_size=4096):
+def serving_leg(ctx, pids, pool, params, rate_evals, load, duration_s, seed=5, max_size=4096, mode="device_loop"):
     """Poisson arrivals of requests of floor(exp(U(0, ln max_size))) ligands at
     `load` times `rate_evals` ligands/s for `duration_s` seconds, each aimed at
     a pocket drawn uniformly from `pids`, submitted to the library's serving
-    loop; latency is submit-to-done as the library measures it."""
+    loop (mode "device_loop": the device-resident loop; "host_merge": the host
+    worker's merged launches); latency is submit-to-done as the library
+    measures it."""
     from paper_2110_11644_gb300 import lg
+    ctx.set_option("serve_device_loop", 1 if mode == "device_loop" else 0)
     rng = np.random.default_rng(seed)
     target = rng.integers(0, len(pids), size=1 << 20)
     mean_size = (max_size - 1) / np.log(max_size)
@@ -258,7 +261,10 @@ def serving_leg(ctx, pids, pool, params, rate_evals, load, duration_s, seed=5, m
     wall = time.perf_counter() - t0
     lat = np.array([x for x, _ in done_lat])
     ligs = int(sum(s for _, s in done_lat))
-    return {"offered_load": load, "offered_evals_per_s": load * rate_evals, "duration_s": round(wall, 2),
+    st = ctx.stats()
+    return {"mode": mode, "offered_load": load, "offered_evals_per_s": load * rate_evals,
+            "load_basis": "fraction of this serving path's measured peak (serving_peak)", "duration_s": round(wall, 2),
+            "loop_launches": int(st.serve_loop_launches) if mode == "device_loop" else None,
             "requests": len(lat), "ligands": ligs, "sustained_evals_per_s": ligs / wall,
             "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
             "pockets": len(pids),
@@ -515,6 +521,8 @@ def summary_of(line) -> dict:
     if line.get("plain"):
         out["plain"] = r3(line["plain"]["value"])
         out["batched_over_plain"] = r3(line["plain"]["batched_over_plain"])
+    if line.get("serving_peak"):
+        out["serve_peak"] = {k: r3(v) for k, v in line["serving_peak"].items()}
     for leg in line.get("serving") or []:
         key = "serve_%d" % round(100 * leg["offered_load"]) + ("" if leg.get("mode") == "device_loop" else "_host")
         out[key] = [r3(leg["p50_latency_s"] * 1e3), r3(leg["p99_latency_s"] * 1e3), r3(leg["sustained_evals_per_s"])]
@@ -769,12 +777,25 @@ def main():
 
         # serving: requests aimed at a random pocket of the 15-pocket set when it
         # is loaded, else at the throughput pocket
-        serving = None
+        serving, serving_peak = None, None
         if args.serve_seconds > 0:
-            # warm-up (not reported): the serving slots grow their buffers once
-            serving_leg(ctx, mp_pids or [pid], batch, params, value / world, 0.9, 1.0, seed=4)
-            serving = [serving_leg(ctx, mp_pids or [pid], batch, params, value / world, float(ld), args.serve_seconds)
+            # Each serving path's peak: its sustained rate under an offered load
+            # above the batched rate (the queue never empties); the offered
+            # loads are fractions of that peak.  Warm-up first (not reported).
+            sp = mp_pids or [pid]
+            ps = max(3.0, args.serve_seconds / 10)
+            serving_peak = {"batched_evals_per_s": value / world}
+            for mode in ("device_loop", "host_merge"):
+                serving_leg(ctx, sp, batch, params, value / world, 0.9, 1.0, seed=4, mode=mode)
+                serving_peak[mode] = serving_leg(ctx, sp, batch, params, value / world, 1.5, ps, seed=6,
+                                                 mode=mode)["sustained_evals_per_s"]
+            serving = [serving_leg(ctx, sp, batch, params, serving_peak["device_loop"], float(ld), args.serve_seconds)
                        for ld in args.serve_loads.split(",")]
+            # the host worker's merged launches at the highest load, for comparison
+            hs = max(1.0, args.serve_seconds / 6)
+            serving.append(serving_leg(ctx, sp, batch, params, serving_peak["host_merge"],
+                                       max(float(x) for x in args.serve_loads.split(",")), hs, mode="host_merge"))
+            ctx.set_option("serve_device_loop", 1)
         for q in mp_pids:
             ctx.unload_pocket(q)
 
@@ -787,7 +808,8 @@ def main():
                            "warps_per_cta": st.warps_per_cta, "ctas_per_sm": st.ctas_per_sm, "grid": st.grid},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "clocks": clk, "gpu_launches": launches_per_step * args.steps, "plain": plain,
-                "serving": serving, "multi_pocket": multi, "flatten": flatten, "heavy_tailed": heavy,
+                "serving": serving, "serving_peak": serving_peak, "multi_pocket": multi, "flatten": flatten,
+                "heavy_tailed": heavy,
                 "small_batch": small, "stages": stages}
         line["summary"] = summary_of(line)  # last key: the headline figures of every leg, short
         print(json.dumps(line), flush=True)

@@ -103,7 +103,13 @@ typedef struct {
 /* Copy a pocket (host pointers) into device memory owned by the context and
  * return its id.  The caller's buffers may be freed on return.  Requires
  * 2 <= n <= 512, h > 0, n_pp >= 1 and every pocket point inside the grid.
- * Errors: LG_EINVAL, LG_ENOMEM, LG_ECUDA. */
+ * L2 residency (the paper keeps the site in texture memory, Sec. 3.2): the
+ * call sizes the context's persisting L2 set-aside for the largest loaded
+ * pocket's overlap cells (32 bytes per node; within the device's limit; a
+ * context setting that ends with the context), and every later docking
+ * launch against one pocket carries an access-policy window that marks that
+ * pocket's cells persisting (option "l2_window").  The window never changes a
+ * result.  Errors: LG_EINVAL, LG_ENOMEM, LG_ECUDA. */
 int lg_pocket_load(lg_ctx *ctx, const lg_pocket_desc *d, int32_t *pocket_id);
 
 /* Free a pocket.  The caller must not have docking in flight on it.
@@ -392,6 +398,23 @@ int lg_score_poses(lg_ctx *ctx, int32_t pocket_id, const lg_pose_batch *batch, d
  * DONE or FAILED.  Requests are admitted to the device when enough free
  * device memory and in-flight slots exist, and their ligands share the device
  * with the other requests in flight.  Never blocks on the GPU.
+ *
+ * By default (option "serve_device_loop" = 1) the requests are served by a
+ * device-resident loop: one persistent launch takes ligands, one per CTA, in
+ * admission order from a ring of request descriptors that the host fills with
+ * copies, docks each against its request's own pocket and writes the results
+ * straight into the request's pinned output image, and the CTA that finishes
+ * a request's last ligand raises the request's completion flag in mapped host
+ * memory.  A request that arrives while others run is docked as soon as CTAs
+ * free up.  The loop serves one kind of request at a time (restarts, passes,
+ * seed, clash distance, ranking and rigid settings, optional outputs, atom
+ * and torsion maxima up to 64/128 and 16/32): a request of another kind waits
+ * until the requests in flight finish, and the loop is then set up for it.
+ * Its CTAs leave after "serve_loop_idle_ms" without a ligand to claim, so an
+ * idle loop ends by itself; lg_stats.serve_loop_status says how the last
+ * launch ended.  With "serve_device_loop" = 0 a host worker instead merges
+ * queued requests into ordinary batched launches on up to
+ * "serve_max_inflight" streams.
  * Errors: LG_EINVAL, LG_ENOPOCKET, LG_EAGAIN (host queue full), LG_ENOMEM. */
 int lg_stream_submit(lg_ctx *ctx, int32_t pocket_id, const lg_ligand_batch *batch, const lg_dock_params *params,
                      lg_dock_result *out, uint64_t *ticket);
@@ -452,7 +475,16 @@ int lg_get_stats(lg_ctx *ctx, lg_stats *out);
  * pockets into one launch, each ligand docked against its own request's
  * pocket), "multi_order" (lg_dock_multi's visiting order: 0 =
  * pocket-major, the default; 1 = ligand-major, a CTA docks one ligand against
- * every pocket in turn).  Errors: LG_EINVAL. */
+ * every pocket in turn), "l2_window" (0/1, default 1: every docking launch
+ * against one pocket marks that pocket's overlap cells persisting in the L2
+ * set-aside that lg_pocket_load reserves), "serve_device_loop" (0/1, default
+ * 1: the device-resident loop serves the requests, see lg_stream_submit;
+ * changing it stops the serving worker -- requests on the device finish,
+ * queued ones fail -- and the next submission starts one of the other kind),
+ * "serve_loop_idle_ms" (1..60000, default
+ * 100: how long a CTA of the loop waits for a ligand before it leaves; the
+ * first CTA to leave ends the launch as a whole).
+ * Errors: LG_EINVAL. */
 int lg_set_option(lg_ctx *ctx, const char *key, int64_t value);
 
 /* The autotuner's cached choices as JSON text, to carry them to another

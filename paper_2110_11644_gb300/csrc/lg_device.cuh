@@ -90,6 +90,7 @@ enum CheckSite {
     kChkDecision,      // decision record of a restart slot
     kChkRankSlot,      // ranking scratch slot
     kChkAtom,          // atom index of a moving or fixed atom
+    kChkRing,          // request-descriptor slot of the serving loop
 };
 #ifdef LG_CHECKS
 __device__ int lg_check_rec[4];  // site, index, bound of the first failure; failures

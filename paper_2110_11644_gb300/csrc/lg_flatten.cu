@@ -9,19 +9,6 @@
 
 using namespace lg;
 
-namespace {
-
-struct Carve {
-    size_t off = 0;
-    size_t take(size_t bytes) {
-        size_t o = off;
-        off = (off + bytes + 255) & ~(size_t)255;
-        return o;
-    }
-};
-
-}  // namespace
-
 extern "C" int lg_flatten_batch(lg_ctx *c, const lg_ligand_batch *b, const lg_flatten_params *p, lg_flatten_result *o,
                                 void *stream) {
     if (!c || !b || !p || !o) return fail(LG_EINVAL, "null argument");

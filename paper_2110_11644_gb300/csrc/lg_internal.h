@@ -114,18 +114,21 @@ constexpr int kPoolCap = LG_RT_POOL;  // flagged clash pairs buffered per warp (
 // Per-warp shared memory of a restart-tiled warp.
 struct LayoutRT {
     int o_axis, o_X, o_pool, o_mask, o_near, o_best, o_tcur, o_tbest, warp_bytes;
+    int near_stride;  // bytes between the restart slots' near lists: an odd number of 4-byte words, so
+                      // the 8 slots' entries fall in 8 different banks
 };
 
 __host__ __device__ inline LayoutRT make_layout_rt(int nmax, int rmax, int P, int want_pose) {
     LayoutRT L;
     nmax = (nmax + 3) & ~3;
     if (rmax < 1) rmax = 1;
+    L.near_stride = ((nmax / 4) & 1) ? nmax : nmax + 4;
     int w = 0;
     L.o_axis = w;  w = lg_align16(w + 16 * rmax * kTile);            // float4 [rmax][8]
     L.o_X = w;     w = lg_align16(w + 12 * nmax * kTile);            // float [3][nmax][8]
     L.o_pool = w;  w = lg_align16(w + 16 * kPoolCap);                // float4 (C, A2, B2, restart slot)
     L.o_mask = w;  w = lg_align16(w + 4 * 32);                       // uint32 clash bits per lane
-    L.o_near = w;  w = lg_align16(w + nmax * kTile);                 // uint8 [8][nmax] near fixed atoms
+    L.o_near = w;  w = lg_align16(w + L.near_stride * kTile);        // uint8 [8][near_stride] near fixed atoms
     L.o_best = w;  w = lg_align16(w + (want_pose ? 12 * nmax : 0));  // float [3][nmax]
     L.o_tcur = w;  w = lg_align16(w + P * rmax * kTile);             // uint8 [P*rmax][8]
     L.o_tbest = w; w = lg_align16(w + P * rmax);                     // uint8 [P*rmax]
@@ -149,6 +152,7 @@ struct Scratch {
     float *rk_cen;         // [slots][S][3] its centroid (centred grid units)
     int rk_slots;          // ranking slots
     size_t rk_floats;      // capacity of rk_pose (floats)
+    int per_cta;           // 1: centroid and rot_end hold one entry per CTA (the serving loop), not per ligand
 };
 
 // Ranking step: row p of the "within the RMSD threshold" bit matrix holds
@@ -247,6 +251,63 @@ struct MultiDev {
     const int32_t *lig_pocket;
 };
 
+// Device-resident serving loop (k_serve_loop): one persistent launch docks
+// the ligands of admitted requests.  Each request's ligands are copied into a
+// ring arena of CSR arrays in device memory (offsets global to the arena, one
+// spare entry after each request), and its outputs land in an arena of mapped
+// pinned host memory with the same indexing, so the launch's arguments name
+// the arenas once and every ligand is a slot of them; pockets come from a
+// table in the launch's arguments.  Work items are ligands numbered in
+// admission order; a ring of request descriptors in device memory maps an
+// item to its arena slot and pocket.  The host publishes items by raising
+// `tail` (copies on a feed stream, after the data and the descriptor), a CTA
+// claims the next item by fetch-and-add on `next` (one atomic per ligand,
+// whatever the contention) and docks it once it is published; the CTA that
+// finishes a request's last ligand raises the request's completion flag in
+// mapped host memory.  A CTA that leaves while holding an unpublished item
+// records it in held[CTA], and the same CTA of the next launch docks it
+// first.  Every wait of the kernel is bounded (see k_serve_loop).
+constexpr uint64_t kDescBusy = ~0ull;  // seq of a descriptor being rewritten
+constexpr int kLoopPockets = LG_MAX_MULTI_POCKETS;
+
+struct LoopDesc {       // one admitted request; `seq` first (seqlock: kDescBusy while rewritten)
+    uint64_t seq;
+    uint64_t first;     // global index of its first ligand
+    int32_t L;          // its ligands
+    int32_t slot;       // arena slot of its first ligand
+    int32_t pocket;     // its pocket in the launch's table
+    int32_t pad;
+};
+
+struct LoopCtl {        // device memory
+    // written by the host (copies on the feed stream)
+    uint64_t tail;      // ligands published
+    uint64_t head_seq;  // descriptors before it are complete
+    uint32_t stop;      // leave the loop after the current ligand
+    uint32_t pad0;
+    // written by the kernel
+    uint64_t next;      // next ligand to claim
+    uint32_t live;      // CTAs inside the loop
+    uint32_t idle_exits;  // CTAs that left after the idle limit
+    uint32_t bad;       // a claimed ligand had no descriptor
+    uint32_t closing;   // a CTA reached the idle limit: the others leave instead of claiming
+    int32_t status;     // how the launch ended: LG_OK (stopped), LG_ETIMEOUT (idle limit), LG_EINVAL (bad item)
+};
+
+struct LoopArgs {
+    LoopCtl *ctl;
+    const LoopDesc *desc;    // [ring]
+    uint32_t *done;          // [ring] ligands finished per descriptor (reset by the last)
+    uint64_t *flags;         // [ring] mapped host memory: seq + 1 once the descriptor is complete
+    long long *held;         // [grid] an item the CTA claimed but left without docking (-1: none)
+    int ring;
+    uint64_t idle_ns;        // idle limit of a CTA (no ligand to claim)
+    uint64_t first_seq;      // descriptors before it were complete at launch
+    int np;                  // pockets in the table
+    PocketDev pk[kLoopPockets];
+    float dc2g[kLoopPockets], thr2g[kLoopPockets], rigid_shift_g[kLoopPockets];  // per pocket, grid units
+};
+
 // Byte size of the scratch of a launch, and its carving.
 size_t scratch_bytes(int L, int rmax, int rank_slots = 0, int S = 0, int P = 0, int nmax = 0);
 Scratch carve_scratch(void *base, int L, int rmax, int rank_slots = 0, int S = 0, int P = 0, int nmax = 0);
@@ -262,6 +323,8 @@ cudaError_t launch_diag_philox(int n, const uint32_t *ctr, const uint32_t *key, 
                                cudaStream_t s);
 cudaError_t launch_dock_multi(const DockArgs &a, const MultiDev &m, int grid, int smem, cudaStream_t s);
 cudaError_t launch_flatten(const FlatArgs &f, int L, cudaStream_t s);
+cudaError_t launch_serve_loop(const DockArgs &a, const LoopArgs &la, int grid, int smem, cudaStream_t s);
+cudaError_t loop_kernel_attributes(int W, int smem, int *ctas_per_sm, bool ranking, bool rigid);
 int checks_collect(cudaStream_t s, int rec[4]);  // bounds-check record of a debug build (0 otherwise)
 cudaError_t dock_kernel_attributes(int W, int smem, int *ctas_per_sm, bool ranking, bool rigid, bool trace);
 cudaError_t multi_kernel_attributes(int W, int smem, int *ctas_per_sm, bool ranking, bool rigid);

@@ -103,13 +103,30 @@ __device__ __forceinline__ CtaView cta_view(char *sm, const Layout &L) {
     return v;
 }
 
+// Where a docked ligand comes from, with the constants that depend on its
+// pocket's grid spacing: the launch's batch and constants for the batched
+// kernels, the request's for the serving loop.
+struct LigSrc {
+    BatchDev batch;
+    float dc2g, thr2g, rigid_shift_g;  // d_clash^2, cluster RMSD^2, rigid shift in grid units
+};
+
+__device__ __forceinline__ LigSrc launch_src(const DockArgs &A) {
+    LigSrc q;
+    q.batch = A.batch;
+    q.dc2g = A.dc2g;
+    q.thr2g = A.thr2g;
+    q.rigid_shift_g = A.rigid_shift_g;
+    return q;
+}
+
 // Stage ligand l: centroid-relative coordinates in grid units (FP64
 // difference), parents, per-atom (type weight, charge), torsional children,
 // subtree ends and input bond vectors in grid units.
-__device__ __forceinline__ void stage_ligand(const DockArgs &A, const PocketDev &Pk, const CtaView &cv, int l, int a0,
-                                             int N, int r0, int R) {
-    const BatchDev &B = A.batch;
-    const double cx = A.scr.centroid[3 * l], cy = A.scr.centroid[3 * l + 1], cz = A.scr.centroid[3 * l + 2];
+__device__ __forceinline__ void stage_ligand(const DockArgs &A, const BatchDev &B, const PocketDev &Pk,
+                                             const CtaView &cv, int l, int a0, int N, int r0, int R) {
+    const size_t li = A.scr.per_cta ? (size_t)blockIdx.x : (size_t)l;  // the preparation's entry
+    const double cx = A.scr.centroid[3 * li], cy = A.scr.centroid[3 * li + 1], cz = A.scr.centroid[3 * li + 2];
     const double ih = (double)Pk.inv_h;
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
         cv.d0x[i] = (float)(((double)B.x[a0 + i] - cx) * ih);
@@ -121,7 +138,7 @@ __device__ __forceinline__ void stage_ligand(const DockArgs &A, const PocketDev 
     for (int k = threadIdx.x; k < R; k += blockDim.x) {
         const int b = B.rot_child[r0 + k], p = B.parent[a0 + b];
         cv.rch[k] = b;
-        cv.rend[k] = A.scr.rot_end[(size_t)l * A.rmax_lim + k];
+        cv.rend[k] = A.scr.rot_end[li * A.rmax_lim + k];
         cv.dv[k] = make_float4((B.x[a0 + b] - B.x[a0 + p]) * Pk.inv_h, (B.y[a0 + b] - B.y[a0 + p]) * Pk.inv_h,
                                (B.z[a0 + b] - B.z[a0 + p]) * Pk.inv_h, 0.0f);
     }
@@ -241,8 +258,8 @@ __device__ __forceinline__ int rank_slot(const DockArgs &A, int slot) {
 // centroids are farther apart than the threshold (with a 1e-4 relative margin
 // over the FP32 sum's rounding) cannot be, since the mean squared distance is
 // at least the squared distance of the means, and skip the sum.
-__device__ void rank_finish(const DockArgs &A, const PocketDev &Pk, const OutDev &O, int l, int slot, int a0, int N, int r0,
-                            int PR, char *rbase) {
+__device__ void rank_finish(const DockArgs &A, const PocketDev &Pk, const OutDev &O, float thr2g, int l, int slot, int a0,
+                            int N, int r0, int PR, char *rbase) {
     const int S = A.S, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, W = blockDim.x >> 5;
     char *q = rbase;
     double *sG = (double *)q;
@@ -260,7 +277,7 @@ __device__ void rank_finish(const DockArgs &A, const PocketDev &Pk, const OutDev
     int *bestv = (int *)q;
     const float *pose0 = A.scr.rk_pose + rk_pose_off(A, slot, 0);
     const size_t pstride = (size_t)A.ly.nmax * 3;
-    const bool cluster = A.thr2g > 0.0f;
+    const bool cluster = thr2g > 0.0f;
 
     // 1. geometric scores and centroids, computed when each restart finished
     for (int r = tid; r < S; r += blockDim.x) {
@@ -283,11 +300,11 @@ __device__ void rank_finish(const DockArgs &A, const PocketDev &Pk, const OutDev
     }
     __syncthreads();
     // 3a. pairs within the threshold: bit q of row p for positions q < p
-    const float lim = A.thr2g * (float)N;
+    const float lim = thr2g * (float)N;
     if (cluster) {
         // the 1e-3 margin covers the FP32 rounding of the centroids (at most
         // ~1e-4 of the squared threshold for 100 atoms in the box)
-        const float cut = A.thr2g * (1.0f + 1e-3f);
+        const float cut = thr2g * (1.0f + 1e-3f);
         for (int p = warp; p < S; p += W) {
             const int rp = ord[p];
             const float *x = pose0 + pstride * rp;
@@ -625,7 +642,7 @@ __global__ void __launch_bounds__(1024) k_dock_plain(const __grid_constant__ Doc
     const int a0 = B.atom_off[l], N = B.atom_off[l + 1] - a0;
     const int r0 = B.rot_off[l], R = B.rot_off[l + 1] - r0;
     const int S = A.S, P = A.P, PR = P * R;
-    stage_ligand(A, Pk, cv, l, a0, N, r0, R);
+    stage_ligand(A, B, Pk, cv, l, a0, N, r0, R);
     __syncthreads();
 
     const float cl = c_cos[lane], sl = c_sin[lane];
@@ -741,7 +758,7 @@ __global__ void __launch_bounds__(1024) k_dock_plain(const __grid_constant__ Doc
     }
     if (A.ranking) {
         __syncthreads();
-        rank_finish(A, Pk, A.out, l, slot, a0, N, r0, PR, sm + Ly.cta_bytes);
+        rank_finish(A, Pk, A.out, A.thr2g, l, slot, a0, N, r0, PR, sm + Ly.cta_bytes);
         return;
     }
     if (lane == 0) {
@@ -764,7 +781,7 @@ struct RtView {
     float *Xx, *Xy, *Xz;   // [nmax][8]
     float4 *pool;          // [kPoolCap] flagged clash pairs (C, A2, B2, restart slot)
     unsigned *mask;        // [32] clash bits of each lane's steps
-    uint8_t *near;         // [8][nmax] fixed atoms that can come within d_clash
+    uint8_t *near;         // [8][nstride] fixed atoms that can come within d_clash
     int nstride;
     float *Bx, *By, *Bz;   // [nmax] best pose of the warp
     uint8_t *tcur;         // [P*R][8]
@@ -781,7 +798,7 @@ __device__ __forceinline__ RtView rt_view(char *sm, const Layout &L, const Layou
     v.pool = (float4 *)(b + T.o_pool);
     v.mask = (unsigned *)(b + T.o_mask);
     v.near = (uint8_t *)(b + T.o_near);
-    v.nstride = L.nmax;
+    v.nstride = T.near_stride;
     v.Bx = (float *)(b + T.o_best);
     v.By = v.Bx + L.nmax;
     v.Bz = v.By + L.nmax;
@@ -814,8 +831,9 @@ __device__ __forceinline__ void flush_pool(const RtView &v, int rs, int g, int &
 // slot rs, steps g, g+4, ..., g+32 (cosines cs[], sines sn[]) -- the 4 lanes
 // of a restart score neighbouring steps in the same instruction.  Returns the
 // step chosen for the lane's restart.
-__device__ __forceinline__ int sweep_bond_rt(const DockArgs &A, const GridK &G, const CtaView &cv, const RtView &v, int N, int R, int k,
-                             int rs, int g, bool valid, const float *cs, const float *sn, bool want_rank, int &jr) {
+__device__ __forceinline__ int sweep_bond_rt(float dc2g, const GridK &G, const CtaView &cv, const RtView &v, int N, int R,
+                                             int k, int rs, int g, bool valid, const float *cs, const float *sn,
+                                             bool want_rank, int &jr) {
     const int b = cv.rch[k], a = cv.par[b], e = cv.rend[k];
     const int m = e - b - 1;
     jr = 1;
@@ -823,7 +841,7 @@ __device__ __forceinline__ int sweep_bond_rt(const DockArgs &A, const GridK &G, 
 
     const float xbx = v.Xx[b * kTile + rs], xby = v.Xy[b * kTile + rs], xbz = v.Xz[b * kTile + rs];
     const float3 u = unit_axis(v.axis[k * kTile + rs]);
-    const float c0 = 0.5f * G.gmax, dc2 = A.dc2g;  // (n - 1) / 2, exact
+    const float c0 = 0.5f * G.gmax, dc2 = dc2g;  // (n - 1) / 2, exact
     const int nF = N - (e - b);
     const int lane = kLanesPerRestart * rs + g;
     const unsigned gmask = 0xFu << (kLanesPerRestart * rs), below = (1u << lane) - 1u;
@@ -994,9 +1012,10 @@ __device__ __forceinline__ int sweep_bond_rt(const DockArgs &A, const GridK &G, 
 // FP32 sums s_g; a candidate's score is (s0 + s1) + (s2 + s3) of the FP32
 // overlap lookups of the atoms at their moved positions; the best (highest
 // score, lowest candidate) moves the atoms and turns the bond axes.
-__device__ __forceinline__ bool rigid_moves_rt(const DockArgs &A, const GridK &Go, const OutDev &O, const RtView &v,
+__device__ __forceinline__ bool rigid_moves_rt(const DockArgs &A, float rigid_shift_g, const GridK &Go, const OutDev &O,
+                                               const RtView &v,
                                                int l, int r, int ps, int N, int R, int rs, int g, bool valid) {
-    const float c0 = 0.5f * Go.gmax, dg = A.rigid_shift_g, ca = c_cos[1], sa = c_sin[1];
+    const float c0 = 0.5f * Go.gmax, dg = rigid_shift_g, ca = c_cos[1], sa = c_sin[1];
     bool moved = false;
     for (int j = 0; j < A.rigid_steps; ++j) {
         float sx = 0.0f, sy = 0.0f, sz = 0.0f;  // centroid: sums over atoms i = g (mod 4), (s0 + s1) + (s2 + s3)
@@ -1060,18 +1079,19 @@ __device__ __forceinline__ bool rigid_moves_rt(const DockArgs &A, const GridK &G
 // ranks recorded (separate instantiations, so the plain best-restart form
 // carries none of their code)
 template <bool kRank, bool kRigid, bool kTrace = false>
-__device__ __forceinline__ void dock_ligand_rt(const DockArgs &A, const PocketDev &Pk, const OutDev &O, int l, char *sm) {
+__device__ __forceinline__ void dock_ligand_rt(const DockArgs &A, const PocketDev &Pk, const OutDev &O, const LigSrc &Q, int l,
+                                               char *sm) {
     if (O.status[l] != LG_OK) return;  // rejected by the preparation kernel (uniform)
     const Layout &Ly = A.ly;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
     const int rs = lane / kLanesPerRestart, g = lane % kLanesPerRestart;
     const CtaView cv = cta_view(sm, Ly);
     const RtView v = rt_view(sm, Ly, A.lrt, warp);
-    const BatchDev &B = A.batch;
+    const BatchDev &B = Q.batch;
     const int a0 = B.atom_off[l], N = B.atom_off[l + 1] - a0;
     const int r0 = B.rot_off[l], R = B.rot_off[l + 1] - r0;
     const int S = A.S, P = A.P, PR = P * R;
-    stage_ligand(A, Pk, cv, l, a0, N, r0, R);
+    stage_ligand(A, B, Pk, cv, l, a0, N, r0, R);
     __syncthreads();
 
     float cs[kStepsPerLane], sn[kStepsPerLane];
@@ -1223,7 +1243,7 @@ __device__ __forceinline__ void dock_ligand_rt(const DockArgs &A, const PocketDe
             // them from here on (step 0, no move): its lanes skip the work
             const bool sv = kRigid || zrun < R;
             int jr;
-            const int t = sweep_bond_rt(A, Go, cv, v, N, R, k, rs, g, active && sv, cs, sn, kTrace, jr);
+            const int t = sweep_bond_rt(Q.dc2g, Go, cv, v, N, R, k, rs, g, active && sv, cs, sn, kTrace, jr);
             if (active && g == 0) {
                 v.tcur[LG_IDX(pc * R + k, P * Ly.rmax, kChkDecision) * kTile + rs] = (uint8_t)t;
                 if (kTrace) {  // a skipped decision repeats the bond's previous one
@@ -1243,13 +1263,13 @@ __device__ __forceinline__ void dock_ligand_rt(const DockArgs &A, const PocketDe
                 break;
             }
         }
-        if (kRigid) movedp = rigid_moves_rt(A, Go, O, v, l, r, pc, N, R, rs, g, active) || movedp;
+        if (kRigid) movedp = rigid_moves_rt(A, Q.rigid_shift_g, Go, O, v, l, r, pc, N, R, rs, g, active) || movedp;
         if (active) pc++;
         __syncwarp();
     }
     if (kRank) {
         __syncthreads();
-        rank_finish(A, Pk, O, l, rank_slot(A, blockIdx.x), a0, N, r0, PR, sm + Ly.cta_bytes);
+        rank_finish(A, Pk, O, Q.thr2g, l, rank_slot(A, blockIdx.x), a0, N, r0, PR, sm + Ly.cta_bytes);
         return;
     }
     if (lane == 0) {
@@ -1294,7 +1314,7 @@ __global__ void __launch_bounds__(128, LG_RT_MIN_BLOCKS) k_dock_batched(const __
         const int l = s_lig;
         __syncthreads();
         if (l < 0) break;
-        dock_ligand_rt<kRank, kRigid, kTrace>(A, A.pocket, A.out, l, sm);
+        dock_ligand_rt<kRank, kRigid, kTrace>(A, A.pocket, A.out, launch_src(A), l, sm);
     }
 }
 
@@ -1330,7 +1350,7 @@ __global__ void __launch_bounds__(128, LG_RT_MIN_BLOCKS) k_dock_multi(const __gr
             }
             __syncthreads();
         }
-        dock_ligand_rt<kRank, kRigid>(A, M.pk[p], O, l, sm);
+        dock_ligand_rt<kRank, kRigid>(A, M.pk[p], O, launch_src(A), l, sm);
         __syncthreads();
     };
     for (;;) {
@@ -1342,7 +1362,7 @@ __global__ void __launch_bounds__(128, LG_RT_MIN_BLOCKS) k_dock_multi(const __gr
         const int at = item * stride;
         if (M.lig_pocket) {  // one pocket per ligand
             const int l = A.order ? A.order[at] : at;
-            dock_ligand_rt<kRank, kRigid>(A, M.pk[M.lig_pocket[l]], A.out, l, sm);
+            dock_ligand_rt<kRank, kRigid>(A, M.pk[M.lig_pocket[l]], A.out, launch_src(A), l, sm);
             __syncthreads();
         } else if (M.pocket_major) {
             const int p = at / L, i = at - p * L;
@@ -1542,6 +1562,125 @@ __global__ void __launch_bounds__(32 * kFlatWarps) k_flatten(const __grid_consta
 //   cost ~ restarts * (passes * 36 * sum of moving atoms + 8 * atoms + 64):
 // 4 buckets per octave, or (sort_classes) the size class and 2 buckets per
 // octave within it (rejected ligands: class 0).
+// Where the preparation reads a ligand's atoms: the batch in global memory,
+// or a copy of them in shared memory.
+struct AtomsGlobal {
+    const BatchDev &B;
+    int a0, r0;
+    __device__ float x(int i) const { return B.x[a0 + i]; }
+    __device__ float y(int i) const { return B.y[a0 + i]; }
+    __device__ float z(int i) const { return B.z[a0 + i]; }
+    __device__ int parent(int i) const { return B.parent[a0 + i]; }
+    __device__ int type(int i) const { return B.type[a0 + i]; }
+    __device__ int rot_child(int k) const { return B.rot_child[r0 + k]; }
+};
+
+struct AtomsShared {
+    const float *xs, *ys, *zs;
+    const int16_t *par, *rc;
+    const uint8_t *ty;
+    __device__ float x(int i) const { return xs[i]; }
+    __device__ float y(int i) const { return ys[i]; }
+    __device__ float z(int i) const { return zs[i]; }
+    __device__ int parent(int i) const { return par[i]; }
+    __device__ int type(int i) const { return ty[i]; }
+    __device__ int rot_child(int k) const { return rc[k]; }
+};
+
+// The preparation of ligand l (one thread): validation, the end of every
+// torsional child's subtree and the FP64 centroid (atoms summed in order),
+// written at entry li of the scratch; the ligand's status (and, when
+// rejected, its score and best restart) in O.  Returns whether the ligand is
+// valid and, in msum, the sum of its moving atoms.
+template <class Src>
+__device__ bool prep_core(const DockArgs &A, const Src &at, int N, int R, const OutDev &O, int l, size_t li, long &msum) {
+    bool ok = N >= 1 && N <= A.nmax_lim && R >= 0 && R <= A.rmax_lim;
+    msum = 0;
+    if (ok) {
+        int endv[LG_MAX_ATOMS], size[LG_MAX_ATOMS];
+        ok = at.parent(0) == -1;
+        double sx = 0.0, sy = 0.0, sz = 0.0;
+        for (int i = 0; i < N && ok; i++) {
+            endv[i] = i + 1;
+            size[i] = 1;
+            const float x = at.x(i), y = at.y(i), z = at.z(i);
+            if (i > 0) {
+                const int p = at.parent(i);
+                ok = p >= 0 && p < i;
+            }
+            ok = ok && at.type(i) < LG_NUM_TYPES && isfinite(x) && isfinite(y) && isfinite(z);
+            sx += x;
+            sy += y;
+            sz += z;
+        }
+        if (ok) {
+            for (int i = N - 1; i >= 1; i--) {
+                const int p = at.parent(i);
+                endv[p] = max(endv[p], endv[i]);
+                size[p] += size[i];
+            }
+            for (int i = 0; i < N && ok; i++) ok = size[i] == endv[i] - i;
+            int prev = 0;
+            for (int k = 0; k < R && ok; k++) {
+                const int b = at.rot_child(k);
+                ok = b >= 1 && b < N && b > prev;
+                if (ok) {
+                    A.scr.rot_end[li * A.rmax_lim + k] = (int16_t)endv[b];
+                    msum += endv[b] - b - 1;
+                    prev = b;
+                }
+            }
+        }
+        if (ok) {
+            A.scr.centroid[3 * li] = sx / N;
+            A.scr.centroid[3 * li + 1] = sy / N;
+            A.scr.centroid[3 * li + 2] = sz / N;
+        }
+    }
+    O.status[l] = ok ? LG_OK : LG_EINVAL;
+    if (!ok) {
+        O.score[l] = __longlong_as_double(0x7ff8000000000000ll);
+        O.best_restart[l] = -1;
+    }
+    return ok;
+}
+
+__device__ bool prep_one(const DockArgs &A, const BatchDev &B, const OutDev &O, int l, size_t li, long &msum) {
+    const int a0 = B.atom_off[l], N = B.atom_off[l + 1] - a0;
+    const int r0 = B.rot_off[l], R = B.rot_off[l + 1] - r0;
+    return prep_core(A, AtomsGlobal{B, a0, r0}, N, R, O, l, li, msum);
+}
+
+// The preparation of ligand l by a CTA: its atoms are copied to shared memory
+// (`buf`, room for the atom and torsion maxima) by every thread, then thread
+// 0 prepares it from there (the same steps and order as prep_one).  Ends
+// after a CTA barrier.
+__device__ __noinline__ void prep_cta(const DockArgs &A, const BatchDev &B, const OutDev &O, int l, size_t li, char *buf) {
+    const int a0 = B.atom_off[l], N = B.atom_off[l + 1] - a0;
+    const int r0 = B.rot_off[l], R = B.rot_off[l + 1] - r0;
+    const int nm = (A.nmax_lim + 3) & ~3;
+    float *xs = (float *)buf, *ys = xs + nm, *zs = ys + nm;
+    int16_t *par = (int16_t *)(zs + nm), *rc = par + nm;
+    uint8_t *ty = (uint8_t *)(rc + ((A.rmax_lim + 1) & ~1));
+    const bool fits = N >= 1 && N <= A.nmax_lim && R >= 0 && R <= A.rmax_lim;
+    if (fits) {
+        for (int i = threadIdx.x; i < N; i += blockDim.x) {
+            xs[i] = B.x[a0 + i];
+            ys[i] = B.y[a0 + i];
+            zs[i] = B.z[a0 + i];
+            par[i] = B.parent[a0 + i];
+            ty[i] = B.type[a0 + i];
+        }
+        for (int k = threadIdx.x; k < R; k += blockDim.x) rc[k] = B.rot_child[r0 + k];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long msum;
+        prep_core(A, AtomsShared{xs, ys, zs, par, rc, ty}, N, R, O, l, li, msum);
+    }
+    __syncthreads();
+}
+
 __global__ void k_prep(const __grid_constant__ DockArgs A, int sort) {
     __shared__ int sh[kSortBuckets];
     if (sort)
@@ -1549,57 +1688,9 @@ __global__ void k_prep(const __grid_constant__ DockArgs A, int sort) {
     __syncthreads();
     const int l = blockIdx.x * blockDim.x + threadIdx.x;
     if (l < A.batch.L) {
-        const BatchDev &B = A.batch;
-        const int a0 = B.atom_off[l], N = B.atom_off[l + 1] - a0;
-        const int r0 = B.rot_off[l], R = B.rot_off[l + 1] - r0;
-        bool ok = N >= 1 && N <= A.nmax_lim && R >= 0 && R <= A.rmax_lim;
+        const int N = A.batch.atom_off[l + 1] - A.batch.atom_off[l];
         long msum = 0;
-        if (ok) {
-            int endv[LG_MAX_ATOMS], size[LG_MAX_ATOMS];
-            ok = B.parent[a0] == -1;
-            double sx = 0.0, sy = 0.0, sz = 0.0;
-            for (int i = 0; i < N && ok; i++) {
-                endv[i] = i + 1;
-                size[i] = 1;
-                const float x = B.x[a0 + i], y = B.y[a0 + i], z = B.z[a0 + i];
-                if (i > 0) {
-                    const int p = B.parent[a0 + i];
-                    ok = p >= 0 && p < i;
-                }
-                ok = ok && B.type[a0 + i] < LG_NUM_TYPES && isfinite(x) && isfinite(y) && isfinite(z);
-                sx += x;
-                sy += y;
-                sz += z;
-            }
-            if (ok) {
-                for (int i = N - 1; i >= 1; i--) {
-                    const int p = B.parent[a0 + i];
-                    endv[p] = max(endv[p], endv[i]);
-                    size[p] += size[i];
-                }
-                for (int i = 0; i < N && ok; i++) ok = size[i] == endv[i] - i;
-                int prev = 0;
-                for (int k = 0; k < R && ok; k++) {
-                    const int b = B.rot_child[r0 + k];
-                    ok = b >= 1 && b < N && b > prev;
-                    if (ok) {
-                        A.scr.rot_end[(size_t)l * A.rmax_lim + k] = (int16_t)endv[b];
-                        msum += endv[b] - b - 1;
-                        prev = b;
-                    }
-                }
-            }
-            if (ok) {
-                A.scr.centroid[3 * l] = sx / N;
-                A.scr.centroid[3 * l + 1] = sy / N;
-                A.scr.centroid[3 * l + 2] = sz / N;
-            }
-        }
-        A.out.status[l] = ok ? LG_OK : LG_EINVAL;
-        if (!ok) {
-            A.out.score[l] = __longlong_as_double(0x7ff8000000000000ll);
-            A.out.best_restart[l] = -1;
-        }
+        const bool ok = prep_one(A, A.batch, A.out, l, (size_t)l, msum);
         if (sort) {
             const double cost = ok ? (double)A.S * ((double)A.P * 36.0 * (double)msum + 8.0 * N + 64.0) : 1.0;
             int key;
@@ -1653,6 +1744,200 @@ __global__ void k_sort_scan(int32_t *hist, int L) {
 __global__ void k_sort_scatter(int L, const int32_t *keys, int32_t *hist, int32_t *order) {
     const int l = blockIdx.x * blockDim.x + threadIdx.x;
     if (l < L) order[atomicAdd(&hist[keys[l]], 1)] = l;
+}
+
+// ================================================================== device-resident serving loop
+__device__ __forceinline__ uint64_t ld_acquire_u64(const uint64_t *p) {
+    uint64_t v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_sys_u64(uint64_t *p, uint64_t v) {
+    asm volatile("st.release.sys.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// The next ligand of the CTA (thread 0): the one it holds, else a new one by
+// fetch-and-add on `next`; it is docked once published (below `tail`).
+// Returns its index; or -1 when the host asked the loop to stop or another
+// CTA reached the idle limit (the launch then ends as a whole, so the host
+// relaunches it at full width and nothing waits on CTAs that have left), or
+// -2 when the CTA has waited the idle limit itself.  On -1 / -2 `held` keeps
+// an unpublished ligand for the next launch.  Every wait here ends.
+__device__ __noinline__ long long loop_claim(const LoopArgs &S, long long &held, uint64_t &deadline) {
+    if (held < 0) {
+        // once the launch is stopping or closing no CTA claims a new ligand,
+        // so every CTA leaves after the one it holds and the launch ends
+        // promptly; the ligands left unclaimed wait for the next launch
+        if (ld_acquire_u32(&S.ctl->stop) || ld_acquire_u32(&S.ctl->closing)) return -1;
+        held = (long long)atomicAdd((unsigned long long *)&S.ctl->next, 1ull);
+        deadline = global_ns() + S.idle_ns;
+    }
+    unsigned nap = 64;
+    for (int poll = 0;; ++poll) {
+        if ((uint64_t)held < ld_acquire_u64(&S.ctl->tail)) {
+            const long long n = held;
+            held = -1;
+            return n;
+        }
+        if ((poll & 7) == 0 && (ld_acquire_u32(&S.ctl->stop) || ld_acquire_u32(&S.ctl->closing))) return -1;
+        if (global_ns() > deadline) {
+            atomicExch(&S.ctl->closing, 1u);
+            return -2;
+        }
+        __nanosleep(nap);
+        nap = nap < 4096 ? 2 * nap : 4096;
+    }
+}
+
+// The descriptor of ligand `item` (thread 0): scanned forward from `hint`
+// (descriptors are published in ligand order).  A slot whose sequence number
+// is not the one looked for was recycled, so its request is complete and its
+// ligands lie below `item`; a descriptor is read between two reads of its
+// sequence number (the host invalidates it before rewriting the body).
+// Returns false when no descriptor holds the item within 2 * ring steps.
+__device__ __noinline__ bool loop_find(const LoopArgs &S, long long item, uint64_t &hint, uint64_t &seq, uint64_t &first, int &L,
+                          int &slot, int &pocket) {
+    for (int step = 0; step < 2 * S.ring; ++step) {
+        const uint64_t head = ld_acquire_u64(&S.ctl->head_seq);
+        if (head > hint) hint = head;
+        const LoopDesc *d = S.desc + LG_IDX(hint % (uint64_t)S.ring, S.ring, kChkRing);
+        if (ld_acquire_u64(&d->seq) != hint) {
+            ++hint;
+            continue;
+        }
+        const uint64_t f = d->first;
+        const int n = d->L, sl = d->slot, pk = d->pocket;
+        __threadfence();
+        if (ld_acquire_u64(&d->seq) != hint) {  // rewritten while read: it was complete
+            ++hint;
+            continue;
+        }
+        if ((uint64_t)item >= f + (uint64_t)n) {
+            ++hint;
+            continue;
+        }
+        if ((uint64_t)item < f || pk < 0 || pk >= S.np) return false;
+        seq = hint;
+        first = f;
+        L = n;
+        slot = sl;
+        pocket = pk;
+        return true;
+    }
+    return false;
+}
+
+// A ligand of request `seq` (L ligands) is docked: its outputs are made
+// visible to the host before it is counted, and the CTA that counts the
+// request's last ligand raises the request's completion flag (thread 0).
+__device__ __noinline__ void loop_count(const LoopArgs &S, uint64_t seq, int L) {
+    __threadfence_system();
+    const uint32_t k = (uint32_t)LG_IDX(seq % (uint64_t)S.ring, S.ring, kChkRing);
+    if (atomicAdd(&S.done[k], 1u) + 1u == (uint32_t)L) {
+        S.done[k] = 0u;  // the slot's next request counts from 0
+        __threadfence_system();
+        st_release_sys_u64(&S.flags[k], seq + 1);
+    }
+}
+
+// One persistent launch serving every admitted request of one kind (restarts,
+// passes, outputs, atom and torsion maxima): CTAs claim ligands in admission
+// order, prepare and dock each one (the batched kernel's docking code, one
+// ligand per CTA) as a slot of the arenas named in A0 (ligands and outputs)
+// against its request's pocket from the table in S -- all kernel parameters,
+// so the docking code reads them as constants -- and the CTA that finishes a
+// request's last ligand raises its completion flag.  Waits are bounded: a CTA
+// with no ligand to claim for idle_ns leaves; a stop request makes every CTA
+// leave after its current ligand; the last CTA out records how the launch
+// ended.
+template <bool kRank, bool kRigid>
+__global__ void __launch_bounds__(128, LG_RT_MIN_BLOCKS) k_serve_loop(const __grid_constant__ DockArgs A0,
+                                                                       const __grid_constant__ LoopArgs S) {
+    extern __shared__ __align__(16) char sm[];
+    __shared__ long long s_item;
+    __shared__ uint64_t s_seq, s_first;
+    __shared__ int s_L, s_slot, s_pocket;
+    // thread 0's claim state, kept in shared memory so that nothing extra is
+    // live in registers while the CTA docks
+    __shared__ uint64_t s_hint, s_deadline;
+    __shared__ long long s_held;
+    __shared__ int s_why;  // 1 stopped, 2 idle limit, 3 bad item
+    if (threadIdx.x == 0) {
+        atomicAdd(&S.ctl->live, 1u);
+        s_held = S.held[blockIdx.x];  // left by this CTA's predecessor
+        s_hint = S.first_seq;
+        s_deadline = global_ns() + S.idle_ns;
+        s_why = 0;
+        s_seq = kDescBusy;
+        s_first = 0;
+        s_L = 0;
+    }
+    __syncthreads();
+    for (;;) {
+        if (threadIdx.x == 0) {
+            long long held = s_held;
+            uint64_t deadline = s_deadline, hint = s_hint;
+            long long item = loop_claim(S, held, deadline);
+            if (item >= 0 && !(s_seq != kDescBusy && (uint64_t)item >= s_first &&
+                               (uint64_t)item < s_first + (uint64_t)s_L)) {
+                uint64_t sq, f;
+                int n, sl, pk;
+                if (loop_find(S, item, hint, sq, f, n, sl, pk)) {
+                    s_seq = sq;
+                    s_first = f;
+                    s_L = n;
+                    s_slot = sl;
+                    s_pocket = pk;
+                } else {
+                    atomicAdd(&S.ctl->bad, 1u);
+                    item = -3;
+                }
+            }
+            s_held = held;
+            s_deadline = deadline;
+            s_hint = hint;
+            s_why = item >= 0 ? 0 : (int)(-item);
+            s_item = item;
+        }
+        __syncthreads();
+        const long long item = s_item;
+        if (item < 0) break;
+        const int l = s_slot + (int)((uint64_t)item - s_first);
+        const int p = s_pocket;
+        prep_cta(A0, A0.batch, A0.out, l, (size_t)blockIdx.x, sm);
+        LigSrc q;
+        q.batch = A0.batch;
+        q.dc2g = S.dc2g[p];
+        q.thr2g = S.thr2g[p];
+        q.rigid_shift_g = S.rigid_shift_g[p];
+        dock_ligand_rt<kRank, kRigid>(A0, S.pk[p], A0.out, q, l, sm);
+        __syncthreads();
+        if (threadIdx.x == 0) loop_count(S, s_seq, s_L);
+    }
+    if (threadIdx.x == 0) {
+        S.held[blockIdx.x] = s_held;
+        if (s_why == 2) atomicAdd(&S.ctl->idle_exits, 1u);
+        __threadfence();
+        if (atomicSub(&S.ctl->live, 1u) == 1u) {  // the last CTA out
+            const int st = ld_acquire_u32(&S.ctl->bad) ? LG_EINVAL
+                           : (ld_acquire_u32(&S.ctl->idle_exits) && !ld_acquire_u32(&S.ctl->stop)) ? LG_ETIMEOUT
+                                                                                                   : LG_OK;
+            S.ctl->status = st;
+        }
+    }
 }
 
 // ================================================================== pose scoring and diagnostics
@@ -1724,6 +2009,7 @@ Scratch carve_scratch(void *base, int L, int rmax, int rank_slots, int S, int P,
     s.rk_cen = nullptr;
     s.rk_slots = rank_slots > 0 ? rank_slots : 0;
     s.rk_floats = 0;
+    s.per_cta = 0;
     if (rank_slots > 0) {
         const size_t nm = (size_t)((nmax + 3) & ~3);
         s.rk_floats = 3 * (size_t)rank_slots * S * nm;
@@ -1832,6 +2118,23 @@ cudaError_t launch_dock_multi(const DockArgs &a, const MultiDev &m, int grid, in
     if (a.ranking) return cudaLaunchKernelEx(&dl.cfg, k_dock_multi<true, false>, a, m);
     if (rigid) return cudaLaunchKernelEx(&dl.cfg, k_dock_multi<false, true>, a, m);
     return cudaLaunchKernelEx(&dl.cfg, k_dock_multi<false, false>, a, m);
+}
+
+template <typename F>
+static cudaError_t with_loop(bool ranking, bool rigid, F &&f) {
+    if (ranking) return rigid ? f(k_serve_loop<true, true>) : f(k_serve_loop<true, false>);
+    return rigid ? f(k_serve_loop<false, true>) : f(k_serve_loop<false, false>);
+}
+
+cudaError_t loop_kernel_attributes(int W, int smem, int *ctas_per_sm, bool ranking, bool rigid) {
+    return with_loop(ranking, rigid, [&](auto kernel) { return kernel_attributes(kernel, W, smem, ctas_per_sm); });
+}
+
+cudaError_t launch_serve_loop(const DockArgs &a, const LoopArgs &la, int grid, int smem, cudaStream_t s) {
+    return with_loop(a.ranking, a.rigid_steps > 0, [&](auto kernel) {
+        kernel<<<grid, 32 * a.ly.W, smem, s>>>(a, la);
+        return cudaGetLastError();
+    });
 }
 
 cudaError_t launch_flatten(const FlatArgs &f, int L, cudaStream_t s) {

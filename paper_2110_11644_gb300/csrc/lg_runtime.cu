@@ -44,15 +44,6 @@ void DevBuf::release() {
     cap = 0;
 }
 
-// Carves aligned sub-arrays out of one allocation.
-struct Carve {
-    size_t off = 0;
-    size_t take(size_t bytes) {
-        size_t o = off;
-        off = (off + bytes + 255) & ~(size_t)255;
-        return o;
-    }
-};
 
 // Pose ranking replaces the plain lowest-score choice when poses are
 // clustered or only the first K ranked poses are rescored.
@@ -97,17 +88,22 @@ int host_batch_shape(const lg_ligand_batch *b, int64_t *A, int64_t *R, int *nmax
     return LG_OK;
 }
 
+size_t batch_image_bytes(int L, int64_t A, int64_t R) { return BatchImage(L, A, R).bytes; }
+
 // Stage a host batch into device buffer `buf`; fills `d` with device pointers.
 int stage_batch(DevBuf &buf, const lg_ligand_batch *b, int64_t A, int64_t R, BatchDev *d, cudaStream_t s) {
+    if (buf.ensure(batch_image_bytes(b->L, A, R))) return fail(LG_ENOMEM, "device staging allocation failed");
+    return upload_batch(buf.p, b, A, R, d, s);
+}
+
+// Copy a host batch into device memory at `dev` (batch_image_bytes bytes,
+// 256-byte aligned); fills `d` with device pointers.
+int upload_batch(void *dev, const lg_ligand_batch *b, int64_t A, int64_t R, BatchDev *d, cudaStream_t s) {
     const int L = b->L;
-    Carve c;
-    const size_t o_aoff = c.take(4 * (size_t)(L + 1)), o_roff = c.take(4 * (size_t)(L + 1));
-    const size_t o_uid = c.take(8 * (size_t)L);
-    const size_t o_x = c.take(4 * (size_t)A), o_y = c.take(4 * (size_t)A), o_z = c.take(4 * (size_t)A);
-    const size_t o_q = c.take(4 * (size_t)A), o_t = c.take((size_t)A), o_p = c.take(2 * (size_t)A);
-    const size_t o_rc = c.take(2 * (size_t)std::max<int64_t>(R, 1));
-    if (buf.ensure(c.off)) return fail(LG_ENOMEM, "device staging allocation failed");
-    char *base = (char *)buf.p;
+    const BatchImage im(L, A, R);
+    const size_t o_aoff = im.o_aoff, o_roff = im.o_roff, o_uid = im.o_uid, o_x = im.o_x, o_y = im.o_y, o_z = im.o_z,
+                 o_q = im.o_q, o_t = im.o_t, o_p = im.o_p, o_rc = im.o_rc;
+    char *base = (char *)dev;
     auto cp = [&](size_t off, const void *src, size_t n) -> cudaError_t {
         if (n == 0) return cudaSuccess;
         return cudaMemcpyAsync(base + off, src, n, cudaMemcpyHostToDevice, s);
@@ -900,6 +896,10 @@ int lg_pocket_load(lg_ctx *c, const lg_pocket_desc *d, int32_t *pid) {
         c->pockets[id] = r;
     }
     l2_reserve(c);
+    {
+        std::lock_guard<std::mutex> pg(c->pk_mu);
+        c->live_pockets.push_back(pd);
+    }
     *pid = id;
     return LG_OK;
 }
@@ -909,6 +909,15 @@ int lg_pocket_unload(lg_ctx *c, int32_t pid) {
     std::lock_guard<std::mutex> g(c->mu);
     if (pid < 0 || pid >= (int)c->pockets.size() || !c->pockets[pid].live) return fail(LG_ENOPOCKET, "unknown pocket");
     cudaSetDevice(c->device);
+    {
+        std::lock_guard<std::mutex> pg(c->pk_mu);
+        auto &v = c->live_pockets;
+        for (size_t i = 0; i < v.size(); ++i)
+            if (v[i].cell_o == c->pockets[pid].dev.cell_o) {
+                v.erase(v.begin() + i);
+                break;
+            }
+    }
     cudaFree(c->pockets[pid].mem);
     c->pockets[pid] = PocketRec();
     l2_reserve(c);
@@ -1106,6 +1115,7 @@ int lg_get_stats(lg_ctx *c, lg_stats *out) {
     cudaSetDevice(c->device);
     harvest_timing(c);
     *out = c->stats;
+    serve_stats(c, out);
     return LG_OK;
 }
 
@@ -1126,6 +1136,14 @@ int lg_set_option(lg_ctx *c, const char *key, int64_t v) {
         c->serve_max_merge = (int)v;
     } else if (!strcmp(key, "serve_cross_pocket")) {
         c->serve_cross_pocket = v != 0;
+    } else if (!strcmp(key, "serve_device_loop")) {
+        if (c->serve_device_loop != (v != 0)) {
+            c->serve_device_loop = v != 0;
+            serve_stop(c);  // the next submission starts a worker of the other kind
+        }
+    } else if (!strcmp(key, "serve_loop_idle_ms")) {
+        if (v < 1 || v > 60000) return fail(LG_EINVAL, "serve_loop_idle_ms must be in [1, 60000]");
+        c->serve_loop_idle_ms = (int)v;
     } else if (!strcmp(key, "serve_max_inflight")) {
         if (v < 1 || v > 64) return fail(LG_EINVAL, "serve_max_inflight must be in [1, 64]");
         c->serve_max_inflight = (int)v;

@@ -31,6 +31,35 @@ struct DevBuf {
     void release();
 };
 
+// Carves aligned sub-arrays out of one allocation.
+struct Carve {
+    size_t off = 0;
+    size_t take(size_t bytes) {
+        size_t o = off;
+        off = (off + bytes + 255) & ~(size_t)255;
+        return o;
+    }
+};
+
+// Device image of a host batch: byte offsets of its arrays and its size.
+struct BatchImage {
+    size_t o_aoff, o_roff, o_uid, o_x, o_y, o_z, o_q, o_t, o_p, o_rc, bytes;
+    BatchImage(int L, int64_t A, int64_t R) {
+        Carve c;
+        o_aoff = c.take(4 * (size_t)(L + 1));
+        o_roff = c.take(4 * (size_t)(L + 1));
+        o_uid = c.take(8 * (size_t)L);
+        o_x = c.take(4 * (size_t)A);
+        o_y = c.take(4 * (size_t)A);
+        o_z = c.take(4 * (size_t)A);
+        o_q = c.take(4 * (size_t)A);
+        o_t = c.take((size_t)A);
+        o_p = c.take(2 * (size_t)A);
+        o_rc = c.take(2 * (size_t)std::max<int64_t>(R, 1));
+        bytes = c.off;
+    }
+};
+
 struct PocketRec {
     bool live = false;
     PocketDev dev{};
@@ -45,6 +74,9 @@ bool ranking_on(const lg_dock_params *p);
 int check_params(const lg_dock_params *p);
 int host_batch_shape(const lg_ligand_batch *b, int64_t *A, int64_t *R, int *nmax, int *rmax);
 int stage_batch(DevBuf &buf, const lg_ligand_batch *b, int64_t A, int64_t R, BatchDev *d, cudaStream_t s);
+size_t batch_image_bytes(int L, int64_t A, int64_t R);
+int upload_batch(void *dev, const lg_ligand_batch *b, int64_t A, int64_t R, BatchDev *d, cudaStream_t s);
+void serve_stats(lg_ctx *c, lg_stats *st);  // the serving loop's figures (lg_get_stats)
 int stage_out(DevBuf &buf, const lg_dock_result *o, int L, int S, int P, int64_t A, int64_t R, int Rs, OutDev *d);
 int fetch_out(const OutDev &d, const lg_dock_result *o, int L, int S, int P, int64_t A, int64_t R, int Rs,
               cudaStream_t s);
@@ -84,6 +116,8 @@ struct lg_ctx {
     // options read by the serving worker too (lg_set_option writes them)
     std::atomic<int> warps_opt{0};
     int serve_max_inflight = 8;  // read when the server starts
+    bool serve_device_loop = true;    // read when the server starts: the device-resident loop serves requests
+    std::atomic<int> serve_loop_idle_ms{100};  // idle limit of the loop's CTAs
     std::atomic<int> serve_max_merge{4096};        // ligands per merged batch
     std::atomic<bool> serve_cross_pocket{false};   // merge requests aimed at different pockets
     int64_t serve_reserve_mb = 1024;
@@ -115,6 +149,10 @@ struct lg_ctx {
     size_t l2_persist_prev = 0;  // the limit found at creation, restored at destruction
     size_t l2_persist_set = 0;   // the set-aside this context asked for (0: none)
     std::atomic<bool> l2_window{true};
+    // the loaded pockets, for the serving loop's pocket table (its worker
+    // does not take `mu`)
+    std::mutex pk_mu;
+    std::vector<lg::PocketDev> live_pockets;
     // orders the calls that share `scratch` (and `flat_buf`) on the device: a
     // call's stream waits for the previous such call's work to finish
     cudaEvent_t scratch_ev = nullptr;

@@ -4,7 +4,7 @@ of the docking kernels, and every ranking scratch slot, is checked, and a
 failure turns into an error of the call.  The checked library docks the
 parity cases (best restart, ranking, rigid moves, heavy-tailed size classes
 at every width and with ranking, several pockets, flattening, the
-allocation-free entry point) without a
+allocation-free entry point, the serving loop) without a
 failure and with results equal to the product build's bit for bit."""
 import os
 import subprocess
@@ -69,6 +69,19 @@ st.synchronize()
 for k, v in outs.items():
     if v is not None:
         out["noalloc/" + k] = v.cpu().numpy()
+# the device-resident serving loop (descriptor ring and per-CTA slots checked)
+keep = []
+for j in range(3):
+    sub = b1.subset(range(50 * j, 50 * j + 50))
+    arrs = lg.host_batch_arrays(sub)
+    bs = lg.make_batch_struct(arrs, sub.L)
+    ps = lg.make_params(prm1.restarts, prm1.passes, prm1.seed, prm1.d_clash)
+    rr, oo = lg.alloc_result(sub.L, int(sub.atom_off[-1]), int(sub.rot_off[-1]), prm1.restarts, prm1.passes)
+    keep.append((arrs, bs, ps, rr, oo, lg.lg_stream_submit(ctx.h, pid if j != 1 else pid2, bs, ps, rr)))
+for j, (_, _, _, _, oo, t) in enumerate(keep):
+    lg.lg_stream_wait(ctx.h, t, 120000)
+    for k in ("score", "best_restart", "status", "tors_idx", "pose"):
+        out["loop%d/%s" % (j, k)] = oo[k]
 ctx.close()
 np.savez(sys.argv[2], **out)
 """

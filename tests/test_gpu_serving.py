@@ -1,6 +1,8 @@
-"""Serving loop (lg_stream_submit / poll / wait) on the GPU: continuous batching
+"""Serving (lg_stream_submit / poll / wait) on the GPU: continuous batching
 of requests of uneven size, results identical to docking each request alone,
-bounded waits, admission under a tight free-memory reserve."""
+bounded waits, admission under a tight free-memory reserve -- through the
+device-resident loop (the default) and, where marked, the host worker that
+merges requests into ordinary launches."""
 import time
 
 import numpy as np
@@ -86,12 +88,14 @@ def test_bounded_wait_and_unknown_ticket(served):
     assert e.value.code == lg.LG_EINVAL
 
 
-def test_admission_under_tight_memory_still_completes():
+@pytest.mark.parametrize("device_loop", [1, 0])
+def test_admission_under_tight_memory_still_completes(device_loop):
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     ctx = lg.Context(0)
     try:
+        ctx.set_option("serve_device_loop", device_loop)
         # a reserve larger than the device: every request beyond the first in
         # flight waits for memory, but an idle device always admits one
         ctx.set_option("serve_mem_reserve_mb", 1 << 30)
@@ -195,14 +199,17 @@ def test_heavy_tailed_ranking_requests_equal_direct_calls(served):
             assert np.array_equal(outs[k][:m], d[k][:m]), k
 
 
-def test_requests_for_different_pockets_share_launches():
-    # requests aimed at three pockets are merged into one launch (one pocket per
-    # ligand); every result equals docking the request alone against its pocket
+@pytest.mark.parametrize("device_loop", [1, 0])
+def test_requests_for_different_pockets_share_launches(device_loop):
+    # requests aimed at three pockets share one launch (the loop always; the
+    # host worker with serve_cross_pocket, one pocket per ligand); every result
+    # equals docking the request alone against its pocket
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     ctx = lg.Context(0)
     try:
+        ctx.set_option("serve_device_loop", device_loop)
         ctx.set_option("serve_max_inflight", 1)  # one slot: everything queued is merged
         ctx.set_option("serve_cross_pocket", 1)
         pockets = [synth.config_pocket(1), synth.config_pocket(4, 0), synth.config_pocket(4, 3)]
@@ -238,6 +245,7 @@ def test_admission_holds_back_a_ranked_request_while_a_slot_is_busy():
     import dataclasses
     ctx = lg.Context(0)
     try:
+        ctx.set_option("serve_device_loop", 0)  # the host worker's merged launches
         ctx.set_option("serve_max_inflight", 2)
         ctx.set_option("serve_mem_reserve_mb", 0)
         pid = ctx.load_pocket(synth.config_pocket(2))
@@ -279,3 +287,96 @@ def test_admission_holds_back_a_ranked_request_while_a_slot_is_busy():
             assert np.array_equal(outs[k][:sub.L], d[k][:sub.L]), k
     finally:
         ctx.close()
+
+
+def _loop_ctx(idle_ms=None):
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    ctx = lg.Context(0)
+    if idle_ms is not None:
+        ctx.set_option("serve_loop_idle_ms", idle_ms)
+    return ctx
+
+
+def test_loop_requests_arriving_while_others_run():
+    # requests of uneven size aimed at three pockets arrive one by one while
+    # earlier ones are on the device: each result equals the request docked
+    # alone, and the loop docked every ligand
+    ctx = _loop_ctx()
+    try:
+        pockets = [synth.config_pocket(2), synth.config_pocket(4, 0), synth.config_pocket(4, 5)]
+        pids = [ctx.load_pocket(p) for p in pockets]
+        params = synth.DockParams(restarts=64, passes=3)
+        pool = synth.config_ligands(2, 12000)
+        rng = np.random.default_rng(11)
+        sizes = [int(v) for v in np.floor(np.exp(rng.uniform(0, np.log(2000), 14)))]
+        starts = np.cumsum([0] + sizes)
+        reqs, tickets = [], []
+        for k, n in enumerate(sizes):
+            sub = pool.subset(range(starts[k], starts[k] + n))
+            req = _request(sub, params)
+            pid = pids[k % 3]
+            reqs.append((sub, pid, req))
+            tickets.append(lg.lg_stream_submit(ctx.h, pid, req["b"], req["p"], req["r"]))
+            time.sleep(2e-4)
+        states = [lg.lg_stream_poll(ctx.h, t)[0] for t in tickets]
+        for t in tickets:
+            assert lg.lg_stream_wait(ctx.h, t, 120000) == lg.LG_OK
+        st = ctx.stats()
+        assert st.serve_loop_launches >= 1 and st.serve_loop_items == sum(sizes)
+        for sub, pid, req in reqs:
+            alone = ctx.dock(pid, sub, params)
+            got = _trim(req, params.passes)
+            for k in got:
+                assert np.array_equal(got[k], alone[k][:len(got[k])]), k
+        assert any(s < lg.LG_REQ_DONE for s in states)  # some were still running when the last arrived
+    finally:
+        ctx.close()
+
+
+def test_loop_idle_limit_ends_the_launch_and_work_relaunches_it():
+    # every wait of the loop is bounded: with no ligand to claim for the idle
+    # limit its CTAs leave and the launch ends with LG_ETIMEOUT; a later
+    # request launches it again
+    ctx = _loop_ctx(idle_ms=5)
+    try:
+        pid = ctx.load_pocket(synth.config_pocket(1))
+        params = synth.config_params(1)
+        full = synth.config_ligands(1)
+        first = _request(full.subset(range(0, 40)), params)
+        t = lg.lg_stream_submit(ctx.h, pid, first["b"], first["p"], first["r"])
+        assert lg.lg_stream_wait(ctx.h, t, 60000) == lg.LG_OK
+        deadline = time.time() + 10.0
+        while ctx.stats().serve_loop_status != lg.LG_ETIMEOUT and time.time() < deadline:
+            time.sleep(0.01)
+        st = ctx.stats()
+        assert st.serve_loop_status == lg.LG_ETIMEOUT and st.serve_loop_launches == 1
+        second = _request(full.subset(range(40, 100)), params)
+        t = lg.lg_stream_submit(ctx.h, pid, second["b"], second["p"], second["r"])
+        assert lg.lg_stream_wait(ctx.h, t, 60000) == lg.LG_OK
+        assert ctx.stats().serve_loop_launches == 2
+        for req, rng in ((first, range(0, 40)), (second, range(40, 100))):
+            alone = ctx.dock(pid, full.subset(rng), params)
+            got = _trim(req, params.passes)
+            for k in got:
+                assert np.array_equal(got[k], alone[k][:len(got[k])]), k
+    finally:
+        ctx.close()
+
+
+def test_loop_closes_with_requests_in_flight():
+    # closing the context stops the loop after the ligands on the device: the
+    # call returns, and every request is either done or failed
+    ctx = _loop_ctx()
+    pid = ctx.load_pocket(synth.config_pocket(2))
+    params = synth.config_params(2)
+    pool = synth.config_ligands(2, 3000)
+    reqs, tickets = [], []
+    for k in range(6):
+        req = _request(pool.subset(range(500 * k, 500 * k + 500)), params)
+        reqs.append(req)
+        tickets.append(lg.lg_stream_submit(ctx.h, pid, req["b"], req["p"], req["r"]))
+    t0 = time.time()
+    ctx.close()
+    assert time.time() - t0 < 60.0
