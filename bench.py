@@ -504,9 +504,27 @@ def small_batch_leg(ctx, pid, dev, n_lig, calls):
         for _ in range(calls):
             lg.lg_dock_batch(ctx.h, pid, b, p, r, side.cuda_stream)
         side.synchronize()
-        res[name] = {"us_per_call": (time.perf_counter() - t0) / calls * 1e6, "graph_mode": ctx.stats().graph}
+        st = ctx.stats()
+        res[name] = {"us_per_call": (time.perf_counter() - t0) / calls * 1e6, "graph_mode": st.graph,
+                     "restart_lanes": st.restart_lanes, "warps_per_cta": st.warps_per_cta}
     ctx.set_option("graphs", 0)
-    return {"ligands": L, "calls": calls, **res}
+    # the same direct calls with each restart tile forced (lanes per restart;
+    # every restart of a ligand in flight at once)
+    by_lanes = {}
+    for lanes in (4, 8, 16):
+        ctx.set_option("restart_lanes", lanes)
+        for _ in range(3):
+            lg.lg_dock_batch(ctx.h, pid, b, p, r, side.cuda_stream)
+        side.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(calls // 2):
+            lg.lg_dock_batch(ctx.h, pid, b, p, r, side.cuda_stream)
+        side.synchronize()
+        st = ctx.stats()
+        by_lanes[str(lanes)] = {"us_per_call": (time.perf_counter() - t0) / (calls // 2) * 1e6,
+                                "warps_per_cta": st.warps_per_cta}
+    ctx.set_option("restart_lanes", 0)
+    return {"ligands": L, "calls": calls, **res, "by_lanes": by_lanes}
 
 
 def summary_of(line) -> dict:
@@ -805,7 +823,8 @@ def main():
                 "config": {"workload": WORKLOAD, "ligands_per_gpu": L, "restarts": S, "passes": P,
                            "angle_steps": 36, "mode": "batched persistent, cost-sorted",
                            "l2": "flushed before every step (256 MiB write)", "inputs": "device-resident",
-                           "warps_per_cta": st.warps_per_cta, "ctas_per_sm": st.ctas_per_sm, "grid": st.grid},
+                           "warps_per_cta": st.warps_per_cta, "restart_lanes": st.restart_lanes,
+                           "ctas_per_sm": st.ctas_per_sm, "grid": st.grid},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "clocks": clk, "gpu_launches": launches_per_step * args.steps, "plain": plain,
                 "serving": serving, "serving_peak": serving_peak, "multi_pocket": multi, "flatten": flatten,

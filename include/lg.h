@@ -447,7 +447,7 @@ typedef struct {
     int32_t serve_loop_status;   /* device-resident serving loop: how its last launch ended (LG_OK after a
                                     stop, LG_ETIMEOUT after its idle limit, LG_EINVAL for a bad work item;
                                     -1 while running or never launched) */
-    int32_t reserved;
+    int32_t restart_lanes;       /* lanes per restart of the last call's first batched launch (32: plain mode) */
     int64_t l2_window_bytes;     /* L2 access-policy window of the last docking launch (0: none) */
     int64_t l2_persist_bytes;    /* persisting L2 set-aside of the context (0: none) */
     int64_t serve_loop_launches; /* launches of the device-resident serving loop */
@@ -457,12 +457,20 @@ typedef struct {
 int lg_get_stats(lg_ctx *ctx, lg_stats *out);
 
 /* Context options: "timing" (0/1, default 0), "warps_per_cta" (0 = the
- * autotuner's or the default choice, else 1..4 for every batched launch),
+ * autotuner's or the default choice, else 1..4 for every batched launch; up
+ * to 8 or 16 with 8 or 16 lanes per restart), "restart_lanes" (0 = the
+ * autotuner's or the default choice, else 2, 4, 8 or 16 lanes per restart --
+ * 16, 8, 4 or 2 restart slots per warp -- for every single-pocket batched
+ * launch without pose ranking or decision ranks; the others always use 4),
  * "autotune" (0/1, default 1; setting it clears the tuned choices: with it on,
  * the first batched call of a (size class, restarts, passes, atom and torsion
- * maxima, features) combination times 4, 2 and 1 warps per CTA on the same
- * even sample of that class's ligands (16 waves of the widest grid, at least
- * 4,096) and keeps the fastest; results do not depend on the choice), "graphs" (0/1, default 0: an lg_dock_batch call with device
+ * maxima, features) combination times the candidate tiles -- (lanes per
+ * restart, warps per CTA) = (4, 4), (4, 2), (4, 1), (2, 2), (2, 1), (8, 4),
+ * (8, 2), or (4, 4), (4, 2), (4, 1) where only 4 lanes per restart exist --
+ * on the same even sample of that class's ligands (16 waves of the widest
+ * grid, at least 4,096) and keeps the fastest; a batch that fits in one wave
+ * instead takes 16 (else 8, else 4) lanes per restart with every restart of a
+ * ligand in flight at once, untuned; results never depend on the choice), "graphs" (0/1, default 0: an lg_dock_batch call with device
  * batch and result on a non-default stream is captured, preparation and
  * docking kernels together, as a CUDA graph and replayed when a later call
  * has the same arguments; with timing on, such a call's device time then
@@ -490,8 +498,9 @@ int lg_set_option(lg_ctx *ctx, const char *key, int64_t value);
 /* The autotuner's cached choices as JSON text, to carry them to another
  * context or process on the same kind of GPU:
  *   {"device": "<name>", "sms": <SM count>, "entries": [[size class,
- *    restarts, passes, atom maximum, torsion maximum, ranking, rigid,
- *    kind, warps per CTA], ...]}
+ *    restarts, passes, atom maximum, torsion maximum, ranking + 2 * decision
+ *    ranks, rigid, kind, lanes per restart, warps per CTA], ...]}
+ * (an entry of 9 integers, without the lanes per restart, means 4)
  * lg_tune_export writes the text, NUL-terminated, into buf (cap bytes,
  * caller-owned) and sets *len to its length without the NUL; when cap is too
  * small it writes nothing, sets *len and returns LG_EINVAL (buf may be NULL

@@ -101,36 +101,39 @@ __host__ __device__ inline Layout make_layout(int nmax, int rmax, int P, int W, 
     return L;
 }
 
-// Restart-tiled warps (batched kernel): a warp docks 8 restarts of one ligand
-// at once, 4 lanes per restart, each lane owning 9 of the 36 torsion steps.
-constexpr int kTile = 8;          // restarts per warp tile
+// Restart-tiled warps (batched kernel): a warp docks several restarts of one
+// ligand at once, kLanesPerRestart lanes per restart by default (8 restart
+// slots, 9 of the 36 torsion steps per lane); the batched kernel also comes
+// with 2, 8 and 16 lanes per restart (16, 4 and 2 slots).  The flattening
+// kernel uses the same 4-lane step groups.
+constexpr int kTile = 8;          // restarts per warp tile at 4 lanes per restart
 constexpr int kLanesPerRestart = 4;
 constexpr int kStepsPerLane = 9;  // 36 / 4
 #ifndef LG_RT_POOL
 #define LG_RT_POOL 96
 #endif
-constexpr int kPoolCap = LG_RT_POOL;  // flagged clash pairs buffered per warp (all 8 restarts)
+constexpr int kPoolCap = LG_RT_POOL;  // flagged clash pairs buffered per warp (all its restarts)
 
 // Per-warp shared memory of a restart-tiled warp.
 struct LayoutRT {
     int o_axis, o_X, o_pool, o_mask, o_near, o_best, o_tcur, o_tbest, warp_bytes;
     int near_stride;  // bytes between the restart slots' near lists: an odd number of 4-byte words, so
-                      // the 8 slots' entries fall in 8 different banks
+                      // the slots' entries fall in different banks
 };
 
-__host__ __device__ inline LayoutRT make_layout_rt(int nmax, int rmax, int P, int want_pose) {
+__host__ __device__ inline LayoutRT make_layout_rt(int nmax, int rmax, int P, int want_pose, int slots = kTile) {
     LayoutRT L;
     nmax = (nmax + 3) & ~3;
     if (rmax < 1) rmax = 1;
     L.near_stride = ((nmax / 4) & 1) ? nmax : nmax + 4;
     int w = 0;
-    L.o_axis = w;  w = lg_align16(w + 16 * rmax * kTile);            // float4 [rmax][8]
-    L.o_X = w;     w = lg_align16(w + 12 * nmax * kTile);            // float [3][nmax][8]
+    L.o_axis = w;  w = lg_align16(w + 16 * rmax * slots);            // float4 [rmax][slots]
+    L.o_X = w;     w = lg_align16(w + 12 * nmax * slots);            // float [3][nmax][slots]
     L.o_pool = w;  w = lg_align16(w + 16 * kPoolCap);                // float4 (C, A2, B2, restart slot)
     L.o_mask = w;  w = lg_align16(w + 4 * 32);                       // uint32 clash bits per lane
-    L.o_near = w;  w = lg_align16(w + L.near_stride * kTile);        // uint8 [8][near_stride] near fixed atoms
+    L.o_near = w;  w = lg_align16(w + L.near_stride * slots);        // uint8 [slots][near_stride] near fixed atoms
     L.o_best = w;  w = lg_align16(w + (want_pose ? 12 * nmax : 0));  // float [3][nmax]
-    L.o_tcur = w;  w = lg_align16(w + P * rmax * kTile);             // uint8 [P*rmax][8]
+    L.o_tcur = w;  w = lg_align16(w + P * rmax * slots);             // uint8 [P*rmax][slots]
     L.o_tbest = w; w = lg_align16(w + P * rmax);                     // uint8 [P*rmax]
     L.warp_bytes = w;
     return L;
@@ -193,6 +196,7 @@ struct DockArgs {
     int cls;                   // with cls_off: the size class this launch docks
     int item_cap;              // > 0: dock only item_cap items evenly spread over the range (autotuning trials)
     int sort_classes;          // preparation: 1 = size class major, then cost; 0 = cost only
+    int lanes;                 // batched kernel: lanes per restart of the warps' tile (2, 4, 8 or 16)
     // L2 access-policy window of the launch (host side only: the docking
     // launches carry it as a launch attribute; l2_bytes = 0: none)
     const void *l2_base;
@@ -326,7 +330,7 @@ cudaError_t launch_flatten(const FlatArgs &f, int L, cudaStream_t s);
 cudaError_t launch_serve_loop(const DockArgs &a, const LoopArgs &la, int grid, int smem, cudaStream_t s);
 cudaError_t loop_kernel_attributes(int W, int smem, int *ctas_per_sm, bool ranking, bool rigid);
 int checks_collect(cudaStream_t s, int rec[4]);  // bounds-check record of a debug build (0 otherwise)
-cudaError_t dock_kernel_attributes(int W, int smem, int *ctas_per_sm, bool ranking, bool rigid, bool trace);
+cudaError_t dock_kernel_attributes(int W, int smem, int *ctas_per_sm, bool ranking, bool rigid, bool trace, int lanes = 4);
 cudaError_t multi_kernel_attributes(int W, int smem, int *ctas_per_sm, bool ranking, bool rigid);
 cudaError_t plain_kernel_attributes(int smem);
 

@@ -776,25 +776,46 @@ __global__ void __launch_bounds__(1024) k_dock_plain(const __grid_constant__ Doc
 }
 
 // ================================================================== restart-tiled form
+// Restart tile of a warp: LPR lanes per restart (2, 4, 8 or 16) and 32 / LPR
+// restart slots; lane g of a restart owns the steps g, g + LPR, ...
+// (ceil(36 / LPR) of them).  With 8 or 16 lanes the last round is ragged: its
+// missing steps are evaluated at step 0's angle and never chosen.  Sums whose
+// rounding reaches a result (pose score, rigid candidates and centroid, the
+// ranking's geometric score) keep one order in every tile -- partial sums s_g
+// over atoms i = g (mod 4) in order, combined as (s0 + s1) + (s2 + s3) -- and
+// a step's score sums its moving atoms in order in one lane, so every tile
+// gives the same bits.
+template <int LPR>
+struct Rt {
+    static_assert(LPR == 2 || LPR == 4 || LPR == 8 || LPR == 16, "lanes per restart");
+    static constexpr int slots = 32 / LPR;
+    static constexpr int steps = (LG_ANGLE_STEPS + LPR - 1) / LPR;
+    static constexpr bool ragged = steps * LPR != LG_ANGLE_STEPS;
+    static constexpr int first_missing = LG_ANGLE_STEPS - LPR * (steps - 1);  // lanes g >= this lack the last step
+    static constexpr unsigned gbits = (1u << LPR) - 1u;
+    static constexpr int max_warps = LPR > 4 ? LPR : 4;  // warps per CTA the launch bounds allow
+};
+
 struct RtView {
-    float4 *axis;          // [rmax][8]
-    float *Xx, *Xy, *Xz;   // [nmax][8]
+    float4 *axis;          // [rmax][slots]
+    float *Xx, *Xy, *Xz;   // [nmax][slots]
     float4 *pool;          // [kPoolCap] flagged clash pairs (C, A2, B2, restart slot)
     unsigned *mask;        // [32] clash bits of each lane's steps
-    uint8_t *near;         // [8][nstride] fixed atoms that can come within d_clash
+    uint8_t *near;         // [slots][nstride] fixed atoms that can come within d_clash
     int nstride;
     float *Bx, *By, *Bz;   // [nmax] best pose of the warp
-    uint8_t *tcur;         // [P*R][8]
+    uint8_t *tcur;         // [P*R][slots]
     uint8_t *tbest;        // [P*R]
 };
 
+template <int LPR>
 __device__ __forceinline__ RtView rt_view(char *sm, const Layout &L, const LayoutRT &T, int w) {
     char *b = sm + L.cta_bytes + w * T.warp_bytes;
     RtView v;
     v.axis = (float4 *)(b + T.o_axis);
     v.Xx = (float *)(b + T.o_X);
-    v.Xy = v.Xx + L.nmax * kTile;
-    v.Xz = v.Xy + L.nmax * kTile;
+    v.Xy = v.Xx + L.nmax * Rt<LPR>::slots;
+    v.Xz = v.Xy + L.nmax * Rt<LPR>::slots;
     v.pool = (float4 *)(b + T.o_pool);
     v.mask = (unsigned *)(b + T.o_mask);
     v.near = (uint8_t *)(b + T.o_near);
@@ -807,53 +828,95 @@ __device__ __forceinline__ RtView rt_view(char *sm, const Layout &L, const Layou
     return v;
 }
 
+// K sums over atoms 0..N-1 in the tile-independent order: add(i, acc) adds
+// atom i's K terms; s_g over i = g (mod 4) in order, combined as
+// (s0 + s1) + (s2 + s3).  Lanes with on = false add nothing.  Every lane of
+// the restart gets the sums.  All lanes of the warp call it.
+template <int LPR, int K, typename T, typename F>
+__device__ __forceinline__ void sum4(int g, int N, bool on, T (&out)[K], F &&add) {
+    T a[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) a[k] = T(0);
+    if constexpr (LPR == 2) {  // lane g holds s_g and s_(g+2)
+        T b[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) b[k] = T(0);
+        if (on) {
+            for (int i = g; i < N; i += 4) add(i, a);
+            for (int i = g + 2; i < N; i += 4) add(i, b);
+        }
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            a[k] += __shfl_xor_sync(LG_FULL, a[k], 1);
+            b[k] += __shfl_xor_sync(LG_FULL, b[k], 1);
+            out[k] = a[k] + b[k];
+        }
+    } else {  // lanes g < 4 hold s_g
+        if (on && g < 4)
+            for (int i = g; i < N; i += 4) add(i, a);
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            a[k] += __shfl_xor_sync(LG_FULL, a[k], 1);
+            a[k] += __shfl_xor_sync(LG_FULL, a[k], 2);
+            if constexpr (LPR > 4) a[k] = __shfl_sync(LG_FULL, a[k], (int)(threadIdx.x & 31) & ~(LPR - 1));
+            out[k] = a[k];
+        }
+    }
+}
+
 // Evaluate the pooled flagged pairs: in each round every restart group takes
 // one entry (of any restart) and each of its lanes ORs the clash bits of its
-// own 9 steps into that restart's mask word for the same lane position.
+// own steps into that restart's mask word for the same lane position.
+template <int LPR>
 __device__ __forceinline__ void flush_pool(const RtView &v, int rs, int g, int &pc, const float *cs, const float *sn,
                                            float dc2) {
     __syncwarp();
-    for (int base = 0; base < pc; base += kTile) {
+    for (int base = 0; base < pc; base += Rt<LPR>::slots) {
         const int e = base + rs;
         if (e < pc) {
             const float4 q = v.pool[e];
             unsigned bits = 0;
 #pragma unroll
-            for (int j = 0; j < kStepsPerLane; ++j) bits |= (unsigned)pair_clash(q.x, q.y, q.z, cs[j], sn[j], dc2) << j;
-            if (bits) atomicOr(&v.mask[kLanesPerRestart * __float_as_int(q.w) + g], bits);
+            for (int j = 0; j < Rt<LPR>::steps; ++j)
+                bits |= (unsigned)pair_clash(q.x, q.y, q.z, cs[j], sn[j], dc2) << j;
+            if (bits) atomicOr(&v.mask[LPR * __float_as_int(q.w) + g], bits);
         }
     }
     __syncwarp();
     pc = 0;
 }
 
-// One torsion decision for the warp's 8 restarts.  Lane = 4*rs + g: restart
-// slot rs, steps g, g+4, ..., g+32 (cosines cs[], sines sn[]) -- the 4 lanes
+// One torsion decision for the warp's restart slots.  Lane = LPR*rs + g:
+// restart slot rs, steps g, g+LPR, ... (cosines cs[], sines sn[]) -- the lanes
 // of a restart score neighbouring steps in the same instruction.  Returns the
 // step chosen for the lane's restart.
+template <int LPR>
 __device__ __forceinline__ int sweep_bond_rt(float dc2g, const GridK &G, const CtaView &cv, const RtView &v, int N, int R,
                                              int k, int rs, int g, bool valid, const float *cs, const float *sn,
                                              bool want_rank, int &jr) {
+    using T = Rt<LPR>;
+    constexpr int ST = T::slots;
     const int b = cv.rch[k], a = cv.par[b], e = cv.rend[k];
     const int m = e - b - 1;
     jr = 1;
     if (m <= 0) return 0;  // nothing moves: every step scores 0, step 0 wins
 
-    const float xbx = v.Xx[b * kTile + rs], xby = v.Xy[b * kTile + rs], xbz = v.Xz[b * kTile + rs];
-    const float3 u = unit_axis(v.axis[k * kTile + rs]);
+    const float xbx = v.Xx[b * ST + rs], xby = v.Xy[b * ST + rs], xbz = v.Xz[b * ST + rs];
+    const float3 u = unit_axis(v.axis[k * ST + rs]);
     const float c0 = 0.5f * G.gmax, dc2 = dc2g;  // (n - 1) / 2, exact
     const int nF = N - (e - b);
-    const int lane = kLanesPerRestart * rs + g;
-    const unsigned gmask = 0xFu << (kLanesPerRestart * rs), below = (1u << lane) - 1u;
+    const int lane = LPR * rs + g;
+    const unsigned gmask = T::gbits << (LPR * rs), below = (1u << lane) - 1u;
 
     // Every moving atom stays at its distance from xb, so the subtree's circles
     // lie in the ball of radius max |x_i - xb| about xb: when that ball is in
-    // the grid box for all 8 restarts, no lookup of this decision needs clamping.
-    // The same loop bounds the subtree in cylindrical coordinates about the
-    // axis: axial t = (x - xb).u in [tlo, thi], squared radius in [q2lo, q2hi].
+    // the grid box for all restarts of the warp, no lookup of this decision
+    // needs clamping.  The same loop bounds the subtree in cylindrical
+    // coordinates about the axis: axial t = (x - xb).u in [tlo, thi], squared
+    // radius in [q2lo, q2hi].
     float rho2 = 0.0f, tlo = INFINITY, thi = -INFINITY, q2lo = INFINITY, q2hi = 0.0f;
-    for (int i = b + 1 + g; i < e; i += kLanesPerRestart) {
-        const float dx = v.Xx[i * kTile + rs] - xbx, dy = v.Xy[i * kTile + rs] - xby, dz = v.Xz[i * kTile + rs] - xbz;
+    for (int i = b + 1 + g; i < e; i += LPR) {
+        const float dx = v.Xx[i * ST + rs] - xbx, dy = v.Xy[i * ST + rs] - xby, dz = v.Xz[i * ST + rs] - xbz;
         const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz)), t = fmaf(u.x, dx, fmaf(u.y, dy, u.z * dz));
         const float q2 = fmaf(-t, t, d2);
         rho2 = fmaxf(rho2, d2);
@@ -863,7 +926,7 @@ __device__ __forceinline__ int sweep_bond_rt(float dc2g, const GridK &G, const C
         q2hi = fmaxf(q2hi, q2);
     }
 #pragma unroll
-    for (int o = 1; o < kLanesPerRestart; o <<= 1) {
+    for (int o = 1; o < LPR; o <<= 1) {
         rho2 = fmaxf(rho2, __shfl_xor_sync(LG_FULL, rho2, o));
         tlo = fminf(tlo, __shfl_xor_sync(LG_FULL, tlo, o));
         thi = fmaxf(thi, __shfl_xor_sync(LG_FULL, thi, o));
@@ -891,14 +954,14 @@ __device__ __forceinline__ int sweep_bond_rt(float dc2g, const GridK &G, const C
     const float rlo = fmaxf(sqrtf(fmaxf(q2lo, 0.0f)) - dm, 0.0f), rhi = sqrtf(q2hi) + dm;
     q2lo = rlo > 0.0f ? rlo * rlo : -INFINITY;  // atoms on the axis (rounding may make q2 < 0) stay in
     q2hi = rhi * rhi;
-    int ncnt = 0;  // near fixed atoms of this restart (same in its 4 lanes)
-    for (int jb = 0; jb < nF; jb += kLanesPerRestart) {
+    int ncnt = 0;  // near fixed atoms of this restart (same in all its lanes)
+    for (int jb = 0; jb < nF; jb += LPR) {
         const int jj = jb + g;
         bool nr = false;
         int j = 0;
         if (valid && jj < nF) {
             j = jj < b ? jj : jj + (e - b);
-            const float dx = v.Xx[j * kTile + rs] - xbx, dy = v.Xy[j * kTile + rs] - xby, dz = v.Xz[j * kTile + rs] - xbz;
+            const float dx = v.Xx[j * ST + rs] - xbx, dy = v.Xy[j * ST + rs] - xby, dz = v.Xz[j * ST + rs] - xbz;
             const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz)), t = fmaf(u.x, dx, fmaf(u.y, dy, u.z * dz));
             const float q2 = fmaf(-t, t, d2);
             nr = d2 < rlim2 && t > tlo && t < thi && q2 > q2lo && q2 < q2hi;
@@ -912,21 +975,21 @@ __device__ __forceinline__ int sweep_bond_rt(float dc2g, const GridK &G, const C
     const int nnear = (int)__reduce_max_sync(LG_FULL, (unsigned)ncnt);
 
     // Clash pairs of moving atom i (circle C): pairs that can come within
-    // d_clash somewhere on the circle are pooled over the 8 restarts and
+    // d_clash somewhere on the circle are pooled over the warp's restarts and
     // evaluated step by step.
     int pc = 0;  // pooled pairs (warp-uniform)
     auto pool_pairs = [&](int i, const Circle &C) {
         const int excl = (cv.par[i] == b) ? a : -1;  // two bonds apart through the bond itself
-        for (int jb = 0; jb < nnear; jb += kLanesPerRestart) {
-            if (pc > kPoolCap - 32) flush_pool(v, rs, g, pc, cs, sn, dc2);
+        for (int jb = 0; jb < nnear; jb += LPR) {
+            if (pc > kPoolCap - 32) flush_pool<LPR>(v, rs, g, pc, cs, sn, dc2);
             const int jj = jb + g;
             PairC q;
             q.near = false;
             if (jj < ncnt) {
                 const int j = v.near[rs * v.nstride + jj];
                 if (j != excl)
-                    q = pair_coeffs(C.px, C.py, C.pz, C.e1x, C.e1y, C.e1z, C.e2x, C.e2y, C.e2z, C.r2, v.Xx[j * kTile + rs],
-                                    v.Xy[j * kTile + rs], v.Xz[j * kTile + rs], dc2);
+                    q = pair_coeffs(C.px, C.py, C.pz, C.e1x, C.e1y, C.e1z, C.e2x, C.e2y, C.e2z, C.r2, v.Xx[j * ST + rs],
+                                    v.Xy[j * ST + rs], v.Xz[j * ST + rs], dc2);
             }
             const unsigned bal = __ballot_sync(LG_FULL, q.near);
             if (q.near) v.pool[LG_IDX(pc + __popc(bal & below), kPoolCap, kChkPool)] = make_float4(q.C, q.A2, q.B2, __int_as_float(rs));
@@ -934,46 +997,48 @@ __device__ __forceinline__ int sweep_bond_rt(float dc2g, const GridK &G, const C
         }
     };
 
-    // Overlap scores of the lane's 9 steps over the moving atoms (in order),
+    // Overlap scores of the lane's steps over the moving atoms (in order),
     // and each atom's clash pairs while its cell loads are in flight.  Lanes
     // of an idle slot issue no loads.
-    float acc[kStepsPerLane];
+    float acc[T::steps];
 #pragma unroll
-    for (int j = 0; j < kStepsPerLane; ++j) acc[j] = 0.0f;
+    for (int j = 0; j < T::steps; ++j) acc[j] = 0.0f;
     for (int i = b + 1; i < e; ++i) {
-        const Circle C = make_circle(v.Xx[i * kTile + rs], v.Xy[i * kTile + rs], v.Xz[i * kTile + rs], xbx, xby, xbz, u,
-                                     c0, G.gmax);
+        const Circle C = make_circle(v.Xx[i * ST + rs], v.Xy[i * ST + rs], v.Xz[i * ST + rs], xbx, xby, xbz, u, c0,
+                                     G.gmax);
         if (!valid) {
         } else if (all_in) {
 #pragma unroll
-            for (int j = 0; j < kStepsPerLane; ++j) {
+            for (int j = 0; j < T::steps; ++j) {
                 const float3 q = circle_index(C.Px, C.Py, C.Pz, C.e1x, C.e1y, C.e1z, C.e2x, C.e2y, C.e2z, cs[j], sn[j]);
                 acc[j] += lookup_in(G, q.x, q.y, q.z);
             }
         } else {
 #pragma unroll
-            for (int j = 0; j < kStepsPerLane; ++j) {
+            for (int j = 0; j < T::steps; ++j) {
                 const float3 q = circle_index(C.Px, C.Py, C.Pz, C.e1x, C.e1y, C.e1z, C.e2x, C.e2y, C.e2z, cs[j], sn[j]);
                 acc[j] += lookup_clamped(G, q.x, q.y, q.z);
             }
         }
         if (nnear > 0) pool_pairs(i, C);
     }
-    flush_pool(v, rs, g, pc, cs, sn, dc2);
-    unsigned clash = v.mask[lane];  // bit j: step 4j + g clashes
+    flush_pool<LPR>(v, rs, g, pc, cs, sn, dc2);
+    unsigned clash = v.mask[lane];  // bit j: step LPR*j + g clashes
     if (g == 0) clash &= ~1u;        // step 0 (the current pose) is always admissible
+    const bool short_lane = T::ragged && g >= T::first_missing;  // no last step
+    if (short_lane) clash |= 1u << (T::steps - 1);
 
     // highest-scoring admissible step of the restart, lowest step on ties
     float bs = -INFINITY;
     int bt = 1024;
 #pragma unroll
-    for (int j = 0; j < kStepsPerLane; ++j)
+    for (int j = 0; j < T::steps; ++j)
         if (!((clash >> j) & 1u) && acc[j] > bs) {
             bs = acc[j];
-            bt = kLanesPerRestart * j + g;
+            bt = LPR * j + g;
         }
 #pragma unroll
-    for (int o = 1; o < kLanesPerRestart; o <<= 1) {
+    for (int o = 1; o < LPR; o <<= 1) {
         const float os = __shfl_xor_sync(LG_FULL, bs, o);
         const int ot = __shfl_xor_sync(LG_FULL, bt, o);
         if (better(os, ot, bs, bt)) {
@@ -985,90 +1050,78 @@ __device__ __forceinline__ int sweep_bond_rt(float dc2g, const GridK &G, const C
     if (want_rank) {  // steps ranked before the chosen one, admissible or not
         int cnt = 0;
 #pragma unroll
-        for (int j = 0; j < kStepsPerLane; ++j)
-            cnt += (acc[j] > bs || (acc[j] == bs && kLanesPerRestart * j + g < t)) ? 1 : 0;
-        cnt += __shfl_xor_sync(LG_FULL, cnt, 1);
-        cnt += __shfl_xor_sync(LG_FULL, cnt, 2);
+        for (int j = 0; j < T::steps; ++j)
+            if (!(short_lane && j == T::steps - 1))
+                cnt += (acc[j] > bs || (acc[j] == bs && LPR * j + g < t)) ? 1 : 0;
+#pragma unroll
+        for (int o = 1; o < LPR; o <<= 1) cnt += __shfl_xor_sync(LG_FULL, cnt, o);
         jr = 1 + cnt;
     }
     if (t != 0) {
         const float c = c_cos[t], s = c_sin[t];
-        for (int i = b + 1 + g; i < e; i += kLanesPerRestart) {
-            const float3 x = rotate_point(v.Xx[i * kTile + rs], v.Xy[i * kTile + rs], v.Xz[i * kTile + rs], xbx, xby,
-                                          xbz, u, c, s);
-            v.Xx[i * kTile + rs] = x.x;
-            v.Xy[i * kTile + rs] = x.y;
-            v.Xz[i * kTile + rs] = x.z;
+        for (int i = b + 1 + g; i < e; i += LPR) {
+            const float3 x = rotate_point(v.Xx[i * ST + rs], v.Xy[i * ST + rs], v.Xz[i * ST + rs], xbx, xby, xbz, u,
+                                          c, s);
+            v.Xx[i * ST + rs] = x.x;
+            v.Xy[i * ST + rs] = x.y;
+            v.Xz[i * ST + rs] = x.z;
         }
-        for (int kk = k + 1 + g; kk < R; kk += kLanesPerRestart)
-            if (cv.rch[kk] < e) v.axis[kk * kTile + rs] = rotate_vec(v.axis[kk * kTile + rs], u, c, s);
+        for (int kk = k + 1 + g; kk < R; kk += LPR)
+            if (cv.rch[kk] < e) v.axis[kk * ST + rs] = rotate_vec(v.axis[kk * ST + rs], u, c, s);
     }
     __syncwarp();
     return t;
 }
 
-// Rigid greedy moves of the warp's restart slots after torsion pass ps: lane g of
-// a restart scores all 13 candidates on atoms i = g (mod 4), in order, with
-// FP32 sums s_g; a candidate's score is (s0 + s1) + (s2 + s3) of the FP32
-// overlap lookups of the atoms at their moved positions; the best (highest
-// score, lowest candidate) moves the atoms and turns the bond axes.
+// Rigid greedy moves of the warp's restart slots after torsion pass ps: the
+// 13 candidates are scored by sums over atoms in the tile-independent order
+// (FP32 overlap lookups of the atoms at their moved positions); the best
+// (highest score, lowest candidate) moves the atoms and turns the bond axes.
+template <int LPR>
 __device__ __forceinline__ bool rigid_moves_rt(const DockArgs &A, float rigid_shift_g, const GridK &Go, const OutDev &O,
-                                               const RtView &v,
-                                               int l, int r, int ps, int N, int R, int rs, int g, bool valid) {
+                                               const RtView &v, int l, int r, int ps, int N, int R, int rs, int g,
+                                               bool valid) {
+    constexpr int ST = Rt<LPR>::slots;
     const float c0 = 0.5f * Go.gmax, dg = rigid_shift_g, ca = c_cos[1], sa = c_sin[1];
     bool moved = false;
     for (int j = 0; j < A.rigid_steps; ++j) {
-        float sx = 0.0f, sy = 0.0f, sz = 0.0f;  // centroid: sums over atoms i = g (mod 4), (s0 + s1) + (s2 + s3)
-        for (int i = g; i < N; i += kLanesPerRestart) {
-            sx += v.Xx[i * kTile + rs];
-            sy += v.Xy[i * kTile + rs];
-            sz += v.Xz[i * kTile + rs];
-        }
-        sx += __shfl_xor_sync(LG_FULL, sx, 1);
-        sy += __shfl_xor_sync(LG_FULL, sy, 1);
-        sz += __shfl_xor_sync(LG_FULL, sz, 1);
-        sx += __shfl_xor_sync(LG_FULL, sx, 2);
-        sy += __shfl_xor_sync(LG_FULL, sy, 2);
-        sz += __shfl_xor_sync(LG_FULL, sz, 2);
-        const float cx = sx / (float)N, cy = sy / (float)N, cz = sz / (float)N;
+        float cen[3];
+        sum4<LPR>(g, N, true, cen, [&](int i, float(&s)[3]) {
+            s[0] += v.Xx[i * ST + rs];
+            s[1] += v.Xy[i * ST + rs];
+            s[2] += v.Xz[i * ST + rs];
+        });
+        const float cx = cen[0] / (float)N, cy = cen[1] / (float)N, cz = cen[2] / (float)N;
         float Gc[kRigidCandidates];
+        sum4<LPR>(g, N, valid, Gc, [&](int i, float(&s)[kRigidCandidates]) {  // idle slots issue no loads
+            const float x = v.Xx[i * ST + rs], y = v.Xy[i * ST + rs], z = v.Xz[i * ST + rs];
 #pragma unroll
-        for (int c = 0; c < kRigidCandidates; ++c) Gc[c] = 0.0f;
-        if (valid)  // idle slots issue no loads
-            for (int i = g; i < N; i += kLanesPerRestart) {
-                const float x = v.Xx[i * kTile + rs], y = v.Xy[i * kTile + rs], z = v.Xz[i * kTile + rs];
-#pragma unroll
-                for (int c = 0; c < kRigidCandidates; ++c) {
-                    const float3 q = rigid_candidate(c, x, y, z, cx, cy, cz, dg, ca, sa);
-                    Gc[c] += lookup_clamped(Go, q.x + c0, q.y + c0, q.z + c0);
-                }
+            for (int c = 0; c < kRigidCandidates; ++c) {
+                const float3 q = rigid_candidate(c, x, y, z, cx, cy, cz, dg, ca, sa);
+                s[c] += lookup_clamped(Go, q.x + c0, q.y + c0, q.z + c0);
             }
+        });
         float bG = -INFINITY;
         int bC = kRigidCandidates;
 #pragma unroll
-        for (int c = 0; c < kRigidCandidates; ++c) {
-            float G = Gc[c];
-            G += __shfl_xor_sync(LG_FULL, G, 1);
-            G += __shfl_xor_sync(LG_FULL, G, 2);
-            if (G > bG) {  // ascending candidates: ties keep the lower one
-                bG = G;
+        for (int c = 0; c < kRigidCandidates; ++c)
+            if (Gc[c] > bG) {  // ascending candidates: ties keep the lower one
+                bG = Gc[c];
                 bC = c;
             }
-        }
         if (valid && g == 0 && O.restart_rigid)
             O.restart_rigid[(((size_t)l * A.S + r) * A.P + ps) * A.rigid_steps + j] = (uint8_t)bC;
         __syncwarp();
         moved = moved || bC != 0;
         if (bC != 0) {
-            for (int i = g; i < N; i += kLanesPerRestart) {
-                const float3 y = rigid_candidate(bC, v.Xx[i * kTile + rs], v.Xy[i * kTile + rs], v.Xz[i * kTile + rs],
-                                                 cx, cy, cz, dg, ca, sa);
-                v.Xx[i * kTile + rs] = y.x;
-                v.Xy[i * kTile + rs] = y.y;
-                v.Xz[i * kTile + rs] = y.z;
+            for (int i = g; i < N; i += LPR) {
+                const float3 y = rigid_candidate(bC, v.Xx[i * ST + rs], v.Xy[i * ST + rs], v.Xz[i * ST + rs], cx, cy,
+                                                 cz, dg, ca, sa);
+                v.Xx[i * ST + rs] = y.x;
+                v.Xy[i * ST + rs] = y.y;
+                v.Xz[i * ST + rs] = y.z;
             }
-            for (int k = g; k < R; k += kLanesPerRestart)
-                v.axis[k * kTile + rs] = rigid_candidate_vec(bC, v.axis[k * kTile + rs], ca, sa);
+            for (int k = g; k < R; k += LPR) v.axis[k * ST + rs] = rigid_candidate_vec(bC, v.axis[k * ST + rs], ca, sa);
         }
         __syncwarp();
     }
@@ -1077,16 +1130,18 @@ __device__ __forceinline__ bool rigid_moves_rt(const DockArgs &A, float rigid_sh
 
 // kRank: pose ranking on; kRigid: rigid refinement on; kTrace: decision
 // ranks recorded (separate instantiations, so the plain best-restart form
-// carries none of their code)
-template <bool kRank, bool kRigid, bool kTrace = false>
+// carries none of their code); LPR: lanes per restart of the warp's tile
+template <bool kRank, bool kRigid, bool kTrace, int LPR>
 __device__ __forceinline__ void dock_ligand_rt(const DockArgs &A, const PocketDev &Pk, const OutDev &O, const LigSrc &Q, int l,
                                                char *sm) {
+    using T = Rt<LPR>;
+    constexpr int ST = T::slots;
     if (O.status[l] != LG_OK) return;  // rejected by the preparation kernel (uniform)
     const Layout &Ly = A.ly;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
-    const int rs = lane / kLanesPerRestart, g = lane % kLanesPerRestart;
+    const int rs = lane / LPR, g = lane % LPR;
     const CtaView cv = cta_view(sm, Ly);
-    const RtView v = rt_view(sm, Ly, A.lrt, warp);
+    const RtView v = rt_view<LPR>(sm, Ly, A.lrt, warp);
     const BatchDev &B = Q.batch;
     const int a0 = B.atom_off[l], N = B.atom_off[l + 1] - a0;
     const int r0 = B.rot_off[l], R = B.rot_off[l + 1] - r0;
@@ -1094,17 +1149,18 @@ __device__ __forceinline__ void dock_ligand_rt(const DockArgs &A, const PocketDe
     stage_ligand(A, B, Pk, cv, l, a0, N, r0, R);
     __syncthreads();
 
-    float cs[kStepsPerLane], sn[kStepsPerLane];
+    float cs[T::steps], sn[T::steps];
 #pragma unroll
-    for (int j = 0; j < kStepsPerLane; ++j) {
-        cs[j] = c_cos[kLanesPerRestart * j + g];
-        sn[j] = c_sin[kLanesPerRestart * j + g];
+    for (int j = 0; j < T::steps; ++j) {
+        const int t = LPR * j + g < LG_ANGLE_STEPS ? LPR * j + g : 0;  // a ragged round's missing step: step 0's angle
+        cs[j] = c_cos[t];
+        sn[j] = c_sin[t];
     }
     const uint64_t uid = B.uid[l];
     const uint2 key = make_uint2(A.seed_lo, A.seed_hi);
     const GridK Go = grid_k(Pk, Pk.cell_o), Gve = grid_k(Pk, Pk.cell_ve);
     // Restart streaming: warp w owns restarts w, w + W, w + 2W, ... and runs
-    // them through its 8 restart slots.  All slots take the same bond at the
+    // them through its restart slots.  All slots take the same bond at the
     // same time, pass after pass; a slot whose restart has finished (P passes,
     // or converged: R decisions in a row without a move, or with rigid moves a
     // pass without one -- every later decision would repeat step 0) is emptied
@@ -1113,7 +1169,7 @@ __device__ __forceinline__ void dock_ligand_rt(const DockArgs &A, const PocketDe
     // does not depend on its slot, so results are those of restarts run alone.
     int r = warp + W * rs;  // this slot's restart (-1: idle)
     if (r >= S) r = -1;
-    int qnext = kTile;      // next index into the warp's restart list (uniform)
+    int qnext = ST;         // next index into the warp's restart list (uniform)
     int pc = 0;             // passes this slot's restart has completed
     int zrun = 0;           // its decisions in a row without a move
     bool movedp = true;     // whether it moved in its last pass
@@ -1121,20 +1177,20 @@ __device__ __forceinline__ void dock_ligand_rt(const DockArgs &A, const PocketDe
     double bestE = INFINITY;
     int bestR = -1;
     for (;;) {
-        // 1. initial pose of newly filled slots (the 4 lanes of a slot split atoms and bonds)
+        // 1. initial pose of newly filled slots (the lanes of a slot split atoms and bonds)
         if (fresh) {
             const Pose pose = restart_pose(uid, (uint32_t)(r >= 0 ? r : 0), key, Pk.n_pp);
             const float4 pp = __ldg(Pk.pp + pose.pp);
-            for (int i = g; i < N; i += kLanesPerRestart) {
+            for (int i = g; i < N; i += LPR) {
                 const float3 x = rot_add(pose.R, cv.d0x[i], cv.d0y[i], cv.d0z[i], pp.x, pp.y, pp.z);
-                v.Xx[i * kTile + rs] = x.x;
-                v.Xy[i * kTile + rs] = x.y;
-                v.Xz[i * kTile + rs] = x.z;
+                v.Xx[i * ST + rs] = x.x;
+                v.Xy[i * ST + rs] = x.y;
+                v.Xz[i * ST + rs] = x.z;
             }
-            for (int k = g; k < R; k += kLanesPerRestart) {
+            for (int k = g; k < R; k += LPR) {
                 const float4 d = cv.dv[k];
                 const float3 w = rot_vec(pose.R, d.x, d.y, d.z);
-                v.axis[k * kTile + rs] = make_float4(w.x, w.y, w.z, 0.0f);
+                v.axis[k * ST + rs] = make_float4(w.x, w.y, w.z, 0.0f);
             }
             fresh = false;
         }
@@ -1145,7 +1201,7 @@ __device__ __forceinline__ void dock_ligand_rt(const DockArgs &A, const PocketDe
         const bool done = active && (pc >= P || conv);
         if (__any_sync(LG_FULL, done)) {
             if (done) {
-                for (int q = pc * R + g; q < PR; q += kLanesPerRestart) v.tcur[q * kTile + rs] = 0;
+                for (int q = pc * R + g; q < PR; q += LPR) v.tcur[q * ST + rs] = 0;
                 if (kTrace && g == 0) {  // skipped passes repeat the last one, marked skipped
                     uint8_t *dr = O.decision_rank + (size_t)S * P * r0 + (size_t)r * PR;
                     for (int q = pc * R; q < PR; ++q) dr[q] = dr[q - R] | kRankSkipped;
@@ -1155,52 +1211,54 @@ __device__ __forceinline__ void dock_ligand_rt(const DockArgs &A, const PocketDe
                         O.restart_rigid[((size_t)l * S + r) * P * A.rigid_steps + q] = 0;
             }
             __syncwarp();
-            // pose score: FP32 per-atom terms; FP64 sums s_g over atoms i = g
-            // (mod 4) in order, combined as (s0 + s1) + (s2 + s3)
-            double E = 0.0;
-            if (done)
-                for (int i = g; i < N; i += kLanesPerRestart) {
-                    const float2 wq = cv.wq[i];
-                    E += (double)atom_energy(Pk, Gve, v.Xx[i * kTile + rs], v.Xy[i * kTile + rs], v.Xz[i * kTile + rs],
-                                             wq.x, wq.y);
-                }
-            E += __shfl_xor_sync(LG_FULL, E, 1);
-            E += __shfl_xor_sync(LG_FULL, E, 2);
+            // pose score: FP32 per-atom terms, FP64 sums in the tile-independent order
+            double Es[1];
+            sum4<LPR>(g, N, done, Es, [&](int i, double(&s)[1]) {
+                const float2 wq = cv.wq[i];
+                s[0] += (double)atom_energy(Pk, Gve, v.Xx[i * ST + rs], v.Xy[i * ST + rs], v.Xz[i * ST + rs], wq.x,
+                                            wq.y);
+            });
+            const double E = Es[0];
             if (done) {
                 if (O.restart_score && g == 0) O.restart_score[(size_t)l * S + r] = E;
                 if (O.restart_tors)
-                    for (int t = g; t < PR; t += kLanesPerRestart)
-                        O.restart_tors[(size_t)S * P * r0 + (size_t)r * PR + t] = v.tcur[t * kTile + rs];
+                    for (int t = g; t < PR; t += LPR)
+                        O.restart_tors[(size_t)S * P * r0 + (size_t)r * PR + t] = v.tcur[t * ST + rs];
                 if (kRank) {  // keep the restart for the ranking step
                     const int slot = rank_slot(A, blockIdx.x);
                     float *x = A.scr.rk_pose + rk_pose_off(A, slot, r);
-                    for (int i = g; i < N; i += kLanesPerRestart) {
-                        x[3 * i] = v.Xx[i * kTile + rs];
-                        x[3 * i + 1] = v.Xy[i * kTile + rs];
-                        x[3 * i + 2] = v.Xz[i * kTile + rs];
+                    for (int i = g; i < N; i += LPR) {
+                        x[3 * i] = v.Xx[i * ST + rs];
+                        x[3 * i + 1] = v.Xy[i * ST + rs];
+                        x[3 * i + 2] = v.Xz[i * ST + rs];
                     }
-                    for (int t = g; t < PR; t += kLanesPerRestart)
-                        A.scr.rk_tors[((size_t)slot * S + r) * P * Ly.rmax + t] = v.tcur[t * kTile + rs];
+                    for (int t = g; t < PR; t += LPR)
+                        A.scr.rk_tors[((size_t)slot * S + r) * P * Ly.rmax + t] = v.tcur[t * ST + rs];
                     if (g == 0) A.scr.rk_E[(size_t)slot * S + r] = E;
                 }
             }
             if (kRank) {  // the restart's geometric score and centroid for the ranking step
-                float4 gq = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-                if (done) gq = rank_geo_partial(Go, Pk.c0, v.Xx + rs, v.Xy + rs, v.Xz + rs, kTile, N, g);
-                gq = rank_geo_combine(gq);
+                float gq[4];
+                sum4<LPR>(g, N, done, gq, [&](int i, float(&s)[4]) {
+                    const float x = v.Xx[i * ST + rs], y = v.Xy[i * ST + rs], z = v.Xz[i * ST + rs];
+                    s[0] += lookup_clamped(Go, x + Pk.c0, y + Pk.c0, z + Pk.c0);
+                    s[1] += x;
+                    s[2] += y;
+                    s[3] += z;
+                });
                 if (done && g == 0) {
                     const size_t q = (size_t)rank_slot(A, blockIdx.x) * S + r;
-                    A.scr.rk_G[q] = gq.x;
-                    A.scr.rk_cen[3 * q] = gq.y;
-                    A.scr.rk_cen[3 * q + 1] = gq.z;
-                    A.scr.rk_cen[3 * q + 2] = gq.w;
+                    A.scr.rk_G[q] = gq[0];
+                    A.scr.rk_cen[3 * q] = gq[1];
+                    A.scr.rk_cen[3 * q + 1] = gq[2];
+                    A.scr.rk_cen[3 * q + 2] = gq[3];
                 }
             }
             // best of the finished restarts (lowest E, then lowest restart), then of the warp
             double te = done ? E : INFINITY;
             int tr = done ? r : 0x7fffffff, ts = rs;
 #pragma unroll
-            for (int o = kLanesPerRestart; o < 32; o <<= 1) {
+            for (int o = LPR; o < 32; o <<= 1) {
                 const double oe = __shfl_xor_sync(LG_FULL, te, o);
                 const int orr = __shfl_xor_sync(LG_FULL, tr, o), os = __shfl_xor_sync(LG_FULL, ts, o);
                 if (oe < te || (oe == te && orr < tr)) {
@@ -1212,19 +1270,19 @@ __device__ __forceinline__ void dock_ligand_rt(const DockArgs &A, const PocketDe
             if (tr != 0x7fffffff && (bestR < 0 || te < bestE || (te == bestE && tr < bestR))) {
                 bestE = te;
                 bestR = tr;
-                for (int t = lane; t < PR; t += 32) v.tbest[t] = v.tcur[t * kTile + ts];
+                for (int t = lane; t < PR; t += 32) v.tbest[t] = v.tcur[t * ST + ts];
                 if (Ly.want_pose)
                     for (int i = lane; i < N; i += 32) {
-                        v.Bx[i] = v.Xx[i * kTile + ts];
-                        v.By[i] = v.Xy[i * kTile + ts];
-                        v.Bz[i] = v.Xz[i * kTile + ts];
+                        v.Bx[i] = v.Xx[i * ST + ts];
+                        v.By[i] = v.Xy[i * ST + ts];
+                        v.Bz[i] = v.Xz[i * ST + ts];
                     }
             }
             __syncwarp();
             // refill the finished slots, in slot order, from the warp's restart list
             const unsigned dm = __ballot_sync(LG_FULL, done && g == 0);
             if (done) {
-                const int j = qnext + __popc(dm & ((1u << (kLanesPerRestart * rs)) - 1u));
+                const int j = qnext + __popc(dm & ((1u << (LPR * rs)) - 1u));
                 const int rn = warp + W * j;
                 r = rn < S ? rn : -1;
                 pc = 0;
@@ -1243,9 +1301,9 @@ __device__ __forceinline__ void dock_ligand_rt(const DockArgs &A, const PocketDe
             // them from here on (step 0, no move): its lanes skip the work
             const bool sv = kRigid || zrun < R;
             int jr;
-            const int t = sweep_bond_rt(Q.dc2g, Go, cv, v, N, R, k, rs, g, active && sv, cs, sn, kTrace, jr);
+            const int t = sweep_bond_rt<LPR>(Q.dc2g, Go, cv, v, N, R, k, rs, g, active && sv, cs, sn, kTrace, jr);
             if (active && g == 0) {
-                v.tcur[LG_IDX(pc * R + k, P * Ly.rmax, kChkDecision) * kTile + rs] = (uint8_t)t;
+                v.tcur[LG_IDX(pc * R + k, P * Ly.rmax, kChkDecision) * ST + rs] = (uint8_t)t;
                 if (kTrace) {  // a skipped decision repeats the bond's previous one
                     uint8_t *dr = O.decision_rank + (size_t)S * P * r0 + (size_t)r * PR + pc * R + k;
                     *dr = sv ? (uint8_t)jr : (uint8_t)(dr[-R] | kRankSkipped);
@@ -1255,7 +1313,7 @@ __device__ __forceinline__ void dock_ligand_rt(const DockArgs &A, const PocketDe
             zrun = t != 0 ? 0 : zrun + 1;
             if (!kRigid && !__any_sync(LG_FULL, active && zrun < R)) {  // every active restart converged
                 if (active)
-                    for (int q = pc * R + k + 1 + g; q < (pc + 1) * R; q += kLanesPerRestart) v.tcur[q * kTile + rs] = 0;
+                    for (int q = pc * R + k + 1 + g; q < (pc + 1) * R; q += LPR) v.tcur[q * ST + rs] = 0;
                 if (kTrace && active && g == 0) {
                     uint8_t *dr = O.decision_rank + (size_t)S * P * r0 + (size_t)r * PR;
                     for (int q = pc * R + k + 1; q < (pc + 1) * R; ++q) dr[q] = dr[q - R] | kRankSkipped;
@@ -1263,7 +1321,7 @@ __device__ __forceinline__ void dock_ligand_rt(const DockArgs &A, const PocketDe
                 break;
             }
         }
-        if (kRigid) movedp = rigid_moves_rt(A, Q.rigid_shift_g, Go, O, v, l, r, pc, N, R, rs, g, active) || movedp;
+        if (kRigid) movedp = rigid_moves_rt<LPR>(A, Q.rigid_shift_g, Go, O, v, l, r, pc, N, R, rs, g, active) || movedp;
         if (active) pc++;
         __syncwarp();
     }
@@ -1278,7 +1336,7 @@ __device__ __forceinline__ void dock_ligand_rt(const DockArgs &A, const PocketDe
     }
     finish_ligand(A, Pk, O, cv, l, a0, N, r0, PR, [&](int w, const float *&Bx, const float *&By, const float *&Bz,
                                                      const uint8_t *&tb) {
-        const RtView bv = rt_view(sm, Ly, A.lrt, w);
+        const RtView bv = rt_view<LPR>(sm, Ly, A.lrt, w);
         Bx = bv.Bx;
         By = bv.By;
         Bz = bv.Bz;
@@ -1286,12 +1344,15 @@ __device__ __forceinline__ void dock_ligand_rt(const DockArgs &A, const PocketDe
     });
 }
 
-// Persistent: CTAs pull ligands from a device counter in cost order.
+// Persistent: CTAs pull ligands from a device counter in cost order.  The
+// launch bounds keep 128 registers per thread for every tile (warps per CTA
+// up to Rt<LPR>::max_warps).
 #ifndef LG_RT_MIN_BLOCKS
 #define LG_RT_MIN_BLOCKS 4
 #endif
-template <bool kRank, bool kRigid, bool kTrace>
-__global__ void __launch_bounds__(128, LG_RT_MIN_BLOCKS) k_dock_batched(const __grid_constant__ DockArgs A) {
+template <bool kRank, bool kRigid, bool kTrace, int LPR>
+__global__ void __launch_bounds__(32 * Rt<LPR>::max_warps, 4 * LG_RT_MIN_BLOCKS / Rt<LPR>::max_warps)
+    k_dock_batched(const __grid_constant__ DockArgs A) {
     extern __shared__ __align__(16) char sm[];
     __shared__ int s_lig;
     for (;;) {
@@ -1314,7 +1375,7 @@ __global__ void __launch_bounds__(128, LG_RT_MIN_BLOCKS) k_dock_batched(const __
         const int l = s_lig;
         __syncthreads();
         if (l < 0) break;
-        dock_ligand_rt<kRank, kRigid, kTrace>(A, A.pocket, A.out, launch_src(A), l, sm);
+        dock_ligand_rt<kRank, kRigid, kTrace, LPR>(A, A.pocket, A.out, launch_src(A), l, sm);
     }
 }
 
@@ -1350,7 +1411,7 @@ __global__ void __launch_bounds__(128, LG_RT_MIN_BLOCKS) k_dock_multi(const __gr
             }
             __syncthreads();
         }
-        dock_ligand_rt<kRank, kRigid>(A, M.pk[p], O, launch_src(A), l, sm);
+        dock_ligand_rt<kRank, kRigid, false, 4>(A, M.pk[p], O, launch_src(A), l, sm);
         __syncthreads();
     };
     for (;;) {
@@ -1362,7 +1423,7 @@ __global__ void __launch_bounds__(128, LG_RT_MIN_BLOCKS) k_dock_multi(const __gr
         const int at = item * stride;
         if (M.lig_pocket) {  // one pocket per ligand
             const int l = A.order ? A.order[at] : at;
-            dock_ligand_rt<kRank, kRigid>(A, M.pk[M.lig_pocket[l]], A.out, launch_src(A), l, sm);
+            dock_ligand_rt<kRank, kRigid, false, 4>(A, M.pk[M.lig_pocket[l]], A.out, launch_src(A), l, sm);
             __syncthreads();
         } else if (M.pocket_major) {
             const int p = at / L, i = at - p * L;
@@ -1923,7 +1984,7 @@ __global__ void __launch_bounds__(128, LG_RT_MIN_BLOCKS) k_serve_loop(const __gr
         q.dc2g = S.dc2g[p];
         q.thr2g = S.thr2g[p];
         q.rigid_shift_g = S.rigid_shift_g[p];
-        dock_ligand_rt<kRank, kRigid>(A0, S.pk[p], A0.out, q, l, sm);
+        dock_ligand_rt<kRank, kRigid, false, 4>(A0, S.pk[p], A0.out, q, l, sm);
         __syncthreads();
         if (threadIdx.x == 0) loop_count(S, s_seq, s_L);
     }
@@ -2033,19 +2094,31 @@ static cudaError_t kernel_attributes(K kernel, int W, int smem, int *ctas_per_sm
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, kernel, 32 * W, smem);
 }
 
-// The batched kernel of a feature set, called with the launch's arguments.
+// The batched kernel of a feature set and restart tile, called with the
+// launch's arguments.  Tiles other than 4 lanes per restart exist for the
+// forms without ranking and decision ranks (cudaErrorInvalidValue otherwise).
 template <typename F>
-static cudaError_t with_batched(bool ranking, bool rigid, bool trace, F &&f) {
-    if (ranking) {
-        if (rigid) return trace ? f(k_dock_batched<true, true, true>) : f(k_dock_batched<true, true, false>);
-        return trace ? f(k_dock_batched<true, false, true>) : f(k_dock_batched<true, false, false>);
+static cudaError_t with_batched(bool ranking, bool rigid, bool trace, int lanes, F &&f) {
+    if (lanes != 4) {
+        if (ranking || trace) return cudaErrorInvalidValue;
+        switch (lanes) {
+        case 2: return rigid ? f(k_dock_batched<false, true, false, 2>) : f(k_dock_batched<false, false, false, 2>);
+        case 8: return rigid ? f(k_dock_batched<false, true, false, 8>) : f(k_dock_batched<false, false, false, 8>);
+        case 16: return rigid ? f(k_dock_batched<false, true, false, 16>) : f(k_dock_batched<false, false, false, 16>);
+        default: return cudaErrorInvalidValue;
+        }
     }
-    if (rigid) return trace ? f(k_dock_batched<false, true, true>) : f(k_dock_batched<false, true, false>);
-    return trace ? f(k_dock_batched<false, false, true>) : f(k_dock_batched<false, false, false>);
+    if (ranking) {
+        if (rigid) return trace ? f(k_dock_batched<true, true, true, 4>) : f(k_dock_batched<true, true, false, 4>);
+        return trace ? f(k_dock_batched<true, false, true, 4>) : f(k_dock_batched<true, false, false, 4>);
+    }
+    if (rigid) return trace ? f(k_dock_batched<false, true, true, 4>) : f(k_dock_batched<false, true, false, 4>);
+    return trace ? f(k_dock_batched<false, false, true, 4>) : f(k_dock_batched<false, false, false, 4>);
 }
 
-cudaError_t dock_kernel_attributes(int W, int smem, int *ctas_per_sm, bool ranking, bool rigid, bool trace) {
-    return with_batched(ranking, rigid, trace, [&](auto kernel) { return kernel_attributes(kernel, W, smem, ctas_per_sm); });
+cudaError_t dock_kernel_attributes(int W, int smem, int *ctas_per_sm, bool ranking, bool rigid, bool trace, int lanes) {
+    return with_batched(ranking, rigid, trace, lanes,
+                        [&](auto kernel) { return kernel_attributes(kernel, W, smem, ctas_per_sm); });
 }
 
 cudaError_t multi_kernel_attributes(int W, int smem, int *ctas_per_sm, bool ranking, bool rigid) {
@@ -2107,7 +2180,7 @@ struct DockLaunch {
 
 cudaError_t launch_dock_batched(const DockArgs &a, int grid, int smem, cudaStream_t s) {
     DockLaunch dl(a, grid, smem, s);
-    return with_batched(a.ranking, a.rigid_steps > 0, a.out.decision_rank != nullptr,
+    return with_batched(a.ranking, a.rigid_steps > 0, a.out.decision_rank != nullptr, a.lanes,
                         [&](auto kernel) { return cudaLaunchKernelEx(&dl.cfg, kernel, a); });
 }
 

@@ -118,6 +118,7 @@ extern "C" int lg_dock_batch_noalloc(lg_ctx *c, int32_t pid, const lg_ligand_bat
     a.nmax_lim = nmax;
     a.rmax_lim = rmax;
     a.scr = carve_scratch(base, L, rmax);
+    a.lanes = kLanesPerRestart;
     const int want_pose = o->pose != nullptr;
     int W = choose_warps(a.S, 0), occ = 0, smem = 0;
     cudaError_t e;

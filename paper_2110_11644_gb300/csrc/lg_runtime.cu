@@ -187,12 +187,15 @@ int fetch_out(const OutDev &d, const lg_dock_result *o, int L, int S, int P, int
     return LG_OK;
 }
 
-// Warps per CTA for the batched kernel: restart tiles (8 slots each) are spread over
-// the CTA's warps; up to 4 warps, dividing the tile count when possible,
-// unless the context option fixes the count.
-int choose_warps(int S, int opt) {
-    const int tiles = (S + kTile - 1) / kTile;
-    if (opt > 0) return std::min(opt, 4);
+// Warps per CTA the batched kernel's launch bounds allow for a restart tile.
+static int max_warps_of(int lanes) { return lanes > 4 ? lanes : 4; }
+
+// Warps per CTA for the batched kernel: restart tiles (32 / lanes slots each)
+// are spread over the CTA's warps; up to 4 warps, dividing the tile count
+// when possible, unless the context option fixes the count.
+int choose_warps(int S, int opt, int lanes) {
+    const int slots = 32 / lanes, tiles = (S + slots - 1) / slots;
+    if (opt > 0) return std::min(opt, max_warps_of(lanes));
     for (int w = std::min(tiles, 4); w >= 1; --w)
         if (tiles % w == 0) return w;
     return 1;
@@ -208,22 +211,29 @@ unsigned host_class_mask(const lg_ligand_batch *b) {
     return m;
 }
 
-// Warps per CTA of a batched launch unit: the context option, else the
-// autotuner's cached choice, else the restart-tile heuristic.
-static int tuned_warps(lg_ctx *c, const std::array<int, 8> &key, int S, bool *cached) {
+// Lanes per restart of a batch that fits in one wave, in order of preference
+// (the first whose CTAs, with every restart of a ligand in flight, fit).
+static const int kSmallBatchLanes[3] = {16, 8, 4};
+
+// Restart tile (lanes per restart) and warps per CTA of a batched launch
+// unit: the context options, else the autotuner's cached choice, else 4 lanes
+// per restart and the restart-tile heuristic.  tiles_ok: the unit's kernel
+// comes with every tile (else 4 lanes per restart).
+static std::pair<int, int> tuned_tile(lg_ctx *c, const std::array<int, 8> &key, int S, bool tiles_ok, bool *cached) {
     *cached = false;
-    const int opt = c->warps_opt.load();
-    if (opt > 0) {
+    const int wopt = c->warps_opt.load(), lopt = tiles_ok ? c->lanes_opt.load() : 0;
+    const int lanes = lopt > 0 ? lopt : kLanesPerRestart;
+    if (wopt > 0) {
         *cached = true;
-        return std::min(opt, 4);
+        return {lanes, std::min(wopt, max_warps_of(lanes))};
     }
     std::lock_guard<std::mutex> g(c->tune_mu);
     auto it = c->tune.find(key);
-    if (it != c->tune.end()) {
+    if (it != c->tune.end() && (tiles_ok || it->second.first == kLanesPerRestart) && (lopt == 0 || it->second.first == lopt)) {
         *cached = true;
         return it->second;
     }
-    return choose_warps(S, 0);
+    return {lanes, choose_warps(S, 0, lanes)};
 }
 
 static int dock_device_launch(lg_ctx *ctx, const PocketDev &pk, const BatchDev &bd, const OutDev &od,
@@ -348,6 +358,7 @@ static int dock_device_launch(lg_ctx *ctx, const PocketDev &pk, const BatchDev &
         st->launches = launches + L;
         st->grid = L;
         st->warps_per_cta = W;
+        st->restart_lanes = 32;
         st->ctas_per_sm = 1;
         st->smem_bytes = psmem;
         return LG_OK;
@@ -357,19 +368,23 @@ static int dock_device_launch(lg_ctx *ctx, const PocketDev &pk, const BatchDev &
     // with shared memory for its own maximum, so small ligands keep a high
     // occupancy), else one for the whole batch
     struct Unit {
-        int cls, nmax, W, occ, smem, grid;
+        int cls, nmax, W, lanes, occ, smem, grid;
         bool tuned;
         std::array<int, 8> key;
     };
     std::vector<Unit> units;
     const bool split = !multi && ctx->size_classes && nmax > class_bound(1);
+    const bool trace = a.out.decision_rank != nullptr;
+    // tiles other than 4 lanes per restart: the single-pocket kernel without
+    // ranking or decision ranks
+    const bool tiles_ok = !multi && !a.ranking && !trace;
     auto configure = [&](Unit &u) -> int {
         for (;;) {
             a.ly = make_layout(u.nmax, rmax, a.P, u.W, want_pose);
-            a.lrt = make_layout_rt(u.nmax, rmax, a.P, want_pose);
+            a.lrt = make_layout_rt(u.nmax, rmax, a.P, want_pose, 32 / u.lanes);
             u.smem = std::max(a.ly.cta_bytes + u.W * a.lrt.warp_bytes, a.ly.cta_bytes + rank_smem);
             e = multi ? multi_kernel_attributes(u.W, u.smem, &u.occ, a.ranking, a.rigid_steps > 0)
-                      : dock_kernel_attributes(u.W, u.smem, &u.occ, a.ranking, a.rigid_steps > 0, a.out.decision_rank != nullptr);
+                      : dock_kernel_attributes(u.W, u.smem, &u.occ, a.ranking, a.rigid_steps > 0, trace, u.lanes);
             if (e != cudaSuccess) return fail(LG_ECUDA, std::string("dock kernel attributes: ") + cudaGetErrorString(e));
             if (u.occ > 0 || u.W == 1) break;
             u.W = std::max(1, u.W / 2);
@@ -386,26 +401,37 @@ static int dock_device_launch(lg_ctx *ctx, const PocketDev &pk, const BatchDev &
         u.nmax = c < 0 ? nmax : std::min(nmax, class_bound(c));
         // launch kind: one pocket; several pockets ligand-major, pocket-major, or one pocket per ligand
         const int kind = !multi ? 0 : (multi->lig_pocket ? 3 : (multi->pocket_major ? 2 : 1));
-        u.key = {c, a.S, a.P, u.nmax, rmax, a.ranking, a.rigid_steps > 0 ? 1 : 0, want_pose + 2 * kind};
-        u.W = tuned_warps(ctx, u.key, a.S, &u.tuned);
+        u.key = {c, a.S, a.P, u.nmax, rmax, a.ranking + 2 * (trace ? 1 : 0), a.rigid_steps > 0 ? 1 : 0, want_pose + 2 * kind};
+        const std::pair<int, int> t = tuned_tile(ctx, u.key, a.S, tiles_ok, &u.tuned);
+        u.lanes = t.first;
+        u.W = t.second;
         if (int rc = configure(u)) return rc;
         units.push_back(u);
     }
-    // A batch too small to fill the GPU gets wider CTAs unless the context
-    // fixes the width: when every item fits in one wave of 4 (or 2) warps per
-    // CTA, all run at once and each ligand's restarts spread over more warps
-    // (no more warps than restart tiles), which shortens the call; the tuned
-    // width is for full batches and is neither used nor tuned here
+    // A batch too small to fill the GPU gets a latency tile unless the context
+    // fixes the width: when every item fits in one wave, each ligand runs in
+    // one CTA with all its restarts at once, over as many lanes per restart as
+    // the preference order below allows (more lanes per restart: fewer steps
+    // per lane, so a shorter chain of decisions); the tuned tile is for full
+    // batches and is neither used nor tuned here
     if (ctx->warps_opt.load() <= 0) {
         const long items = multi && multi->pocket_major && !multi->lig_pocket ? (long)L * multi->np : (long)L;
-        const int wcap = std::min(4, (a.S + kTile - 1) / kTile);
+        const int lopt = tiles_ok ? ctx->lanes_opt.load() : 0;
+        std::vector<int> prefs;
+        if (lopt > 0)
+            prefs = {lopt};
+        else if (tiles_ok)
+            prefs = {kSmallBatchLanes[0], kSmallBatchLanes[1], kSmallBatchLanes[2]};
+        else
+            prefs = {kLanesPerRestart};
         for (Unit &u : units)
-            for (int w : {4, 2}) {
-                if (w > wcap) continue;
+            for (int lanes : prefs) {
+                const int slots = 32 / lanes, full = std::min(max_warps_of(lanes), (a.S + slots - 1) / slots);
                 Unit v = u;
-                v.W = w;
-                if (configure(v) == LG_OK && v.W == w && items <= (long)ctx_num_sms(ctx) * v.occ) {
-                    if (w > u.W) u = v;
+                v.lanes = lanes;
+                v.W = full;
+                if (configure(v) == LG_OK && v.W == full && items <= (long)ctx_num_sms(ctx) * v.occ) {
+                    u = v;
                     u.tuned = true;
                     break;
                 }
@@ -413,16 +439,27 @@ static int dock_device_launch(lg_ctx *ctx, const PocketDev &pk, const BatchDev &
     }
     a.sort_classes = split ? 1 : 0;
     for (const Unit &u : units) scr_nmax = std::max(scr_nmax, make_layout(u.nmax, rmax, a.P, 1, want_pose).nmax);
-    static const int kCand[3] = {4, 2, 1};  // autotuning candidates (warps per CTA)
+    // autotuning candidates (lanes per restart, warps per CTA)
+    std::vector<std::pair<int, int>> cands;
+    {
+        const int lopt = tiles_ok ? ctx->lanes_opt.load() : 0;
+        if (lopt > 0)
+            cands = {{lopt, 4}, {lopt, 2}, {lopt, 1}};
+        else if (tiles_ok)
+            cands = {{4, 4}, {4, 2}, {4, 1}, {2, 2}, {2, 1}, {8, 4}, {8, 2}};
+        else
+            cands = {{4, 4}, {4, 2}, {4, 1}};
+    }
     int slots = 1;
     for (const Unit &u : units) slots = std::max(slots, u.grid);
     bool need_tune = false;  // tuning trials run eagerly on the sorted batch: no graph for this call
     for (const Unit &u : units) need_tune = need_tune || (ctx->autotune && !u.tuned);
     if (need_tune)  // ranking slots for every candidate's grid
         for (const Unit &u : units)
-            for (int w : kCand) {
+            for (const auto &c : cands) {
                 Unit v = u;
-                v.W = w;
+                v.lanes = c.first;
+                v.W = c.second;
                 if (!u.tuned && configure(v) == LG_OK) slots = std::max(slots, v.grid);
             }
     const bool graph = allow_graph && ctx->graphs && !multi && s != nullptr && !need_tune && !reuse_prep;
@@ -441,16 +478,23 @@ static int dock_device_launch(lg_ctx *ctx, const PocketDev &pk, const BatchDev &
     }
     a.order = (multi && multi->lig_pocket) ? nullptr : a.scr.order;
     int32_t *counters = a.scr.hist + kSortBuckets;
-    // the kernels' shared-memory limit is per function: the largest of the units
+    // the kernels' shared-memory limit is per function: the largest of the
+    // units that launch the same kernel (same restart tile)
     auto set_limit = [&]() -> cudaError_t {
-        int big = 0, occ = 0;
-        for (const Unit &u : units) big = std::max(big, u.smem);
-        return multi ? multi_kernel_attributes(units.front().W, big, &occ, a.ranking, a.rigid_steps > 0)
-                     : dock_kernel_attributes(units.front().W, big, &occ, a.ranking, a.rigid_steps > 0, a.out.decision_rank != nullptr);
+        for (const Unit &u : units) {
+            int big = 0, occ = 0;
+            for (const Unit &o : units)
+                if (o.lanes == u.lanes) big = std::max(big, o.smem);
+            const cudaError_t r = multi ? multi_kernel_attributes(u.W, big, &occ, a.ranking, a.rigid_steps > 0)
+                                        : dock_kernel_attributes(u.W, big, &occ, a.ranking, a.rigid_steps > 0, trace, u.lanes);
+            if (r != cudaSuccess) return r;
+        }
+        return cudaSuccess;
     };
     auto launch_unit = [&](const Unit &u, int cap) -> cudaError_t {
         a.ly = make_layout(u.nmax, rmax, a.P, u.W, want_pose);
-        a.lrt = make_layout_rt(u.nmax, rmax, a.P, want_pose);
+        a.lrt = make_layout_rt(u.nmax, rmax, a.P, want_pose, 32 / u.lanes);
+        a.lanes = u.lanes;
         a.cls = u.cls;
         a.cls_off = u.cls >= 0 ? counters + kSizeClasses + 1 : nullptr;
         a.work_counter = counters + (u.cls >= 0 ? u.cls : kSizeClasses);
@@ -467,10 +511,11 @@ static int dock_device_launch(lg_ctx *ctx, const PocketDev &pk, const BatchDev &
             // class's cost order, 16 waves of the widest candidate's grid (at
             // least 4,096)
             int cap = 4096;
-            for (int w : kCand) {
+            for (const auto &c : cands) {
                 Unit v = u;
-                v.W = w;
-                if (configure(v) == LG_OK && v.W == w) cap = std::max(cap, 16 * v.grid);
+                v.lanes = c.first;
+                v.W = c.second;
+                if (configure(v) == LG_OK && v.W == c.second) cap = std::max(cap, 16 * v.grid);
             }
             float best = INFINITY;
             Unit keep = u;
@@ -479,10 +524,11 @@ static int dock_device_launch(lg_ctx *ctx, const PocketDev &pk, const BatchDev &
                 if (t0) cudaEventDestroy(t0);
                 return fail(LG_ECUDA, std::string("autotuning events: ") + cudaGetErrorString(e));
             }
-            for (int w : kCand) {
+            for (const auto &c : cands) {
                 Unit v = u;
-                v.W = w;
-                if (configure(v) != LG_OK || v.W != w) continue;
+                v.lanes = c.first;
+                v.W = c.second;
+                if (configure(v) != LG_OK || v.W != c.second) continue;
                 if (v.grid > slots) continue;  // ranking slots are sized for the launches above
                 if ((e = cudaMemsetAsync(counters + (u.cls >= 0 ? u.cls : kSizeClasses), 0, 4, s)) != cudaSuccess ||
                     (e = cudaEventRecord(t0, s)) != cudaSuccess || (e = launch_unit(v, cap)) != cudaSuccess ||
@@ -504,7 +550,7 @@ static int dock_device_launch(lg_ctx *ctx, const PocketDev &pk, const BatchDev &
             u = keep;
             {
                 std::lock_guard<std::mutex> g(ctx->tune_mu);
-                ctx->tune[u.key] = u.W;
+                ctx->tune[u.key] = {u.lanes, u.W};
             }
             if ((e = cudaMemsetAsync(counters + (u.cls >= 0 ? u.cls : kSizeClasses), 0, 4, s)) != cudaSuccess)
                 return fail(LG_ECUDA, std::string("autotuning: ") + cudaGetErrorString(e));
@@ -517,7 +563,7 @@ static int dock_device_launch(lg_ctx *ctx, const PocketDev &pk, const BatchDev &
         memcpy(key.data(), &a, sizeof(DockArgs));
         char *kp = key.data() + sizeof(DockArgs);
         for (const Unit &u : units) {
-            const int v[6] = {u.cls, u.nmax, u.W, u.smem, u.grid, u.occ};
+            const int v[6] = {u.cls, u.nmax, u.W + 64 * u.lanes, u.smem, u.grid, u.occ};
             memcpy(kp, v, sizeof(v));
             kp += sizeof(v);
         }
@@ -568,6 +614,7 @@ static int dock_device_launch(lg_ctx *ctx, const PocketDev &pk, const BatchDev &
         st->launches = cache[hit].launches;
         st->grid = u0.grid;
         st->warps_per_cta = u0.W;
+        st->restart_lanes = u0.lanes;
         st->ctas_per_sm = u0.occ;
         st->smem_bytes = u0.smem;
         return LG_OK;
@@ -581,6 +628,7 @@ static int dock_device_launch(lg_ctx *ctx, const PocketDev &pk, const BatchDev &
     st->launches = launches + (int)units.size();
     st->grid = u0.grid;
     st->warps_per_cta = u0.W;
+    st->restart_lanes = u0.lanes;
     st->ctas_per_sm = u0.occ;
     st->smem_bytes = u0.smem;
     return LG_OK;
@@ -1044,7 +1092,7 @@ int lg_tune_export(lg_ctx *c, char *buf, int64_t cap, int64_t *len) {
             t += first ? "[" : ", [";
             first = false;
             for (int v : kv.first) t += std::to_string(v) + ", ";
-            t += std::to_string(kv.second) + "]";
+            t += std::to_string(kv.second.first) + ", " + std::to_string(kv.second.second) + "]";
         }
     }
     t += "]}";
@@ -1073,8 +1121,9 @@ int lg_tune_import(lg_ctx *c, const char *text) {
         return fail(LG_EINVAL, "tuning text is for another SM count");
     k = field("entries");
     if (k == std::string::npos) return fail(LG_EINVAL, "tuning text: no entries");
-    // entries: a list of lists of 9 integers
-    std::vector<std::pair<std::array<int, 8>, int>> got;
+    // entries: a list of lists of 10 integers (9: an entry without the
+    // restart tile, 4 lanes per restart)
+    std::vector<std::pair<std::array<int, 8>, std::pair<int, int>>> got;
     std::vector<long> cur;
     int depth = 0;
     for (size_t i = k; i < t.size(); ++i) {
@@ -1084,14 +1133,20 @@ int lg_tune_import(lg_ctx *c, const char *text) {
             if (depth == 2) cur.clear();
         } else if (ch == ']') {
             if (depth == 2) {
-                if (cur.size() != 9) return fail(LG_EINVAL, "tuning text: an entry is not 9 integers");
+                if (cur.size() != 9 && cur.size() != 10)
+                    return fail(LG_EINVAL, "tuning text: an entry is not 10 integers");
                 std::array<int, 8> key;
                 for (int j = 0; j < 8; ++j) key[j] = (int)cur[j];
-                const int w = (int)cur[8];
-                if (w != 1 && w != 2 && w != 4) return fail(LG_EINVAL, "tuning text: warps per CTA not 1, 2 or 4");
+                const int lanes = cur.size() == 10 ? (int)cur[8] : kLanesPerRestart, w = (int)cur.back();
+                if (lanes != 2 && lanes != 4 && lanes != 8 && lanes != 16)
+                    return fail(LG_EINVAL, "tuning text: lanes per restart not 2, 4, 8 or 16");
+                if (w < 1 || w > max_warps_of(lanes) || (w & (w - 1)) != 0)
+                    return fail(LG_EINVAL, "tuning text: warps per CTA not a power of 2 within the tile's bound");
                 if (key[0] < -1 || key[0] >= kSizeClasses || key[1] < 1 || key[2] < 0 || key[3] < 1 || key[4] < 1)
                     return fail(LG_EINVAL, "tuning text: bad key");
-                got.push_back({key, w});
+                if (lanes != kLanesPerRestart && (key[5] != 0 || key[7] >= 2))
+                    return fail(LG_EINVAL, "tuning text: that restart tile exists for single-pocket launches without ranking only");
+                got.push_back({key, {lanes, w}});
             }
             if (--depth == 0) break;
         } else if (ch == '-' || (ch >= '0' && ch <= '9')) {
@@ -1131,6 +1186,10 @@ int lg_set_option(lg_ctx *c, const char *key, int64_t v) {
     } else if (!strcmp(key, "warps_per_cta")) {
         if (v < 0 || v > 32) return fail(LG_EINVAL, "warps_per_cta must be in [0, 32]");
         c->warps_opt = (int)v;
+    } else if (!strcmp(key, "restart_lanes")) {
+        if (v != 0 && v != 2 && v != 4 && v != 8 && v != 16)
+            return fail(LG_EINVAL, "restart_lanes must be 0, 2, 4, 8 or 16");
+        c->lanes_opt = (int)v;
     } else if (!strcmp(key, "serve_max_merge")) {
         if (v < 1 || v > (1 << 20)) return fail(LG_EINVAL, "serve_max_merge must be in [1, 2^20]");
         c->serve_max_merge = (int)v;

@@ -93,7 +93,7 @@ int resolve_out(lg_ctx *c, DevBuf &buf, const lg_ligand_batch *b, const lg_dock_
 cudaEvent_t *next_timing_events(lg_ctx *c);
 void harvest_timing(lg_ctx *c);
 void serve_stop(lg_ctx *c);
-int choose_warps(int S, int opt);
+int choose_warps(int S, int opt, int lanes = kLanesPerRestart);
 void l2_window_of(lg_ctx *c, const PocketDev &pk, const void **base, size_t *bytes, float *hit);
 
 }  // namespace lg
@@ -115,6 +115,7 @@ struct lg_ctx {
     int tev_head = 0, tev_pending = 0;
     // options read by the serving worker too (lg_set_option writes them)
     std::atomic<int> warps_opt{0};
+    std::atomic<int> lanes_opt{0};  // lanes per restart of batched launches (0: tuned or chosen)
     int serve_max_inflight = 8;  // read when the server starts
     bool serve_device_loop = true;    // read when the server starts: the device-resident loop serves requests
     std::atomic<int> serve_loop_idle_ms{100};  // idle limit of the loop's CTAs
@@ -125,8 +126,9 @@ struct lg_ctx {
     lg::Server *server = nullptr;
     // several pockets in one launch (lg_dock_multi)
     std::vector<lg::DevBuf> multi_out;
-    // autotuner: warps per CTA chosen by timing, per (size class, restarts,
-    // passes, atoms, torsions, features) of the batched kernel
+    // autotuner: restart tile (lanes per restart) and warps per CTA chosen by
+    // timing, per (size class, restarts, passes, atoms, torsions, features) of
+    // the batched kernel
     std::atomic<bool> autotune{true};
     std::atomic<bool> size_classes{true};  // one batched launch per size class when the atom maximum exceeds 64
     // captured CUDA graphs of device-resident lg_dock_batch calls (most recent last)
@@ -138,7 +140,7 @@ struct lg_ctx {
     };
     std::vector<GraphRec> graph_cache;
     std::mutex tune_mu;
-    std::map<std::array<int, 8>, int> tune;
+    std::map<std::array<int, 8>, std::pair<int, int>> tune;  // key -> (lanes per restart, warps per CTA)
     lg::DevBuf flat_buf;  // lg_flatten_batch: host-output staging and the preparation's unused outputs
     int multi_pocket_major = 1;
     // L2 residency of the pockets: the persisting set-aside (process-local

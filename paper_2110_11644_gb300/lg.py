@@ -70,7 +70,7 @@ class lg_stats(ctypes.Structure):
     _fields_ = [("dock_ms", ctypes.c_float), ("dock_calls", ctypes.c_int32), ("dock_ms_total", ctypes.c_double),
                 ("launches", ctypes.c_int32), ("grid", ctypes.c_int32),
                 ("warps_per_cta", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("smem_bytes", ctypes.c_int32),
-                ("graph", ctypes.c_int32), ("serve_loop_status", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("graph", ctypes.c_int32), ("serve_loop_status", ctypes.c_int32), ("restart_lanes", ctypes.c_int32),
                 ("l2_window_bytes", ctypes.c_int64), ("l2_persist_bytes", ctypes.c_int64),
                 ("serve_loop_launches", ctypes.c_int64), ("serve_loop_items", ctypes.c_int64)]
 

@@ -1,7 +1,10 @@
-"""Size classes and the autotuner of the batched kernels: a batch whose atom
-maximum exceeds 64 is docked by one persistent launch per size class, each
-with shared memory for its own maximum; the warps per CTA of each class are
-chosen by timing on the first call.  Results never depend on either."""
+"""Size classes, restart tiles and the autotuner of the batched kernels: a
+batch whose atom maximum exceeds 64 is docked by one persistent launch per
+size class, each with shared memory for its own maximum; the restart tile
+(lanes per restart) and warps per CTA of each class are chosen by timing on
+the first call.  Results never depend on any of them."""
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -62,6 +65,72 @@ def test_results_do_not_depend_on_warps_or_tuning(ctx, cfg2_pocket, heavy):
         ctx.unload_pocket(pid)
 
 
+# every (lanes per restart, warps per CTA) the batched kernel comes with
+TILES = ((4, 1), (4, 2), (4, 4), (2, 1), (2, 2), (2, 4), (8, 1), (8, 2), (8, 4), (8, 8),
+         (16, 1), (16, 2), (16, 4), (16, 8), (16, 16))
+
+
+@pytest.mark.parametrize("rigid", [0, 2])
+def test_every_restart_tile_gives_the_same_bits(ctx, cfg2_pocket, heavy, rigid):
+    """2, 4, 8 and 16 lanes per restart (16, 8, 4 and 2 restart slots per warp;
+    ragged step rounds at 8 and 16) at every warp count their launch bounds
+    allow, with and without rigid moves, on ligands of all three size
+    classes: every output equals the 4-lane tile's, bit for bit."""
+    pid = ctx.load_pocket(cfg2_pocket)
+    n = heavy.n_atoms()
+    idx = np.concatenate([np.nonzero(n > 64)[0][:60], np.nonzero(n <= 32)[0][:60], np.nonzero((n > 32) & (n <= 64))[0][:60]])
+    sub = heavy.subset(np.sort(idx))
+    params = dataclasses.replace(synth.config_params(3), rigid_steps=rigid, restarts=30 if rigid == 0 else 20)
+    ref = None
+    try:
+        ctx.set_option("autotune", 0)
+        for lanes, warps in TILES:
+            ctx.set_option("restart_lanes", lanes)
+            ctx.set_option("warps_per_cta", warps)
+            out = _dock(ctx, pid, sub, params, restart_rigid=rigid > 0, decision_rank=False)
+            st = ctx.stats()
+            assert (st.restart_lanes, st.warps_per_cta) == (lanes, warps)
+            if ref is None:
+                ref = out
+                # at 4 lanes the outputs match the oracle within the near-tie rule
+                rep = check(cfg2_pocket, sub, params, out)
+                assert rep["deviations"] <= 0.002 * rep["decisions"] + 2, rep
+            for k in KEYS + (("restart_rigid",) if rigid else ()):
+                assert np.array_equal(out[k], ref[k]), (lanes, warps, k)
+    finally:
+        ctx.set_option("restart_lanes", 0)
+        ctx.set_option("warps_per_cta", 0)
+        ctx.set_option("autotune", 1)
+        ctx.unload_pocket(pid)
+
+
+def test_tiles_the_ranking_and_trace_forms_lack_fall_back_to_four_lanes(ctx, cfg1):
+    pocket, full, params = cfg1
+    pid = ctx.load_pocket(pocket)
+    sub = full.subset(range(200))
+    ranked = dataclasses.replace(params, cluster_rmsd=2.0, rescore_top=4)
+    try:
+        ctx.set_option("restart_lanes", 0)
+        ref_r = _dock(ctx, pid, sub, ranked)
+        ref_t = _dock(ctx, pid, sub, params, decision_rank=True)
+        ctx.set_option("restart_lanes", 16)
+        got_r = _dock(ctx, pid, sub, ranked)
+        assert ctx.stats().restart_lanes == 4
+        got_t = _dock(ctx, pid, sub, params, decision_rank=True)
+        assert ctx.stats().restart_lanes == 4
+        _dock(ctx, pid, sub, params)
+        assert ctx.stats().restart_lanes == 16
+        for k in ref_r:
+            if ref_r[k] is not None:
+                assert np.array_equal(got_r[k], ref_r[k]), k
+        assert np.array_equal(got_t["decision_rank"], ref_t["decision_rank"])
+        with pytest.raises(lg.LgError):
+            ctx.set_option("restart_lanes", 3)
+    finally:
+        ctx.set_option("restart_lanes", 0)
+        ctx.unload_pocket(pid)
+
+
 def test_autotuner_caches_its_choice(ctx, cfg2_pocket, heavy):
     pid = ctx.load_pocket(cfg2_pocket)
     params = synth.config_params(3)
@@ -87,7 +156,8 @@ def test_tuning_carries_to_another_context(ctx, cfg2_pocket, heavy):
     ref = _dock(ctx, pid, heavy, params)
     text = ctx.tune_export()
     doc = json.loads(text)
-    assert doc["sms"] > 0 and len(doc["entries"]) == 3 and all(len(e) == 9 and e[8] in (1, 2, 4) for e in doc["entries"])
+    assert doc["sms"] > 0 and len(doc["entries"]) == 3
+    assert all(len(e) == 10 and (e[8], e[9]) in TILES for e in doc["entries"]), doc["entries"]
     ctx.unload_pocket(pid)
     c2 = lg.Context(0)
     try:
@@ -109,17 +179,18 @@ def test_tuning_carries_to_another_context(ctx, cfg2_pocket, heavy):
         c2.close()
 
 
-def test_small_batches_take_wide_ctas_untuned(ctx, cfg1, cfg2_pocket):
-    # a batch that fits in one wave of 4-warp CTAs runs at one CTA per ligand
-    # with its restart tiles over up to 4 warps, without tuning; results as
-    # at any width
+def test_small_batches_take_a_latency_tile_untuned(ctx, cfg1, cfg2_pocket):
+    # a batch that fits in one wave runs at one CTA per ligand with all its
+    # restarts in flight over 16 lanes each, without tuning; results as at
+    # any tile and width
     pocket, full, params = cfg1
     pid = ctx.load_pocket(pocket)
     ctx.set_option("autotune", 1)
     small = full.subset(range(64))
     out = _dock(ctx, pid, small, params)
     st = ctx.stats()
-    assert st.warps_per_cta == 2 and st.launches == 4  # 16 restarts: 2 tiles; prep + sort (2) + one launch
+    # 16 restarts at 2 per warp: 8 warps; prep + sort (2) + one launch
+    assert (st.restart_lanes, st.warps_per_cta, st.launches) == (16, 8, 4)
     ctx.set_option("warps_per_cta", 1)
     try:
         ref = _dock(ctx, pid, small, params)
@@ -130,7 +201,8 @@ def test_small_batches_take_wide_ctas_untuned(ctx, cfg1, cfg2_pocket):
     ctx.unload_pocket(pid)
     pid = ctx.load_pocket(cfg2_pocket)
     _dock(ctx, pid, synth.config_ligands(2, 64), synth.config_params(2))
-    assert ctx.stats().warps_per_cta == 4  # 30 restarts: 4 tiles
+    st = ctx.stats()
+    assert (st.restart_lanes, st.warps_per_cta) == (16, 15)  # 30 restarts at 2 per warp
     ctx.unload_pocket(pid)
 
 

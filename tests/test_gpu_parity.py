@@ -360,8 +360,9 @@ def test_all_stages_together_on_heavy_tailed_ligands(ctx, cfg2_pocket):
 
 
 def test_small_split_batches_take_wide_ctas(ctx, cfg2_pocket):
-    # a heavy-tailed batch small enough for one wave of 4-warp CTAs: every
-    # size class runs at 4 warps untuned, with the results of 1 warp
+    # a heavy-tailed batch small enough for one wave of 8-lane, 8-warp CTAs
+    # (but not of 16-lane, 15-warp ones): every size class runs with all 30
+    # restarts of a ligand in flight, untuned, with the results of 1 warp
     pid = ctx.load_pocket(cfg2_pocket)
     heavy = synth.config_ligands(3, 3000)
     n = heavy.n_atoms()
@@ -370,7 +371,8 @@ def test_small_split_batches_take_wide_ctas(ctx, cfg2_pocket):
     ctx.set_option("autotune", 1)
     a = _dock(ctx, pid, sub, prm)
     st = ctx.stats()
-    assert st.warps_per_cta == 4 and st.launches == 6  # prep + sort (3) + one launch per class, no trials
+    # prep + sort (3) + one launch per class, no trials
+    assert (st.restart_lanes, st.warps_per_cta, st.launches) == (8, 8, 6)
     ctx.set_option("warps_per_cta", 1)
     try:
         b = _dock(ctx, pid, sub, prm)
