@@ -409,6 +409,8 @@ def heavy_tailed_leg(ctx, pid, dev, n_lig, steps, peak_tflops):
 
     ms = timed(steps)
     st = ctx.stats()
+    import json
+    tiles = [e for e in json.loads(ctx.tune_export())["entries"] if e[1] == S and e[2] == P and e[5] == 0]
     scores = outs["score"][:L].cpu().numpy().copy()
     ctx.set_option("autotune", 0)
     ctx.set_option("warps_per_cta", 4)
@@ -422,8 +424,41 @@ def heavy_tailed_leg(ctx, pid, dev, n_lig, steps, peak_tflops):
     assert np.array_equal(outs["score"][:L].cpu().numpy(), scores), "results depend on the launch configuration"
     assert int((outs["status"][:L] != 0).sum()) == 0
     F = algorithmic_flops(batch, S, P)
+    # each size class alone (the batch's ligands of that class, at most
+    # 100,000), tuned, one timed call each
+    pool = batch
+    na = pool.n_atoms()
+    per_class = {}
+    for c, (lo, hi) in enumerate(((1, 32), (33, 64), (65, 1 << 30))):
+        ids = np.nonzero((na >= lo) & (na <= hi))[0][:100_000]
+        if len(ids) == 0:
+            continue
+        sub = pool.subset(ids)
+        Lc, Ac, Rc = sub.L, int(sub.atom_off[-1]), int(sub.rot_off[-1])
+        dc = lg.device_batch_arrays(sub, f"cuda:{dev}")
+        bc = lg.make_batch_struct(dc, Lc)
+        pc = lg.make_params(S, P, params.seed, params.d_clash, lg.LG_MODE_BATCHED, 0, int(sub.n_atoms().max()),
+                            max(1, int(sub.n_rot().max())))
+        rc, _ = lg.alloc_result(Lc, Ac, Rc, S, P, device=True, pose=True, tors=True)
+        lg.lg_dock_batch(ctx.h, pid, bc, pc, rc, sh)  # tunes
+        lg.lg_dock_batch(ctx.h, pid, bc, pc, rc, sh)
+        torch.cuda.synchronize()
+        flush.fill_(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        lg.lg_dock_batch(ctx.h, pid, bc, pc, rc, sh)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        msc = e0.elapsed_time(e1)
+        stc = ctx.stats()
+        per_class[f"{lo}-{hi}" if c < 2 else f">{lo - 1}"] = {
+            "ligands": Lc, "value": Lc / (msc / 1e3), "ms": msc,
+            "frac_jstar1": algorithmic_flops(sub, S, P) / (msc / 1e3) / 1e12 / peak_tflops,
+            "restart_lanes": stc.restart_lanes, "warps_per_cta": stc.warps_per_cta, "ctas_per_sm": stc.ctas_per_sm}
     return {"ligands": L, "value": L / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": steps,
             "frac_jstar1": F / (ms / 1e3) / 1e12 / peak_tflops, "launches_per_step": st.launches,
+            "tuned_tiles": [{"class": e[0], "atom_max": e[3], "lanes": e[8], "warps": e[9]} for e in tiles],
+            "per_class": per_class,
             "untuned_4_warps": {"value": L / (ms4 / 1e3), "ms_per_step": ms4},
             "one_launch_4_warps": {"value": L / (ms1 / 1e3), "ms_per_step": ms1},
             "sample": f"{L} ligands: atoms lognormal (median 28, 10-100), torsions ~0.2 N (0-20), {S} restarts, "
@@ -507,7 +542,7 @@ def small_batch_leg(ctx, pid, dev, n_lig, calls):
         st = ctx.stats()
         res[name] = {"us_per_call": (time.perf_counter() - t0) / calls * 1e6, "graph_mode": st.graph,
                      "restart_lanes": st.restart_lanes, "warps_per_cta": st.warps_per_cta}
-    ctx.set_option("graphs", 0)
+    ctx.set_option("graphs", 0)  # direct launches for the tile comparison below
     # the same direct calls with each restart tile forced (lanes per restart;
     # every restart of a ligand in flight at once)
     by_lanes = {}
@@ -524,6 +559,7 @@ def small_batch_leg(ctx, pid, dev, n_lig, calls):
         by_lanes[str(lanes)] = {"us_per_call": (time.perf_counter() - t0) / (calls // 2) * 1e6,
                                 "warps_per_cta": st.warps_per_cta}
     ctx.set_option("restart_lanes", 0)
+    ctx.set_option("graphs", 2)
     return {"ligands": L, "calls": calls, **res, "by_lanes": by_lanes}
 
 
@@ -550,6 +586,9 @@ def summary_of(line) -> dict:
     h = line.get("heavy_tailed")
     if h:
         out["heavy"] = r3(h["value"])
+        big = (h.get("per_class") or {}).get(">64")
+        if big:
+            out["heavy_gt64_frac_jstar1"] = r3(big["frac_jstar1"])
     if line.get("flatten"):
         out["flatten"] = r3(line["flatten"]["value"])
     if line.get("small_batch"):

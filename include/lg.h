@@ -470,11 +470,13 @@ int lg_get_stats(lg_ctx *ctx, lg_stats *out);
  * on the same even sample of that class's ligands (16 waves of the widest
  * grid, at least 4,096) and keeps the fastest; a batch that fits in one wave
  * instead takes 16 (else 8, else 4) lanes per restart with every restart of a
- * ligand in flight at once, untuned; results never depend on the choice), "graphs" (0/1, default 0: an lg_dock_batch call with device
+ * ligand in flight at once, untuned; results never depend on the choice), "graphs" (0/1/2, default 2: an lg_dock_batch call with device
  * batch and result on a non-default stream is captured, preparation and
- * docking kernels together, as a CUDA graph and replayed when a later call
- * has the same arguments; with timing on, such a call's device time then
- * spans the preparation kernels too), "size_classes" (0/1, default 1: a batch whose atom maximum exceeds
+ * docking kernels together, as a CUDA graph -- with 2 when its arguments
+ * recur, i.e. from the second call with the same arguments on, with 1 on the
+ * first call -- and replayed when a later call has the same arguments; 0: no
+ * graphs; with timing on, a graph call's device time spans the preparation
+ * kernels too; setting the option drops the captured graphs), "size_classes" (0/1, default 1: a batch whose atom maximum exceeds
  * 64 is docked by one launch per size class -- atoms <= 32, <= 64, more --
  * each with shared memory for its own maximum), "serve_max_inflight" (requests on the device at once, default 8),
  * "serve_mem_reserve_mb" (free device memory the server leaves untouched,

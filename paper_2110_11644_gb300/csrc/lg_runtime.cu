@@ -261,6 +261,41 @@ int dock_device(lg_ctx *ctx, const PocketDev &pk, const BatchDev &bd, const OutD
     return rc;
 }
 
+// The launch arguments of a call as key bytes, field by field (structure
+// padding carries no meaning and is left out).
+struct KeyBytes {
+    std::vector<char> b;
+    template <typename T>
+    void put(const T &v) {
+        const char *q = reinterpret_cast<const char *>(&v);
+        b.insert(b.end(), q, q + sizeof(T));
+    }
+};
+
+static void put_args(KeyBytes &k, const DockArgs &a) {
+    const PocketDev &pk = a.pocket;
+    k.put(pk.n), k.put(pk.h), k.put(pk.inv_h), k.put(pk.c0), k.put(pk.gmax);
+    k.put(pk.center.x), k.put(pk.center.y), k.put(pk.center.z);
+    k.put(pk.cell_o), k.put(pk.cell_ve), k.put(pk.pp), k.put(pk.n_pp), k.put(pk.k_out);
+    for (float w : pk.type_w) k.put(w);
+    const BatchDev &bd = a.batch;
+    k.put(bd.L), k.put(bd.atom_off), k.put(bd.x), k.put(bd.y), k.put(bd.z), k.put(bd.q), k.put(bd.type);
+    k.put(bd.parent), k.put(bd.rot_off), k.put(bd.rot_child), k.put(bd.uid);
+    const OutDev &o = a.out;
+    k.put(o.score), k.put(o.best_restart), k.put(o.tors_idx), k.put(o.pose), k.put(o.status), k.put(o.restart_score);
+    k.put(o.restart_tors), k.put(o.rank), k.put(o.leader), k.put(o.restart_geo), k.put(o.restart_rigid);
+    k.put(o.decision_rank);
+    k.put(a.ly), k.put(a.lrt);  // int fields only
+    const Scratch &c = a.scr;
+    k.put(c.hist), k.put(c.keys), k.put(c.order), k.put(c.centroid), k.put(c.rot_end), k.put(c.rk_pose);
+    k.put(c.rk_E), k.put(c.rk_tors), k.put(c.rk_G), k.put(c.rk_cen), k.put(c.rk_slots), k.put(c.rk_floats);
+    k.put(c.per_cta);
+    k.put(a.S), k.put(a.P), k.put(a.seed_lo), k.put(a.seed_hi), k.put(a.dc2g), k.put(a.nmax_lim), k.put(a.rmax_lim);
+    k.put(a.rigid_steps), k.put(a.rigid_shift_g), k.put(a.ranking), k.put(a.thr2g), k.put(a.rescore_top);
+    k.put(a.order), k.put(a.work_counter), k.put(a.cls_off), k.put(a.cls), k.put(a.item_cap), k.put(a.sort_classes);
+    k.put(a.lanes), k.put(a.l2_base), k.put(a.l2_bytes), k.put(a.l2_hit);
+}
+
 static int dock_device_launch(lg_ctx *ctx, const PocketDev &pk, const BatchDev &bd, const OutDev &od,
                               const lg_dock_params *p, int nmax, int rmax, DevBuf &scratch, cudaStream_t s, lg_stats *st,
                               cudaEvent_t *tev, const MultiDev *multi, unsigned class_mask, bool allow_graph,
@@ -462,7 +497,27 @@ static int dock_device_launch(lg_ctx *ctx, const PocketDev &pk, const BatchDev &
                 v.W = c.second;
                 if (!u.tuned && configure(v) == LG_OK) slots = std::max(slots, v.grid);
             }
-    const bool graph = allow_graph && ctx->graphs && !multi && s != nullptr && !need_tune && !reuse_prep;
+    // key of a call: the launch arguments, the units and the stream
+    auto call_key = [&]() {
+        KeyBytes k;
+        put_args(k, a);
+        for (const Unit &u : units) {
+            const int v[7] = {u.cls, u.nmax, u.W, u.lanes, u.smem, u.grid, u.occ};
+            k.put(v);
+        }
+        k.put(s);
+        return std::move(k.b);
+    };
+    bool graph = allow_graph && ctx->graphs.load() > 0 && !multi && s != nullptr && !need_tune && !reuse_prep;
+    if (graph && ctx->graphs.load() == 2) {  // capture only arguments seen before (the second call on)
+        std::vector<char> k = call_key();
+        auto &seen = ctx->graph_seen;
+        if (std::find(seen.begin(), seen.end(), k) == seen.end()) {
+            seen.push_back(std::move(k));
+            if (seen.size() > 16) seen.erase(seen.begin());
+            graph = false;
+        }
+    }
     if (reuse_prep) {  // the same batch was prepared and sorted by the previous call: clear the work counters
         if (scratch.ensure(scratch_bytes(L, rmax, a.ranking ? slots : 0, a.S, a.P, scr_nmax)))
             return fail(LG_ENOMEM, "scratch allocation failed");
@@ -491,7 +546,7 @@ static int dock_device_launch(lg_ctx *ctx, const PocketDev &pk, const BatchDev &
         }
         return cudaSuccess;
     };
-    auto launch_unit = [&](const Unit &u, int cap) -> cudaError_t {
+    auto launch_unit = [&](const Unit &u, int cap, cudaStream_t us) -> cudaError_t {
         a.ly = make_layout(u.nmax, rmax, a.P, u.W, want_pose);
         a.lrt = make_layout_rt(u.nmax, rmax, a.P, want_pose, 32 / u.lanes);
         a.lanes = u.lanes;
@@ -499,7 +554,32 @@ static int dock_device_launch(lg_ctx *ctx, const PocketDev &pk, const BatchDev &
         a.cls_off = u.cls >= 0 ? counters + kSizeClasses + 1 : nullptr;
         a.work_counter = counters + (u.cls >= 0 ? u.cls : kSizeClasses);
         a.item_cap = cap;
-        return multi ? launch_dock_multi(a, *multi, u.grid, u.smem, s) : launch_dock_batched(a, u.grid, u.smem, s);
+        return multi ? launch_dock_multi(a, *multi, u.grid, u.smem, us) : launch_dock_batched(a, u.grid, u.smem, us);
+    };
+    // The units of a call: with several size classes and no pose ranking
+    // (whose slots belong to CTA indices), the classes after the first run on
+    // the context's class streams, forked from s and joined back into it, so
+    // that one class's last wave overlaps the next class's first (each class
+    // has its own work counter; outputs are per ligand)
+    auto launch_units = [&]() -> cudaError_t {
+        if (units.size() == 1 || a.ranking) {
+            for (const Unit &u : units)
+                if (cudaError_t r = launch_unit(u, 0, s)) return r;
+            return cudaSuccess;
+        }
+        std::lock_guard<std::mutex> g(ctx->class_mu);
+        if (ctx_class_streams(ctx)) return cudaErrorMemoryAllocation;
+        cudaError_t r = cudaEventRecord(ctx->class_fork, s);
+        for (size_t i = 0; i < units.size() && r == cudaSuccess; ++i) {
+            cudaStream_t us = i == 0 ? s : ctx->class_streams[i - 1];
+            if (i > 0) r = cudaStreamWaitEvent(us, ctx->class_fork, 0);
+            if (r == cudaSuccess) r = launch_unit(units[i], 0, us);
+        }
+        for (size_t i = 1; i < units.size() && r == cudaSuccess; ++i) {
+            r = cudaEventRecord(ctx->class_join[i - 1], ctx->class_streams[i - 1]);
+            if (r == cudaSuccess) r = cudaStreamWaitEvent(s, ctx->class_join[i - 1], 0);
+        }
+        return r;
     };
     // autotuning: a unit without a cached choice times every candidate on the
     // first ligands of its class (same order, same ligands), keeps the fastest
@@ -531,7 +611,7 @@ static int dock_device_launch(lg_ctx *ctx, const PocketDev &pk, const BatchDev &
                 if (configure(v) != LG_OK || v.W != c.second) continue;
                 if (v.grid > slots) continue;  // ranking slots are sized for the launches above
                 if ((e = cudaMemsetAsync(counters + (u.cls >= 0 ? u.cls : kSizeClasses), 0, 4, s)) != cudaSuccess ||
-                    (e = cudaEventRecord(t0, s)) != cudaSuccess || (e = launch_unit(v, cap)) != cudaSuccess ||
+                    (e = cudaEventRecord(t0, s)) != cudaSuccess || (e = launch_unit(v, cap, s)) != cudaSuccess ||
                     (e = cudaEventRecord(t1, s)) != cudaSuccess || (e = cudaEventSynchronize(t1)) != cudaSuccess) {
                     cudaEventDestroy(t0);
                     cudaEventDestroy(t1);
@@ -559,15 +639,7 @@ static int dock_device_launch(lg_ctx *ctx, const PocketDev &pk, const BatchDev &
         return fail(LG_ECUDA, std::string("dock kernel attributes: ") + cudaGetErrorString(e));
     if (graph) {
         // key: the launch arguments after carving, the units and the stream
-        std::vector<char> key(sizeof(DockArgs) + units.size() * 6 * sizeof(int) + sizeof(void *));
-        memcpy(key.data(), &a, sizeof(DockArgs));
-        char *kp = key.data() + sizeof(DockArgs);
-        for (const Unit &u : units) {
-            const int v[6] = {u.cls, u.nmax, u.W + 64 * u.lanes, u.smem, u.grid, u.occ};
-            memcpy(kp, v, sizeof(v));
-            kp += sizeof(v);
-        }
-        memcpy(kp, &s, sizeof(void *));
+        std::vector<char> key = call_key();
         auto &cache = ctx->graph_cache;
         int hit = -1;
         for (int i = 0; i < (int)cache.size(); i++)
@@ -579,8 +651,7 @@ static int dock_device_launch(lg_ctx *ctx, const PocketDev &pk, const BatchDev &
                 return fail(LG_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
             cudaError_t ec = cudaMemsetAsync(a.scr.hist, 0, 4 * kHistInts, s);
             if (ec == cudaSuccess) ec = launch_prep(a, true, s, &launches);
-            for (const Unit &u : units)
-                if (ec == cudaSuccess) ec = launch_unit(u, 0);
+            if (ec == cudaSuccess) ec = launch_units();
             e = cudaStreamEndCapture(s, &g);
             if (ec != cudaSuccess || e != cudaSuccess) {
                 if (g) cudaGraphDestroy(g);
@@ -620,9 +691,7 @@ static int dock_device_launch(lg_ctx *ctx, const PocketDev &pk, const BatchDev &
         return LG_OK;
     }
     if (timed) cudaEventRecord(tev[0], s);
-    for (const Unit &u : units)
-        if ((e = launch_unit(u, 0)) != cudaSuccess)
-            return fail(LG_ECUDA, std::string("dock launch: ") + cudaGetErrorString(e));
+    if ((e = launch_units()) != cudaSuccess) return fail(LG_ECUDA, std::string("dock launch: ") + cudaGetErrorString(e));
     if (timed) cudaEventRecord(tev[1], s);
     const Unit &u0 = units.front();
     st->launches = launches + (int)units.size();
@@ -860,6 +929,11 @@ void lg_destroy(lg_ctx *c) {
     c->flat_buf.release();
     for (auto s : c->plain_streams) cudaStreamDestroy(s);
     for (auto ev : c->join_events) cudaEventDestroy(ev);
+    for (int i = 0; i < 2; ++i) {
+        if (c->class_streams[i]) cudaStreamDestroy(c->class_streams[i]);
+        if (c->class_join[i]) cudaEventDestroy(c->class_join[i]);
+    }
+    if (c->class_fork) cudaEventDestroy(c->class_fork);
     for (int i = 0; i < 3; i++)
         if (c->ev[i]) cudaEventDestroy(c->ev[i]);
     if (c->scratch_ev) cudaEventDestroy(c->scratch_ev);
@@ -1208,9 +1282,11 @@ int lg_set_option(lg_ctx *c, const char *key, int64_t v) {
         c->serve_max_inflight = (int)v;
     } else if (!strcmp(key, "graphs")) {
         cudaSetDevice(c->device);
-        c->graphs = v != 0;
+        if (v < 0 || v > 2) return fail(LG_EINVAL, "graphs must be 0, 1 or 2");
+        c->graphs = (int)v;
         for (auto &g : c->graph_cache) cudaGraphExecDestroy(g.exec);
         c->graph_cache.clear();
+        c->graph_seen.clear();
     } else if (!strcmp(key, "size_classes")) {
         c->size_classes = v != 0;
     } else if (!strcmp(key, "autotune")) {

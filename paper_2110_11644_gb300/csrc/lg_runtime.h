@@ -131,8 +131,11 @@ struct lg_ctx {
     // the batched kernel
     std::atomic<bool> autotune{true};
     std::atomic<bool> size_classes{true};  // one batched launch per size class when the atom maximum exceeds 64
-    // captured CUDA graphs of device-resident lg_dock_batch calls (most recent last)
-    std::atomic<bool> graphs{false};
+    // captured CUDA graphs of device-resident lg_dock_batch calls (most recent
+    // last); graphs: 0 off, 1 capture a call's arguments on first sight, 2
+    // capture them when they recur (graph_seen: recent calls' arguments)
+    std::atomic<int> graphs{2};
+    std::vector<std::vector<char>> graph_seen;
     struct GraphRec {
         std::vector<char> key;
         cudaGraphExec_t exec = nullptr;
@@ -158,6 +161,12 @@ struct lg_ctx {
     // orders the calls that share `scratch` (and `flat_buf`) on the device: a
     // call's stream waits for the previous such call's work to finish
     cudaEvent_t scratch_ev = nullptr;
+    // size classes launched side by side: the classes after the first run on
+    // these streams, forked from and joined back into the call's stream
+    // (class_mu held while a call enqueues on them)
+    std::mutex class_mu;
+    cudaStream_t class_streams[2] = {};
+    cudaEvent_t class_fork = nullptr, class_join[2] = {};
 };
 
 namespace lg {
@@ -184,6 +193,18 @@ inline int ctx_plain_streams(lg_ctx *c, int n) {
         c->join_events.push_back(e);
     }
     return 0;
+}
+
+// Create the context's size-class streams and events on first use (class_mu held).
+inline int ctx_class_streams(lg_ctx *c) {
+    if (c->class_fork) return 0;
+    for (int i = 0; i < 2; ++i) {
+        if (!c->class_streams[i] && cudaStreamCreateWithFlags(&c->class_streams[i], cudaStreamNonBlocking) != cudaSuccess)
+            return -1;
+        if (!c->class_join[i] && cudaEventCreateWithFlags(&c->class_join[i], cudaEventDisableTiming) != cudaSuccess)
+            return -1;
+    }
+    return cudaEventCreateWithFlags(&c->class_fork, cudaEventDisableTiming) == cudaSuccess ? 0 : -1;
 }
 
 }  // namespace lg

@@ -252,7 +252,45 @@ def test_graph_capture_and_replay(ctx, cfg1):
         torch.cuda.synchronize()
         assert ctx.stats().graph == 0
     finally:
-        ctx.set_option("graphs", 0)
+        ctx.set_option("graphs", 2)
+        ctx.unload_pocket(pid)
+
+
+def test_graphs_by_default_when_arguments_recur(ctx, cfg1):
+    # the default (graphs = 2): a call whose arguments were not seen before
+    # runs directly, the second call with the same arguments is captured,
+    # later ones replay; new arguments start over; results never change
+    import torch
+    pocket, full, params = cfg1
+    pid = ctx.load_pocket(pocket)
+    batch = full.subset(range(96))
+    L, A, R = batch.L, int(batch.atom_off[-1]), int(batch.rot_off[-1])
+    darr = lg.device_batch_arrays(batch)
+    b = lg.make_batch_struct(darr, L)
+    p = lg.make_params(params.restarts, params.passes, params.seed, params.d_clash)
+    side = torch.cuda.Stream()
+    try:
+        ctx.set_option("graphs", 2)
+
+        def run(r):
+            lg.lg_dock_batch(ctx.h, pid, b, p, r, side.cuda_stream)
+            side.synchronize()
+            return ctx.stats().graph
+
+        r1, o1 = lg.alloc_result(L, A, R, params.restarts, params.passes, device=True)
+        modes = [run(r1)]
+        ref = {k: v.cpu().numpy() for k, v in o1.items() if v is not None}
+        for _ in range(3):
+            modes.append(run(r1))
+            for k, v in o1.items():
+                if v is not None:
+                    assert np.array_equal(v.cpu().numpy(), ref[k]), k
+        assert modes == [0, 2, 1, 1], modes
+        r2, o2 = lg.alloc_result(L, A, R, params.restarts, params.passes, device=True)
+        assert [run(r2), run(r2)] == [0, 2]
+        assert np.array_equal(o2["score"].cpu().numpy(), ref["score"])
+    finally:
+        ctx.set_option("graphs", 2)
         ctx.unload_pocket(pid)
 
 
@@ -287,7 +325,7 @@ def test_graph_replay_with_ranking_over_size_classes(ctx, cfg2_pocket, heavy):
                     assert np.array_equal(v.cpu().numpy(), ref[k]), k
         assert modes[-1] == 1, modes
     finally:
-        ctx.set_option("graphs", 0)
+        ctx.set_option("graphs", 2)
         ctx.unload_pocket(pid)
 
 
