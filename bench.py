@@ -578,7 +578,8 @@ def summary_of(line) -> dict:
     if line.get("serving_peak"):
         out["serve_peak"] = {k: r3(v) for k, v in line["serving_peak"].items()}
     for leg in line.get("serving") or []:
-        key = "serve_%d" % round(100 * leg["offered_load"]) + ("" if leg.get("mode") == "device_loop" else "_host")
+        key = "serve_%d" % round(100 * leg["offered_load"]) + {"device_loop": "", "host_merge": "_host"}.get(
+            leg.get("mode"), "_16lanes")
         out[key] = [r3(leg["p50_latency_s"] * 1e3), r3(leg["p99_latency_s"] * 1e3), r3(leg["sustained_evals_per_s"])]
     m = line.get("multi_pocket")
     if m:
@@ -848,6 +849,19 @@ def main():
                                                  mode=mode)["sustained_evals_per_s"]
             serving = [serving_leg(ctx, sp, batch, params, serving_peak["device_loop"], float(ld), args.serve_seconds)
                        for ld in args.serve_loads.split(",")]
+            # the loop with its latency tile (16 lanes per restart, every
+            # restart of a ligand in flight, one CTA per SM) against the
+            # default 4 lanes: its peak and the lowest load
+            ctx.set_option("serve_loop_lanes", 16)
+            serving_leg(ctx, sp, batch, params, value / world, 0.9, 1.0, seed=4)
+            serving_peak["device_loop_16_lanes"] = serving_leg(ctx, sp, batch, params, value / world, 1.5, ps,
+                                                               seed=6)["sustained_evals_per_s"]
+            low = min(float(x) for x in args.serve_loads.split(","))
+            leg = serving_leg(ctx, sp, batch, params, serving_peak["device_loop_16_lanes"], low,
+                              max(1.0, args.serve_seconds / 3))
+            leg["mode"] = "device_loop_16_lanes"
+            serving.append(leg)
+            ctx.set_option("serve_loop_lanes", 4)
             # the host worker's merged launches at the highest load, for comparison
             hs = max(1.0, args.serve_seconds / 6)
             serving.append(serving_leg(ctx, sp, batch, params, serving_peak["host_merge"],

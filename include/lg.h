@@ -493,7 +493,12 @@ int lg_get_stats(lg_ctx *ctx, lg_stats *out);
  * queued ones fail -- and the next submission starts one of the other kind),
  * "serve_loop_idle_ms" (1..60000, default
  * 100: how long a CTA of the loop waits for a ligand before it leaves; the
- * first CTA to leave ends the launch as a whole).
+ * first CTA to leave ends the launch as a whole), "serve_loop_lanes" (4 or
+ * 16, default 4: lanes per restart of the loop's restart tile; at 16 a CTA
+ * holds every restart of its ligand at once, one CTA per SM, which about
+ * halves each ligand's time in the loop at light load but lowers the loop's
+ * peak rate; requests that rank poses use 4; changing it stops the serving
+ * worker as "serve_device_loop" does).
  * Errors: LG_EINVAL. */
 int lg_set_option(lg_ctx *ctx, const char *key, int64_t value);
 

@@ -328,7 +328,7 @@ cudaError_t launch_diag_philox(int n, const uint32_t *ctr, const uint32_t *key, 
 cudaError_t launch_dock_multi(const DockArgs &a, const MultiDev &m, int grid, int smem, cudaStream_t s);
 cudaError_t launch_flatten(const FlatArgs &f, int L, cudaStream_t s);
 cudaError_t launch_serve_loop(const DockArgs &a, const LoopArgs &la, int grid, int smem, cudaStream_t s);
-cudaError_t loop_kernel_attributes(int W, int smem, int *ctas_per_sm, bool ranking, bool rigid);
+cudaError_t loop_kernel_attributes(int W, int smem, int *ctas_per_sm, bool ranking, bool rigid, int lanes = 4);
 int checks_collect(cudaStream_t s, int rec[4]);  // bounds-check record of a debug build (0 otherwise)
 cudaError_t dock_kernel_attributes(int W, int smem, int *ctas_per_sm, bool ranking, bool rigid, bool trace, int lanes = 4);
 cudaError_t multi_kernel_attributes(int W, int smem, int *ctas_per_sm, bool ranking, bool rigid);

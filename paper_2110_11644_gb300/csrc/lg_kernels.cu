@@ -1924,9 +1924,9 @@ __device__ __noinline__ void loop_count(const LoopArgs &S, uint64_t seq, int L) 
 // with no ligand to claim for idle_ns leaves; a stop request makes every CTA
 // leave after its current ligand; the last CTA out records how the launch
 // ended.
-template <bool kRank, bool kRigid>
-__global__ void __launch_bounds__(128, LG_RT_MIN_BLOCKS) k_serve_loop(const __grid_constant__ DockArgs A0,
-                                                                       const __grid_constant__ LoopArgs S) {
+template <bool kRank, bool kRigid, int LPR>
+__global__ void __launch_bounds__(32 * Rt<LPR>::max_warps, 4 * LG_RT_MIN_BLOCKS / Rt<LPR>::max_warps)
+    k_serve_loop(const __grid_constant__ DockArgs A0, const __grid_constant__ LoopArgs S) {
     extern __shared__ __align__(16) char sm[];
     __shared__ long long s_item;
     __shared__ uint64_t s_seq, s_first;
@@ -1984,7 +1984,7 @@ __global__ void __launch_bounds__(128, LG_RT_MIN_BLOCKS) k_serve_loop(const __gr
         q.dc2g = S.dc2g[p];
         q.thr2g = S.thr2g[p];
         q.rigid_shift_g = S.rigid_shift_g[p];
-        dock_ligand_rt<kRank, kRigid, false, 4>(A0, S.pk[p], A0.out, q, l, sm);
+        dock_ligand_rt<kRank, kRigid, false, LPR>(A0, S.pk[p], A0.out, q, l, sm);
         __syncthreads();
         if (threadIdx.x == 0) loop_count(S, s_seq, s_L);
     }
@@ -2193,18 +2193,23 @@ cudaError_t launch_dock_multi(const DockArgs &a, const MultiDev &m, int grid, in
     return cudaLaunchKernelEx(&dl.cfg, k_dock_multi<false, false>, a, m);
 }
 
+// The serving loop of a feature set and restart tile (16 lanes per restart
+// without ranking only; cudaErrorInvalidValue for other tiles).
 template <typename F>
-static cudaError_t with_loop(bool ranking, bool rigid, F &&f) {
-    if (ranking) return rigid ? f(k_serve_loop<true, true>) : f(k_serve_loop<true, false>);
-    return rigid ? f(k_serve_loop<false, true>) : f(k_serve_loop<false, false>);
+static cudaError_t with_loop(bool ranking, bool rigid, int lanes, F &&f) {
+    if (lanes == 16 && !ranking) return rigid ? f(k_serve_loop<false, true, 16>) : f(k_serve_loop<false, false, 16>);
+    if (lanes != 4) return cudaErrorInvalidValue;
+    if (ranking) return rigid ? f(k_serve_loop<true, true, 4>) : f(k_serve_loop<true, false, 4>);
+    return rigid ? f(k_serve_loop<false, true, 4>) : f(k_serve_loop<false, false, 4>);
 }
 
-cudaError_t loop_kernel_attributes(int W, int smem, int *ctas_per_sm, bool ranking, bool rigid) {
-    return with_loop(ranking, rigid, [&](auto kernel) { return kernel_attributes(kernel, W, smem, ctas_per_sm); });
+cudaError_t loop_kernel_attributes(int W, int smem, int *ctas_per_sm, bool ranking, bool rigid, int lanes) {
+    return with_loop(ranking, rigid, lanes,
+                     [&](auto kernel) { return kernel_attributes(kernel, W, smem, ctas_per_sm); });
 }
 
 cudaError_t launch_serve_loop(const DockArgs &a, const LoopArgs &la, int grid, int smem, cudaStream_t s) {
-    return with_loop(a.ranking, a.rigid_steps > 0, [&](auto kernel) {
+    return with_loop(a.ranking, a.rigid_steps > 0, a.lanes, [&](auto kernel) {
         kernel<<<grid, 32 * a.ly.W, smem, s>>>(a, la);
         return cudaGetLastError();
     });

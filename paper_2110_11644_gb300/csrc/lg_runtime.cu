@@ -1274,6 +1274,12 @@ int lg_set_option(lg_ctx *c, const char *key, int64_t v) {
             c->serve_device_loop = v != 0;
             serve_stop(c);  // the next submission starts a worker of the other kind
         }
+    } else if (!strcmp(key, "serve_loop_lanes")) {
+        if (v != 4 && v != 16) return fail(LG_EINVAL, "serve_loop_lanes must be 4 or 16");
+        if (c->serve_loop_lanes != (int)v) {
+            c->serve_loop_lanes = (int)v;
+            serve_stop(c);  // the next submission starts a loop with the new tile
+        }
     } else if (!strcmp(key, "serve_loop_idle_ms")) {
         if (v < 1 || v > 60000) return fail(LG_EINVAL, "serve_loop_idle_ms must be in [1, 60000]");
         c->serve_loop_idle_ms = (int)v;

@@ -632,13 +632,17 @@ static int loop_configure(lg_ctx *c, DeviceLoop &dl, const std::shared_ptr<Reque
     a.rescore_top = p.rescore_top;
     const int want_pose = r->out.pose != nullptr;
     const int rank_smem = a.ranking ? rank_smem_bytes(a.S) : 0;
-    int W = choose_warps(a.S, c->warps_opt.load());
+    // restart tile: 4 lanes per restart (the throughput tile), or with the
+    // option 16, every restart of a ligand in flight (a short chain per
+    // ligand, one CTA per SM) for requests that do not rank poses
+    a.lanes = (!a.ranking && c->serve_loop_lanes.load() == 16) ? 16 : kLanesPerRestart;
+    int W = a.lanes == kLanesPerRestart ? choose_warps(a.S, c->warps_opt.load()) : std::min(16, (a.S + 1) / 2);
     cudaError_t e;
     for (;;) {
         a.ly = make_layout(dl.nmax, dl.rmax, a.P, W, want_pose);
-        a.lrt = make_layout_rt(dl.nmax, dl.rmax, a.P, want_pose);
+        a.lrt = make_layout_rt(dl.nmax, dl.rmax, a.P, want_pose, 32 / a.lanes);
         dl.smem = std::max(a.ly.cta_bytes + W * a.lrt.warp_bytes, a.ly.cta_bytes + rank_smem);
-        if ((e = loop_kernel_attributes(W, dl.smem, &dl.occ, a.ranking, a.rigid_steps > 0)) != cudaSuccess)
+        if ((e = loop_kernel_attributes(W, dl.smem, &dl.occ, a.ranking, a.rigid_steps > 0, a.lanes)) != cudaSuccess)
             return fail(LG_ECUDA, std::string("serving loop kernel attributes: ") + cudaGetErrorString(e));
         if (dl.occ > 0 || W == 1) break;
         W = std::max(1, W / 2);

@@ -299,12 +299,15 @@ def _loop_ctx(idle_ms=None):
     return ctx
 
 
-def test_loop_requests_arriving_while_others_run():
+@pytest.mark.parametrize("lanes", [16, 4])
+def test_loop_requests_arriving_while_others_run(lanes):
     # requests of uneven size aimed at three pockets arrive one by one while
     # earlier ones are on the device: each result equals the request docked
-    # alone, and the loop docked every ligand
+    # alone, and the loop docked every ligand -- with either restart tile of
+    # the loop (4 lanes per restart, the default, or 16)
     ctx = _loop_ctx()
     try:
+        ctx.set_option("serve_loop_lanes", lanes)
         pockets = [synth.config_pocket(2), synth.config_pocket(4, 0), synth.config_pocket(4, 5)]
         pids = [ctx.load_pocket(p) for p in pockets]
         params = synth.DockParams(restarts=64, passes=3)
