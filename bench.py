@@ -265,6 +265,7 @@ def serving_leg(ctx, pids, pool, params, rate_evals, load, duration_s, seed=5, m
     return {"mode": mode, "offered_load": load, "offered_evals_per_s": load * rate_evals,
             "load_basis": "fraction of this serving path's measured peak (serving_peak)", "duration_s": round(wall, 2),
             "loop_launches": int(st.serve_loop_launches) if mode == "device_loop" else None,
+            "loop_tile_switches": int(st.serve_loop_switches) if mode == "device_loop" else None,
             "requests": len(lat), "ligands": ligs, "sustained_evals_per_s": ligs / wall,
             "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
             "pockets": len(pids),
@@ -578,8 +579,9 @@ def summary_of(line) -> dict:
     if line.get("serving_peak"):
         out["serve_peak"] = {k: r3(v) for k, v in line["serving_peak"].items()}
     for leg in line.get("serving") or []:
-        key = "serve_%d" % round(100 * leg["offered_load"]) + {"device_loop": "", "host_merge": "_host"}.get(
-            leg.get("mode"), "_16lanes")
+        key = "serve_%d" % round(100 * leg["offered_load"]) + {
+            "device_loop": "", "host_merge": "_host", "device_loop_4_lanes": "_4lanes",
+            "device_loop_16_lanes": "_16lanes"}[leg.get("mode")]
         out[key] = [r3(leg["p50_latency_s"] * 1e3), r3(leg["p99_latency_s"] * 1e3), r3(leg["sustained_evals_per_s"])]
     m = line.get("multi_pocket")
     if m:
@@ -849,19 +851,21 @@ def main():
                                                  mode=mode)["sustained_evals_per_s"]
             serving = [serving_leg(ctx, sp, batch, params, serving_peak["device_loop"], float(ld), args.serve_seconds)
                        for ld in args.serve_loads.split(",")]
-            # the loop with its latency tile (16 lanes per restart, every
-            # restart of a ligand in flight, one CTA per SM) against the
-            # default 4 lanes: its peak and the lowest load
-            ctx.set_option("serve_loop_lanes", 16)
-            serving_leg(ctx, sp, batch, params, value / world, 0.9, 1.0, seed=4)
-            serving_peak["device_loop_16_lanes"] = serving_leg(ctx, sp, batch, params, value / world, 1.5, ps,
-                                                               seed=6)["sustained_evals_per_s"]
+            # the loop with each restart tile fixed (4 lanes per restart, the
+            # throughput tile; 16, every restart of a ligand in flight, one CTA
+            # per SM) against the default, which switches between them by the
+            # backlog: each one's peak and the lowest load
             low = min(float(x) for x in args.serve_loads.split(","))
-            leg = serving_leg(ctx, sp, batch, params, serving_peak["device_loop_16_lanes"], low,
-                              max(1.0, args.serve_seconds / 3))
-            leg["mode"] = "device_loop_16_lanes"
-            serving.append(leg)
-            ctx.set_option("serve_loop_lanes", 4)
+            for lanes in (4, 16):
+                ctx.set_option("serve_loop_lanes", lanes)
+                serving_leg(ctx, sp, batch, params, value / world, 0.9, 1.0, seed=4)
+                serving_peak[f"device_loop_{lanes}_lanes"] = serving_leg(
+                    ctx, sp, batch, params, value / world, 1.5, ps, seed=6)["sustained_evals_per_s"]
+                leg = serving_leg(ctx, sp, batch, params, serving_peak[f"device_loop_{lanes}_lanes"], low,
+                                  max(1.0, args.serve_seconds / 3))
+                leg["mode"] = f"device_loop_{lanes}_lanes"
+                serving.append(leg)
+            ctx.set_option("serve_loop_lanes", 0)
             # the host worker's merged launches at the highest load, for comparison
             hs = max(1.0, args.serve_seconds / 6)
             serving.append(serving_leg(ctx, sp, batch, params, serving_peak["host_merge"],

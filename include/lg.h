@@ -452,6 +452,7 @@ typedef struct {
     int64_t l2_persist_bytes;    /* persisting L2 set-aside of the context (0: none) */
     int64_t serve_loop_launches; /* launches of the device-resident serving loop */
     int64_t serve_loop_items;    /* ligands it has docked */
+    int64_t serve_loop_switches; /* its switches between restart tiles (option "serve_loop_lanes" = 0) */
 } lg_stats;
 
 int lg_get_stats(lg_ctx *ctx, lg_stats *out);
@@ -493,12 +494,17 @@ int lg_get_stats(lg_ctx *ctx, lg_stats *out);
  * queued ones fail -- and the next submission starts one of the other kind),
  * "serve_loop_idle_ms" (1..60000, default
  * 100: how long a CTA of the loop waits for a ligand before it leaves; the
- * first CTA to leave ends the launch as a whole), "serve_loop_lanes" (4 or
- * 16, default 4: lanes per restart of the loop's restart tile; at 16 a CTA
- * holds every restart of its ligand at once, one CTA per SM, which about
+ * first CTA to leave ends the launch as a whole), "serve_loop_lanes" (0, 4
+ * or 16, default 0: lanes per restart of the loop's restart tile; at 16 a
+ * CTA holds every restart of its ligand at once, one CTA per SM, which about
  * halves each ligand's time in the loop at light load but lowers the loop's
- * peak rate; requests that rank poses use 4; changing it stops the serving
- * worker as "serve_device_loop" does).
+ * peak rate; 4 is the throughput tile; 0 switches between them by the
+ * backlog -- 16 while the ligands of the requests on the device stay within
+ * eight waves of the 16-lane loop, 4 above that until the backlog has stayed
+ * within one wave for 5 ms; a switch stops the running launch, whose
+ * CTAs leave after their current ligand, and relaunches with the other tile;
+ * requests that rank poses always use 4; changing the option stops the
+ * serving worker as "serve_device_loop" does).
  * Errors: LG_EINVAL. */
 int lg_set_option(lg_ctx *ctx, const char *key, int64_t value);
 

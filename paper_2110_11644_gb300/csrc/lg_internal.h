@@ -303,7 +303,8 @@ struct LoopArgs {
     const LoopDesc *desc;    // [ring]
     uint32_t *done;          // [ring] ligands finished per descriptor (reset by the last)
     uint64_t *flags;         // [ring] mapped host memory: seq + 1 once the descriptor is complete
-    long long *held;         // [grid] an item the CTA claimed but left without docking (-1: none)
+    long long *held;         // [held_n] items CTAs claimed but left without docking (-1: none)
+    int held_n;              // at least the grid of every launch of the loop
     int ring;
     uint64_t idle_ns;        // idle limit of a CTA (no ligand to claim)
     uint64_t first_seq;      // descriptors before it were complete at launch

@@ -1830,14 +1830,26 @@ __device__ __forceinline__ uint64_t global_ns() {
     return t;
 }
 
-// The next ligand of the CTA (thread 0): the one it holds, else a new one by
-// fetch-and-add on `next`; it is docked once published (below `tail`).
-// Returns its index; or -1 when the host asked the loop to stop or another
-// CTA reached the idle limit (the launch then ends as a whole, so the host
-// relaunches it at full width and nothing waits on CTAs that have left), or
-// -2 when the CTA has waited the idle limit itself.  On -1 / -2 `held` keeps
-// an unpublished ligand for the next launch.  Every wait here ends.
-__device__ __noinline__ long long loop_claim(const LoopArgs &S, long long &held, uint64_t &deadline) {
+// The next ligand of the CTA (thread 0): the one it holds, else one that CTAs
+// of an earlier launch left claimed but undocked (CTA b takes held[b],
+// held[b + grid], ...: the earlier launch may have had more CTAs; hk is the
+// next of these slots), else a new one by fetch-and-add on `next`; it is
+// docked once published (below `tail`).  Returns its index; or -1 when the
+// host asked the loop to stop or another CTA reached the idle limit (the
+// launch then ends as a whole, so the host relaunches it at full width and
+// nothing waits on CTAs that have left), or -2 when the CTA has waited the
+// idle limit itself.  On -1 / -2 `held` keeps an unpublished ligand for the
+// next launch.  Every wait here ends.
+__device__ __noinline__ long long loop_claim(const LoopArgs &S, long long &held, int &hk, uint64_t &deadline) {
+    while (held < 0 && hk < S.held_n) {
+        const long long h = S.held[hk];
+        S.held[hk] = -1;
+        hk += (int)gridDim.x;
+        if (h >= 0) {
+            held = h;
+            deadline = global_ns() + S.idle_ns;
+        }
+    }
     if (held < 0) {
         // once the launch is stopping or closing no CTA claims a new ligand,
         // so every CTA leaves after the one it holds and the launch ends
@@ -1935,10 +1947,12 @@ __global__ void __launch_bounds__(32 * Rt<LPR>::max_warps, 4 * LG_RT_MIN_BLOCKS 
     // live in registers while the CTA docks
     __shared__ uint64_t s_hint, s_deadline;
     __shared__ long long s_held;
+    __shared__ int s_hk;   // next slot of the held array this CTA drains
     __shared__ int s_why;  // 1 stopped, 2 idle limit, 3 bad item
     if (threadIdx.x == 0) {
         atomicAdd(&S.ctl->live, 1u);
-        s_held = S.held[blockIdx.x];  // left by this CTA's predecessor
+        s_held = -1;
+        s_hk = blockIdx.x;
         s_hint = S.first_seq;
         s_deadline = global_ns() + S.idle_ns;
         s_why = 0;
@@ -1950,8 +1964,9 @@ __global__ void __launch_bounds__(32 * Rt<LPR>::max_warps, 4 * LG_RT_MIN_BLOCKS 
     for (;;) {
         if (threadIdx.x == 0) {
             long long held = s_held;
+            int hk = s_hk;
             uint64_t deadline = s_deadline, hint = s_hint;
-            long long item = loop_claim(S, held, deadline);
+            long long item = loop_claim(S, held, hk, deadline);
             if (item >= 0 && !(s_seq != kDescBusy && (uint64_t)item >= s_first &&
                                (uint64_t)item < s_first + (uint64_t)s_L)) {
                 uint64_t sq, f;
@@ -1968,6 +1983,7 @@ __global__ void __launch_bounds__(32 * Rt<LPR>::max_warps, 4 * LG_RT_MIN_BLOCKS 
                 }
             }
             s_held = held;
+            s_hk = hk;
             s_deadline = deadline;
             s_hint = hint;
             s_why = item >= 0 ? 0 : (int)(-item);
@@ -1989,7 +2005,7 @@ __global__ void __launch_bounds__(32 * Rt<LPR>::max_warps, 4 * LG_RT_MIN_BLOCKS 
         if (threadIdx.x == 0) loop_count(S, s_seq, s_L);
     }
     if (threadIdx.x == 0) {
-        S.held[blockIdx.x] = s_held;
+        S.held[blockIdx.x] = s_held;  // drained at the CTA's first claim, so free
         if (s_why == 2) atomicAdd(&S.ctl->idle_exits, 1u);
         __threadfence();
         if (atomicSub(&S.ctl->live, 1u) == 1u) {  // the last CTA out

@@ -1275,7 +1275,7 @@ int lg_set_option(lg_ctx *c, const char *key, int64_t v) {
             serve_stop(c);  // the next submission starts a worker of the other kind
         }
     } else if (!strcmp(key, "serve_loop_lanes")) {
-        if (v != 4 && v != 16) return fail(LG_EINVAL, "serve_loop_lanes must be 4 or 16");
+        if (v != 0 && v != 4 && v != 16) return fail(LG_EINVAL, "serve_loop_lanes must be 0, 4 or 16");
         if (c->serve_loop_lanes != (int)v) {
             c->serve_loop_lanes = (int)v;
             serve_stop(c);  // the next submission starts a loop with the new tile

@@ -119,7 +119,7 @@ struct lg_ctx {
     int serve_max_inflight = 8;  // read when the server starts
     bool serve_device_loop = true;    // read when the server starts: the device-resident loop serves requests
     std::atomic<int> serve_loop_idle_ms{100};  // idle limit of the loop's CTAs
-    std::atomic<int> serve_loop_lanes{4};      // lanes per restart of the loop's tile (4 with ranking)
+    std::atomic<int> serve_loop_lanes{0};      // the loop's restart tile: 4 or 16 lanes per restart, 0 by the backlog
     std::atomic<int> serve_max_merge{4096};        // ligands per merged batch
     std::atomic<bool> serve_cross_pocket{false};   // merge requests aimed at different pockets
     int64_t serve_reserve_mb = 1024;

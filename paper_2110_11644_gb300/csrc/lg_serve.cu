@@ -474,6 +474,19 @@ struct DeviceLoop {
     bool running = false;     // a launch may still be on the device
     std::shared_ptr<Request> kind;  // a request of the kind the loop serves
     int nmax = 0, rmax = 0, W = 1, occ = 0, smem = 0, grid = 0;
+    // the kind's restart tiles: [0] 4 lanes per restart (throughput), [1] 16
+    // lanes (latency; not for pose ranking); `cur` is the one launched
+    struct Tile {
+        int lanes = 0, W = 0, occ = 0, smem = 0, grid = 0;
+        Layout ly;
+        LayoutRT lrt;
+    } tiles[2];
+    int ntiles = 1, cur = 0, held_n = 0;
+    bool held_dirty = false;  // a launch of this kind ran: the held array may hold claimed ligands
+    int stale = 0;            // launches in a row that ended idle without a request finishing
+    bool adaptive = false;    // switch tiles by the backlog
+    double low_since = -1.0;  // since when the backlog has been low (throughput tile)
+    int64_t switches = 0;
     DockArgs args;
     std::vector<PocketDev> table;  // pockets of the launch's table
     bool table_launched = false;   // the running launch has the whole table
@@ -494,7 +507,7 @@ struct DeviceLoop {
     int64_t launches = 0, items = 0;
     // the figures lg_get_stats reads while the worker runs
     std::atomic<int> a_status{-1};
-    std::atomic<int64_t> a_launches{0}, a_items{0};
+    std::atomic<int64_t> a_launches{0}, a_items{0}, a_switches{0};
     // views of ctl (device) and host
     LoopCtl *d_ctl = nullptr;
     LoopDesc *d_desc = nullptr;
@@ -610,6 +623,43 @@ static void loop_free_arenas(DeviceLoop &dl) {
     dl.cap_l = dl.cap_a = dl.cap_r = 0;
 }
 
+// Make tile t the one the next launch uses (no launch on the device).
+static void loop_apply_tile(DeviceLoop &dl, int t) {
+    const DeviceLoop::Tile &T = dl.tiles[t];
+    dl.cur = t;
+    dl.args.ly = T.ly;
+    dl.args.lrt = T.lrt;
+    dl.args.lanes = T.lanes;
+    dl.W = T.W;
+    dl.occ = T.occ;
+    dl.smem = T.smem;
+    dl.grid = T.grid;
+}
+
+// The tile the backlog (ligands of the requests on the device) asks for.
+// Claims are first come, first served, so a ligand waits for the backlog
+// ahead of it. One wave of the latency tile (one ligand per SM, about half
+// the throughput tile's time per ligand) clears in half the time of a
+// throughput wave, and a backlog of w latency waves takes w/2 throughput
+// waves; a switch costs the running CTAs' current ligands and leaves the
+// loop at the other tile for the requests that follow. Hence the
+// throughput tile only for a backlog above eight latency waves, and the
+// latency tile again once the backlog has stayed within one wave for 5 ms.
+static int loop_tile_wanted(DeviceLoop &dl, int64_t backlog, double t) {
+    if (!dl.adaptive) return dl.cur;
+    const int64_t wave = dl.tiles[1].grid;
+    if (dl.cur == 1) {
+        dl.low_since = -1.0;
+        return backlog > 8 * wave ? 0 : 1;
+    }
+    if (backlog > wave) {
+        dl.low_since = -1.0;
+        return 0;
+    }
+    if (dl.low_since < 0.0) dl.low_since = t;
+    return t - dl.low_since >= 0.005 ? 1 : 0;
+}
+
 // Set the loop up for requests of r's kind (no launch on the device, no
 // request in flight): layouts for the kind's maxima, per-CTA scratch, arenas
 // with room for at least r (admission by free device memory: the arena's
@@ -632,31 +682,42 @@ static int loop_configure(lg_ctx *c, DeviceLoop &dl, const std::shared_ptr<Reque
     a.rescore_top = p.rescore_top;
     const int want_pose = r->out.pose != nullptr;
     const int rank_smem = a.ranking ? rank_smem_bytes(a.S) : 0;
-    // restart tile: 4 lanes per restart (the throughput tile), or with the
-    // option 16, every restart of a ligand in flight (a short chain per
-    // ligand, one CTA per SM) for requests that do not rank poses
-    a.lanes = (!a.ranking && c->serve_loop_lanes.load() == 16) ? 16 : kLanesPerRestart;
-    int W = a.lanes == kLanesPerRestart ? choose_warps(a.S, c->warps_opt.load()) : std::min(16, (a.S + 1) / 2);
+    // restart tiles: 4 lanes per restart (the throughput tile) and, for
+    // requests that do not rank poses, 16 (every restart of a ligand in
+    // flight: a short chain per ligand, one CTA per SM); the option fixes one
+    // or lets the worker switch between them by the backlog
+    const int lopt = c->serve_loop_lanes.load();
+    dl.ntiles = a.ranking ? 1 : 2;
     cudaError_t e;
-    for (;;) {
-        a.ly = make_layout(dl.nmax, dl.rmax, a.P, W, want_pose);
-        a.lrt = make_layout_rt(dl.nmax, dl.rmax, a.P, want_pose, 32 / a.lanes);
-        dl.smem = std::max(a.ly.cta_bytes + W * a.lrt.warp_bytes, a.ly.cta_bytes + rank_smem);
-        if ((e = loop_kernel_attributes(W, dl.smem, &dl.occ, a.ranking, a.rigid_steps > 0, a.lanes)) != cudaSuccess)
-            return fail(LG_ECUDA, std::string("serving loop kernel attributes: ") + cudaGetErrorString(e));
-        if (dl.occ > 0 || W == 1) break;
-        W = std::max(1, W / 2);
+    for (int t = 0; t < dl.ntiles; ++t) {
+        DeviceLoop::Tile &T = dl.tiles[t];
+        T.lanes = t == 0 ? kLanesPerRestart : 16;
+        int W = t == 0 ? choose_warps(a.S, c->warps_opt.load()) : std::min(16, (a.S + 1) / 2);
+        for (;;) {
+            T.ly = make_layout(dl.nmax, dl.rmax, a.P, W, want_pose);
+            T.lrt = make_layout_rt(dl.nmax, dl.rmax, a.P, want_pose, 32 / T.lanes);
+            T.smem = std::max(T.ly.cta_bytes + W * T.lrt.warp_bytes, T.ly.cta_bytes + rank_smem);
+            if ((e = loop_kernel_attributes(W, T.smem, &T.occ, a.ranking, a.rigid_steps > 0, T.lanes)) != cudaSuccess)
+                return fail(LG_ECUDA, std::string("serving loop kernel attributes: ") + cudaGetErrorString(e));
+            if (T.occ > 0 || W == 1) break;
+            W = std::max(1, W / 2);
+        }
+        if (T.occ <= 0) return fail(LG_EINVAL, "serving loop kernel does not fit on an SM");
+        T.W = W;
+        T.grid = ctx_num_sms(c) * T.occ;
     }
-    if (dl.occ <= 0) return fail(LG_EINVAL, "serving loop kernel does not fit on an SM");
-    dl.W = W;
-    dl.grid = ctx_num_sms(c) * dl.occ;
-    // one entry per CTA: centroid, subtree ends and, with ranking, a pose slot
-    const int slots = a.ranking ? dl.grid : 0;
-    if (dl.scratch.ensure(scratch_bytes(dl.grid, dl.rmax, slots, a.S, a.P, a.ly.nmax)))
+    dl.adaptive = dl.ntiles == 2 && lopt == 0;
+    dl.low_since = -1.0;
+    loop_apply_tile(dl, dl.ntiles == 2 && lopt != kLanesPerRestart ? 1 : 0);
+    dl.held_n = std::max(dl.tiles[0].grid, dl.ntiles == 2 ? dl.tiles[1].grid : 0);
+    // one entry per CTA of the widest tile: centroid, subtree ends and, with
+    // ranking, a pose slot
+    const int slots = a.ranking ? dl.held_n : 0;
+    if (dl.scratch.ensure(scratch_bytes(dl.held_n, dl.rmax, slots, a.S, a.P, a.ly.nmax)))
         return fail(LG_ENOMEM, "serving loop scratch allocation failed");
-    a.scr = carve_scratch(dl.scratch.p, dl.grid, dl.rmax, slots, a.S, a.P, a.ly.nmax);
+    a.scr = carve_scratch(dl.scratch.p, dl.held_n, dl.rmax, slots, a.S, a.P, a.ly.nmax);
     a.scr.per_cta = 1;
-    if (dl.held.ensure(8 * (size_t)dl.grid)) return fail(LG_ENOMEM, "serving loop allocation failed");
+    if (dl.held.ensure(8 * (size_t)dl.held_n)) return fail(LG_ENOMEM, "serving loop allocation failed");
     // arenas: 2^18 ligand slots, 2^23 atoms, 2^21 torsional bonds (about 170 MB of
     // device memory), at least twice the request, halved while free memory
     // minus the reserve cannot hold them
@@ -746,11 +807,13 @@ static int loop_configure(lg_ctx *c, DeviceLoop &dl, const std::shared_ptr<Reque
     if ((e = cudaMemsetAsync(dl.d_ctl, 0, sizeof(LoopCtl), dl.feed)) != cudaSuccess ||
         (e = cudaMemsetAsync(dl.d_desc, 0xff, kRing * sizeof(LoopDesc), dl.feed)) != cudaSuccess ||
         (e = cudaMemsetAsync(dl.d_done, 0, 4 * kRing, dl.feed)) != cudaSuccess ||
-        (e = cudaMemsetAsync(dl.held.p, 0xff, 8 * (size_t)dl.grid, dl.feed)) != cudaSuccess ||
+        (e = cudaMemsetAsync(dl.held.p, 0xff, 8 * (size_t)dl.held_n, dl.feed)) != cudaSuccess ||
         (e = cudaEventRecord(dl.fed, dl.feed)) != cudaSuccess)
         return fail(LG_ECUDA, std::string("serving loop reset: ") + cudaGetErrorString(e));
     memset(dl.h_flags, 0, 8 * kRing);
     dl.next_seq = dl.head = dl.tail = 0;
+    dl.held_dirty = false;
+    dl.stale = 0;
     // the table starts with the loaded pockets (requests then rarely need a relaunch)
     dl.table.clear();
     {
@@ -764,8 +827,34 @@ static int loop_configure(lg_ctx *c, DeviceLoop &dl, const std::shared_ptr<Reque
     return LG_OK;
 }
 
+// Ligands that CTAs of the ended launches claimed but left undocked, sorted
+// ascending into the front of the held array: CTA b of the next launch takes
+// held[b], held[b + grid], ... in turn, so the lowest claimed ligands -- the
+// first to be published -- are at the front of every CTA's list and no CTA
+// waits for a ligand while a lower one sits behind another's (with a grid
+// smaller than the last launch's, a CTA drains several).
+static cudaError_t loop_sort_held(DeviceLoop &dl) {
+    if (!dl.held_dirty) return cudaSuccess;
+    std::vector<long long> h((size_t)dl.held_n);
+    cudaError_t e = cudaMemcpyAsync(h.data(), dl.held.p, 8 * h.size(), cudaMemcpyDeviceToHost, dl.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(dl.stream);
+    if (e != cudaSuccess) return e;
+    std::vector<long long> v;
+    for (long long x : h)
+        if (x >= 0) v.push_back(x);
+    std::sort(v.begin(), v.end());
+    std::fill(h.begin(), h.end(), -1ll);
+    std::copy(v.begin(), v.end(), h.begin());
+    e = cudaMemcpyAsync(dl.held.p, h.data(), 8 * h.size(), cudaMemcpyHostToDevice, dl.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(dl.stream);
+    return e;
+}
+
 static int loop_launch(lg_ctx *c, DeviceLoop &dl) {
     cudaError_t e;
+    if ((e = loop_sort_held(dl)) != cudaSuccess)
+        return fail(LG_ECUDA, std::string("serving loop held ligands: ") + cudaGetErrorString(e));
+    dl.held_dirty = true;
     std::unique_ptr<LoopArgs> la(new LoopArgs());
     memset(la.get(), 0, sizeof(LoopArgs));
     la->ctl = dl.d_ctl;
@@ -773,6 +862,7 @@ static int loop_launch(lg_ctx *c, DeviceLoop &dl) {
     la->done = dl.d_done;
     la->flags = dl.d_flags;
     la->held = (long long *)dl.held.p;
+    la->held_n = dl.held_n;
     la->ring = kRing;
     la->idle_ns = (uint64_t)c->serve_loop_idle_ms.load() * 1000000ull;
     la->first_seq = dl.head;
@@ -998,10 +1088,34 @@ static void worker_loop(Server *sv) {
     cudaSetDevice(c->device);
     std::unique_lock<std::mutex> lk(sv->mu);
     for (;;) {
-        if (dl.ready && loop_collect(dl)) sv->done_cv.notify_all();
+        if (dl.ready && loop_collect(dl)) {
+            sv->done_cv.notify_all();
+            dl.stale = 0;
+        }
         int busy = 0;
-        for (auto &rs : dl.ring) busy += rs.busy;
+        int64_t backlog = 0;
+        for (auto &rs : dl.ring)
+            if (rs.busy) {
+                busy++;
+                backlog += rs.reqs.empty() ? 0 : rs.reqs[0]->L;
+            }
         loop_ended(dl);
+        // the restart tile the backlog asks for: a running launch is stopped
+        // (its CTAs leave after their current ligand, claimed ligands carry
+        // over) and relaunched below with the other tile
+        if (dl.configured && dl.adaptive) {
+            const int want = loop_tile_wanted(dl, backlog, now_s());
+            if (want != dl.cur) {
+                if (dl.running) {
+                    lk.unlock();
+                    loop_stop(dl);
+                    lk.lock();
+                }
+                loop_apply_tile(dl, want);
+                dl.low_since = -1.0;
+                dl.a_switches = ++dl.switches;
+            }
+        }
         if (!dl.running && busy > 0 && dl.last_status != LG_OK && dl.last_status != LG_ETIMEOUT &&
             dl.last_status != -1) {
             // the launch ended on an error with requests unfinished
@@ -1088,6 +1202,16 @@ static void worker_loop(Server *sv) {
         // work left on the device after the launch ended (idle CTAs left
         // while ligands were still being published): launch again
         if (busy > 0 && !dl.running) {
+            // a launch that ended idle with requests unfinished has CTAs
+            // waiting on ligands that are not published: a request's ligands
+            // are all published at admission, so many such launches in a row
+            // with no request finishing mean the loop cannot progress
+            if (dl.last_status == LG_ETIMEOUT && ++dl.stale > 100) {
+                loop_fail_all(dl);
+                sv->done_cv.notify_all();
+                dl.stale = 0;
+                continue;
+            }
             lk.unlock();
             const int rc = loop_launch(c, dl);
             lk.lock();
@@ -1137,6 +1261,7 @@ void serve_stats(lg_ctx *c, lg_stats *st) {
     st->serve_loop_status = sv->loop->a_status.load();
     st->serve_loop_launches = sv->loop->a_launches.load();
     st->serve_loop_items = sv->loop->a_items.load();
+    st->serve_loop_switches = sv->loop->a_switches.load();
 }
 
 void serve_stop(lg_ctx *c) {

@@ -72,7 +72,8 @@ class lg_stats(ctypes.Structure):
                 ("warps_per_cta", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("smem_bytes", ctypes.c_int32),
                 ("graph", ctypes.c_int32), ("serve_loop_status", ctypes.c_int32), ("restart_lanes", ctypes.c_int32),
                 ("l2_window_bytes", ctypes.c_int64), ("l2_persist_bytes", ctypes.c_int64),
-                ("serve_loop_launches", ctypes.c_int64), ("serve_loop_items", ctypes.c_int64)]
+                ("serve_loop_launches", ctypes.c_int64), ("serve_loop_items", ctypes.c_int64),
+                ("serve_loop_switches", ctypes.c_int64)]
 
 
 # Every symbol include/lg.h declares (checked by the ABI test).

@@ -40,7 +40,7 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(lg.lg_dock_params) == 64
     assert ctypes.sizeof(lg.lg_dock_result) == 8 + 12 * 8
     assert ctypes.sizeof(lg.lg_pose_batch) == 8 + 4 * 8
-    assert ctypes.sizeof(lg.lg_stats) == 80
+    assert ctypes.sizeof(lg.lg_stats) == 88
     assert ctypes.sizeof(lg.lg_flatten_params) == 20
     assert ctypes.sizeof(lg.lg_flatten_result) == 8 + 4 * 8
 

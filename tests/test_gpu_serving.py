@@ -299,12 +299,12 @@ def _loop_ctx(idle_ms=None):
     return ctx
 
 
-@pytest.mark.parametrize("lanes", [16, 4])
+@pytest.mark.parametrize("lanes", [0, 16, 4])
 def test_loop_requests_arriving_while_others_run(lanes):
     # requests of uneven size aimed at three pockets arrive one by one while
     # earlier ones are on the device: each result equals the request docked
-    # alone, and the loop docked every ligand -- with either restart tile of
-    # the loop (4 lanes per restart, the default, or 16)
+    # alone, and the loop docked every ligand -- with the loop's restart tile
+    # chosen by the backlog (the default) or fixed at 16 or 4 lanes
     ctx = _loop_ctx()
     try:
         ctx.set_option("serve_loop_lanes", lanes)
@@ -383,3 +383,42 @@ def test_loop_closes_with_requests_in_flight():
     t0 = time.time()
     ctx.close()
     assert time.time() - t0 < 60.0
+
+
+def test_loop_switches_restart_tiles_by_backlog():
+    # the default tile choice: small requests run at 16 lanes per restart; a
+    # request of 4,000 ligands lifts the backlog above eight waves of that
+    # loop, which is stopped and relaunched at 4 lanes with the ligands its
+    # CTAs had claimed carried over; after a quiet spell a small request
+    # brings the 16-lane tile back.  Every result equals the request docked
+    # alone.
+    ctx = _loop_ctx()
+    try:
+        ctx.set_option("serve_loop_lanes", 0)
+        pid = ctx.load_pocket(synth.config_pocket(2))
+        params = synth.config_params(2)
+        pool = synth.config_ligands(2, 4100)
+        parts = [(0, 24), (24, 4024), (4024, 4040), (4040, 4060)]
+        done = []
+        for k, (a, b) in enumerate(parts):
+            sub = pool.subset(range(a, b))
+            req = _request(sub, params)
+            t = lg.lg_stream_submit(ctx.h, pid, req["b"], req["p"], req["r"])
+            assert lg.lg_stream_wait(ctx.h, t, 120000) == lg.LG_OK
+            done.append((sub, req))
+            sw = ctx.stats().serve_loop_switches
+            if k == 0:
+                assert sw == 0
+            elif k == 1:
+                assert sw == 1  # to 4 lanes for the large request
+            elif k == 2:
+                time.sleep(0.05)  # the backlog stays low
+        assert ctx.stats().serve_loop_switches == 2  # back to 16 lanes for the last request
+        assert ctx.stats().serve_loop_items == 4060
+        for sub, req in done:
+            alone = ctx.dock(pid, sub, params)
+            got = _trim(req, params.passes)
+            for k in got:
+                assert np.array_equal(got[k], alone[k][:len(got[k])]), k
+    finally:
+        ctx.close()
