@@ -103,6 +103,12 @@ typedef struct {
 /* Copy a pocket (host pointers) into device memory owned by the context and
  * return its id.  The caller's buffers may be freed on return.  Requires
  * 2 <= n <= 512, h > 0, n_pp >= 1 and every pocket point inside the grid.
+ * The three grids go to the device as they are (12 bytes per node) and a
+ * kernel packs them into per-node cells of trilinear coefficients (32 bytes
+ * per node for phi_o, 64 for phi_v and phi_e side by side; FP64 differences
+ * of the grid values rounded to FP32, see lg_diag_pocket_cells); option
+ * "pocket_pack_host" = 1 packs them on the host instead, with the same
+ * arithmetic and the same result, and uploads the cells.
  * L2 residency (the paper keeps the site in texture memory, Sec. 3.2): the
  * call sizes the context's persisting L2 set-aside for the largest loaded
  * pocket's overlap cells (32 bytes per node; within the device's limit; a
@@ -532,6 +538,14 @@ int lg_tune_import(lg_ctx *ctx, const char *text);
  * Synchronous.  Errors: LG_EINVAL, LG_ECUDA. */
 int lg_diag_philox(lg_ctx *ctx, int32_t n, const uint32_t *ctr, const uint32_t *key, uint32_t *out,
                    int32_t use_curand);
+
+/* The packed cells of a loaded pocket copied to host memory (caller-owned):
+ * cell_o[8 n^3] (overlap grid) and cell_ve[16 n^3] (vdW then electrostatic
+ * coefficients per node), node (i, j, k) at (k n + j) n + i, coefficients
+ * (c000, c100, c010, c001, c110, c101, c011, c111) of the cell's trilinear
+ * polynomial in the cell's local coordinates (see lg_pocket_load).
+ * Synchronous.  Errors: LG_EINVAL (unknown pocket), LG_ECUDA. */
+int lg_diag_pocket_cells(lg_ctx *ctx, int32_t pid, float *cell_o, float *cell_ve);
 
 #ifdef __cplusplus
 }

@@ -34,6 +34,8 @@
 // Positions live in centred grid units (see lg_internal.h).
 #include <curand_philox4x32_x.h>
 
+#include <algorithm>
+
 #include "lg_device.cuh"
 
 namespace lg {
@@ -2015,6 +2017,51 @@ __global__ void __launch_bounds__(32 * Rt<LPR>::max_warps, 4 * LG_RT_MIN_BLOCKS 
             S.ctl->status = st;
         }
     }
+}
+
+// ================================================================== pocket packing
+// Trilinear coefficients of every node's cell, the layout the lookups read
+// (Sec. 3.2: the grids stay on the GPU): for node (i, j, k) the 8
+// coefficients of the polynomial through the cell's corners, corner indices
+// clamped to the last layer, as differences of the FP32 grid values in FP64
+// rounded to FP32 -- the overlap grid into cell_o (8 floats per node), the
+// vdW and electrostatic grids side by side into cell_ve (16 floats per node).
+// Additions only, in one fixed order, so the result is the same on any
+// IEEE machine.
+__device__ __forceinline__ void pack_one(const float *g, int n, int i, int j, int k, float4 &lo, float4 &hi) {
+    const int i1 = min(i + 1, n - 1), j1 = min(j + 1, n - 1), k1 = min(k + 1, n - 1);
+    auto at = [&](int a, int b, int c) { return (double)g[((size_t)c * n + b) * n + a]; };
+    const double v000 = at(i, j, k), v100 = at(i1, j, k), v010 = at(i, j1, k), v110 = at(i1, j1, k);
+    const double v001 = at(i, j, k1), v101 = at(i1, j, k1), v011 = at(i, j1, k1), v111 = at(i1, j1, k1);
+    lo = make_float4((float)v000, (float)(v100 - v000), (float)(v010 - v000), (float)(v001 - v000));
+    hi = make_float4((float)(v110 - v100 - v010 + v000), (float)(v101 - v100 - v001 + v000),
+                     (float)(v011 - v010 - v001 + v000),
+                     (float)(v111 - v110 - v101 - v011 + v100 + v010 + v001 - v000));
+}
+
+__global__ void k_pack_cells(const float *go, const float *gv, const float *ge, int n, float4 *cell_o, float4 *cell_ve) {
+    const size_t n3 = (size_t)n * n * n;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n3; t += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(t % n), j = (int)((t / n) % n), k = (int)(t / ((size_t)n * n));
+        float4 lo, hi;
+        pack_one(go, n, i, j, k, lo, hi);
+        cell_o[2 * t] = lo;
+        cell_o[2 * t + 1] = hi;
+        pack_one(gv, n, i, j, k, lo, hi);
+        cell_ve[4 * t] = lo;
+        cell_ve[4 * t + 1] = hi;
+        pack_one(ge, n, i, j, k, lo, hi);
+        cell_ve[4 * t + 2] = lo;
+        cell_ve[4 * t + 3] = hi;
+    }
+}
+
+cudaError_t launch_pack_cells(const float *go, const float *gv, const float *ge, int n, float4 *cell_o, float4 *cell_ve,
+                              int num_sms, cudaStream_t s) {
+    const size_t n3 = (size_t)n * n * n;
+    const int blocks = (int)std::min<size_t>((n3 + 255) / 256, (size_t)num_sms * 8);
+    k_pack_cells<<<blocks, 256, 0, s>>>(go, gv, ge, n, cell_o, cell_ve);
+    return cudaGetLastError();
 }
 
 // ================================================================== pose scoring and diagnostics

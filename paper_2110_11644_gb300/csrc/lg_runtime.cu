@@ -963,26 +963,47 @@ int lg_pocket_load(lg_ctx *c, const lg_pocket_desc *d, int32_t *pid) {
     std::lock_guard<std::mutex> g(c->mu);
     if (cudaSetDevice(c->device) != cudaSuccess) return fail(LG_ECUDA, "cudaSetDevice failed");
 
-    std::vector<float> h_o(n3 * 8), h_ve(n3 * 16), h_pp(4 * (size_t)d->n_pp);
-    pack_cells(d->phi_o, n, h_o.data(), 8, 0);
-    pack_cells(d->phi_v, n, h_ve.data(), 16, 0);
-    pack_cells(d->phi_e, n, h_ve.data(), 16, 8);
+    std::vector<float> h_pp(4 * (size_t)d->n_pp);
     const double c0 = (n - 1) / 2.0;
     for (int p = 0; p < d->n_pp; p++) {
         for (int c3 = 0; c3 < 3; c3++) h_pp[4 * p + c3] = (float)(d->pocket_points[3 * p + c3] - c0);
         h_pp[4 * p + 3] = 0.0f;
     }
     Carve cv;
-    const size_t o_o = cv.take(h_o.size() * 4), o_ve = cv.take(h_ve.size() * 4), o_pp = cv.take(h_pp.size() * 4);
+    const size_t o_o = cv.take(n3 * 32), o_ve = cv.take(n3 * 64), o_pp = cv.take(h_pp.size() * 4);
     void *mem = nullptr;
     if (cudaMalloc(&mem, cv.off) != cudaSuccess) {
         cudaGetLastError();
         return fail(LG_ENOMEM, "pocket allocation failed");
     }
     char *base = (char *)mem;
-    cudaError_t e = cudaMemcpy(base + o_o, h_o.data(), h_o.size() * 4, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(base + o_ve, h_ve.data(), h_ve.size() * 4, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(base + o_pp, h_pp.data(), h_pp.size() * 4, cudaMemcpyHostToDevice);
+    cudaError_t e = cudaMemcpy(base + o_pp, h_pp.data(), h_pp.size() * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && c->pack_host) {  // the host packing (same arithmetic), for comparison
+        std::vector<float> h_o(n3 * 8), h_ve(n3 * 16);
+        pack_cells(d->phi_o, n, h_o.data(), 8, 0);
+        pack_cells(d->phi_v, n, h_ve.data(), 16, 0);
+        pack_cells(d->phi_e, n, h_ve.data(), 16, 8);
+        e = cudaMemcpy(base + o_o, h_o.data(), h_o.size() * 4, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(base + o_ve, h_ve.data(), h_ve.size() * 4, cudaMemcpyHostToDevice);
+    } else if (e == cudaSuccess) {
+        // the three raw grids (12 B per node, an eighth of the packed cells)
+        // go up once and the device packs them
+        void *raw = nullptr;
+        if (cudaMalloc(&raw, 12 * n3) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(mem);
+            return fail(LG_ENOMEM, "pocket staging allocation failed");
+        }
+        float *r = (float *)raw;
+        e = cudaMemcpy(r, d->phi_o, 4 * n3, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(r + n3, d->phi_v, 4 * n3, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(r + 2 * n3, d->phi_e, 4 * n3, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = launch_pack_cells(r, r + n3, r + 2 * n3, n, (float4 *)(base + o_o), (float4 *)(base + o_ve),
+                                  ctx_num_sms(c), 0);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(0);
+        cudaFree(raw);
+    }
     if (e != cudaSuccess) {
         cudaFree(mem);
         return fail(LG_ECUDA, std::string("pocket upload: ") + cudaGetErrorString(e));
@@ -1307,12 +1328,27 @@ int lg_set_option(lg_ctx *c, const char *key, int64_t v) {
         cudaSetDevice(c->device);
         for (auto &g : c->graph_cache) cudaGraphExecDestroy(g.exec);  // captured launches carry the old choice
         c->graph_cache.clear();
+    } else if (!strcmp(key, "pocket_pack_host")) {
+        c->pack_host = v != 0;
     } else if (!strcmp(key, "serve_mem_reserve_mb")) {
         if (v < 0) return fail(LG_EINVAL, "serve_mem_reserve_mb must be >= 0");
         c->serve_reserve_mb = v;
     } else {
         return fail(LG_EINVAL, std::string("unknown option ") + key);
     }
+    return LG_OK;
+}
+
+int lg_diag_pocket_cells(lg_ctx *c, int32_t pid, float *cell_o, float *cell_ve) {
+    if (!c || !cell_o || !cell_ve) return fail(LG_EINVAL, "null argument");
+    std::lock_guard<std::mutex> g(c->mu);
+    if (pid < 0 || pid >= (int)c->pockets.size() || !c->pockets[pid].live) return fail(LG_EINVAL, "unknown pocket");
+    if (cudaSetDevice(c->device) != cudaSuccess) return fail(LG_ECUDA, "cudaSetDevice failed");
+    const PocketDev &pd = c->pockets[pid].dev;
+    const size_t n3 = (size_t)pd.n * pd.n * pd.n;
+    cudaError_t e = cudaMemcpy(cell_o, pd.cell_o, 32 * n3, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(cell_ve, pd.cell_ve, 64 * n3, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return fail(LG_ECUDA, std::string("pocket cells: ") + cudaGetErrorString(e));
     return LG_OK;
 }
 

@@ -147,6 +147,7 @@ struct lg_ctx {
     std::map<std::array<int, 8>, std::pair<int, int>> tune;  // key -> (lanes per restart, warps per CTA)
     lg::DevBuf flat_buf;  // lg_flatten_batch: host-output staging and the preparation's unused outputs
     int multi_pocket_major = 1;
+    bool pack_host = false;  // lg_pocket_load packs the cells on the host (else on the device)
     // L2 residency of the pockets: the persisting set-aside (process-local
     // context limit, sized for the largest loaded pocket's overlap cells) and
     // the device's limits; the docking launches mark their pocket's overlap

@@ -79,7 +79,7 @@ class lg_stats(ctypes.Structure):
 # Every symbol include/lg.h declares (checked by the ABI test).
 EXPORTS = ("lg_create", "lg_destroy", "lg_last_error", "lg_pocket_load", "lg_pocket_unload", "lg_dock_batch",
            "lg_score_poses", "lg_stream_submit", "lg_stream_poll", "lg_stream_wait", "lg_get_stats", "lg_set_option",
-           "lg_diag_philox", "lg_dock_batch_noalloc", "lg_dock_multi", "lg_flatten_batch", "lg_tune_export",
+           "lg_diag_philox", "lg_diag_pocket_cells", "lg_dock_batch_noalloc", "lg_dock_multi", "lg_flatten_batch", "lg_tune_export",
            "lg_tune_import")
 
 _lib = None
@@ -118,6 +118,7 @@ def load():
             lib.lg_get_stats.argtypes = [V, c.POINTER(lg_stats)]
             lib.lg_set_option.argtypes = [V, c.c_char_p, c.c_int64]
             lib.lg_diag_philox.argtypes = [V, c.c_int32, V, V, V, c.c_int32]
+            lib.lg_diag_pocket_cells.argtypes = [V, c.c_int32, V, V]
             lib.lg_dock_batch_noalloc.argtypes = [V, c.c_int32, c.POINTER(lg_ligand_batch), c.POINTER(lg_dock_params),
                                                   c.POINTER(lg_dock_result), V]
             lib.lg_dock_multi.argtypes = [V, c.POINTER(c.c_int32), c.c_int32, c.POINTER(lg_ligand_batch),
@@ -251,6 +252,15 @@ def lg_set_option(h, key: str, value: int):
 
 def lg_diag_philox(h, n, ctr_ptr, key_ptr, out_ptr, use_curand: int):
     _check(h, load().lg_diag_philox(h, n, ctr_ptr, key_ptr, out_ptr, use_curand))
+
+
+def lg_diag_pocket_cells(h, pid: int, n: int):
+    """The packed cells of a loaded pocket: (cell_o [n^3, 8], cell_ve [n^3, 16]) float32."""
+    import numpy as np
+    o = np.empty((n ** 3, 8), np.float32)
+    ve = np.empty((n ** 3, 16), np.float32)
+    _check(h, load().lg_diag_pocket_cells(h, pid, o.ctypes.data, ve.ctypes.data))
+    return o, ve
 
 
 # ----------------------------------------------------------------------------- conveniences
