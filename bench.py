@@ -719,6 +719,8 @@ def main():
         pass
     sm_max_mhz = float(peaks.get("sm_max_mhz") or (clk or {}).get("sm_max_mhz") or 2070.0)
     peak_tflops = sm_count * FP32_LANES_PER_SM * FLOP_PER_FMA * sm_max_mhz * 1e6 / 1e12
+    # cross-check of the derived peak: the library's FMA microbenchmark
+    fma_tflops, fma_s = lg.lg_diag_fp32_peak(ctx.h, 5)
     achieved = F / (dock_ms / 1e3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": achieved / peak_tflops, "traffic": traffic_for_current_kernel(),
@@ -731,6 +733,9 @@ def main():
                                 "skipped by exact convergence stops and not credited" % (100 * skipped),
                 "flop_per_launch_circle_form": circle_form_flops(batch, S, P),
                 "peak_basis": f"{sm_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max_mhz:.0f} MHz",
+                "peak_measured_fma": {"value": fma_tflops, "unit": "TFLOP/s", "frac_of_derived": fma_tflops / peak_tflops,
+                                      "how": "lg_diag_fp32_peak: best of 5 launches (%.0f ms in all) of 8 independent "
+                                             "FMA chains per thread, 64 warps per SM" % (1e3 * fma_s)},
                 "limiter": "L1 data pipe ~59% (scattered 32-byte trilinear-cell gathers plus shared-memory "
                            "wavefronts), L1->L2 requests ~53%, issue ~56% at 16 warps/SM; "
                            "see profiles/dock_batched_ncu_small.md"}

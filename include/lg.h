@@ -539,6 +539,14 @@ int lg_tune_import(lg_ctx *ctx, const char *text);
 int lg_diag_philox(lg_ctx *ctx, int32_t n, const uint32_t *ctr, const uint32_t *key, uint32_t *out,
                    int32_t use_curand);
 
+/* Measured FP32 FMA throughput of the context's device in TFLOP/s (the
+ * roofline's denominator for the FP32-bound docking kernels): reps timed
+ * launches (1..100, after one warm-up) of a kernel whose threads run 8
+ * independent FMA chains, 8 CTAs of 256 threads per SM, 2 FLOP per FMA;
+ * *tflops gets the best launch, *seconds (may be NULL) the timed total.
+ * Synchronous.  Errors: LG_EINVAL, LG_ECUDA. */
+int lg_diag_fp32_peak(lg_ctx *ctx, int32_t reps, double *tflops, double *seconds);
+
 /* The packed cells of a loaded pocket copied to host memory (caller-owned):
  * cell_o[8 n^3] (overlap grid) and cell_ve[16 n^3] (vdW then electrostatic
  * coefficients per node), node (i, j, k) at (k n + j) n + i, coefficients

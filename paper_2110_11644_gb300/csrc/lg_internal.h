@@ -320,6 +320,7 @@ Scratch carve_scratch(void *base, int L, int rmax, int rank_slots = 0, int S = 0
 // Launchers (lg_kernels.cu)
 void set_angle_tables(const float *cosv, const float *sinv);
 cudaError_t launch_prep(const DockArgs &a, bool sort, cudaStream_t s, int *launches);
+cudaError_t launch_fp32_peak(float *out, int blocks, int iters, cudaStream_t s);
 cudaError_t launch_pack_cells(const float *go, const float *gv, const float *ge, int n, float4 *cell_o, float4 *cell_ve,
                               int num_sms, cudaStream_t s);
 cudaError_t launch_dock_plain(const DockArgs &a, int ligand, int slot, cudaStream_t s);

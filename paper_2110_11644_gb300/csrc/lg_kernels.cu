@@ -2064,6 +2064,30 @@ cudaError_t launch_pack_cells(const float *go, const float *gv, const float *ge,
     return cudaGetLastError();
 }
 
+// ================================================================== FP32 peak
+// FP32 FMA throughput of the device, for the roofline's denominator: every
+// thread runs 8 independent FMA chains (enough to cover the pipe's latency
+// at 8 warps per SM) for `iters` steps; each FMA is 2 FLOP.  The sums are
+// stored so that nothing is dropped.
+__global__ void __launch_bounds__(256) k_fp32_peak(float *out, int iters, float a, float b) {
+    float x[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) x[c] = (float)(threadIdx.x + c);
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) x[c] = fmaf(x[c], a, b);
+    }
+    float s = 0.0f;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) s += x[c];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+cudaError_t launch_fp32_peak(float *out, int blocks, int iters, cudaStream_t s) {
+    k_fp32_peak<<<blocks, 256, 0, s>>>(out, iters, 0.999999f, 1e-6f);
+    return cudaGetLastError();
+}
+
 // ================================================================== pose scoring and diagnostics
 __global__ void k_score_poses(const __grid_constant__ PocketDev P, int L, const int32_t *atom_off, const float *xyz,
                               const float *q, const uint8_t *type, double *E) {

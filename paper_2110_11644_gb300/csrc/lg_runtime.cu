@@ -1339,6 +1339,40 @@ int lg_set_option(lg_ctx *c, const char *key, int64_t v) {
     return LG_OK;
 }
 
+int lg_diag_fp32_peak(lg_ctx *c, int32_t reps, double *tflops, double *seconds) {
+    if (!c || !tflops || reps < 1 || reps > 100) return fail(LG_EINVAL, "bad argument");
+    std::lock_guard<std::mutex> g(c->mu);
+    if (cudaSetDevice(c->device) != cudaSuccess) return fail(LG_ECUDA, "cudaSetDevice failed");
+    const int blocks = ctx_num_sms(c) * 8, iters = 1 << 18;
+    float *out = nullptr;
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    cudaError_t e = cudaMalloc(&out, sizeof(float) * 256 * (size_t)blocks);
+    if (e == cudaSuccess) e = cudaEventCreate(&t0);
+    if (e == cudaSuccess) e = cudaEventCreate(&t1);
+    double best = 0.0, total = 0.0;
+    if (e == cudaSuccess) e = launch_fp32_peak(out, blocks, iters, 0);  // warm-up
+    for (int r = 0; r < reps && e == cudaSuccess; ++r) {
+        cudaEventRecord(t0, 0);
+        e = launch_fp32_peak(out, blocks, iters, 0);
+        cudaEventRecord(t1, 0);
+        if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
+        if (e == cudaSuccess && ms > 0.0f) {
+            const double flop = 2.0 * 8.0 * iters * 256.0 * blocks;
+            best = std::max(best, flop / (ms * 1e-3) / 1e12);
+            total += ms * 1e-3;
+        }
+    }
+    if (t0) cudaEventDestroy(t0);
+    if (t1) cudaEventDestroy(t1);
+    if (out) cudaFree(out);
+    if (e != cudaSuccess) return fail(LG_ECUDA, std::string("FP32 peak: ") + cudaGetErrorString(e));
+    *tflops = best;
+    if (seconds) *seconds = total;
+    return LG_OK;
+}
+
 int lg_diag_pocket_cells(lg_ctx *c, int32_t pid, float *cell_o, float *cell_ve) {
     if (!c || !cell_o || !cell_ve) return fail(LG_EINVAL, "null argument");
     std::lock_guard<std::mutex> g(c->mu);

@@ -79,7 +79,7 @@ class lg_stats(ctypes.Structure):
 # Every symbol include/lg.h declares (checked by the ABI test).
 EXPORTS = ("lg_create", "lg_destroy", "lg_last_error", "lg_pocket_load", "lg_pocket_unload", "lg_dock_batch",
            "lg_score_poses", "lg_stream_submit", "lg_stream_poll", "lg_stream_wait", "lg_get_stats", "lg_set_option",
-           "lg_diag_philox", "lg_diag_pocket_cells", "lg_dock_batch_noalloc", "lg_dock_multi", "lg_flatten_batch", "lg_tune_export",
+           "lg_diag_philox", "lg_diag_pocket_cells", "lg_diag_fp32_peak", "lg_dock_batch_noalloc", "lg_dock_multi", "lg_flatten_batch", "lg_tune_export",
            "lg_tune_import")
 
 _lib = None
@@ -119,6 +119,7 @@ def load():
             lib.lg_set_option.argtypes = [V, c.c_char_p, c.c_int64]
             lib.lg_diag_philox.argtypes = [V, c.c_int32, V, V, V, c.c_int32]
             lib.lg_diag_pocket_cells.argtypes = [V, c.c_int32, V, V]
+            lib.lg_diag_fp32_peak.argtypes = [V, c.c_int32, c.POINTER(c.c_double), c.POINTER(c.c_double)]
             lib.lg_dock_batch_noalloc.argtypes = [V, c.c_int32, c.POINTER(lg_ligand_batch), c.POINTER(lg_dock_params),
                                                   c.POINTER(lg_dock_result), V]
             lib.lg_dock_multi.argtypes = [V, c.POINTER(c.c_int32), c.c_int32, c.POINTER(lg_ligand_batch),
@@ -252,6 +253,13 @@ def lg_set_option(h, key: str, value: int):
 
 def lg_diag_philox(h, n, ctr_ptr, key_ptr, out_ptr, use_curand: int):
     _check(h, load().lg_diag_philox(h, n, ctr_ptr, key_ptr, out_ptr, use_curand))
+
+
+def lg_diag_fp32_peak(h, reps: int = 5):
+    """Measured FP32 FMA throughput (TFLOP/s, best of reps) and the timed seconds."""
+    t, sec = ctypes.c_double(), ctypes.c_double()
+    _check(h, load().lg_diag_fp32_peak(h, reps, ctypes.byref(t), ctypes.byref(sec)))
+    return t.value, sec.value
 
 
 def lg_diag_pocket_cells(h, pid: int, n: int):

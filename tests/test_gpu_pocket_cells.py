@@ -105,3 +105,16 @@ def test_cell_polynomial_reproduces_the_corner_values(ctx):
                          + a * b * cc * c[7])
                     want = g[min(k + cc, n - 1), min(j + b, n - 1), min(i + a, n - 1)]
                     assert abs(p - want) <= 4e-6 * max(1.0, np.abs(g).max()), (i, j, k, a, b, cc)
+
+
+def test_fp32_peak_microbenchmark_is_near_the_derived_peak(ctx):
+    # the FMA microbenchmark that cross-checks the roofline's derived FP32
+    # peak (SMs x 128 lanes x 2 FLOP x clock) lands near it
+    import torch
+    t, sec = lg.lg_diag_fp32_peak(ctx.h, 3)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    derived = sms * 128 * 2 * 2.07e9 / 1e12
+    assert 0.5 * derived < t < 1.05 * derived, (t, derived)
+    assert sec > 0
+    with pytest.raises(lg.LgError):
+        lg.lg_diag_fp32_peak(ctx.h, 0)
