@@ -230,34 +230,51 @@ def serving_leg(ctx, pids, pool, params, rate_evals, load, duration_s, seed=5, m
     arrive = np.cumsum(gaps)
     p = lg.make_params(params.restarts, params.passes, params.seed, params.d_clash)
     cursor, pending, done_lat, live = 0, [], [], {}
+
+    def drain():  # completed requests, in submission order
+        while pending:
+            st, lat = lg.lg_stream_poll(ctx.h, pending[0])
+            if st < lg.LG_REQ_DONE:
+                break
+            done_lat.append((lat, live.pop(pending[0])[2]))
+            pending.pop(0)
+
     t0 = time.perf_counter()
     i = 0
-    while i < n:
-        now = time.perf_counter() - t0
-        if now >= arrive[i]:
-            size = int(sizes[i])
-            if cursor + size > pool.L:
-                cursor = 0
-            arrs, L, A, R = contiguous_request(pool, cursor, size)
-            cursor += size
-            b = lg.make_batch_struct(arrs, L)
-            r, outs = lg.alloc_result(L, A, R, params.restarts, params.passes, device=False, pose=False, tors=False)
-            t = lg.lg_stream_submit(ctx.h, pids[int(target[i % len(target)])], b, p, r)
-            live[t] = (arrs, outs, L)
-            pending.append(t)
-            i += 1
-        else:
-            while pending:
-                st, lat = lg.lg_stream_poll(ctx.h, pending[0])
-                if st < lg.LG_REQ_DONE:
-                    break
-                done_lat.append((lat, live.pop(pending[0])[2]))
-                pending.pop(0)
-            time.sleep(2e-4)
-    for t in pending:
-        lg.lg_stream_wait(ctx.h, t, 600000)
-        st, lat = lg.lg_stream_poll(ctx.h, t)
-        done_lat.append((lat, live.pop(t)[2]))
+    try:
+        while i < n:
+            now = time.perf_counter() - t0
+            if now >= arrive[i]:
+                size = int(sizes[i])
+                if cursor + size > pool.L:
+                    cursor = 0
+                arrs, L, A, R = contiguous_request(pool, cursor, size)
+                cursor += size
+                b = lg.make_batch_struct(arrs, L)
+                r, outs = lg.alloc_result(L, A, R, params.restarts, params.passes, device=False, pose=False,
+                                          tors=False)
+                while True:  # a full host queue pushes back: wait for completions, then resubmit
+                    try:
+                        t = lg.lg_stream_submit(ctx.h, pids[int(target[i % len(target)])], b, p, r)
+                        break
+                    except lg.LgError as e:
+                        if e.code != lg.LG_EAGAIN:
+                            raise
+                        drain()
+                        time.sleep(2e-4)
+                live[t] = (arrs, outs, L)
+                pending.append(t)
+                i += 1
+            else:
+                drain()
+                time.sleep(2e-4)
+    finally:
+        # the library writes into each request's buffers until it is done:
+        # keep them alive until then, also when leaving on an error
+        for t in pending:
+            lg.lg_stream_wait(ctx.h, t, 600000)
+            st, lat = lg.lg_stream_poll(ctx.h, t)
+            done_lat.append((lat, live.pop(t)[2]))
     wall = time.perf_counter() - t0
     lat = np.array([x for x, _ in done_lat])
     ligs = int(sum(s for _, s in done_lat))
@@ -613,6 +630,8 @@ def main():
                     help="seconds per offered load of the serving leg (0 = off)")
     ap.add_argument("--serve-loads", default="0.25,0.5,0.9",
                     help="comma-separated offered loads (fractions of the measured batched rate)")
+    ap.add_argument("--serve-extra", type=int, default=1,
+                    help="1: also the loop's fixed restart tiles and the host-merge path (0 = only the default loop)")
     ap.add_argument("--stage-ligands", type=int, default=20000,
                     help="ligands of the optional-stages leg (ranking, rigid refinement; 0 = off)")
     ap.add_argument("--multi-ligands", type=int, default=20000,
@@ -848,9 +867,9 @@ def main():
             # above the batched rate (the queue never empties); the offered
             # loads are fractions of that peak.  Warm-up first (not reported).
             sp = mp_pids or [pid]
-            ps = max(3.0, args.serve_seconds / 10)
+            ps = min(10.0, max(3.0, args.serve_seconds / 10))
             serving_peak = {"batched_evals_per_s": value / world}
-            for mode in ("device_loop", "host_merge"):
+            for mode in (("device_loop", "host_merge") if args.serve_extra else ("device_loop",)):
                 serving_leg(ctx, sp, batch, params, value / world, 0.9, 1.0, seed=4, mode=mode)
                 serving_peak[mode] = serving_leg(ctx, sp, batch, params, value / world, 1.5, ps, seed=6,
                                                  mode=mode)["sustained_evals_per_s"]
@@ -861,7 +880,7 @@ def main():
             # per SM) against the default, which switches between them by the
             # backlog: each one's peak and the lowest load
             low = min(float(x) for x in args.serve_loads.split(","))
-            for lanes in (4, 16):
+            for lanes in ((4, 16) if args.serve_extra else ()):
                 ctx.set_option("serve_loop_lanes", lanes)
                 serving_leg(ctx, sp, batch, params, value / world, 0.9, 1.0, seed=4)
                 serving_peak[f"device_loop_{lanes}_lanes"] = serving_leg(
@@ -873,8 +892,9 @@ def main():
             ctx.set_option("serve_loop_lanes", 0)
             # the host worker's merged launches at the highest load, for comparison
             hs = max(1.0, args.serve_seconds / 6)
-            serving.append(serving_leg(ctx, sp, batch, params, serving_peak["host_merge"],
-                                       max(float(x) for x in args.serve_loads.split(",")), hs, mode="host_merge"))
+            if args.serve_extra:
+                serving.append(serving_leg(ctx, sp, batch, params, serving_peak["host_merge"],
+                                           max(float(x) for x in args.serve_loads.split(",")), hs, mode="host_merge"))
             ctx.set_option("serve_device_loop", 1)
         for q in mp_pids:
             ctx.unload_pocket(q)

@@ -9,9 +9,11 @@ raises: there is no CPU fallback.
 """
 from __future__ import annotations
 
+import atexit
 import ctypes
 import os
 import threading
+import weakref
 
 import numpy as np
 
@@ -389,12 +391,28 @@ def pocket_desc(pocket):
     return d, keep
 
 
+# Contexts still open when the interpreter exits are destroyed first (at
+# exit, before modules and buffers are torn down), so the library's serving
+# worker is stopped and joined while the buffers it writes into still exist.
+_live_contexts = weakref.WeakSet()
+
+
+@atexit.register
+def _close_live_contexts():
+    for c in list(_live_contexts):
+        try:
+            c.close()
+        except Exception:
+            pass
+
+
 class Context:
     """One liblgdock context on a CUDA device."""
 
     def __init__(self, device: int = 0):
         self.h = lg_create(device)
         self.device = device
+        _live_contexts.add(self)
 
     def close(self):
         if self.h is not None:

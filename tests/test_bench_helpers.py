@@ -49,3 +49,86 @@ def test_algorithmic_flops_are_the_cost_model():
     assert bench.circle_form_flops(b, 30, 3) < bench.algorithmic_flops(b, 30, 3)
     ones = np.ones(int(30 * 3 * b.rot_off[-1]))
     assert np.isclose(shard.ligand_flops_ranked(b, 30, 3, ones).sum(), bench.algorithmic_flops(b, 30, 3))
+
+
+class _FakeQueue:
+    """Stand-in for the library's serving calls: at most `cap` requests in
+    flight (a full queue answers LG_EAGAIN), each poll finishes the oldest."""
+
+    def __init__(self, lg, cap, fail_at=None):
+        self.lg, self.cap, self.fail_at = lg, cap, fail_at
+        self.next, self.flight, self.done, self.waited, self.eagain = 0, [], set(), [], 0
+
+    def submit(self, h, pid, b, p, r):
+        if self.fail_at is not None and self.next == self.fail_at:
+            raise self.lg.LgError(self.lg.LG_EINVAL, "bad request")
+        if len(self.flight) >= self.cap:
+            self.eagain += 1
+            raise self.lg.LgError(self.lg.LG_EAGAIN, "serving queue full")
+        t = self.next
+        self.next += 1
+        self.flight.append(t)
+        return t
+
+    def poll(self, h, t):
+        if self.flight:
+            self.done.add(self.flight.pop(0))
+        return (self.lg.LG_REQ_DONE, 1e-3) if t in self.done else (self.lg.LG_REQ_RUNNING, 0.0)
+
+    def wait(self, h, t, timeout_ms):
+        self.waited.append(t)
+        if t in self.flight:
+            self.flight.remove(t)
+        self.done.add(t)
+
+
+def _fake_serving(monkeypatch, q):
+    from paper_2110_11644_gb300 import lg
+
+    class Ctx:
+        h = None
+
+        def set_option(self, k, v):
+            pass
+
+        def stats(self):
+            return type("S", (), {"serve_loop_launches": 1, "serve_loop_switches": 0})()
+
+    monkeypatch.setattr(lg, "lg_stream_submit", q.submit)
+    monkeypatch.setattr(lg, "lg_stream_poll", q.poll)
+    monkeypatch.setattr(lg, "lg_stream_wait", q.wait)
+    monkeypatch.setattr(lg, "make_params", lambda *a, **k: None)
+    monkeypatch.setattr(lg, "make_batch_struct", lambda *a, **k: None)
+    monkeypatch.setattr(lg, "alloc_result", lambda *a, **k: (None, {}))
+    return Ctx()
+
+
+def test_serving_client_waits_on_a_full_queue(monkeypatch):
+    # a full host queue pushes back: the request is resubmitted once earlier
+    # ones finish, and every request of the leg completes
+    from paper_2110_11644_gb300 import lg
+    bench = _bench()
+    q = _FakeQueue(lg, cap=2)
+    ctx = _fake_serving(monkeypatch, q)
+    pool = synth.config_ligands(2, 64)
+    r = bench.serving_leg(ctx, [0], pool, synth.config_params(2), 1000.0, 1.0, 0.2, max_size=8)
+    assert q.eagain > 0
+    assert r["requests"] == q.next and not q.flight and len(q.done) == q.next
+    assert r["ligands"] > 0 and r["p99_latency_s"] == 1e-3
+
+
+def test_serving_client_keeps_buffers_until_requests_finish(monkeypatch):
+    # an error of one submission leaves the leg only after every request
+    # already in flight has finished (the library writes into their buffers)
+    from paper_2110_11644_gb300 import lg
+    bench = _bench()
+    q = _FakeQueue(lg, cap=1 << 20, fail_at=6)
+    q.poll = lambda h, t: (lg.LG_REQ_RUNNING, 0.0)  # nothing finishes on its own
+    ctx = _fake_serving(monkeypatch, q)
+    pool = synth.config_ligands(2, 64)
+    try:
+        bench.serving_leg(ctx, [0], pool, synth.config_params(2), 1000.0, 1.0, 0.5, max_size=8)
+        raise AssertionError("the failed submission was not reported")
+    except lg.LgError as e:
+        assert e.code == lg.LG_EINVAL
+    assert q.waited == list(range(6)) and not q.flight
