@@ -108,8 +108,8 @@ class ClockSampler:
                     reasons.add(nm)
         if not sm:
             return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+        return {"sm_mhz": statistics.median(sm), "sm_mhz_min": min(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
 
 
 def env_rank():
@@ -239,6 +239,8 @@ def serving_leg(ctx, pids, pool, params, rate_evals, load, duration_s, seed=5, m
             done_lat.append((lat, live.pop(pending[0])[2]))
             pending.pop(0)
 
+    clocks = ClockSampler(getattr(ctx, "device", 0))  # SM clocks and throttle reasons over the leg
+    clocks.start()
     t0 = time.perf_counter()
     i = 0
     try:
@@ -275,6 +277,7 @@ def serving_leg(ctx, pids, pool, params, rate_evals, load, duration_s, seed=5, m
             lg.lg_stream_wait(ctx.h, t, 600000)
             st, lat = lg.lg_stream_poll(ctx.h, t)
             done_lat.append((lat, live.pop(t)[2]))
+        clk = clocks.stop()
     wall = time.perf_counter() - t0
     lat = np.array([x for x, _ in done_lat])
     ligs = int(sum(s for _, s in done_lat))
@@ -285,7 +288,7 @@ def serving_leg(ctx, pids, pool, params, rate_evals, load, duration_s, seed=5, m
             "loop_tile_switches": int(st.serve_loop_switches) if mode == "device_loop" else None,
             "requests": len(lat), "ligands": ligs, "sustained_evals_per_s": ligs / wall,
             "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
-            "pockets": len(pids),
+            "pockets": len(pids), "clocks": clk,
             "request_sizes": f"floor(exp(U(0, ln {max_size}))) ligands, Poisson arrivals, uniform pocket"}
 
 
