@@ -865,7 +865,7 @@ def main():
         # serving: requests aimed at a random pocket of the 15-pocket set when it
         # is loaded, else at the throughput pocket
         serving, serving_peak = None, None
-        if args.serve_seconds > 0:
+        if args.serve_seconds > 0 and world == 1:
             # Each serving path's peak: its sustained rate under an offered load
             # above the batched rate (the queue never empties); the offered
             # loads are fractions of that peak.  Warm-up first (not reported).
