@@ -280,7 +280,15 @@ def serving_leg(ctx, pids, pool, params, rate_evals, load, duration_s, seed=5, m
         clk = clocks.stop()
     wall = time.perf_counter() - t0
     lat = np.array([x for x, _ in done_lat])
-    ligs = int(sum(s for _, s in done_lat))
+    size_of = np.array([s for _, s in done_lat])
+    ligs = int(size_of.sum())
+    # first-come claims: a request's wait hardly depends on its own size
+    by_size = {}
+    for lo, hi in ((1, 64), (64, 512), (512, 2048), (2048, max_size + 1)):
+        m = (size_of >= lo) & (size_of < hi)
+        if m.any():
+            by_size[f"{lo}-{hi - 1}"] = {"requests": int(m.sum()), "p50_latency_s": float(np.percentile(lat[m], 50)),
+                                         "p99_latency_s": float(np.percentile(lat[m], 99))}
     st = ctx.stats()
     return {"mode": mode, "offered_load": load, "offered_evals_per_s": load * rate_evals,
             "load_basis": "fraction of this serving path's measured peak (serving_peak)", "duration_s": round(wall, 2),
@@ -288,6 +296,7 @@ def serving_leg(ctx, pids, pool, params, rate_evals, load, duration_s, seed=5, m
             "loop_tile_switches": int(st.serve_loop_switches) if mode == "device_loop" else None,
             "requests": len(lat), "ligands": ligs, "sustained_evals_per_s": ligs / wall,
             "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+            "p999_latency_s": float(np.percentile(lat, 99.9)), "by_request_size": by_size,
             "pockets": len(pids), "clocks": clk,
             "request_sizes": f"floor(exp(U(0, ln {max_size}))) ligands, Poisson arrivals, uniform pocket"}
 

@@ -132,3 +132,16 @@ def test_serving_client_keeps_buffers_until_requests_finish(monkeypatch):
     except lg.LgError as e:
         assert e.code == lg.LG_EINVAL
     assert q.waited == list(range(6)) and not q.flight
+
+
+def test_serving_leg_reports_latency_by_request_size(monkeypatch):
+    from paper_2110_11644_gb300 import lg
+    bench = _bench()
+    q = _FakeQueue(lg, cap=4)
+    ctx = _fake_serving(monkeypatch, q)
+    pool = synth.config_ligands(2, 600)
+    r = bench.serving_leg(ctx, [0], pool, synth.config_params(2), 2e5, 1.0, 0.2, max_size=512)
+    groups = r["by_request_size"]
+    assert sum(g["requests"] for g in groups.values()) == r["requests"]
+    assert set(groups) <= {"1-63", "64-511", "512-2047"}
+    assert r["p999_latency_s"] >= r["p99_latency_s"] >= r["p50_latency_s"]
